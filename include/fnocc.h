@@ -1,0 +1,207 @@
+/*
+ * fnocc.h -- C ABI of libfnocc: frozen-natural-orbital EOM-CCSDT on one GPU.
+ *
+ * Method: Manisha & Manohar, "Frozen Natural Orbitals based Equation-of-motion
+ * coupled-cluster singles, doubles and triples for Ionized, Double-Ionized,
+ * Electron Attached and Two-Electron Attached states" (arXiv 2509.14157).
+ *   - FNO truncation of the virtual space: Sec. 1.2, Eq. 8-10.
+ *   - CCSDT ground state: Eq. 5-7.
+ *   - EOM-CCSDT for IP / EA / DIP / DEA: Eq. 1-4.
+ *   - XFNO extrapolation over three thresholds: Sec. 2.
+ *
+ * Conventions used by every call:
+ *   - Everything is IEEE double, row-major, C-contiguous.
+ *   - Spin orbital P = 2*p + s (alpha s = 0, beta s = 1); occupied first.
+ *     o = 2*nocc occupied and v = 2*nkept virtual spin orbitals.
+ *   - Antisymmetrised integrals <PQ||RS> = <PQ|RS> - <PQ|SR>.
+ *   - Packed amplitude layout: unique elements with strictly increasing hole
+ *     indices i1<..<i_nh and strictly increasing particle indices
+ *     a1<..<a_np, hole tuple major; each tuple list in lexicographic order.
+ *     T_n has nh = np = n. EOM components (R1, R2, R3) per variant:
+ *       IP  (1,0) (2,1) (3,2)     EA  (0,1) (1,2) (2,3)
+ *       DIP (2,0) (3,1) (4,2)     DEA (0,2) (1,3) (2,4)
+ *     An EOM vector is R1, R2, R3 concatenated.
+ *   - Operator normalisation: T_n = (1/n!)^2 sum t a^+..i and
+ *     R = 1/(nh! np!) sum r a^+..a^+ i..i, i.e. one packed coefficient per
+ *     determinant a1^+..a_np^+ i_nh..i1 |Phi_0>.
+ *
+ * Ownership: host pointers are read (or written) only during the call; the
+ * library copies inputs to device memory it owns. A context owns all device
+ * memory and frees it in fnocc_destroy. Output buffers belong to the caller.
+ *
+ * Errors: every call returns an fnocc_status; nothing is thrown across the
+ * ABI. fnocc_last_error gives a text for the last failing call on a context.
+ * FNOCC_NOT_CONVERGED still fills every output with the last iterate.
+ *
+ * Threading: a context is not thread-safe; use one context per host thread.
+ * All GPU work of a context runs on its stream.
+ */
+#ifndef FNOCC_H
+#define FNOCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FNOCC_OK = 0,
+  FNOCC_NOT_CONVERGED = 1,   /* results valid but flagged */
+  FNOCC_E_INVALID = -1,      /* bad argument */
+  FNOCC_E_NOMEM = -2,        /* device allocation failed */
+  FNOCC_E_CUDA = -3,         /* CUDA runtime error */
+  FNOCC_E_STATE = -4,        /* call order violated (e.g. ccsdt before a Hamiltonian) */
+  FNOCC_E_NUMERIC = -5,      /* NaN or Inf detected */
+  FNOCC_E_TIMEOUT = -6       /* a bounded device wait expired */
+} fnocc_status;
+
+typedef enum { FNOCC_IP = 0, FNOCC_EA = 1, FNOCC_DIP = 2, FNOCC_DEA = 3 } fnocc_variant;
+typedef enum { FNOCC_GUESS_KOOPMANS = 0, FNOCC_GUESS_DIAGONAL = 1 } fnocc_guess;
+typedef enum { FNOCC_CRIT_ABS = 0, FNOCC_CRIT_OCCT = 1 } fnocc_criterion;
+
+typedef struct fnocc_ctx fnocc_ctx;
+
+/* Truncation options (Sec. 1.2; readings of the paper's two unnamed schemes).
+ * criterion ABS keeps natural virtuals with occupation >= threshold;
+ * OCCT keeps the smallest prefix whose cumulative occupation fraction
+ * reaches threshold (e.g. 0.999). nkeep > 0 keeps exactly the top nkeep. */
+typedef struct {
+  int criterion;        /* fnocc_criterion */
+  int nkeep;            /* 0 = use the threshold */
+  int scf_maxiter;      /* default 200 */
+  double scf_e_tol;     /* default 1e-12 */
+  double scf_comm_tol;  /* default 1e-10 */
+} fno_options;
+
+typedef struct {
+  double e_rhf;           /* reference (RHF) energy */
+  double e_mp2;           /* MP2 correlation energy over the full virtual space */
+  int nkept;              /* kept spatial virtuals */
+  int nvir;               /* all spatial virtuals */
+  double kept_fraction;   /* sum kept occupations / sum all occupations */
+  int scf_iters;
+} fno_info;
+
+typedef struct {
+  double tol_res;   /* max |residual| for convergence, default 1e-10 */
+  double tol_e;     /* |dE| for convergence, default 1e-12 */
+  int maxiter;      /* default 200 */
+  int diis;         /* DIIS history length, default 8 (0 = plain Jacobi) */
+} ccsdt_options;
+
+typedef struct {
+  double e_corr;    /* CCSDT correlation energy (Eq. 7) */
+  double e_tot;     /* reference + correlation */
+  int iters;
+  double res_max;   /* max |residual| of the last iteration */
+  double seconds;   /* wall time of the solve */
+  double seconds_per_iter;
+} ccsdt_info;
+
+typedef struct {
+  double tol_res;   /* residual 2-norm per root, default 1e-8 */
+  double tol_e;     /* |d omega| per root, default 1e-10 */
+  int max_sub;      /* subspace size before collapse, default max(4*nroots, nguess+2*nroots) */
+  int maxiter;      /* default 200 */
+  int nguess;       /* guess vectors, default nroots */
+} eom_options;
+
+typedef struct {
+  int iters;              /* Davidson iterations */
+  int sigma_calls;        /* sigma = H-bar R products evaluated */
+  double seconds;
+  double seconds_per_iter;
+  int complex_roots;      /* roots whose Ritz value had |Im| > 1e-8 */
+  double res_max;         /* max residual norm over roots at exit */
+} eom_info;
+
+/* Context ---------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`. cuda_stream may be NULL (the
+ * context creates its own stream) or a cudaStream_t owned by the caller. */
+fnocc_status fnocc_create(fnocc_ctx **ctx, int device, void *cuda_stream);
+void fnocc_destroy(fnocc_ctx *ctx);
+const char *fnocc_last_error(const fnocc_ctx *ctx);
+
+/* FNO setup (Sec. 1.2, Eq. 8-10) -------------------------------------------
+ * h: n*n symmetric one-electron operator; eri: n^4 chemists' (pq|rs) with
+ * 8-fold symmetry, in an orthonormal basis (overlap = identity); nocc doubly
+ * occupied spatial orbitals. Runs RHF, MP2 amplitudes (Eq. 8-9), the MP2
+ * virtual-virtual density (Eq. 10), its eigenvectors (natural orbitals,
+ * sorted by occupation), truncation, semicanonicalisation of the kept
+ * natural virtuals and the active-space spin-orbital integral transform.
+ * occ: optional caller buffer of n - nocc natural occupations (descending),
+ * or NULL. The active Hamiltonian stays on the device for the next calls. */
+fnocc_status fno_truncate(fnocc_ctx *ctx, const double *h, const double *eri, int n, int nocc,
+                          double occ_threshold, const fno_options *opt, fno_info *out,
+                          double *occ);
+
+/* Loads an active-space Hamiltonian directly (bypasses fno_truncate): h_mo
+ * (n*n) and eri_mo (n^4, chemists' order) are spatial integrals in an
+ * orthonormal MO basis whose first nocc orbitals are doubly occupied. f_pq
+ * and the reference energy follow from normal ordering. */
+fnocc_status fnocc_set_mo_hamiltonian(fnocc_ctx *ctx, const double *h_mo, const double *eri_mo,
+                                      int n, int nocc);
+
+/* CCSDT (Eq. 5-7) ------------------------------------------------------------
+ * Solves <Phi^n| e^{-T} H e^{T} |Phi_0> = 0, n = 1..3, from T1 = 0,
+ * T2 = MP2, T3 = 0 with Jacobi steps and DIIS. opt may be NULL. */
+fnocc_status ccsdt_solve(fnocc_ctx *ctx, const ccsdt_options *opt, ccsdt_info *out);
+
+/* One evaluation of the CCSDT residuals and energy for given packed
+ * amplitudes (host pointers t1, t2, t3; outputs r1, r2, r3 host, same
+ * layout; e_corr the Eq. 7 energy of these amplitudes). */
+fnocc_status ccsdt_residual(fnocc_ctx *ctx, const double *t1, const double *t2, const double *t3,
+                            double *r1, double *r2, double *r3, double *e_corr);
+
+/* Same with device pointers on the context stream (no host copies). */
+fnocc_status ccsdt_residual_dev(fnocc_ctx *ctx, const double *t1, const double *t2,
+                                const double *t3, double *r1, double *r2, double *r3,
+                                double *e_corr);
+
+/* EOM-CCSDT (Eq. 1-4) ----------------------------------------------------------
+ * Lowest nroots roots (by real part) of H-bar in the variant's operator space
+ * and target spin sector (IP, EA: 2*dM_s = +1; DIP, DEA: 0), by
+ * non-symmetric Davidson. Needs a preceding ccsdt_solve (or
+ * fnocc_set_amplitudes). energies: total energies E_CC + omega (ascending);
+ * omegas may be NULL. */
+fnocc_status eom_ccsdt_solve(fnocc_ctx *ctx, int variant, int nroots, int guess,
+                             const eom_options *opt, double *energies, double *omegas,
+                             eom_info *out);
+
+/* sigma = (H-bar R)_c for a packed EOM vector (host pointers). */
+fnocc_status eom_sigma(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
+fnocc_status eom_sigma_dev(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
+
+/* Packed sizes of the three EOM components of a variant for the loaded
+ * Hamiltonian (sizes[3]). */
+fnocc_status fnocc_eom_sizes(const fnocc_ctx *ctx, int variant, size_t *sizes);
+
+/* Sets packed ground-state amplitudes (host) without solving. */
+fnocc_status fnocc_set_amplitudes(fnocc_ctx *ctx, const double *t1, const double *t2,
+                                  const double *t3);
+
+/* Dimensions of the loaded Hamiltonian: o, v spin orbitals and the
+ * reference energy. */
+fnocc_status fnocc_dims(const fnocc_ctx *ctx, int *o, int *v, double *e_ref);
+
+/* Copies a packed block to the host. which: 1..3 = T1..T3 of the ground
+ * state; 11..13 = R1..R3 of EOM root `root` of the last eom_ccsdt_solve.
+ * len must equal the block's packed size. */
+fnocc_status fnocc_get_block(fnocc_ctx *ctx, int which, int root, double *buf, size_t len);
+
+/* XFNO (Sec. 2): least-squares line E(f) through (kept_fraction, energy)
+ * points evaluated at f = 1 (the paper prints no formula; this is the
+ * library's reading). Returns NaN for npts < 1. Pure host function. */
+double xfno_extrapolate(const double *kept_fraction, const double *energy, int npts);
+
+/* Count of kernel launches issued by the context so far. */
+uint64_t fnocc_launch_count(const fnocc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FNOCC_H */

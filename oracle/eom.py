@@ -1,0 +1,211 @@
+"""Oracle: IP / EA / DIP / DEA EOM-CCSDT (Eq. 1-4) and the Davidson solver.
+
+Operator spaces (reading Z2 of the paper's silent points: every variant has
+three components; removal uses n = m..m+2 holes, attachment n = 0..2):
+    IP  1h, 2h1p, 3h2p        EA  1p, 1h2p, 2h3p
+    DIP 2h, 3h1p, 4h2p        DEA 2p, 1h3p, 2h4p
+sigma = <mu| (H-bar R)_c |Phi_0> from the Wick term lists (oracle/wick.py);
+the eigenvalue omega is the energy relative to the CC ground state, so the
+state's total energy is E_CC + omega.
+
+Spin sector (reading Z9): 2*M_s change of +1 for IP (a beta electron is
+removed) and EA (an alpha electron is added), 0 for DIP and DEA. The roots are
+the lowest Re(omega) in that sector.
+
+Davidson (the paper names no eigensolver; this follows the standard
+non-symmetric Davidson method): orthonormal subspace V, projected matrix
+G = V^T sigma(V), Ritz pairs of G ordered by real part, residual
+r = sigma(x) - theta x, diagonal preconditioner (theta - D)^-1 with D built
+from diag(f), Gram-Schmidt (twice), collapse to the Ritz vectors when the
+subspace exceeds max_sub. Guesses are Koopmans-like unit vectors on the
+lowest diagonal elements of the first component.
+
+Parity: sigma pinned to the Fock-space definition for all four variants on
+random T and R; eigenvalues pinned to FCI where the operator space spans the
+whole (N +- m) sector; Davidson pinned to dense diagonalisation of the
+explicitly built sigma matrix.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from . import packing, wick
+
+SECTOR_MS2 = {"ip": 1, "ea": 1, "dip": 0, "dea": 0}
+
+
+def comps(variant):
+    return wick.EOM_SPACES[variant]
+
+
+def sizes(variant, o, v):
+    return [packing.packed_size(nh, np_, o, v) for nh, np_ in comps(variant)]
+
+
+def ms_mask(variant, o, v):
+    """Packed-vector mask of the target spin sector (alpha = even spin orbital)."""
+    out = []
+    for nh, np_ in comps(variant):
+        hs = list(itertools.combinations(range(o), nh))
+        ps = list(itertools.combinations(range(v), np_))
+        sh = np.array([sum(1 if i % 2 == 0 else -1 for i in t) for t in hs])
+        sp_ = np.array([sum(1 if a % 2 == 0 else -1 for a in t) for t in ps])
+        out.append((sp_[None, :] - sh[:, None] == SECTOR_MS2[variant]).reshape(-1))
+    return np.concatenate(out)
+
+
+def split(variant, o, v, vec):
+    s = sizes(variant, o, v)
+    parts = np.split(vec, np.cumsum(s)[:-1])
+    return [packing.unpack(p, nh, np_, o, v) for p, (nh, np_) in zip(parts, comps(variant))]
+
+
+def sigma_dense(variant, f, g, o, v, t1, t2, t3, rs):
+    amps = {"t1": t1, "t2": t2, "t3": t3, "r1": rs[0], "r2": rs[1], "r3": rs[2]}
+    out = []
+    for oc, (nh, np_) in enumerate(comps(variant)):
+        acc = np.zeros((o,) * nh + (v,) * np_)
+        for ic in range(3):
+            acc += wick.evaluate(wick.eom_terms(variant, oc, ic), nh, np_, f, g, amps, o, v)
+        out.append(acc)
+    return out
+
+
+def sigma_packed(variant, f, g, o, v, t1, t2, t3, vec):
+    rs = split(variant, o, v, vec)
+    out = sigma_dense(variant, f, g, o, v, t1, t2, t3, rs)
+    return np.concatenate([packing.pack(x, nh, np_, o, v) for x, (nh, np_) in zip(out, comps(variant))])
+
+
+def diagonal(variant, f, o, v):
+    """Orbital-energy estimate of diag(H-bar): sum f_aa - sum f_ii per element."""
+    fo = np.diag(f)[:o]
+    fv = np.diag(f)[o:]
+    out = []
+    for nh, np_ in comps(variant):
+        hs = list(itertools.combinations(range(o), nh))
+        ps = list(itertools.combinations(range(v), np_))
+        eh = np.array([sum(fo[i] for i in t) for t in hs])
+        ep = np.array([sum(fv[a] for a in t) for t in ps])
+        out.append((ep[None, :] - eh[:, None]).reshape(-1))
+    return np.concatenate(out)
+
+
+def _orthonormalise(vec, basis, tol=1e-10):
+    for _ in range(2):
+        for b in basis:
+            vec = vec - (b @ vec) * b
+    nrm = np.linalg.norm(vec)
+    if nrm < tol:
+        return None
+    return vec / nrm
+
+
+def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
+             maxiter=200, nguess=None, guess_mask=None):
+    """Lowest-Re roots of a non-symmetric operator restricted to `mask`.
+    Guess unit vectors sit on the lowest `diag` entries inside guess_mask."""
+    n = len(diag)
+    allowed = np.where(mask)[0]
+    if nguess is None:
+        nguess = nroots
+    nguess = min(nguess, len(allowed))
+    nroots = min(nroots, len(allowed))
+    if max_sub is None:
+        max_sub = max(4 * nroots, nguess + 2 * nroots)
+    pref = allowed if guess_mask is None else np.where(mask & guess_mask)[0]
+    rest = np.setdiff1d(allowed, pref)
+    order = np.concatenate([pref[np.argsort(diag[pref], kind="stable")],
+                            rest[np.argsort(diag[rest], kind="stable")]])[:nguess]
+    basis, sig = [], []
+    for k in order:
+        e = np.zeros(n)
+        e[k] = 1.0
+        basis.append(e)
+        sig.append(apply(e) * mask)
+    theta_old = None
+    for it in range(1, maxiter + 1):
+        vmat = np.array(basis)
+        smat = np.array(sig)
+        gmat = vmat @ smat.T
+        w, y = np.linalg.eig(gmat)
+        srt = np.argsort(w.real, kind="stable")
+        w = w[srt][:nroots]
+        y = y[:, srt][:, :nroots]
+        theta = w.real
+        yr = np.real(y)
+        xs, res, norms = [], [], []
+        for r in range(nroots):
+            yv = yr[:, r] / np.linalg.norm(vmat.T @ yr[:, r])
+            x = vmat.T @ yv
+            rv = smat.T @ yv - theta[r] * x
+            xs.append(x)
+            res.append(rv)
+            norms.append(np.linalg.norm(rv))
+        done = [norms[r] < tol_res and theta_old is not None and abs(theta[r] - theta_old[r]) < tol_e
+                for r in range(nroots)]
+        if all(done):
+            return dict(omega=theta, vectors=np.array(xs), iters=it, res=np.array(norms),
+                        converged=True, imag=np.abs(w.imag))
+        theta_old = theta.copy()
+        new = []
+        for r in range(nroots):
+            if done[r]:
+                continue
+            den = theta[r] - diag
+            den = np.where(np.abs(den) < 1e-8, 1e-8, den)
+            new.append((res[r] / den) * mask)
+        if len(basis) + len(new) > max_sub:
+            nb = []
+            for x in xs:
+                q = _orthonormalise(x, nb)
+                if q is not None:
+                    nb.append(q)
+            basis = nb
+            sig = [apply(b) * mask for b in basis]
+        for d in new:
+            q = _orthonormalise(d, basis)
+            if q is not None:
+                basis.append(q)
+                sig.append(apply(q) * mask)
+    return dict(omega=theta, vectors=np.array(xs), iters=maxiter, res=np.array(norms),
+                converged=False, imag=np.abs(w.imag))
+
+
+def eom_ccsdt(variant, f, g, o, v, t1, t2, t3, nroots, tol_res=1e-8, tol_e=1e-10,
+              max_sub=None, maxiter=200, nguess=None, guess="diagonal"):
+    """Lowest nroots EOM-CCSDT excitation energies omega in the target sector.
+
+    guess 'koopmans': unit vectors on the lowest diagonal elements of the
+    first component (1h, 1p, 2h or 2p); 'diagonal': on the lowest diagonal
+    elements of the whole operator space."""
+    mask = ms_mask(variant, o, v)
+    diag = diagonal(variant, f, o, v)
+    first = sizes(variant, o, v)[0]
+    gmask = np.zeros_like(mask)
+    if guess == "koopmans":
+        gmask[:first] = True
+    elif guess == "diagonal":
+        gmask[:] = True
+    else:
+        raise ValueError(guess)
+
+    def apply(x):
+        return sigma_packed(variant, f, g, o, v, t1, t2, t3, x)
+
+    return davidson(apply, diag, mask, nroots, tol_res, tol_e, max_sub, maxiter, nguess, gmask)
+
+
+def sigma_matrix(variant, f, g, o, v, t1, t2, t3):
+    """Explicit H-bar matrix in the target sector (for small pins)."""
+    mask = ms_mask(variant, o, v)
+    idx = np.where(mask)[0]
+    n = len(mask)
+    cols = []
+    for k in idx:
+        e = np.zeros(n)
+        e[k] = 1.0
+        cols.append(sigma_packed(variant, f, g, o, v, t1, t2, t3, e)[idx])
+    return np.array(cols).T

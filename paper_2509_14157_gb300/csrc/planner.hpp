@@ -1,0 +1,99 @@
+// Symbolic planner: derives the projected equations of the method by Wick's
+// theorem and turns every distinct term into GEMM-shaped contraction steps.
+//
+// Equations (arXiv 2509.14157):
+//   CCSDT residual  <Phi^n| (H~ e^{T2+T3})_c |Phi_0>, n = 1..3   (Eq. 6)
+//   EOM product     <mu| (H~ e^{T2+T3} R)_c |Phi_0>             (Eq. 1-4)
+// with H~ = e^{-T1} H e^{T1} the T1-similarity-transformed Hamiltonian in
+// normal order (general one-body f~ and antisymmetric two-body v~ with every
+// occupied/virtual block), so T1 never appears explicitly.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace fnocc {
+
+enum Space : int { SP_O = 0, SP_V = 1 };
+
+// Tensor kinds that appear in terms.
+enum TensorKind : int { TK_F = 0, TK_V = 1, TK_T2 = 2, TK_T3 = 3, TK_R1 = 4, TK_R2 = 5, TK_R3 = 6,
+                        TK_INTERMEDIATE = 100 };
+
+struct Frac {
+  long long n = 0, d = 1;
+  Frac() {}
+  Frac(long long a, long long b = 1);
+  Frac operator+(const Frac &o) const;
+  Frac operator*(const Frac &o) const;
+  bool zero() const { return n == 0; }
+  double value() const { return double(n) / double(d); }
+};
+
+// A label is (id << 1) | space. Externals have ids 0..nh+np-1 (holes first).
+inline int lab_space(int lab) { return lab & 1; }
+inline int make_label(int id, int sp) { return (id << 1) | sp; }
+
+struct Factor {
+  int kind;                              // TensorKind
+  std::vector<std::vector<int>> groups;  // antisymmetric slot groups, labels in slot order
+};
+
+struct Term {
+  double coef;                 // numeric coefficient applied to the representative
+  std::vector<Factor> factors;
+};
+
+// Term list of one projection: output holes nh, particles np.
+struct Equation {
+  int nh = 0, np = 0;
+  std::vector<Term> terms;     // orbit representatives, coefficient already divided by |Stab|
+};
+
+// CCSDT: rank 1..3 residual (0 = energy) with T2, T3 clusters.
+Equation cc_equation(int rank);
+// EOM: variant 0..3 (IP, EA, DIP, DEA), output component and input component (0..2).
+Equation eom_equation(int variant, int out_comp, int in_comp);
+// (nh, np) of component c of a variant.
+void eom_component(int variant, int comp, int *nh, int *np);
+
+std::string equation_to_string(const Equation &eq);
+
+// ---------------------------------------------------------------------------
+// Contraction plans
+// ---------------------------------------------------------------------------
+
+// One index group of a GEMM dimension: the slots (positions in the operand
+// storage) it addresses, all of one space; packed = strictly increasing tuples.
+struct DimGroup {
+  int space;
+  int k;                    // number of indices in the group
+  bool packed;
+  std::vector<int> labels;  // labels in tuple order
+};
+
+// Operand of a step: an input tensor or an intermediate.
+struct Operand {
+  int kind;                 // TensorKind or TK_INTERMEDIATE
+  int inter = -1;           // intermediate id
+  std::vector<int> labels;  // storage slot order
+};
+
+struct Step {
+  Operand a, b;             // b.kind < 0 for a one-operand (copy) step
+  std::vector<DimGroup> mg, kg, ng;  // GEMM dims: rows from a, contraction, columns from b
+  bool to_output = false;   // write into the output accumulator
+  int out_inter = -1;       // else the intermediate it creates (layout: mg then ng, unpacked)
+  double alpha = 1.0;       // coefficient incl. packing multiplicities
+};
+
+struct TermPlan {
+  std::vector<Step> steps;
+  std::vector<std::vector<int>> inter_labels;  // per intermediate: its labels in storage order
+};
+
+// Builds the contraction steps of a term for output holes nh, particles np,
+// sized with o and v (used by the cost model that orders contractions).
+TermPlan plan_term(const Term &t, int nh, int np, int o, int v);
+
+}  // namespace fnocc
