@@ -1,0 +1,251 @@
+"""Python binding of libfnocc: frozen-natural-orbital EOM-CCSDT on one GB300.
+
+Argument marshalling only: every step runs in the CUDA library behind the C
+ABI of include/fnocc.h. Importing this package fails loudly when the compiled
+library is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfnocc.so")
+
+IP, EA, DIP, DEA = 0, 1, 2, 3
+VARIANTS = {"ip": IP, "ea": EA, "dip": DIP, "dea": DEA}
+GUESS = {"koopmans": 0, "diagonal": 1}
+CRITERIA = {"abs": 0, "occt": 1}
+STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "E_INVALID", -2: "E_NOMEM", -3: "E_CUDA",
+          -4: "E_STATE", -5: "E_NUMERIC", -6: "E_TIMEOUT"}
+# (holes, particles) of R1, R2, R3 per variant
+EOM_SPACES = {IP: [(1, 0), (2, 1), (3, 2)], EA: [(0, 1), (1, 2), (2, 3)],
+              DIP: [(2, 0), (3, 1), (4, 2)], DEA: [(0, 2), (1, 3), (2, 4)]}
+
+
+class FnoccError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class FnoOptions(ctypes.Structure):
+    _fields_ = [("criterion", ctypes.c_int), ("nkeep", ctypes.c_int), ("scf_maxiter", ctypes.c_int),
+                ("scf_e_tol", ctypes.c_double), ("scf_comm_tol", ctypes.c_double)]
+
+
+class FnoInfo(ctypes.Structure):
+    _fields_ = [("e_rhf", ctypes.c_double), ("e_mp2", ctypes.c_double), ("nkept", ctypes.c_int),
+                ("nvir", ctypes.c_int), ("kept_fraction", ctypes.c_double), ("scf_iters", ctypes.c_int)]
+
+
+class CcsdtOptions(ctypes.Structure):
+    _fields_ = [("tol_res", ctypes.c_double), ("tol_e", ctypes.c_double), ("maxiter", ctypes.c_int),
+                ("diis", ctypes.c_int)]
+
+
+class CcsdtInfo(ctypes.Structure):
+    _fields_ = [("e_corr", ctypes.c_double), ("e_tot", ctypes.c_double), ("iters", ctypes.c_int),
+                ("res_max", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("seconds_per_iter", ctypes.c_double)]
+
+
+class EomOptions(ctypes.Structure):
+    _fields_ = [("tol_res", ctypes.c_double), ("tol_e", ctypes.c_double), ("max_sub", ctypes.c_int),
+                ("maxiter", ctypes.c_int), ("nguess", ctypes.c_int)]
+
+
+class EomInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("sigma_calls", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("seconds_per_iter", ctypes.c_double), ("complex_roots", ctypes.c_int),
+                ("res_max", ctypes.c_double)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_cp = ctypes.c_void_p
+
+# exported symbol -> (restype, argtypes)
+SIGNATURES = {
+    "fnocc_create": (ctypes.c_int, [ctypes.POINTER(_cp), ctypes.c_int, _vp]),
+    "fnocc_destroy": (None, [_cp]),
+    "fnocc_last_error": (ctypes.c_char_p, [_cp]),
+    "fnocc_launch_count": (ctypes.c_uint64, [_cp]),
+    "fno_truncate": (ctypes.c_int, [_cp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.POINTER(FnoOptions), ctypes.POINTER(FnoInfo), _dp]),
+    "fnocc_set_mo_hamiltonian": (ctypes.c_int, [_cp, _dp, _dp, ctypes.c_int, ctypes.c_int]),
+    "ccsdt_solve": (ctypes.c_int, [_cp, ctypes.POINTER(CcsdtOptions), ctypes.POINTER(CcsdtInfo)]),
+    "ccsdt_residual": (ctypes.c_int, [_cp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
+    "ccsdt_residual_dev": (ctypes.c_int, [_cp, _vp, _vp, _vp, _vp, _vp, _vp, _dp]),
+    "eom_ccsdt_solve": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(EomOptions), _dp, _dp, ctypes.POINTER(EomInfo)]),
+    "eom_sigma": (ctypes.c_int, [_cp, ctypes.c_int, _dp, _dp]),
+    "eom_sigma_dev": (ctypes.c_int, [_cp, ctypes.c_int, _vp, _vp]),
+    "fnocc_eom_sizes": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "fnocc_set_amplitudes": (ctypes.c_int, [_cp, _dp, _dp, _dp]),
+    "fnocc_dims": (ctypes.c_int, [_cp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]),
+    "fnocc_get_block": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]),
+    "xfno_extrapolate": (ctypes.c_double, [_dp, _dp, ctypes.c_int]),
+}
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Loads libfnocc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libfnocc.so not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _arr(x):
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def xfno_extrapolate(kept_fraction, energy):
+    lib = load_library()
+    f, fp = _arr(kept_fraction)
+    e, ep = _arr(energy)
+    return float(lib.xfno_extrapolate(fp, ep, len(f)))
+
+
+class Context:
+    """One library context (device memory, stream, loaded Hamiltonian)."""
+
+    def __init__(self, device=0, stream=None):
+        self.lib = load_library()
+        self._h = _cp()
+        st = self.lib.fnocc_create(ctypes.byref(self._h), int(device), stream)
+        if st != 0:
+            raise FnoccError(st, "fnocc_create failed")
+
+    def close(self):
+        if self._h:
+            self.lib.fnocc_destroy(self._h)
+            self._h = _cp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=(0,)):
+        if st not in allow:
+            msg = self.lib.fnocc_last_error(self._h)
+            raise FnoccError(st, msg.decode() if msg else "")
+        return st
+
+    @property
+    def launches(self):
+        return int(self.lib.fnocc_launch_count(self._h))
+
+    def dims(self):
+        o, v, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.fnocc_dims(self._h, ctypes.byref(o), ctypes.byref(v), ctypes.byref(e)))
+        return o.value, v.value, e.value
+
+    def fno_truncate(self, h, eri, nocc, threshold, criterion="abs", nkeep=0):
+        h, hp = _arr(h)
+        eri, ep = _arr(eri)
+        n = h.shape[0]
+        opt = FnoOptions(CRITERIA[criterion], int(nkeep), 200, 1e-12, 1e-10)
+        info = FnoInfo()
+        occ = np.zeros(n - nocc)
+        self._check(self.lib.fno_truncate(self._h, hp, ep, n, int(nocc), float(threshold), ctypes.byref(opt),
+                                          ctypes.byref(info), occ.ctypes.data_as(_dp)))
+        return dict(e_rhf=info.e_rhf, e_mp2=info.e_mp2, nkept=info.nkept, nvir=info.nvir,
+                    kept_fraction=info.kept_fraction, scf_iters=info.scf_iters, occ=occ)
+
+    def set_mo_hamiltonian(self, h_mo, eri_mo, nocc):
+        h, hp = _arr(h_mo)
+        e, ep = _arr(eri_mo)
+        self._check(self.lib.fnocc_set_mo_hamiltonian(self._h, hp, ep, h.shape[0], int(nocc)))
+
+    def ccsdt_solve(self, tol_res=1e-10, tol_e=1e-12, maxiter=200, diis=8):
+        opt = CcsdtOptions(tol_res, tol_e, maxiter, diis)
+        info = CcsdtInfo()
+        st = self._check(self.lib.ccsdt_solve(self._h, ctypes.byref(opt), ctypes.byref(info)), allow=(0, 1))
+        return dict(e_corr=info.e_corr, e_tot=info.e_tot, iters=info.iters, res_max=info.res_max,
+                    seconds=info.seconds, seconds_per_iter=info.seconds_per_iter, converged=(st == 0))
+
+    def amp_sizes(self):
+        from math import comb
+        o, v, _ = self.dims()
+        return [comb(o, r) * comb(v, r) for r in (1, 2, 3)]
+
+    def ccsdt_residual(self, t1, t2, t3):
+        sizes = self.amp_sizes()
+        ins = [_arr(t) for t in (t1, t2, t3)]
+        outs = [np.zeros(s) for s in sizes]
+        e = ctypes.c_double()
+        self._check(self.lib.ccsdt_residual(self._h, ins[0][1], ins[1][1], ins[2][1],
+                                            *[o_.ctypes.data_as(_dp) for o_ in outs], ctypes.byref(e)))
+        return outs, e.value
+
+    def ccsdt_residual_dev(self, t1_ptr, t2_ptr, t3_ptr, r1_ptr, r2_ptr, r3_ptr):
+        e = ctypes.c_double()
+        self._check(self.lib.ccsdt_residual_dev(self._h, t1_ptr, t2_ptr, t3_ptr, r1_ptr, r2_ptr, r3_ptr,
+                                                ctypes.byref(e)))
+        return e.value
+
+    def set_amplitudes(self, t1, t2, t3):
+        ins = [_arr(t) for t in (t1, t2, t3)]
+        self._check(self.lib.fnocc_set_amplitudes(self._h, ins[0][1], ins[1][1], ins[2][1]))
+
+    def eom_sizes(self, variant):
+        sz = (ctypes.c_size_t * 3)()
+        self._check(self.lib.fnocc_eom_sizes(self._h, VARIANTS.get(variant, variant), sz))
+        return [int(x) for x in sz]
+
+    def eom_sigma(self, variant, r):
+        var = VARIANTS.get(variant, variant)
+        r, rp = _arr(r)
+        s = np.zeros_like(r)
+        self._check(self.lib.eom_sigma(self._h, var, rp, s.ctypes.data_as(_dp)))
+        return s
+
+    def eom_sigma_dev(self, variant, r_ptr, s_ptr):
+        self._check(self.lib.eom_sigma_dev(self._h, VARIANTS.get(variant, variant), r_ptr, s_ptr))
+
+    def eom_solve(self, variant, nroots, guess="diagonal", tol_res=1e-8, tol_e=1e-10, max_sub=0,
+                  maxiter=200, nguess=0):
+        var = VARIANTS.get(variant, variant)
+        self._last_sizes = self.eom_sizes(var)
+        opt = EomOptions(tol_res, tol_e, max_sub, maxiter, nguess)
+        info = EomInfo()
+        en = np.zeros(nroots)
+        om = np.zeros(nroots)
+        st = self._check(self.lib.eom_ccsdt_solve(self._h, var, int(nroots), GUESS[guess], ctypes.byref(opt),
+                                                  en.ctypes.data_as(_dp), om.ctypes.data_as(_dp),
+                                                  ctypes.byref(info)), allow=(0, 1))
+        return dict(energies=en, omegas=om, iters=info.iters, sigma_calls=info.sigma_calls,
+                    seconds=info.seconds, seconds_per_iter=info.seconds_per_iter,
+                    complex_roots=info.complex_roots, res_max=info.res_max, converged=(st == 0))
+
+    def get_block(self, which, root=0):
+        """which: 't1','t2','t3' or ('r', k) for component k=1..3 of EOM root `root`."""
+        if isinstance(which, str):
+            k = int(which[1])
+            size = self.amp_sizes()[k - 1]
+            code = k
+        else:
+            k = which[1]
+            var_sizes = self._last_sizes
+            size = var_sizes[k - 1]
+            code = 10 + k
+        buf = np.zeros(size)
+        self._check(self.lib.fnocc_get_block(self._h, code, int(root), buf.ctypes.data_as(_dp), size))
+        return buf

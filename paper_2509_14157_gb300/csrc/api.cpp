@@ -1,0 +1,1354 @@
+// C ABI of libfnocc (include/fnocc.h): context, FNO setup, CCSDT and EOM-CCSDT.
+#include "../../include/fnocc.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.hpp"
+#include "engine.hpp"
+#include "linalg.hpp"
+#include "planner.hpp"
+
+using namespace fnocc;
+
+namespace {
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double s() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+struct StatusError : std::runtime_error {
+  fnocc_status st;
+  StatusError(fnocc_status s, const std::string &m) : std::runtime_error(m), st(s) {}
+};
+
+DMap stride_map(std::initializer_list<std::pair<long long, long long>> dims, std::vector<long long> &host,
+                std::vector<std::pair<DMap *, std::vector<long long>>> &fix, DMap *m) {
+  m->ng = (int)dims.size();
+  m->maxoff = 0;
+  std::vector<long long> offs;
+  int g = 0;
+  for (auto &d : dims) {
+    offs.push_back((long long)host.size());
+    for (long long x = 0; x < d.first; ++x) host.push_back(x * d.second);
+    m->n[g++] = d.first;
+    m->maxoff += (d.first - 1) * d.second;
+  }
+  fix.push_back({m, offs});
+  return *m;
+}
+
+// A set of stride maps uploaded once.
+struct MapSet {
+  std::vector<long long> host;
+  std::vector<std::pair<DMap *, std::vector<long long>>> fix;
+  DevBuf dev;
+  void add(DMap *m, std::initializer_list<std::pair<long long, long long>> dims) { stride_map(dims, host, fix, m); }
+  void upload() {
+    if (host.empty()) host.push_back(0);
+    dev.reserve(host.size() * sizeof(long long));
+    FNOCC_CUDA(cudaMemcpy(dev.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    for (auto &f : fix)
+      for (size_t g = 0; g < f.second.size(); ++g) f.first->tab[g] = dev.as<long long>() + f.second[g];
+  }
+};
+
+// Maps of one index-transformation pass of a 4-index tensor (dims n_out before
+// index `idx`, n_in after), contracting index idx with a (n_in x n_out) matrix.
+struct PassMaps {
+  DMap arow, acol, brow, bcol, crow, ccol;
+};
+
+struct TransformPlan {
+  int n_in = 0, n_out = 0;
+  PassMaps pass[4];
+  PassMaps two[2];  // one-body transform passes (index 0, then index 1)
+  MapSet set;
+  void build(int ni, int no) {
+    n_in = ni;
+    n_out = no;
+    set.host.clear();
+    set.fix.clear();
+    for (int idx = 0; idx < 4; ++idx) {
+      long long din[4], dout[4];
+      for (int k = 0; k < 4; ++k) {
+        din[k] = k < idx ? no : ni;
+        dout[k] = k <= idx ? no : ni;
+      }
+      long long sin[4], sout[4];
+      sin[3] = sout[3] = 1;
+      for (int k = 2; k >= 0; --k) {
+        sin[k] = sin[k + 1] * din[k + 1];
+        sout[k] = sout[k + 1] * dout[k + 1];
+      }
+      PassMaps &p = pass[idx];
+      set.add(&p.arow, {{no, 1}});
+      set.add(&p.acol, {{ni, no}});
+      set.add(&p.brow, {{ni, sin[idx]}});
+      set.add(&p.crow, {{no, sout[idx]}});
+      int others[3], c = 0;
+      for (int k = 0; k < 4; ++k)
+        if (k != idx) others[c++] = k;
+      set.add(&p.bcol, {{din[others[0]], sin[others[0]]}, {din[others[1]], sin[others[1]]}, {din[others[2]], sin[others[2]]}});
+      set.add(&p.ccol, {{dout[others[0]], sout[others[0]]}, {dout[others[1]], sout[others[1]]}, {dout[others[2]], sout[others[2]]}});
+    }
+    // one-body: X[p', q] = sum_p A[p,p'] h[p,q] ; out[p', q'] = sum_q X[p', q] A[q, q']
+    set.add(&two[0].arow, {{no, 1}});
+    set.add(&two[0].acol, {{ni, no}});
+    set.add(&two[0].brow, {{ni, ni}});
+    set.add(&two[0].bcol, {{ni, 1}});
+    set.add(&two[0].crow, {{no, ni}});
+    set.add(&two[0].ccol, {{ni, 1}});
+    set.add(&two[1].arow, {{no, 1}});
+    set.add(&two[1].acol, {{ni, no}});
+    set.add(&two[1].brow, {{ni, 1}});
+    set.add(&two[1].bcol, {{no, ni}});
+    set.add(&two[1].crow, {{no, 1}});
+    set.add(&two[1].ccol, {{no, no}});
+    set.upload();
+  }
+};
+
+}  // namespace
+
+struct fnocc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  uint64_t launches = 0;
+  Launch L() { return Launch{stream, &launches}; }
+
+  // active Hamiltonian (spin orbitals, bare)
+  bool have_ham = false;
+  int o = 0, v = 0, n = 0;
+  double e_ref = 0;
+  DevBuf hso, gso, fso, fdiag;
+  std::vector<double> fdiag_host;
+
+  // T1-dressed operators
+  DevBuf hd, gd, fdr, tmpA, tmpB, Lm, Mm, tmph, eref2;
+  double e_ref_dressed = 0;
+  TransformPlan dress_plan;
+
+  TupleTable otab[5], vtab[5];
+
+  // amplitudes: packed [t1 | t2 | t3] in one buffer
+  bool have_amps = false;
+  size_t nt[4] = {0, 0, 0, 0};
+  DevBuf tpk, rpk, t2d, t3d, den;
+  double e_corr = 0;
+
+  std::unique_ptr<ExecEquation> cc_eq[4];
+  DevBuf Y[4], scratch, red, small;
+
+  // EOM
+  std::unique_ptr<ExecEquation> eom_eq[4][3][3];
+  DevBuf rd[3], sy[3];
+  int last_variant = -1, last_nroots = 0;
+  size_t last_dim = 0;
+  DevBuf eom_vecs;
+  double flops_cc_last = 0, flops_sigma_last = 0;
+
+  // fno scratch
+  DevBuf eri_ao, h_ao, c_mo, dens, fock, jmat, kmat, ctmp, evals, evecs, work, diis_f, diis_e, t2full, w2full,
+      dvv, c_act, eri_act, h_act;
+  DevBuf ints;  // int scratch
+};
+
+namespace {
+
+void set_err(fnocc_ctx *c, const std::string &m) {
+  if (c) c->err = m;
+}
+
+template <class F>
+fnocc_status guarded(fnocc_ctx *c, F &&fn) {
+  try {
+    return fn();
+  } catch (const StatusError &e) {
+    set_err(c, e.what());
+    return e.st;
+  } catch (const CudaError &e) {
+    set_err(c, e.what());
+    return e.code == (int)cudaErrorMemoryAllocation ? FNOCC_E_NOMEM : FNOCC_E_CUDA;
+  } catch (const std::exception &e) {
+    set_err(c, e.what());
+    return FNOCC_E_INVALID;
+  }
+}
+
+void sync(fnocc_ctx *c) { FNOCC_CUDA(cudaStreamSynchronize(c->stream)); }
+
+void to_dev(fnocc_ctx *c, DevBuf &b, const double *h, size_t n) {
+  b.reserve(n * sizeof(double));
+  FNOCC_CUDA(cudaMemcpyAsync(b.p, h, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+}
+
+std::vector<double> to_host(fnocc_ctx *c, const double *d, size_t n) {
+  std::vector<double> h(n);
+  if (n) FNOCC_CUDA(cudaMemcpyAsync(h.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  sync(c);
+  return h;
+}
+
+long long ipow(long long b, int e) {
+  long long r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+const int kEom[4][3][2] = {{{1, 0}, {2, 1}, {3, 2}}, {{0, 1}, {1, 2}, {2, 3}}, {{2, 0}, {3, 1}, {4, 2}}, {{0, 2}, {1, 3}, {2, 4}}};
+const int kSectorMs2[4] = {1, 1, 0, 0};
+
+// ---- Hamiltonian installation ---------------------------------------------------
+
+void install_hamiltonian(fnocc_ctx *c, int nocc, int nact_spatial) {
+  // expects c->hso (n x n) and c->gso (n^4) filled for n = 2 * nact_spatial
+  c->n = 2 * nact_spatial;
+  c->o = 2 * nocc;
+  c->v = c->n - c->o;
+  Launch L = c->L();
+  c->fso.reserve(sizeof(double) * c->n * c->n);
+  c->eref2.reserve(sizeof(double) * 2);
+  normal_order(L, c->hso.d(), c->gso.d(), c->n, c->o, c->fso.d(), c->eref2.d());
+  auto er = to_host(c, c->eref2.d(), 2);
+  c->e_ref = er[0] + er[1];
+  c->fdiag.reserve(sizeof(double) * c->n);
+  diag_of(L, c->fso.d(), c->n, c->fdiag.d());
+  c->fdiag_host = to_host(c, c->fdiag.d(), c->n);
+  for (int k = 0; k <= 4; ++k) {
+    c->otab[k].build(c->o, k);
+    c->vtab[k].build(c->v, k);
+  }
+  c->dress_plan.build(c->n, c->n);
+  for (int r = 0; r < 4; ++r) c->cc_eq[r].reset();
+  for (auto &a : c->eom_eq)
+    for (auto &b : a)
+      for (auto &e : b) e.reset();
+  c->nt[1] = (size_t)binom_ll(c->o, 1) * binom_ll(c->v, 1);
+  c->nt[2] = (size_t)binom_ll(c->o, 2) * binom_ll(c->v, 2);
+  c->nt[3] = (size_t)binom_ll(c->o, 3) * binom_ll(c->v, 3);
+  c->have_ham = true;
+  c->have_amps = false;
+  c->last_variant = -1;
+}
+
+// ---- T1 similarity transformation -----------------------------------------------
+
+void dress(fnocc_ctx *c, const double *t1) {
+  Launch L = c->L();
+  const int n = c->n;
+  const size_t n4 = (size_t)n * n * n * n;
+  c->Lm.reserve(sizeof(double) * n * n);
+  c->Mm.reserve(sizeof(double) * n * n);
+  c->tmpA.reserve(sizeof(double) * n4);
+  c->tmpB.reserve(sizeof(double) * n4);
+  c->gd.reserve(sizeof(double) * n4);
+  c->hd.reserve(sizeof(double) * n * n);
+  c->tmph.reserve(sizeof(double) * n * n);
+  c->fdr.reserve(sizeof(double) * n * n);
+  t1_transform_mats(L, t1, c->o, c->v, c->Lm.d(), c->Mm.d());
+  const TransformPlan &tp = c->dress_plan;
+  const double *mats[4] = {c->Lm.d(), c->Lm.d(), c->Mm.d(), c->Mm.d()};
+  const double *src = c->gso.d();
+  double *dst[4] = {c->tmpA.d(), c->tmpB.d(), c->tmpA.d(), c->gd.d()};
+  for (int i = 0; i < 4; ++i) {
+    const PassMaps &p = tp.pass[i];
+    gather_gemm(L, n, (long long)n * n * n, n, 1.0, mats[i], p.arow, p.acol, src, p.brow, p.bcol, dst[i], p.crow,
+                p.ccol, false, (long long)n * n, (long long)n4, (long long)n4);
+    src = dst[i];
+  }
+  gather_gemm(L, n, n, n, 1.0, c->Lm.d(), tp.two[0].arow, tp.two[0].acol, c->hso.d(), tp.two[0].brow,
+              tp.two[0].bcol, c->tmph.d(), tp.two[0].crow, tp.two[0].ccol, false, (long long)n * n, (long long)n * n,
+              (long long)n * n);
+  gather_gemm(L, n, n, n, 1.0, c->Mm.d(), tp.two[1].arow, tp.two[1].acol, c->tmph.d(), tp.two[1].brow,
+              tp.two[1].bcol, c->hd.d(), tp.two[1].crow, tp.two[1].ccol, false, (long long)n * n, (long long)n * n,
+              (long long)n * n);
+  normal_order(L, c->hd.d(), c->gd.d(), n, c->o, c->fdr.d(), c->eref2.d());
+  auto er = to_host(c, c->eref2.d(), 2);
+  c->e_ref_dressed = er[0] + er[1];
+}
+
+void ensure_cc_plans(fnocc_ctx *c) {
+  int rd[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int r = 0; r < 4; ++r)
+    if (!c->cc_eq[r]) c->cc_eq[r].reset(new ExecEquation(cc_equation(r), c->o, c->v, rd));
+}
+
+// residual of packed amplitudes tp (device) into rp (device); returns E_corr
+double cc_residual_dev(fnocc_ctx *c, const double *tp, double *rp) {
+  Launch L = c->L();
+  ensure_cc_plans(c);
+  const int o = c->o, v = c->v;
+  const double *t1 = tp, *t2 = tp + c->nt[1], *t3 = tp + c->nt[1] + c->nt[2];
+  dress(c, t1);
+  c->t2d.reserve(sizeof(double) * ipow(o, 2) * ipow(v, 2));
+  c->t3d.reserve(sizeof(double) * std::max<long long>(1, ipow(o, 3) * ipow(v, 3)));
+  unpack_dense(L, t2, 2, 2, o, v, c->otab[2].dev.as<int>(), c->otab[2].count, c->vtab[2].dev.as<int>(),
+               c->vtab[2].count, c->t2d.d());
+  unpack_dense(L, t3, 3, 3, o, v, c->otab[3].dev.as<int>(), c->otab[3].count, c->vtab[3].dev.as<int>(),
+               c->vtab[3].count, c->t3d.d());
+  Operands ops;
+  ops.f = c->fdr.d();
+  ops.v = c->gd.d();
+  ops.t2 = c->t2d.d();
+  ops.t3 = c->t3d.d();
+  const long long nn = c->n;
+  ops.f_size = nn * nn;
+  ops.v_size = nn * nn * nn * nn;
+  ops.t2_size = ipow(o, 2) * ipow(v, 2);
+  ops.t3_size = std::max<long long>(1, ipow(o, 3) * ipow(v, 3));
+  double flops = 0;
+  for (int r = 0; r <= 3; ++r) {
+    long long ysz = std::max<long long>(1, ipow(o, r) * ipow(v, r));
+    c->Y[r].reserve(sizeof(double) * ysz);
+    FNOCC_CUDA(cudaMemsetAsync(c->Y[r].p, 0, sizeof(double) * ysz, c->stream));
+    c->cc_eq[r]->run(L, ops, c->Y[r].d(), ysz, c->scratch);
+    flops += c->cc_eq[r]->flops();
+  }
+  c->flops_cc_last = flops;
+  size_t off = 0;
+  for (int r = 1; r <= 3; ++r) {
+    antisym_pack(L, c->Y[r].d(), r, r, o, v, c->otab[r].dev.as<int>(), c->otab[r].count, c->vtab[r].dev.as<int>(),
+                 c->vtab[r].count, rp + off, 1.0, false);
+    off += c->nt[r];
+  }
+  auto y0 = to_host(c, c->Y[0].d(), 1);
+  return (c->e_ref_dressed - c->e_ref) + y0[0];
+}
+
+void require_ham(fnocc_ctx *c) {
+  if (!c->have_ham) throw StatusError(FNOCC_E_STATE, "no Hamiltonian loaded (call fno_truncate or fnocc_set_mo_hamiltonian)");
+}
+
+// ---- EOM sigma --------------------------------------------------------------
+
+void eom_sizes(const fnocc_ctx *c, int var, size_t *s) {
+  for (int k = 0; k < 3; ++k) s[k] = (size_t)binom_ll(c->o, kEom[var][k][0]) * binom_ll(c->v, kEom[var][k][1]);
+}
+
+void ensure_eom_plans(fnocc_ctx *c, int var) {
+  int rd[3][2];
+  for (int k = 0; k < 3; ++k) {
+    rd[k][0] = kEom[var][k][0];
+    rd[k][1] = kEom[var][k][1];
+  }
+  for (int oc = 0; oc < 3; ++oc)
+    for (int ic = 0; ic < 3; ++ic)
+      if (!c->eom_eq[var][oc][ic]) c->eom_eq[var][oc][ic].reset(new ExecEquation(eom_equation(var, oc, ic), c->o, c->v, rd));
+}
+
+// prepares dressed operators and dense T2/T3 from the stored amplitudes
+void prepare_hbar(fnocc_ctx *c) {
+  if (!c->have_amps) throw StatusError(FNOCC_E_STATE, "no ground-state amplitudes (call ccsdt_solve or fnocc_set_amplitudes)");
+  Launch L = c->L();
+  const int o = c->o, v = c->v;
+  const double *tp = c->tpk.d();
+  dress(c, tp);
+  c->t2d.reserve(sizeof(double) * ipow(o, 2) * ipow(v, 2));
+  c->t3d.reserve(sizeof(double) * std::max<long long>(1, ipow(o, 3) * ipow(v, 3)));
+  unpack_dense(L, tp + c->nt[1], 2, 2, o, v, c->otab[2].dev.as<int>(), c->otab[2].count, c->vtab[2].dev.as<int>(),
+               c->vtab[2].count, c->t2d.d());
+  unpack_dense(L, tp + c->nt[1] + c->nt[2], 3, 3, o, v, c->otab[3].dev.as<int>(), c->otab[3].count,
+               c->vtab[3].dev.as<int>(), c->vtab[3].count, c->t3d.d());
+}
+
+void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s) {
+  Launch L = c->L();
+  const int o = c->o, v = c->v;
+  ensure_eom_plans(c, var);
+  size_t sz[3];
+  eom_sizes(c, var, sz);
+  size_t off = 0;
+  Operands ops;
+  ops.f = c->fdr.d();
+  ops.v = c->gd.d();
+  ops.t2 = c->t2d.d();
+  ops.t3 = c->t3d.d();
+  const long long nn = c->n;
+  ops.f_size = nn * nn;
+  ops.v_size = nn * nn * nn * nn;
+  ops.t2_size = ipow(o, 2) * ipow(v, 2);
+  ops.t3_size = std::max<long long>(1, ipow(o, 3) * ipow(v, 3));
+  for (int k = 0; k < 3; ++k) {
+    int nh = kEom[var][k][0], np = kEom[var][k][1];
+    long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
+    c->rd[k].reserve(sizeof(double) * dn);
+    unpack_dense(L, x + off, nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count, c->vtab[np].dev.as<int>(),
+                 c->vtab[np].count, c->rd[k].d());
+    ops.r[k] = c->rd[k].d();
+    ops.r_size[k] = dn;
+    off += sz[k];
+  }
+  off = 0;
+  double flops = 0;
+  for (int oc = 0; oc < 3; ++oc) {
+    int nh = kEom[var][oc][0], np = kEom[var][oc][1];
+    long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
+    c->sy[oc].reserve(sizeof(double) * dn);
+    FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, c->stream));
+    for (int ic = 0; ic < 3; ++ic) {
+      c->eom_eq[var][oc][ic]->run(L, ops, c->sy[oc].d(), dn, c->scratch);
+      flops += c->eom_eq[var][oc][ic]->flops();
+    }
+    antisym_pack(L, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
+                 c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
+    off += sz[oc];
+  }
+  c->flops_sigma_last = flops;
+}
+
+// ---- small helpers on device vectors ---------------------------------------------
+
+double dot_dev(fnocc_ctx *c, long long n, const double *x, const double *y) {
+  c->small.reserve(sizeof(double) * 64);
+  multi_dot(c->L(), n, x, y, 0, 1, c->small.d(), c->red);
+  return to_host(c, c->small.d(), 1)[0];
+}
+
+void absmax_dev(fnocc_ctx *c, long long n, const double *x, double *amax, double *nrm) {
+  c->small.reserve(sizeof(double) * 64);
+  absmax_sumsq(c->L(), n, x, c->small.d(), c->red);
+  auto h = to_host(c, c->small.d(), 2);
+  *amax = h[0];
+  *nrm = std::sqrt(h[1]);
+}
+
+// y = sum_j coef[j] * X[j] (X rows of length n, ld = n)
+void combine_rows(fnocc_ctx *c, long long n, const double *X, int k, const std::vector<double> &coef, double *y,
+                  bool accumulate) {
+  if (k == 0) {
+    if (!accumulate) FNOCC_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, c->stream));
+    return;
+  }
+  c->small.reserve(sizeof(double) * std::max<size_t>(64, coef.size()));
+  FNOCC_CUDA(cudaMemcpyAsync(c->small.p, coef.data(), sizeof(double) * k, cudaMemcpyHostToDevice, c->stream));
+  MapSet ms;
+  DMap arow, acol, brow, bcol, crow, ccol;
+  ms.add(&arow, {{n, 1}});
+  ms.add(&acol, {{k, n}});
+  ms.add(&brow, {{k, 1}});
+  ms.add(&bcol, {{1, 0}});
+  ms.add(&crow, {{n, 1}});
+  ms.add(&ccol, {{1, 0}});
+  ms.upload();
+  if (!accumulate) FNOCC_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, c->stream));
+  gather_gemm(c->L(), n, 1, k, 1.0, X, arow, acol, c->small.d(), brow, bcol, y, crow, ccol, true, n * (long long)k,
+              (long long)k, n);
+  sync(c);  // MapSet and coefficients must outlive the launch
+}
+
+// ---- FNO setup --------------------------------------------------------------------
+
+// symmetric eigen-decomposition of a device n x n matrix; evecs columns sorted
+// ascending (descending if desc) with fixed phase; returns eigenvalues (host)
+std::vector<double> sym_eig(fnocc_ctx *c, const double *A, int n, double *V, bool desc = false) {
+  Launch L = c->L();
+  c->work.reserve(sizeof(double) * n * n);
+  c->evecs.reserve(sizeof(double) * n * n);
+  c->evals.reserve(sizeof(double) * n);
+  c->ints.reserve(sizeof(int) * std::max(n, 4));
+  FNOCC_CUDA(cudaMemcpyAsync(c->work.p, A, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream));
+  jacobi_eig(L, c->work.d(), n, c->evals.d(), c->evecs.d(), c->ints.as<int>());
+  auto ev = to_host(c, c->evals.d(), n);
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return desc ? ev[a] > ev[b] : ev[a] < ev[b]; });
+  FNOCC_CUDA(cudaMemcpyAsync(c->ints.p, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+  permute_columns(L, c->evecs.d(), n, n, c->ints.as<int>(), n, V);
+  fix_phase(L, V, n, n);
+  sync(c);
+  std::vector<double> out(n);
+  for (int i = 0; i < n; ++i) out[i] = ev[perm[i]];
+  return out;
+}
+
+// C = A(rows x k) * B(k x cols), all row-major with leading dims
+void matmul(fnocc_ctx *c, int rows, int cols, int k, const double *A, int lda, bool transA, const double *B, int ldb,
+            bool transB, double *C, int ldc, long long asz, long long bsz, long long csz) {
+  MapSet ms;
+  DMap arow, acol, brow, bcol, crow, ccol;
+  if (!transA) {
+    ms.add(&arow, {{rows, lda}});
+    ms.add(&acol, {{k, 1}});
+  } else {
+    ms.add(&arow, {{rows, 1}});
+    ms.add(&acol, {{k, lda}});
+  }
+  if (!transB) {
+    ms.add(&brow, {{k, ldb}});
+    ms.add(&bcol, {{cols, 1}});
+  } else {
+    ms.add(&brow, {{k, 1}});
+    ms.add(&bcol, {{cols, ldb}});
+  }
+  ms.add(&crow, {{rows, ldc}});
+  ms.add(&ccol, {{cols, 1}});
+  ms.upload();
+  gather_gemm(c->L(), rows, cols, k, 1.0, A, arow, acol, B, brow, bcol, C, crow, ccol, false, asz, bsz, csz);
+  sync(c);
+}
+
+// eri (n_in^4) -> out (n_out^4) with the same n_in x n_out matrix on all indices
+void transform4(fnocc_ctx *c, const double *eri, const double *C, int ni, int no, double *out) {
+  TransformPlan tp;
+  tp.build(ni, no);
+  size_t big = (size_t)std::max(ni, no);
+  big = big * big * big * big;
+  c->tmpA.reserve(sizeof(double) * big);
+  c->tmpB.reserve(sizeof(double) * big);
+  const double *src = eri;
+  double *dst[4] = {c->tmpA.d(), c->tmpB.d(), c->tmpA.d(), out};
+  for (int i = 0; i < 4; ++i) {
+    long long N = 1;
+    for (int k = 0; k < 4; ++k)
+      if (k != i) N *= (k < i ? no : ni);
+    const PassMaps &p = tp.pass[i];
+    long long ssz = ipow(no, i) * ipow(ni, 4 - i), dsz = ipow(no, i + 1) * ipow(ni, 3 - i);
+    gather_gemm(c->L(), no, N, ni, 1.0, C, p.arow, p.acol, src, p.brow, p.bcol, dst[i], p.crow, p.ccol, false,
+                (long long)ni * no, ssz, dsz);
+    src = dst[i];
+  }
+  sync(c);
+}
+
+void transform2(fnocc_ctx *c, const double *h, const double *C, int ni, int no, double *out) {
+  // out = C^T h C
+  c->tmph.reserve(sizeof(double) * ni * no);
+  const long long s1 = (long long)ni * no, s2 = (long long)ni * ni, s3 = (long long)no * no;
+  matmul(c, no, ni, ni, C, no, true, h, ni, false, c->tmph.d(), ni, s1, s2, s1);
+  matmul(c, no, no, ni, c->tmph.d(), ni, false, C, no, false, out, no, s1, s1, s3);
+}
+
+int choose_kept(const std::vector<double> &occ, double thr, int crit, int nkeep) {
+  int m = (int)occ.size();
+  int k;
+  if (nkeep > 0) {
+    k = std::min(nkeep, m);
+  } else if (crit == FNOCC_CRIT_ABS) {
+    k = 0;
+    for (double x : occ)
+      if (x >= thr) ++k;
+  } else {
+    double tot = 0;
+    for (double x : occ) tot += x;
+    if (tot <= 0) {
+      k = m;
+    } else {
+      double cum = 0;
+      k = m;
+      for (int i = 0; i < m; ++i) {
+        cum += occ[i];
+        if (cum / tot >= thr - 1e-15) {
+          k = i + 1;
+          break;
+        }
+      }
+    }
+  }
+  if (k > 0 && k < m && nkeep <= 0) {
+    double tol = 1e-10 * std::max(std::fabs(occ[0]), 1e-300);
+    while (k < m && std::fabs(occ[k] - occ[k - 1]) <= tol) ++k;
+  }
+  return k;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+fnocc_status fnocc_create(fnocc_ctx **out, int device, void *cuda_stream) {
+  if (!out) return FNOCC_E_INVALID;
+  *out = nullptr;
+  fnocc_ctx *c = new (std::nothrow) fnocc_ctx();
+  if (!c) return FNOCC_E_NOMEM;
+  fnocc_status st = guarded(c, [&]() -> fnocc_status {
+    int ndev = 0;
+    FNOCC_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) throw StatusError(FNOCC_E_INVALID, "invalid device index");
+    FNOCC_CUDA(cudaSetDevice(device));
+    c->device = device;
+    if (cuda_stream) {
+      c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      FNOCC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    return FNOCC_OK;
+  });
+  if (st != FNOCC_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return FNOCC_OK;
+}
+
+void fnocc_destroy(fnocc_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  bool own = c->own_stream;
+  cudaStream_t s = c->stream;
+  delete c;
+  if (own && s) cudaStreamDestroy(s);
+}
+
+const char *fnocc_last_error(const fnocc_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+uint64_t fnocc_launch_count(const fnocc_ctx *c) { return c ? c->launches : 0; }
+
+fnocc_status fnocc_set_mo_hamiltonian(fnocc_ctx *c, const double *h_mo, const double *eri_mo, int n, int nocc) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (!h_mo || !eri_mo || n <= 0 || nocc <= 0 || nocc >= n || n > 64)
+      throw StatusError(FNOCC_E_INVALID, "invalid Hamiltonian dimensions");
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    size_t n4 = (size_t)n * n * n * n;
+    to_dev(c, c->h_act, h_mo, (size_t)n * n);
+    to_dev(c, c->eri_act, eri_mo, n4);
+    int ns = 2 * n;
+    c->hso.reserve(sizeof(double) * ns * ns);
+    c->gso.reserve(sizeof(double) * (size_t)ns * ns * ns * ns);
+    spin_orbital_h(c->L(), c->h_act.d(), n, c->hso.d());
+    spin_orbital_eri(c->L(), c->eri_act.d(), n, c->gso.d());
+    install_hamiltonian(c, nocc, n);
+    sync(c);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status fnocc_dims(const fnocc_ctx *c, int *o, int *v, double *e_ref) {
+  if (!c) return FNOCC_E_INVALID;
+  if (!c->have_ham) return FNOCC_E_STATE;
+  if (o) *o = c->o;
+  if (v) *v = c->v;
+  if (e_ref) *e_ref = c->e_ref;
+  return FNOCC_OK;
+}
+
+fnocc_status fno_truncate(fnocc_ctx *c, const double *h, const double *eri, int n, int nocc, double thr,
+                          const fno_options *opt, fno_info *out, double *occ_out) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (!h || !eri || n <= 1 || nocc <= 0 || nocc >= n || n > 128) throw StatusError(FNOCC_E_INVALID, "invalid dimensions");
+    if (!(thr >= 0.0) || !std::isfinite(thr)) throw StatusError(FNOCC_E_INVALID, "invalid threshold");
+    fno_options o;
+    o.criterion = FNOCC_CRIT_ABS;
+    o.nkeep = 0;
+    o.scf_maxiter = 200;
+    o.scf_e_tol = 1e-12;
+    o.scf_comm_tol = 1e-10;
+    if (opt) o = *opt;
+    if (o.scf_maxiter <= 0) o.scf_maxiter = 200;
+    if (o.scf_e_tol <= 0) o.scf_e_tol = 1e-12;
+    if (o.scf_comm_tol <= 0) o.scf_comm_tol = 1e-10;
+    if (o.criterion != FNOCC_CRIT_ABS && o.criterion != FNOCC_CRIT_OCCT) throw StatusError(FNOCC_E_INVALID, "bad criterion");
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    Launch L = c->L();
+    const size_t n2 = (size_t)n * n, n4 = n2 * n2;
+    to_dev(c, c->h_ao, h, n2);
+    to_dev(c, c->eri_ao, eri, n4);
+    c->c_mo.reserve(sizeof(double) * n2);
+    c->dens.reserve(sizeof(double) * n2);
+    c->fock.reserve(sizeof(double) * n2);
+    c->jmat.reserve(sizeof(double) * n2);
+    c->kmat.reserve(sizeof(double) * n2);
+    c->ctmp.reserve(sizeof(double) * n2);
+    const int maxd = 8;
+    c->diis_f.reserve(sizeof(double) * n2 * maxd);
+    c->diis_e.reserve(sizeof(double) * n2 * maxd);
+    // Fock-build maps
+    MapSet ms;
+    DMap j_arow, j_acol, j_brow, j_bcol, j_crow, j_ccol, k_arow, k_acol, k_brow, k_bcol;
+    ms.add(&j_arow, {{(long long)n2, (long long)n2}});
+    ms.add(&j_acol, {{(long long)n2, 1}});
+    ms.add(&j_brow, {{(long long)n2, 1}});
+    ms.add(&j_bcol, {{1, 0}});
+    ms.add(&j_crow, {{(long long)n2, 1}});
+    ms.add(&j_ccol, {{1, 0}});
+    ms.add(&k_arow, {{n, (long long)n2 * n}, {n, n}});
+    ms.add(&k_acol, {{n, (long long)n2}, {n, 1}});
+    ms.add(&k_brow, {{n, n}, {n, 1}});
+    ms.add(&k_bcol, {{1, 0}});
+    ms.upload();
+    // initial guess: core Hamiltonian
+    std::vector<double> eps = sym_eig(c, c->h_ao.d(), n, c->c_mo.d());
+    auto build_density = [&]() {
+      matmul(c, n, n, nocc, c->c_mo.d(), n, false, c->c_mo.d(), n, true, c->dens.d(), n, (long long)n2, (long long)n2,
+             (long long)n2);
+    };
+    build_density();
+    std::vector<double> diis_b(maxd * maxd, 0.0);
+    int nd = 0, head = 0;
+    double e_old = 0, e = 0;
+    int it;
+    bool conv = false;
+    for (it = 1; it <= o.scf_maxiter; ++it) {
+      gather_gemm(L, n2, 1, n2, 1.0, c->eri_ao.d(), j_arow, j_acol, c->dens.d(), j_brow, j_bcol, c->jmat.d(), j_crow,
+                  j_ccol, false, (long long)n4, (long long)n2, (long long)n2);
+      gather_gemm(L, n2, 1, n2, 1.0, c->eri_ao.d(), k_arow, k_acol, c->dens.d(), k_brow, k_bcol, c->kmat.d(), j_crow,
+                  j_ccol, false, (long long)n4, (long long)n2, (long long)n2);
+      lincomb3(L, n2, c->fock.d(), c->h_ao.d(), 2.0, c->jmat.d(), -1.0, c->kmat.d());
+      lincomb3(L, n2, c->ctmp.d(), c->h_ao.d(), 1.0, c->fock.d(), 0.0, c->fock.d());
+      e = dot_dev(c, n2, c->dens.d(), c->ctmp.d());
+      // error FD - DF into the DIIS slot
+      double *ef = c->diis_e.d() + (size_t)head * n2;
+      double *ff = c->diis_f.d() + (size_t)head * n2;
+      matmul(c, n, n, n, c->fock.d(), n, false, c->dens.d(), n, false, ef, n, n2, n2, n2);
+      matmul(c, n, n, n, c->dens.d(), n, false, c->fock.d(), n, false, c->ctmp.d(), n, n2, n2, n2);
+      axpby(L, n2, -1.0, c->ctmp.d(), 1.0, ef);
+      FNOCC_CUDA(cudaMemcpyAsync(ff, c->fock.d(), sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+      double emax, enrm;
+      absmax_dev(c, n2, ef, &emax, &enrm);
+      if (!std::isfinite(e) || !std::isfinite(emax)) throw StatusError(FNOCC_E_NUMERIC, "NaN in SCF");
+      if (std::fabs(e - e_old) < o.scf_e_tol && emax < o.scf_comm_tol) {
+        conv = true;
+        break;
+      }
+      e_old = e;
+      // DIIS bookkeeping (ring buffer of maxd)
+      if (nd < maxd) ++nd;
+      std::vector<double> dots(maxd);
+      c->small.reserve(sizeof(double) * 64);
+      multi_dot(L, n2, ef, c->diis_e.d(), n2, nd, c->small.d(), c->red);
+      dots = to_host(c, c->small.d(), nd);
+      for (int j = 0; j < nd; ++j) {
+        diis_b[head * maxd + j] = dots[j];
+        diis_b[j * maxd + head] = dots[j];
+      }
+      head = (head + 1) % maxd;
+      double *use = c->fock.d();
+      if (nd >= 2) {
+        int m = nd;
+        std::vector<double> B((m + 1) * (m + 1), 0.0), rhs(m + 1, 0.0), x;
+        for (int a = 0; a < m; ++a)
+          for (int b = 0; b < m; ++b) B[a * (m + 1) + b] = diis_b[a * maxd + b];
+        for (int a = 0; a < m; ++a) B[a * (m + 1) + m] = B[m * (m + 1) + a] = -1.0;
+        rhs[m] = -1.0;
+        if (solve_linear(m + 1, B, rhs, x)) {
+          std::vector<double> coef(x.begin(), x.begin() + m);
+          combine_rows(c, n2, c->diis_f.d(), m, coef, c->ctmp.d(), false);
+          use = c->ctmp.d();
+        }
+      }
+      eps = sym_eig(c, use, n, c->c_mo.d());
+      build_density();
+    }
+    if (!conv) throw StatusError(FNOCC_E_NUMERIC, "RHF did not converge");
+    // canonical orbitals of the converged Fock matrix
+    eps = sym_eig(c, c->fock.d(), n, c->c_mo.d());
+    const double e_rhf = e;
+    const int nvir = n - nocc;
+    // MO integrals over the full space
+    c->work.reserve(sizeof(double) * n4);
+    DevBuf eri_mo;
+    eri_mo.reserve(sizeof(double) * n4);
+    transform4(c, c->eri_ao.d(), c->c_mo.d(), n, n, eri_mo.d());
+    // spin-orbital MP2 amplitudes over the full space (Eq. 8-9)
+    const int ns = 2 * n, so = 2 * nocc, sv = 2 * nvir;
+    DevBuf gfull, hfull, ffull, fdfull, hmo;
+    gfull.reserve(sizeof(double) * (size_t)ns * ns * ns * ns);
+    spin_orbital_eri(L, eri_mo.d(), n, gfull.d());
+    hmo.reserve(sizeof(double) * n2);
+    transform2(c, c->h_ao.d(), c->c_mo.d(), n, n, hmo.d());
+    hfull.reserve(sizeof(double) * ns * ns);
+    spin_orbital_h(L, hmo.d(), n, hfull.d());
+    ffull.reserve(sizeof(double) * ns * ns);
+    normal_order(L, hfull.d(), gfull.d(), ns, so, ffull.d(), nullptr);
+    fdfull.reserve(sizeof(double) * ns);
+    diag_of(L, ffull.d(), ns, fdfull.d());
+    size_t t2n = (size_t)so * so * sv * sv;
+    c->t2full.reserve(sizeof(double) * std::max<size_t>(t2n, 1));
+    mp2_amplitudes(L, gfull.d(), fdfull.d(), ns, so, c->t2full.d());
+    // E_MP2 = 1/4 sum <ij||ab> t_ij^ab, <ij||ab> read from gfull through maps
+    {
+      MapSet em;
+      DMap arow, acol, brow, bcol, crow, ccol;
+      const long long s3 = (long long)ns * ns * ns, s2 = (long long)ns * ns;
+      em.add(&arow, {{1, 0}});
+      em.add(&acol, {{so, (long long)so * sv * sv}, {so, (long long)sv * sv}, {sv, sv}, {sv, 1}});
+      em.add(&brow, {{so, s3}, {so, s2}, {sv, ns}, {sv, 1}});
+      em.add(&bcol, {{1, 0}});
+      em.add(&crow, {{1, 0}});
+      em.add(&ccol, {{1, 0}});
+      em.upload();
+      // B must point at g[0,0,o,o] for the (i,j,a,b) -> <ij||ab> block
+      c->small.reserve(sizeof(double) * 64);
+      const long long gsz = (long long)ns * ns * ns * ns - ((long long)so * ns + so);
+      gather_gemm(L, 1, 1, t2n, 0.25, c->t2full.d(), arow, acol, gfull.d() + (size_t)so * ns + so, brow, bcol,
+                  c->small.d(), crow, ccol, false, (long long)t2n, gsz, 64);
+      sync(c);
+    }
+    const double e_mp2 = to_host(c, c->small.d(), 1)[0];
+    // D_ab = 1/2 sum_ijc t_ij^cb t_ij^ca  (Eq. 10), spin-orbital v x v, then alpha block
+    c->dvv.reserve(sizeof(double) * sv * sv);
+    {
+      MapSet dm;
+      DMap arow, acol, brow, bcol, crow, ccol;
+      dm.add(&arow, {{sv, 1}});
+      dm.add(&acol, {{so, (long long)so * sv * sv}, {so, (long long)sv * sv}, {sv, sv}});
+      dm.add(&brow, {{so, (long long)so * sv * sv}, {so, (long long)sv * sv}, {sv, sv}});
+      dm.add(&bcol, {{sv, 1}});
+      dm.add(&crow, {{sv, sv}});
+      dm.add(&ccol, {{sv, 1}});
+      dm.upload();
+      gather_gemm(L, sv, sv, (long long)so * so * sv, 0.5, c->t2full.d(), arow, acol, c->t2full.d(), brow, bcol,
+                  c->dvv.d(), crow, ccol, false, (long long)t2n, (long long)t2n, (long long)sv * sv);
+      sync(c);
+    }
+    DevBuf dsp, uno;
+    dsp.reserve(sizeof(double) * nvir * nvir);
+    alpha_block(L, c->dvv.d(), sv, dsp.d());
+    uno.reserve(sizeof(double) * nvir * nvir);
+    std::vector<double> occ = sym_eig(c, dsp.d(), nvir, uno.d(), true);
+    int k = choose_kept(occ, thr, o.criterion, o.nkeep);
+    double tot = 0, kept = 0;
+    for (int i = 0; i < nvir; ++i) {
+      tot += occ[i];
+      if (i < k) kept += occ[i];
+    }
+    const double frac = tot > 0 ? kept / tot : 1.0;
+    // semicanonicalise: F_vv in the kept NO basis, diagonalised
+    int nact = nocc + k;
+    c->c_act.reserve(sizeof(double) * n * nact);
+    if (k > 0) {
+      DevBuf evir, fno_, w, uw, tmp;
+      std::vector<double> dg(nvir * nvir, 0.0);
+      for (int a = 0; a < nvir; ++a) dg[a * nvir + a] = eps[nocc + a];
+      to_dev(c, evir, dg.data(), dg.size());
+      tmp.reserve(sizeof(double) * nvir * k);
+      fno_.reserve(sizeof(double) * k * k);
+      // tmp = diag(eps_v) U_k ; F_no = U_k^T tmp
+      DevBuf uk;
+      uk.reserve(sizeof(double) * nvir * k);
+      FNOCC_CUDA(cudaMemcpy2DAsync(uk.p, sizeof(double) * k, uno.p, sizeof(double) * nvir, sizeof(double) * k, nvir,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+      const long long nvk = (long long)nvir * k;
+      matmul(c, nvir, k, nvir, evir.d(), nvir, false, uk.d(), k, false, tmp.d(), k, (long long)nvir * nvir, nvk, nvk);
+      matmul(c, k, k, nvir, uk.d(), k, true, tmp.d(), k, false, fno_.d(), k, nvk, nvk, (long long)k * k);
+      w.reserve(sizeof(double) * k * k);
+      sym_eig(c, fno_.d(), k, w.d());
+      uw.reserve(sizeof(double) * nvir * k);
+      matmul(c, nvir, k, k, uk.d(), k, false, w.d(), k, false, uw.d(), k, nvk, (long long)k * k, nvk);
+      // C_vir_new = C[:, nocc:] * UW
+      DevBuf cv;
+      cv.reserve(sizeof(double) * n * k);
+      matmul(c, n, k, nvir, c->c_mo.d() + nocc, n, false, uw.d(), k, false, cv.d(), k, (long long)n2 - nocc, nvk,
+             (long long)n * k);
+      fix_phase(L, cv.d(), n, k);
+      FNOCC_CUDA(cudaMemcpy2DAsync(c->c_act.d() + nocc, sizeof(double) * nact, cv.p, sizeof(double) * k,
+                                   sizeof(double) * k, n, cudaMemcpyDeviceToDevice, c->stream));
+      sync(c);
+    }
+    FNOCC_CUDA(cudaMemcpy2DAsync(c->c_act.p, sizeof(double) * nact, c->c_mo.p, sizeof(double) * n,
+                                 sizeof(double) * nocc, n, cudaMemcpyDeviceToDevice, c->stream));
+    // active-space integrals
+    c->eri_act.reserve(sizeof(double) * (size_t)nact * nact * nact * nact);
+    transform4(c, c->eri_ao.d(), c->c_act.d(), n, nact, c->eri_act.d());
+    c->h_act.reserve(sizeof(double) * nact * nact);
+    transform2(c, c->h_ao.d(), c->c_act.d(), n, nact, c->h_act.d());
+    const int nsa = 2 * nact;
+    c->hso.reserve(sizeof(double) * nsa * nsa);
+    c->gso.reserve(sizeof(double) * (size_t)nsa * nsa * nsa * nsa);
+    spin_orbital_h(L, c->h_act.d(), nact, c->hso.d());
+    spin_orbital_eri(L, c->eri_act.d(), nact, c->gso.d());
+    install_hamiltonian(c, nocc, nact);
+    sync(c);
+    if (out) {
+      out->e_rhf = e_rhf;
+      out->e_mp2 = e_mp2;
+      out->nkept = k;
+      out->nvir = nvir;
+      out->kept_fraction = frac;
+      out->scf_iters = it;
+    }
+    if (occ_out) std::memcpy(occ_out, occ.data(), sizeof(double) * nvir);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status fnocc_set_amplitudes(fnocc_ctx *c, const double *t1, const double *t2, const double *t3) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    require_ham(c);
+    if (!t1 || !t2 || (!t3 && c->nt[3] > 0)) throw StatusError(FNOCC_E_INVALID, "null amplitude pointer");
+    size_t tot = c->nt[1] + c->nt[2] + c->nt[3];
+    c->tpk.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    FNOCC_CUDA(cudaMemcpyAsync(c->tpk.d(), t1, sizeof(double) * c->nt[1], cudaMemcpyHostToDevice, c->stream));
+    FNOCC_CUDA(cudaMemcpyAsync(c->tpk.d() + c->nt[1], t2, sizeof(double) * c->nt[2], cudaMemcpyHostToDevice, c->stream));
+    if (c->nt[3])
+      FNOCC_CUDA(cudaMemcpyAsync(c->tpk.d() + c->nt[1] + c->nt[2], t3, sizeof(double) * c->nt[3], cudaMemcpyHostToDevice,
+                                 c->stream));
+    sync(c);
+    c->have_amps = true;
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status ccsdt_residual_dev(fnocc_ctx *c, const double *t1, const double *t2, const double *t3, double *r1,
+                                double *r2, double *r3, double *e_corr) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    require_ham(c);
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    size_t tot = c->nt[1] + c->nt[2] + c->nt[3];
+    c->tpk.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    c->rpk.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    auto cp = [&](double *dst, const double *src, size_t n) {
+      if (n) FNOCC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    };
+    DevBuf tin;
+    tin.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    cp(tin.d(), t1, c->nt[1]);
+    cp(tin.d() + c->nt[1], t2, c->nt[2]);
+    cp(tin.d() + c->nt[1] + c->nt[2], t3, c->nt[3]);
+    double e = cc_residual_dev(c, tin.d(), c->rpk.d());
+    cp(r1, c->rpk.d(), c->nt[1]);
+    cp(r2, c->rpk.d() + c->nt[1], c->nt[2]);
+    cp(r3, c->rpk.d() + c->nt[1] + c->nt[2], c->nt[3]);
+    sync(c);
+    if (e_corr) *e_corr = e;
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status ccsdt_residual(fnocc_ctx *c, const double *t1, const double *t2, const double *t3, double *r1, double *r2,
+                            double *r3, double *e_corr) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    require_ham(c);
+    if (!t1 || !t2 || !r1 || !r2 || (c->nt[3] && (!t3 || !r3))) throw StatusError(FNOCC_E_INVALID, "null pointer");
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    size_t tot = c->nt[1] + c->nt[2] + c->nt[3];
+    DevBuf tin, rout;
+    tin.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    rout.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    FNOCC_CUDA(cudaMemcpyAsync(tin.d(), t1, sizeof(double) * c->nt[1], cudaMemcpyHostToDevice, c->stream));
+    FNOCC_CUDA(cudaMemcpyAsync(tin.d() + c->nt[1], t2, sizeof(double) * c->nt[2], cudaMemcpyHostToDevice, c->stream));
+    if (c->nt[3])
+      FNOCC_CUDA(cudaMemcpyAsync(tin.d() + c->nt[1] + c->nt[2], t3, sizeof(double) * c->nt[3], cudaMemcpyHostToDevice,
+                                 c->stream));
+    double e = cc_residual_dev(c, tin.d(), rout.d());
+    FNOCC_CUDA(cudaMemcpyAsync(r1, rout.d(), sizeof(double) * c->nt[1], cudaMemcpyDeviceToHost, c->stream));
+    FNOCC_CUDA(cudaMemcpyAsync(r2, rout.d() + c->nt[1], sizeof(double) * c->nt[2], cudaMemcpyDeviceToHost, c->stream));
+    if (c->nt[3])
+      FNOCC_CUDA(cudaMemcpyAsync(r3, rout.d() + c->nt[1] + c->nt[2], sizeof(double) * c->nt[3], cudaMemcpyDeviceToHost,
+                                 c->stream));
+    sync(c);
+    if (e_corr) *e_corr = e;
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    require_ham(c);
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    Timer timer;
+    ccsdt_options o{1e-10, 1e-12, 200, 8};
+    if (opt) o = *opt;
+    if (o.tol_res <= 0) o.tol_res = 1e-10;
+    if (o.tol_e <= 0) o.tol_e = 1e-12;
+    if (o.maxiter <= 0) o.maxiter = 200;
+    if (o.diis < 0) o.diis = 0;
+    if (o.diis > 16) o.diis = 16;
+    Launch L = c->L();
+    const int oo = c->o, vv = c->v;
+    const size_t n1 = c->nt[1], n2 = c->nt[2], n3 = c->nt[3], tot = n1 + n2 + n3;
+    c->tpk.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    c->rpk.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    c->den.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    // denominators
+    for (int r = 1; r <= 3; ++r) {
+      size_t off = (r >= 2 ? n1 : 0) + (r >= 3 ? n2 : 0);
+      cc_denominators(L, c->fdiag.d(), oo, r, c->otab[r].dev.as<int>(), c->otab[r].count, c->vtab[r].dev.as<int>(),
+                      c->vtab[r].count, c->den.d() + off);
+    }
+    // T1 = 0, T2 = MP2 (packed), T3 = 0
+    FNOCC_CUDA(cudaMemsetAsync(c->tpk.p, 0, sizeof(double) * tot, c->stream));
+    {
+      DevBuf t2dense;
+      t2dense.reserve(sizeof(double) * (size_t)oo * oo * vv * vv);
+      mp2_amplitudes(L, c->gso.d(), c->fdiag.d(), c->n, oo, t2dense.d());
+      antisym_pack(L, t2dense.d(), 2, 2, oo, vv, c->otab[2].dev.as<int>(), c->otab[2].count, c->vtab[2].dev.as<int>(),
+                   c->vtab[2].count, c->tpk.d() + n1, 0.25, false);
+      sync(c);
+    }
+    const int md = o.diis;
+    DevBuf hv, he;
+    if (md > 0) {
+      hv.reserve(sizeof(double) * tot * md);
+      he.reserve(sizeof(double) * tot * md);
+    }
+    std::vector<double> bmat(md * md, 0.0);
+    int nd = 0, head = 0;
+    double e_old = 0, e = 0, rmax = 0, rn = 0;
+    bool conv = false;
+    int it;
+    for (it = 1; it <= o.maxiter; ++it) {
+      e = cc_residual_dev(c, c->tpk.d(), c->rpk.d());
+      absmax_dev(c, tot, c->rpk.d(), &rmax, &rn);
+      if (!std::isfinite(e) || !std::isfinite(rmax)) throw StatusError(FNOCC_E_NUMERIC, "NaN/Inf in CCSDT iterations");
+      if (it > 1 && rmax < o.tol_res && std::fabs(e - e_old) < o.tol_e) {
+        conv = true;
+        break;
+      }
+      e_old = e;
+      // Jacobi step, error = R / D
+      jacobi_update(L, tot, c->rpk.d(), c->den.d(), c->tpk.d());
+      if (md > 0) {
+        double *ev = he.d() + (size_t)head * tot;
+        double *tv = hv.d() + (size_t)head * tot;
+        FNOCC_CUDA(cudaMemsetAsync(ev, 0, sizeof(double) * tot, c->stream));
+        jacobi_update(L, tot, c->rpk.d(), c->den.d(), ev);
+        FNOCC_CUDA(cudaMemcpyAsync(tv, c->tpk.d(), sizeof(double) * tot, cudaMemcpyDeviceToDevice, c->stream));
+        if (nd < md) ++nd;
+        c->small.reserve(sizeof(double) * 64);
+        multi_dot(L, tot, ev, he.d(), tot, nd, c->small.d(), c->red);
+        auto dots = to_host(c, c->small.d(), nd);
+        for (int j = 0; j < nd; ++j) {
+          bmat[head * md + j] = dots[j];
+          bmat[j * md + head] = dots[j];
+        }
+        head = (head + 1) % md;
+        if (nd >= 2) {
+          int m = nd;
+          std::vector<double> B((m + 1) * (m + 1), 0.0), rhs(m + 1, 0.0), x;
+          for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b) B[a * (m + 1) + b] = bmat[a * md + b];
+          for (int a = 0; a < m; ++a) B[a * (m + 1) + m] = B[m * (m + 1) + a] = -1.0;
+          rhs[m] = -1.0;
+          if (solve_linear(m + 1, B, rhs, x)) {
+            std::vector<double> coef(x.begin(), x.begin() + m);
+            combine_rows(c, tot, hv.d(), m, coef, c->tpk.d(), false);
+          }
+        }
+      }
+    }
+    c->have_amps = true;
+    c->e_corr = e;
+    double secs = timer.s();
+    if (out) {
+      out->e_corr = e;
+      out->e_tot = c->e_ref + e;
+      out->iters = conv ? it : o.maxiter;
+      out->res_max = rmax;
+      out->seconds = secs;
+      out->seconds_per_iter = secs / std::max(1, conv ? it : o.maxiter);
+    }
+    return conv ? FNOCC_OK : FNOCC_NOT_CONVERGED;
+  });
+}
+
+fnocc_status fnocc_eom_sizes(const fnocc_ctx *c, int variant, size_t *sizes) {
+  if (!c || !sizes || variant < 0 || variant > 3) return FNOCC_E_INVALID;
+  if (!c->have_ham) return FNOCC_E_STATE;
+  eom_sizes(c, variant, sizes);
+  return FNOCC_OK;
+}
+
+fnocc_status eom_sigma_dev(fnocc_ctx *c, int variant, const double *r, double *s) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    require_ham(c);
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    prepare_hbar(c);
+    sigma_dev(c, variant, r, s);
+    sync(c);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status eom_sigma(fnocc_ctx *c, int variant, const double *r, double *s) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (variant < 0 || variant > 3 || !r || !s) throw StatusError(FNOCC_E_INVALID, "bad argument");
+    require_ham(c);
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    size_t sz[3];
+    eom_sizes(c, variant, sz);
+    size_t dim = sz[0] + sz[1] + sz[2];
+    DevBuf x, y;
+    x.reserve(sizeof(double) * dim);
+    y.reserve(sizeof(double) * dim);
+    FNOCC_CUDA(cudaMemcpyAsync(x.p, r, sizeof(double) * dim, cudaMemcpyHostToDevice, c->stream));
+    prepare_hbar(c);
+    sigma_dev(c, variant, x.d(), y.d());
+    FNOCC_CUDA(cudaMemcpyAsync(s, y.p, sizeof(double) * dim, cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, const eom_options *opt,
+                             double *energies, double *omegas, eom_info *out) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    if (nroots <= 0 || !energies) throw StatusError(FNOCC_E_INVALID, "bad nroots or null energies");
+    if (guess != FNOCC_GUESS_KOOPMANS && guess != FNOCC_GUESS_DIAGONAL) throw StatusError(FNOCC_E_INVALID, "bad guess");
+    require_ham(c);
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    Timer timer;
+    eom_options o{1e-8, 1e-10, 0, 200, 0};
+    if (opt) o = *opt;
+    if (o.tol_res <= 0) o.tol_res = 1e-8;
+    if (o.tol_e <= 0) o.tol_e = 1e-10;
+    if (o.maxiter <= 0) o.maxiter = 200;
+    Launch L = c->L();
+    prepare_hbar(c);
+    size_t sz[3];
+    eom_sizes(c, variant, sz);
+    const long long dim = (long long)(sz[0] + sz[1] + sz[2]);
+    // diagonal estimate and sector mask
+    DevBuf dg, mk;
+    dg.reserve(sizeof(double) * dim);
+    mk.reserve(dim);
+    size_t off = 0;
+    for (int k = 0; k < 3; ++k) {
+      int nh = kEom[variant][k][0], np = kEom[variant][k][1];
+      eom_diag(L, c->fdiag.d(), c->o, nh, np, c->otab[nh].dev.as<int>(), c->otab[nh].count, c->vtab[np].dev.as<int>(),
+               c->vtab[np].count, dg.d() + off);
+      ms_mask(L, nh, np, c->otab[nh].dev.as<int>(), c->otab[nh].count, c->vtab[np].dev.as<int>(), c->vtab[np].count,
+              kSectorMs2[variant], mk.as<unsigned char>() + off);
+      off += sz[k];
+    }
+    auto dgh = to_host(c, dg.d(), dim);
+    std::vector<unsigned char> mkh(dim);
+    FNOCC_CUDA(cudaMemcpy(mkh.data(), mk.p, dim, cudaMemcpyDeviceToHost));
+    std::vector<long long> allowed, pref;
+    for (long long i = 0; i < dim; ++i)
+      if (mkh[i]) {
+        allowed.push_back(i);
+        if (guess == FNOCC_GUESS_DIAGONAL || i < (long long)sz[0]) pref.push_back(i);
+      }
+    if (allowed.empty()) throw StatusError(FNOCC_E_INVALID, "empty spin sector");
+    int nr = std::min<long long>(nroots, (long long)allowed.size());
+    int ng = o.nguess > 0 ? o.nguess : nr;
+    ng = std::min<long long>(ng, (long long)allowed.size());
+    int max_sub = o.max_sub > 0 ? o.max_sub : std::max(4 * nr, ng + 2 * nr);
+    if (max_sub < ng + nr) max_sub = ng + nr;
+    auto by_diag = [&](long long a, long long b) { return dgh[a] < dgh[b] || (dgh[a] == dgh[b] && a < b); };
+    std::stable_sort(pref.begin(), pref.end(), by_diag);
+    std::vector<long long> rest;
+    {
+      std::vector<unsigned char> inpref(dim, 0);
+      for (auto i : pref) inpref[i] = 1;
+      for (auto i : allowed)
+        if (!inpref[i]) rest.push_back(i);
+      std::stable_sort(rest.begin(), rest.end(), by_diag);
+    }
+    std::vector<long long> order(pref);
+    order.insert(order.end(), rest.begin(), rest.end());
+    order.resize(ng);
+    // subspace storage
+    const int cap = max_sub + nr + 1;
+    DevBuf Vb, Sb, xr, rr, tmp;
+    Vb.reserve(sizeof(double) * dim * cap);
+    Sb.reserve(sizeof(double) * dim * cap);
+    xr.reserve(sizeof(double) * dim * nr);
+    rr.reserve(sizeof(double) * dim * nr);
+    tmp.reserve(sizeof(double) * dim);
+    const unsigned char *mask = mk.as<unsigned char>();
+    int kb = 0, sigma_calls = 0;
+    std::vector<double> G;  // kb x kb, row-major, G[i][j] = V_i . S_j
+    auto vrow = [&](int i) { return Vb.d() + (size_t)i * dim; };
+    auto srow = [&](int i) { return Sb.d() + (size_t)i * dim; };
+    auto add_vector = [&](const double *src) -> bool {
+      // orthonormalise src against the basis (twice), append V and sigma(V)
+      double *dst = vrow(kb);
+      FNOCC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
+      scale_mask(L, dim, dst, mask);
+      for (int pass = 0; pass < 2 && kb > 0; ++pass) {
+        c->small.reserve(sizeof(double) * std::max(64, kb));
+        multi_dot(L, dim, dst, Vb.d(), dim, kb, c->small.d(), c->red);
+        auto d = to_host(c, c->small.d(), kb);
+        for (auto &x : d) x = -x;
+        combine_rows(c, dim, Vb.d(), kb, d, dst, true);
+      }
+      double amax, nrm;
+      absmax_dev(c, dim, dst, &amax, &nrm);
+      if (!(nrm > 1e-10)) return false;
+      axpby(L, dim, 0.0, dst, 1.0 / nrm, dst);
+      sigma_dev(c, variant, dst, srow(kb));
+      scale_mask(L, dim, srow(kb), mask);
+      ++sigma_calls;
+      // extend G
+      int k1 = kb + 1;
+      std::vector<double> Gn((size_t)k1 * k1, 0.0);
+      for (int i = 0; i < kb; ++i)
+        for (int j = 0; j < kb; ++j) Gn[i * k1 + j] = G[i * kb + j];
+      c->small.reserve(sizeof(double) * std::max(64, k1));
+      multi_dot(L, dim, srow(kb), Vb.d(), dim, k1, c->small.d(), c->red);  // V_i . S_new
+      auto col = to_host(c, c->small.d(), k1);
+      for (int i = 0; i < k1; ++i) Gn[i * k1 + kb] = col[i];
+      if (kb > 0) {
+        multi_dot(L, dim, vrow(kb), Sb.d(), dim, kb, c->small.d(), c->red);  // V_new . S_j
+        auto row = to_host(c, c->small.d(), kb);
+        for (int j = 0; j < kb; ++j) Gn[kb * k1 + j] = row[j];
+      }
+      G.swap(Gn);
+      kb = k1;
+      return true;
+    };
+    for (long long idx : order) {
+      FNOCC_CUDA(cudaMemsetAsync(tmp.p, 0, sizeof(double) * dim, c->stream));
+      double one = 1.0;
+      FNOCC_CUDA(cudaMemcpyAsync(tmp.d() + idx, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      sync(c);
+      add_vector(tmp.d());
+    }
+    std::vector<double> theta(nr, 0.0), theta_old(nr, 0.0), norms(nr, 0.0);
+    bool have_old = false, conv = false;
+    int it, ncomplex = 0;
+    for (it = 1; it <= o.maxiter; ++it) {
+      std::vector<std::complex<double>> w, Y;
+      eig_nonsym(kb, G, w, Y);
+      std::vector<int> idx(kb);
+      std::iota(idx.begin(), idx.end(), 0);
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a].real() < w[b].real(); });
+      ncomplex = 0;
+      std::vector<std::vector<double>> ys(nr);
+      for (int r = 0; r < nr; ++r) {
+        int j = idx[r];
+        theta[r] = w[j].real();
+        if (std::fabs(w[j].imag()) > 1e-8) ++ncomplex;
+        std::vector<double> y(kb);
+        for (int i = 0; i < kb; ++i) y[i] = Y[(size_t)i * kb + j].real();
+        // normalise the Ritz vector: basis is orthonormal, so |x| = |y|
+        double nn = 0;
+        for (double a : y) nn += a * a;
+        nn = std::sqrt(nn);
+        if (nn == 0) nn = 1;
+        for (double &a : y) a /= nn;
+        ys[r] = y;
+        double *x = xr.d() + (size_t)r * dim;
+        double *res = rr.d() + (size_t)r * dim;
+        combine_rows(c, dim, Vb.d(), kb, y, x, false);
+        combine_rows(c, dim, Sb.d(), kb, y, res, false);
+        axpby(L, dim, -theta[r], x, 1.0, res);
+        double amax, nrm;
+        absmax_dev(c, dim, res, &amax, &nrm);
+        if (!std::isfinite(nrm)) throw StatusError(FNOCC_E_NUMERIC, "NaN in Davidson residual");
+        norms[r] = nrm;
+      }
+      std::vector<bool> done(nr);
+      bool all = true;
+      for (int r = 0; r < nr; ++r) {
+        done[r] = norms[r] < o.tol_res && have_old && std::fabs(theta[r] - theta_old[r]) < o.tol_e;
+        all = all && done[r];
+      }
+      if (all) {
+        conv = true;
+        break;
+      }
+      theta_old = theta;
+      have_old = true;
+      int nnew = 0;
+      for (int r = 0; r < nr; ++r)
+        if (!done[r]) ++nnew;
+      if (kb + nnew > max_sub) {
+        // collapse onto the current Ritz vectors
+        DevBuf keep;
+        keep.reserve(sizeof(double) * dim * nr);
+        FNOCC_CUDA(cudaMemcpyAsync(keep.p, xr.p, sizeof(double) * dim * nr, cudaMemcpyDeviceToDevice, c->stream));
+        kb = 0;
+        G.clear();
+        for (int r = 0; r < nr; ++r) add_vector(keep.d() + (size_t)r * dim);
+      }
+      for (int r = 0; r < nr; ++r) {
+        if (done[r]) continue;
+        precondition(L, dim, rr.d() + (size_t)r * dim, dg.d(), theta[r], mask, tmp.d());
+        add_vector(tmp.d());
+      }
+    }
+    if (!conv) it = o.maxiter;
+    // results
+    for (int r = 0; r < nroots; ++r) {
+      double th = r < nr ? theta[r] : NAN;
+      energies[r] = c->e_ref + c->e_corr + th;
+      if (omegas) omegas[r] = th;
+    }
+    c->eom_vecs.reserve(sizeof(double) * dim * nr);
+    FNOCC_CUDA(cudaMemcpyAsync(c->eom_vecs.p, xr.p, sizeof(double) * dim * nr, cudaMemcpyDeviceToDevice, c->stream));
+    sync(c);
+    c->last_variant = variant;
+    c->last_nroots = nr;
+    c->last_dim = dim;
+    double secs = timer.s();
+    if (out) {
+      out->iters = it;
+      out->sigma_calls = sigma_calls;
+      out->seconds = secs;
+      out->seconds_per_iter = secs / std::max(1, it);
+      out->complex_roots = ncomplex;
+      double mx = 0;
+      for (double x : norms) mx = std::max(mx, x);
+      out->res_max = mx;
+    }
+    return conv ? FNOCC_OK : FNOCC_NOT_CONVERGED;
+  });
+}
+
+fnocc_status fnocc_get_block(fnocc_ctx *c, int which, int root, double *buf, size_t len) {
+  if (!c || !buf) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    require_ham(c);
+    if (which >= 1 && which <= 3) {
+      if (!c->have_amps) throw StatusError(FNOCC_E_STATE, "no amplitudes");
+      size_t off = (which >= 2 ? c->nt[1] : 0) + (which >= 3 ? c->nt[2] : 0);
+      if (len != c->nt[which]) throw StatusError(FNOCC_E_INVALID, "length mismatch");
+      FNOCC_CUDA(cudaMemcpy(buf, c->tpk.d() + off, sizeof(double) * len, cudaMemcpyDeviceToHost));
+      return FNOCC_OK;
+    }
+    if (which >= 11 && which <= 13) {
+      if (c->last_variant < 0 || root < 0 || root >= c->last_nroots) throw StatusError(FNOCC_E_STATE, "no such EOM root");
+      size_t sz[3];
+      eom_sizes(c, c->last_variant, sz);
+      int k = which - 11;
+      size_t off = (k >= 1 ? sz[0] : 0) + (k >= 2 ? sz[1] : 0);
+      if (len != sz[k]) throw StatusError(FNOCC_E_INVALID, "length mismatch");
+      FNOCC_CUDA(cudaMemcpy(buf, c->eom_vecs.d() + (size_t)root * c->last_dim + off, sizeof(double) * len,
+                            cudaMemcpyDeviceToHost));
+      return FNOCC_OK;
+    }
+    throw StatusError(FNOCC_E_INVALID, "unknown block");
+  });
+}
+
+double xfno_extrapolate(const double *f, const double *e, int npts) {
+  if (!f || !e || npts < 1) return NAN;
+  double mf = 0, me = 0;
+  for (int i = 0; i < npts; ++i) {
+    mf += f[i];
+    me += e[i];
+  }
+  mf /= npts;
+  me /= npts;
+  double sff = 0, sfe = 0;
+  for (int i = 0; i < npts; ++i) {
+    sff += (f[i] - mf) * (f[i] - mf);
+    sfe += (f[i] - mf) * (e[i] - me);
+  }
+  if (sff == 0) return me;
+  double slope = sfe / sff;
+  return me + slope * (1.0 - mf);
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Shared declarations of the fnocc CUDA library: device buffers, index maps
+// and the kernel launch wrappers (kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace fnocc {
+
+struct CudaError : std::runtime_error {
+  int code;
+  CudaError(const std::string &m, int c) : std::runtime_error(m), code(c) {}
+};
+
+#define FNOCC_CUDA(x)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (x);                                                                     \
+    if (e_ != cudaSuccess)                                                                    \
+      throw ::fnocc::CudaError(std::string(#x) + ": " + cudaGetErrorString(e_), (int)e_);     \
+  } while (0)
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() {}
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void reserve(size_t nbytes) {
+    if (nbytes <= bytes && p) return;
+    release();
+    size_t nb = nbytes ? nbytes : 8;
+    cudaError_t e = cudaMalloc(&p, nb);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw CudaError(std::string("cudaMalloc of ") + std::to_string(nb) + " bytes failed: " +
+                          cudaGetErrorString(e), (int)cudaErrorMemoryAllocation);
+    }
+    bytes = nb;
+  }
+  double *d() const { return static_cast<double *>(p); }
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Offset map of one GEMM dimension: index m decodes (mixed radix, first group
+// most significant) into digits; offset(m) = sum_g tab_g[digit_g].
+constexpr int kMaxGroups = 8;
+struct DMap {
+  int ng = 0;
+  long long n[kMaxGroups] = {0};
+  const long long *tab[kMaxGroups] = {nullptr};
+  long long maxoff = 0;  // host-side bound: sum over groups of the largest table entry
+};
+
+struct Launch {
+  cudaStream_t stream;
+  uint64_t *counter;  // incremented per kernel launch
+};
+
+// C[crow(m) + ccol(n)] (+)= alpha * sum_k A[arow(m)+acol(k)] * B[brow(k)+bcol(n)]
+// asize, bsize, csize: element counts of the buffers; every launch checks on
+// the host that maxoff(row) + maxoff(col) < size for each operand, so a wrong
+// table is reported as an error instead of reaching the device.
+void gather_gemm(const Launch &L, long long M, long long N, long long K, double alpha,
+                 const double *A, const DMap &arow, const DMap &acol, const double *B,
+                 const DMap &brow, const DMap &bcol, double *C, const DMap &crow,
+                 const DMap &ccol, bool accumulate, long long asize, long long bsize,
+                 long long csize);
+// C[crow(m)] += alpha * A[arow(m)]
+void gather_axpy(const Launch &L, long long M, double alpha, const double *A, const DMap &arow,
+                 double *C, const DMap &crow, long long asize, long long csize);
+
+// Antisymmetrise a dense [o^nh v^np] accumulator into packed unique elements:
+// out[h,p] = sum_{perm} sign * Y[perm(h), perm(p)] (out overwritten, or
+// accumulated into when accumulate).
+void antisym_pack(const Launch &L, const double *Y, int nh, int np, int o, int v,
+                  const int *htab, long long nhtup, const int *ptab, long long nptup, double *out,
+                  double scale, bool accumulate);
+// Dense antisymmetric tensor from packed elements (dense zeroed here).
+void unpack_dense(const Launch &L, const double *packed, int nh, int np, int o, int v,
+                  const int *htab, long long nhtup, const int *ptab, long long nptup,
+                  double *dense);
+
+void fill(const Launch &L, double *x, double val, long long n);
+void axpby(const Launch &L, long long n, double a, const double *x, double b, double *y);  // y = a x + b y
+void scale_mask(const Launch &L, long long n, double *x, const unsigned char *mask);       // x *= mask
+void jacobi_update(const Launch &L, long long n, const double *r, const double *d, double *t);  // t += r/d
+void precondition(const Launch &L, long long n, const double *r, const double *d, double theta,
+                  const unsigned char *mask, double *out);  // out = mask * r / (theta - d)
+// dots[j] = sum_i x[i] * Y[j*ld + i] for j < nvec  (reduction over i)
+void multi_dot(const Launch &L, long long n, const double *x, const double *Y, long long ld,
+               int nvec, double *dots_dev, DevBuf &scratch);
+// max |x| and sum x^2 into out2[0], out2[1] (NaN reported as an infinite max)
+void absmax_sumsq(const Launch &L, long long n, const double *x, double *out2_dev, DevBuf &scratch);
+// spin-orbital antisymmetrised integrals from spatial (pq|rs) over n spatial orbitals
+void spin_orbital_eri(const Launch &L, const double *eri_sp, int n, double *g);
+void spin_orbital_h(const Launch &L, const double *h_sp, int n, double *hso);
+// f_pq = h_pq + sum_i g[p,i,q,i]; eref2[0] = sum_i h_ii, eref2[1] = 1/2 sum_ij g_ijij
+void normal_order(const Launch &L, const double *h, const double *g, int n, int o, double *f,
+                  double *eref2_dev);
+// L, M matrices of the T1 similarity transformation from t1 [o x v]
+void t1_transform_mats(const Launch &L, const double *t1, int o, int v, double *Lm, double *Mm);
+// symmetric eigen-decomposition by cyclic Jacobi in one block: A n x n (destroyed),
+// evals[n] unsorted, V n x n (columns = eigenvectors). Returns via device flag.
+void jacobi_eig(const Launch &L, double *A, int n, double *evals, double *V, int *info_dev);
+// out[:, j] = sign_j * in[:, perm[j]] for an n x m column-major-by-index matrix stored row-major
+void permute_columns(const Launch &L, const double *in, int rows, int cols_in, const int *perm,
+                     int cols_out, double *out);
+// fix phase: make the largest |.| entry of each column positive (row-major rows x cols)
+void fix_phase(const Launch &L, double *c, int rows, int cols);
+// elementwise: out = a + alpha*b + beta*c (any may alias)
+void lincomb3(const Launch &L, long long n, double *out, const double *a, double alpha,
+              const double *b, double beta, const double *c);
+// MP2 amplitudes t[i,j,a,b] = g[a,b,i,j] / (f_ii+f_jj-f_aa-f_bb) over a spin-orbital space
+void mp2_amplitudes(const Launch &L, const double *g, const double *fdiag, int n, int o, double *t);
+// diagonal of an n x n matrix
+void diag_of(const Launch &L, const double *a, int n, double *d);
+// dense alpha block of a spin-orbital matrix: out[p,q] = in[2p, 2q]
+void alpha_block(const Launch &L, const double *in, int nso, double *out);
+// orbital-energy EOM diagonal for packed tuples: d = sum f_pp - sum f_hh
+void eom_diag(const Launch &L, const double *fdiag, int o, int nh, int np, const int *htab,
+              long long nhtup, const int *ptab, long long nptup, double *d);
+// spin-sector mask for packed tuples: 2*M_s change == ms2
+void ms_mask(const Launch &L, int nh, int np, const int *htab, long long nhtup, const int *ptab,
+             long long nptup, int ms2, unsigned char *mask);
+// Jacobi denominators for a packed cluster block (d = sum f_ii - sum f_aa)
+void cc_denominators(const Launch &L, const double *fdiag, int o, int rank, const int *htab,
+                     long long nhtup, const int *ptab, long long nptup, double *d);
+
+}  // namespace fnocc

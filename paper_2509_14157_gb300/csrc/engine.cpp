@@ -1,0 +1,281 @@
+// Compiles planned terms (planner.cpp) into offset tables and launches them
+// through the gather-GEMM-scatter kernel (kernels.cu).
+#include "engine.hpp"
+
+#include <algorithm>
+#include <map>
+
+namespace fnocc {
+
+long long binom_ll(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  long long r = 1;
+  for (int i = 0; i < k; ++i) r = r * (n - i) / (i + 1);
+  return r;
+}
+
+void TupleTable::build(int n_, int k_) {
+  n = n_;
+  k = k_;
+  count = binom_ll(n, k);
+  std::vector<int> host;
+  host.reserve((size_t)std::max<long long>(count, 1) * std::max(k, 1));
+  std::vector<int> cur(k);
+  for (int i = 0; i < k; ++i) cur[i] = i;
+  if (count > 0) {
+    while (true) {
+      for (int i = 0; i < k; ++i) host.push_back(cur[i]);
+      int i = k - 1;
+      while (i >= 0 && cur[i] == n - k + i) --i;
+      if (i < 0) break;
+      ++cur[i];
+      for (int j = i + 1; j < k; ++j) cur[j] = cur[j - 1] + 1;
+    }
+  }
+  if (host.empty()) host.push_back(0);
+  dev.reserve(host.size() * sizeof(int));
+  FNOCC_CUDA(cudaMemcpy(dev.p, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice));
+}
+
+namespace {
+
+// Storage description of an operand: label -> (stride, base offset of its space)
+struct Storage {
+  std::vector<int> labels;
+  std::vector<long long> stride;
+  std::vector<long long> base;
+  long long find(int lab, long long *st, long long *bs) const {
+    for (size_t i = 0; i < labels.size(); ++i)
+      if (labels[i] == lab) {
+        *st = stride[i];
+        *bs = base[i];
+        return 1;
+      }
+    throw std::runtime_error("engine: label not in operand storage");
+  }
+};
+
+Storage dense_storage(const std::vector<int> &labels, int o, int v) {
+  Storage s;
+  s.labels = labels;
+  s.stride.resize(labels.size());
+  s.base.assign(labels.size(), 0);
+  long long st = 1;
+  for (int i = (int)labels.size() - 1; i >= 0; --i) {
+    s.stride[i] = st;
+    st *= lab_space(labels[i]) == SP_O ? o : v;
+  }
+  return s;
+}
+
+Storage full_storage(const std::vector<int> &labels, int o, int v) {
+  const long long n = o + v;
+  Storage s;
+  s.labels = labels;
+  s.stride.resize(labels.size());
+  s.base.resize(labels.size());
+  long long st = 1;
+  for (int i = (int)labels.size() - 1; i >= 0; --i) {
+    s.stride[i] = st;
+    st *= n;
+    s.base[i] = lab_space(labels[i]) == SP_O ? 0 : o;
+  }
+  return s;
+}
+
+// Output accumulator: externals in id order (holes then particles).
+Storage output_storage(int nh, int np, int o, int v) {
+  std::vector<int> labs;
+  for (int k = 0; k < nh; ++k) labs.push_back(make_label(k, SP_O));
+  for (int k = 0; k < np; ++k) labs.push_back(make_label(nh + k, SP_V));
+  return dense_storage(labs, o, v);
+}
+
+struct TableBuilder {
+  std::vector<long long> host;
+  struct Pending { DMap *map; std::vector<long long> offs; };
+  std::vector<Pending> pend;
+
+  // appends the tables of `groups` over storage `s` and records a map to fix up
+  long long add(DMap *map, const std::vector<DimGroup> &groups, const Storage &s, int o, int v) {
+    if ((int)groups.size() > kMaxGroups) throw std::runtime_error("engine: too many dimension groups");
+    map->ng = (int)groups.size();
+    map->maxoff = 0;
+    Pending p;
+    p.map = map;
+    long long total = 1;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      const DimGroup &dg = groups[g];
+      int n = dg.space == SP_O ? o : v;
+      std::vector<long long> st(dg.k), bs(dg.k);
+      for (int j = 0; j < dg.k; ++j) s.find(dg.labels[j], &st[j], &bs[j]);
+      p.offs.push_back((long long)host.size());
+      long long cnt = 0;
+      std::vector<int> cur(dg.k);
+      if (dg.packed) {
+        for (int j = 0; j < dg.k; ++j) cur[j] = j;
+        if (binom_ll(n, dg.k) > 0)
+          while (true) {
+            long long off = 0;
+            for (int j = 0; j < dg.k; ++j) off += st[j] * (bs[j] + cur[j]);
+            host.push_back(off);
+            ++cnt;
+            int i = dg.k - 1;
+            while (i >= 0 && cur[i] == n - dg.k + i) --i;
+            if (i < 0) break;
+            ++cur[i];
+            for (int j = i + 1; j < dg.k; ++j) cur[j] = cur[j - 1] + 1;
+          }
+      } else {
+        long long tot = 1;
+        for (int j = 0; j < dg.k; ++j) tot *= n;
+        for (long long x = 0; x < tot; ++x) {
+          long long rem = x, off = 0;
+          for (int j = dg.k - 1; j >= 0; --j) {
+            off += st[j] * (bs[j] + rem % n);
+            rem /= n;
+          }
+          host.push_back(off);
+          ++cnt;
+        }
+      }
+      map->n[g] = cnt;
+      long long mx = 0;
+      for (long long q = p.offs.back(); q < (long long)host.size(); ++q) mx = std::max(mx, host[q]);
+      map->maxoff += mx;
+      total *= cnt;
+    }
+    pend.push_back(p);
+    return total;
+  }
+
+  void upload(DevBuf &buf) {
+    if (host.empty()) host.push_back(0);
+    buf.reserve(host.size() * sizeof(long long));
+    FNOCC_CUDA(cudaMemcpy(buf.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    const long long *base = buf.as<long long>();
+    for (auto &p : pend)
+      for (size_t g = 0; g < p.offs.size(); ++g) p.map->tab[g] = base + p.offs[g];
+  }
+};
+
+}  // namespace
+
+ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2])
+    : nh_(eq.nh), np_(eq.np), o_(o), v_(v) {
+  TableBuilder tb;
+  Storage outs = output_storage(nh_, np_, o, v);
+  terms_.reserve(eq.terms.size());
+  for (const Term &t : eq.terms) {
+    TermPlan plan = plan_term(t, nh_, np_, o, v);
+    ExecTerm et;
+    long long off = 0;
+    for (auto &labs : plan.inter_labels) {
+      long long sz = 1;
+      for (int lab : labs) sz *= lab_space(lab) == SP_O ? o : v;
+      et.inter_off.push_back(off);
+      et.inter_size.push_back(sz);
+      off += sz;
+    }
+    scratch_need_ = std::max(scratch_need_, off);
+    auto storage_of = [&](const Operand &op) -> Storage {
+      switch (op.kind) {
+        case TK_F:
+        case TK_V:
+          return full_storage(op.labels, o, v);
+        case TK_INTERMEDIATE:
+          return dense_storage(op.labels, o, v);
+        default:
+          return dense_storage(op.labels, o, v);
+      }
+    };
+    et.steps.reserve(plan.steps.size());
+    for (const Step &s : plan.steps) {
+      ExecStep x;
+      x.a_kind = s.a.kind;
+      x.a_inter = s.a.inter;
+      x.b_kind = s.b.kind;
+      x.b_inter = s.b.inter;
+      x.to_output = s.to_output;
+      x.out_inter = s.out_inter;
+      x.alpha = s.alpha;
+      Storage sa = storage_of(s.a);
+      Storage sc = s.to_output ? outs : dense_storage(plan.inter_labels[s.out_inter], o, v);
+      et.steps.push_back(x);
+      ExecStep &e = et.steps.back();
+      e.M = tb.add(&e.arow, s.mg, sa, o, v);
+      tb.add(&e.crow, s.mg, sc, o, v);
+      if (s.b.kind >= 0) {
+        Storage sb = storage_of(s.b);
+        e.K = tb.add(&e.acol, s.kg, sa, o, v);
+        tb.add(&e.brow, s.kg, sb, o, v);
+        e.N = tb.add(&e.bcol, s.ng, sb, o, v);
+        tb.add(&e.ccol, s.ng, sc, o, v);
+        flops_ += 2.0 * double(e.M) * double(e.N) * double(e.K);
+      } else {
+        e.N = 1;
+        e.K = 1;
+        flops_ += double(e.M);
+      }
+    }
+    terms_.push_back(std::move(et));
+  }
+  (void)rdims;
+  tb.upload(tables_);
+}
+
+void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch) const {
+  if (scratch_need_ > 0) scratch.reserve(sizeof(double) * (size_t)scratch_need_);
+  for (const ExecTerm &t : terms_) {
+    auto ptr = [&](int kind, int inter) -> const double * {
+      switch (kind) {
+        case TK_F: return ops.f;
+        case TK_V: return ops.v;
+        case TK_T2: return ops.t2;
+        case TK_T3: return ops.t3;
+        case TK_R1: return ops.r[0];
+        case TK_R2: return ops.r[1];
+        case TK_R3: return ops.r[2];
+        case TK_INTERMEDIATE: return scratch.d() + t.inter_off[inter];
+        default: throw std::runtime_error("engine: unknown operand kind");
+      }
+    };
+    auto size = [&](int kind, int inter) -> long long {
+      switch (kind) {
+        case TK_F: return ops.f_size;
+        case TK_V: return ops.v_size;
+        case TK_T2: return ops.t2_size;
+        case TK_T3: return ops.t3_size;
+        case TK_R1: return ops.r_size[0];
+        case TK_R2: return ops.r_size[1];
+        case TK_R3: return ops.r_size[2];
+        case TK_INTERMEDIATE: return t.inter_size[inter];
+        default: return 0;
+      }
+    };
+    for (const ExecStep &s : t.steps) {
+      double *C;
+      long long csize;
+      if (s.to_output) {
+        C = Y;
+        csize = y_size;
+      } else {
+        csize = t.inter_size[s.out_inter];
+        C = scratch.d() + t.inter_off[s.out_inter];
+        FNOCC_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * t.inter_size[s.out_inter], L.stream));
+      }
+      const double *A = ptr(s.a_kind, s.a_inter);
+      if (!A) throw std::runtime_error("engine: missing operand");
+      if (s.b_kind < 0) {
+        gather_axpy(L, s.M, s.alpha, A, s.arow, C, s.crow, size(s.a_kind, s.a_inter), csize);
+      } else {
+        const double *B = ptr(s.b_kind, s.b_inter);
+        if (!B) throw std::runtime_error("engine: missing operand");
+        gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol, true,
+                    size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize);
+      }
+    }
+  }
+}
+
+}  // namespace fnocc

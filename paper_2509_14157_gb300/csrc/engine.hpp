@@ -1,0 +1,68 @@
+// Execution of planned equations on the device: offset tables, intermediate
+// scratch and the launch sequence of one projected equation.
+#pragma once
+#include "common.hpp"
+#include "planner.hpp"
+
+#include <memory>
+
+namespace fnocc {
+
+// Device pointers of the operands an equation reads.
+struct Operands {
+  const double *f = nullptr;    // n x n one-body operator (n = o + v), full
+  const double *v = nullptr;    // n^4 antisymmetrised two-body operator, full
+  const double *t2 = nullptr;   // dense [o,o,v,v]
+  const double *t3 = nullptr;   // dense [o,o,o,v,v,v]
+  const double *r[3] = {nullptr, nullptr, nullptr};  // dense EOM components
+  // element counts of the buffers above (checked against every index map)
+  long long f_size = 0, v_size = 0, t2_size = 0, t3_size = 0, r_size[3] = {0, 0, 0};
+};
+
+struct ExecStep {
+  int a_kind, a_inter, b_kind, b_inter;
+  bool to_output;
+  int out_inter;
+  long long M, N, K;
+  double alpha;
+  DMap arow, acol, brow, bcol, crow, ccol;
+};
+
+struct ExecTerm {
+  std::vector<ExecStep> steps;
+  std::vector<long long> inter_off;   // offsets (doubles) of intermediates in scratch
+  std::vector<long long> inter_size;
+};
+
+// One equation <mu_out| ... |0> compiled for fixed (o, v) and operand shapes.
+class ExecEquation {
+ public:
+  // rdims: (nh, np) of the three EOM input components (ignored for CC)
+  ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2]);
+  // Y (dense output accumulator [o^nh v^np]) += sum of terms
+  void run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch) const;
+  long long scratch_doubles() const { return scratch_need_; }
+  double flops() const { return flops_; }
+  int nh() const { return nh_; }
+  int np() const { return np_; }
+  size_t nterms() const { return terms_.size(); }
+
+ private:
+  int nh_, np_, o_, v_;
+  std::vector<ExecTerm> terms_;
+  DevBuf tables_;
+  long long scratch_need_ = 0;
+  double flops_ = 0;
+};
+
+// Sorted index tuples (lexicographic) of k out of n, as a device int table.
+struct TupleTable {
+  int n = 0, k = 0;
+  long long count = 0;
+  DevBuf dev;
+  void build(int n, int k);
+};
+
+long long binom_ll(int n, int k);
+
+}  // namespace fnocc

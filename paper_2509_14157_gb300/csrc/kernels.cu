@@ -1,0 +1,794 @@
+// CUDA kernels of libfnocc (sm_103a). FP64 throughout.
+//
+// The contraction kernel is a gather-GEMM-scatter: every operand element is
+// addressed through per-dimension offset tables (DMap), so index permutations,
+// block slices of the integral tensors and antisymmetry-packed index tuples
+// (i<j<k, a<b, ...) are read and written in place without materialised
+// transposes. On this part FP64 FMA issue (about two FP64 FMAs per clock per
+// SM) is the bound of every contraction, so the kernel is a register-tiled
+// SIMT FP64 GEMM: a 64x64 tile per 256-thread block, 4x4 outputs per thread,
+// K staged through shared memory 16 at a time.
+#include "common.hpp"
+
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cmath>
+
+namespace fnocc {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+struct GemmParams {
+  long long M, N, K;
+  long long kchunk;
+  double alpha;
+  const double *A;
+  const double *B;
+  double *C;
+  DMap arow, acol, brow, bcol, crow, ccol;
+  long long tiles_n;
+  int atomic;
+  int accumulate;
+};
+
+__device__ __forceinline__ long long map_off(const DMap &mp, long long m) {
+  long long off = 0;
+  for (int g = mp.ng - 1; g >= 0; --g) {
+    long long q = m / mp.n[g];
+    long long r = m - q * mp.n[g];
+    off += mp.tab[g][r];
+    m = q;
+  }
+  return off;
+}
+
+__global__ void __launch_bounds__(NT) k_gather_gemm(const GemmParams p) {
+  __shared__ double As[BK][BM];
+  __shared__ double Bs[BK][BN];
+  __shared__ long long arow_s[BM], crow_s[BM], bcol_s[BN], ccol_s[BN], acol_s[BK], brow_s[BK];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const long long tile = blockIdx.x;
+  const long long m0 = (tile / p.tiles_n) * BM;
+  const long long n0 = (tile % p.tiles_n) * BN;
+  const long long kb = (long long)blockIdx.y * p.kchunk;
+  const long long ke = min(p.K, kb + p.kchunk);
+  if (tid < BM) {
+    long long m = m0 + tid;
+    arow_s[tid] = m < p.M ? map_off(p.arow, m) : 0;
+    crow_s[tid] = m < p.M ? map_off(p.crow, m) : 0;
+  } else if (tid < BM + BN) {
+    long long n = n0 + tid - BM;
+    bcol_s[tid - BM] = n < p.N ? map_off(p.bcol, n) : 0;
+    ccol_s[tid - BM] = n < p.N ? map_off(p.ccol, n) : 0;
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long long k0 = kb; k0 < ke; k0 += BK) {
+    __syncthreads();
+    if (tid < BK) {
+      long long k = k0 + tid;
+      acol_s[tid] = k < ke ? map_off(p.acol, k) : 0;
+    } else if (tid < 2 * BK) {
+      long long k = k0 + tid - BK;
+      brow_s[tid - BK] = k < ke ? map_off(p.brow, k) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < (BM * BK) / NT; ++r) {
+      int idx = tid + NT * r;
+      int kk = idx % BK, row = idx / BK;
+      bool ok = (m0 + row < p.M) && (k0 + kk < ke);
+      As[kk][row] = ok ? p.A[arow_s[row] + acol_s[kk]] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < (BN * BK) / NT; ++r) {
+      int idx = tid + NT * r;
+      int col = idx % BN, kk = idx / BN;
+      bool ok = (n0 + col < p.N) && (k0 + kk < ke);
+      Bs[kk][col] = ok ? p.B[brow_s[kk] + bcol_s[col]] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    long long m = m0 + ty * 4 + i;
+    if (m >= p.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      long long n = n0 + tx * 4 + j;
+      if (n >= p.N) continue;
+      double *dst = p.C + crow_s[ty * 4 + i] + ccol_s[tx * 4 + j];
+      double val = p.alpha * acc[i][j];
+      if (p.atomic)
+        atomicAdd(dst, val);
+      else if (p.accumulate)
+        *dst += val;
+      else
+        *dst = val;
+    }
+  }
+}
+
+__global__ void k_gather_axpy(long long M, double alpha, const double *A, DMap arow, double *C, DMap crow) {
+  long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  C[map_off(crow, m)] += alpha * A[map_off(arow, m)];
+}
+
+// permutation tables for up to 4 elements, generated on the device side once
+__constant__ signed char c_perm[5][24][4];
+__constant__ signed char c_psign[5][24];
+__constant__ int c_pcount[5];
+
+__device__ __forceinline__ void dense_strides(int nh, int np, int o, int v, long long *sh, long long *sp) {
+  long long s = 1;
+  for (int k = np - 1; k >= 0; --k) { sp[k] = s; s *= v; }
+  for (int k = nh - 1; k >= 0; --k) { sh[k] = s; s *= o; }
+}
+
+__global__ void k_antisym_pack(const double *Y, int nh, int np, int o, int v, const int *htab, long long nhtup,
+                               const int *ptab, long long nptup, double *out, double scale, int accumulate) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= nhtup * nptup) return;
+  long long hi = r / nptup, pi = r - hi * nptup;
+  long long sh[4], sp[4];
+  dense_strides(nh, np, o, v, sh, sp);
+  int h[4], pv[4];
+  for (int k = 0; k < nh; ++k) h[k] = htab[hi * nh + k];
+  for (int k = 0; k < np; ++k) pv[k] = ptab[pi * np + k];
+  double acc = 0.0;
+  const int nph = c_pcount[nh], npp = c_pcount[np];
+  for (int a = 0; a < nph; ++a) {
+    long long offh = 0;
+    for (int k = 0; k < nh; ++k) offh += sh[k] * h[c_perm[nh][a][k]];
+    double part = 0.0;
+    for (int b = 0; b < npp; ++b) {
+      long long off = offh;
+      for (int k = 0; k < np; ++k) off += sp[k] * pv[c_perm[np][b][k]];
+      part += c_psign[np][b] * Y[off];
+    }
+    acc += c_psign[nh][a] * part;
+  }
+  acc *= scale;
+  out[r] = accumulate ? out[r] + acc : acc;
+}
+
+__global__ void k_unpack_dense(const double *packed, int nh, int np, int o, int v, const int *htab, long long nhtup,
+                               const int *ptab, long long nptup, double *dense) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= nhtup * nptup) return;
+  long long hi = r / nptup, pi = r - hi * nptup;
+  long long sh[4], sp[4];
+  dense_strides(nh, np, o, v, sh, sp);
+  int h[4], pv[4];
+  for (int k = 0; k < nh; ++k) h[k] = htab[hi * nh + k];
+  for (int k = 0; k < np; ++k) pv[k] = ptab[pi * np + k];
+  const double val = packed[r];
+  const int nph = c_pcount[nh], npp = c_pcount[np];
+  for (int a = 0; a < nph; ++a) {
+    long long offh = 0;
+    for (int k = 0; k < nh; ++k) offh += sh[k] * h[c_perm[nh][a][k]];
+    for (int b = 0; b < npp; ++b) {
+      long long off = offh;
+      for (int k = 0; k < np; ++k) off += sp[k] * pv[c_perm[np][b][k]];
+      dense[off] = c_psign[nh][a] * c_psign[np][b] * val;
+    }
+  }
+}
+
+__global__ void k_fill(double *x, double val, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = val;
+}
+
+__global__ void k_axpby(long long n, double a, const double *x, double b, double *y) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_scale_mask(long long n, double *x, const unsigned char *mask) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n && !mask[i]) x[i] = 0.0;
+}
+
+__global__ void k_jacobi_update(long long n, const double *r, const double *d, double *t) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) t[i] += r[i] / d[i];
+}
+
+__global__ void k_precondition(long long n, const double *r, const double *d, double theta,
+                               const unsigned char *mask, double *out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double den = theta - d[i];
+  if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+  out[i] = mask[i] ? r[i] / den : 0.0;
+}
+
+// partial dot products: grid (gx, nvec)
+__global__ void k_dot_partial(long long n, const double *x, const double *Y, long long ld, double *part) {
+  __shared__ double red[256];
+  const int j = blockIdx.y;
+  const double *y = Y + j * ld;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_dot_final(int gx, int nvec, const double *part, double *dots) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nvec) return;
+  double s = 0.0;
+  for (int b = 0; b < gx; ++b) s += part[j * gx + b];
+  dots[j] = s;
+}
+
+__global__ void k_absmax_partial(long long n, const double *x, double *part) {
+  __shared__ double rm[256], rs[256];
+  double m = 0.0, s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double a = x[i];
+    m = fmax(m, fabs(a));
+    s = fma(a, a, s);
+    if (a != a) m = CUDART_INF;  // NaN marks as infinite
+  }
+  rm[threadIdx.x] = m;
+  rs[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      rm[threadIdx.x] = fmax(rm[threadIdx.x], rm[threadIdx.x + w]);
+      rs[threadIdx.x] += rs[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = rm[0];
+    part[2 * blockIdx.x + 1] = rs[0];
+  }
+}
+
+__global__ void k_absmax_final(int gx, const double *part, double *out) {
+  if (threadIdx.x != 0) return;
+  double m = 0.0, s = 0.0;
+  for (int b = 0; b < gx; ++b) {
+    m = fmax(m, part[2 * b]);
+    s += part[2 * b + 1];
+  }
+  out[0] = m;
+  out[1] = s;
+}
+
+// <PQ||RS> over spin orbitals P = 2p + s from spatial (pq|rs)
+__global__ void k_spin_eri(const double *e, int n, double *g) {
+  const long long ns = 2LL * n;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= ns * ns * ns * ns) return;
+  long long S = idx % ns, R = (idx / ns) % ns, Q = (idx / (ns * ns)) % ns, P = idx / (ns * ns * ns);
+  int p = P >> 1, q = Q >> 1, r = R >> 1, s = S >> 1;
+  int sp = P & 1, sq = Q & 1, sr = R & 1, ss = S & 1;
+  double val = 0.0;
+  const long long n2 = (long long)n * n;
+  if (sp == sr && sq == ss) val += e[(p * (long long)n + r) * n2 + q * (long long)n + s];
+  if (sp == ss && sq == sr) val -= e[(p * (long long)n + s) * n2 + q * (long long)n + r];
+  g[idx] = val;
+}
+
+__global__ void k_spin_h(const double *h, int n, double *hso) {
+  const int ns = 2 * n;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ns * ns) return;
+  int P = idx / ns, Q = idx % ns;
+  hso[idx] = ((P & 1) == (Q & 1)) ? h[(P >> 1) * n + (Q >> 1)] : 0.0;
+}
+
+__global__ void k_normal_order(const double *h, const double *g, int n, int o, double *f) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  int p = idx / n, q = idx % n;
+  const long long n3 = (long long)n * n * n, n2 = (long long)n * n;
+  double s = h[idx];
+  for (int i = 0; i < o; ++i) s += g[p * n3 + i * n2 + q * (long long)n + i];
+  f[idx] = s;
+}
+
+__global__ void k_eref(const double *h, const double *g, int n, int o, double *out) {
+  __shared__ double r1[256], r2[256];
+  const long long n3 = (long long)n * n * n, n2 = (long long)n * n;
+  double a = 0.0, b = 0.0;
+  for (int idx = threadIdx.x; idx < o * o; idx += blockDim.x) {
+    int i = idx / o, j = idx % o;
+    if (i == j) a += h[i * n + i];
+    b += g[i * n3 + j * n2 + i * (long long)n + j];
+  }
+  r1[threadIdx.x] = a;
+  r2[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+      r2[threadIdx.x] += r2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = r1[0];
+    out[1] = 0.5 * r2[0];
+  }
+}
+
+__global__ void k_t1_mats(const double *t1, int o, int v, double *Lm, double *Mm) {
+  const int n = o + v;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  int p = idx / n, q = idx % n;
+  double l = (p == q) ? 1.0 : 0.0, m = l;
+  if (p < o && q >= o) l = -t1[p * v + (q - o)];  // L[i, a] = -t_i^a
+  if (p >= o && q < o) m = t1[q * v + (p - o)];   // M[a, i] = t_i^a
+  Lm[idx] = l;
+  Mm[idx] = m;
+}
+
+// One-block cyclic Jacobi for symmetric A (n <= 128), tournament ordering.
+__global__ void k_jacobi_eig(double *Ag, int n, double *evals, double *V, int *info) {
+  extern __shared__ double A[];
+  __shared__ double cs[64], sn[64];
+  __shared__ int pp[64], qq[64];
+  __shared__ double red[512], red2[512];
+  __shared__ int stop;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    A[idx] = Ag[idx];
+    V[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+  }
+  const int npad = n + (n & 1);
+  const int half = npad / 2;
+  int sweep;
+  __syncthreads();
+  for (sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int idx = tid; idx < n * n; idx += nt) {
+      double a = A[idx];
+      tot += a * a;
+      if (idx / n != idx % n) off += a * a;
+    }
+    red[tid] = off;
+    red2[tid] = tot;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+      if (tid < w) {
+        red[tid] += red[tid + w];
+        red2[tid] += red2[tid + w];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) stop = (red[0] <= 1e-30 * red2[0] || red[0] < 1e-300) ? 1 : 0;
+    __syncthreads();
+    if (stop) break;
+    for (int rnd = 0; rnd < npad - 1; ++rnd) {
+      if (tid < half) {
+        int k = tid;
+        int a = (k == 0) ? 0 : ((k - 1 + rnd) % (npad - 1)) + 1;
+        int kb = npad - 1 - k;
+        int b = ((kb - 1 + rnd) % (npad - 1)) + 1;
+        int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          double apq = A[p * n + q];
+          if (fabs(apq) > 1e-300) {
+            double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        cs[k] = c;
+        sn[k] = s;
+        pp[k] = p;
+        qq[k] = q < n ? q : -1;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nt) {  // rows
+        int k = idx / n, j = idx % n;
+        int p = pp[k], q = qq[k];
+        if (q < 0) continue;
+        double c = cs[k], s = sn[k];
+        double apj = A[p * n + j], aqj = A[q * n + j];
+        A[p * n + j] = c * apj - s * aqj;
+        A[q * n + j] = s * apj + c * aqj;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nt) {  // columns and V
+        int k = idx / n, i = idx % n;
+        int p = pp[k], q = qq[k];
+        if (q < 0) continue;
+        double c = cs[k], s = sn[k];
+        double aip = A[i * n + p], aiq = A[i * n + q];
+        A[i * n + p] = c * aip - s * aiq;
+        A[i * n + q] = s * aip + c * aiq;
+        double vip = V[i * n + p], viq = V[i * n + q];
+        V[i * n + p] = c * vip - s * viq;
+        V[i * n + q] = s * vip + c * viq;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < n; i += nt) evals[i] = A[i * n + i];
+  if (tid == 0) info[0] = sweep;
+}
+
+__global__ void k_permute_columns(const double *in, int rows, int cols_in, const int *perm, int cols_out, double *out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols_out) return;
+  int i = idx / cols_out, j = idx % cols_out;
+  out[idx] = in[i * cols_in + perm[j]];
+}
+
+__global__ void k_fix_phase(double *c, int rows, int cols) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= cols) return;
+  int best = 0;
+  double bv = -1.0;
+  for (int i = 0; i < rows; ++i) {
+    double a = fabs(c[i * cols + j]);
+    if (a > bv) { bv = a; best = i; }
+  }
+  if (c[best * cols + j] < 0)
+    for (int i = 0; i < rows; ++i) c[i * cols + j] = -c[i * cols + j];
+}
+
+__global__ void k_lincomb3(long long n, double *out, const double *a, double alpha, const double *b, double beta,
+                           const double *c) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + alpha * b[i] + beta * c[i];
+}
+
+__global__ void k_mp2(const double *g, const double *fd, int n, int o, double *t) {
+  const int v = n - o;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)o * o * v * v) return;
+  int b = idx % v, a = (idx / v) % v, j = (idx / (v * v)) % o, i = idx / ((long long)v * v * o);
+  const long long n3 = (long long)n * n * n, n2 = (long long)n * n;
+  double num = g[(o + a) * n3 + (o + b) * n2 + i * (long long)n + j];
+  double den = fd[i] + fd[j] - fd[o + a] - fd[o + b];
+  t[idx] = (i == j || a == b) ? 0.0 : num / den;
+}
+
+__global__ void k_diag(const double *a, int n, double *d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = a[i * n + i];
+}
+
+__global__ void k_alpha_block(const double *in, int nso, double *out) {
+  int m = nso / 2;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  int p = idx / m, q = idx % m;
+  out[idx] = in[(2 * p) * nso + 2 * q];
+}
+
+__global__ void k_eom_diag(const double *fd, int o, int nh, int np, const int *htab, long long nhtup, const int *ptab,
+                           long long nptup, double *d) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= nhtup * nptup) return;
+  long long hi = r / nptup, pi = r - hi * nptup;
+  double s = 0.0;
+  for (int k = 0; k < np; ++k) s += fd[o + ptab[pi * np + k]];
+  for (int k = 0; k < nh; ++k) s -= fd[htab[hi * nh + k]];
+  d[r] = s;
+}
+
+__global__ void k_ms_mask(int nh, int np, const int *htab, long long nhtup, const int *ptab, long long nptup, int ms2,
+                          unsigned char *mask) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= nhtup * nptup) return;
+  long long hi = r / nptup, pi = r - hi * nptup;
+  int s = 0;
+  for (int k = 0; k < np; ++k) s += (ptab[pi * np + k] & 1) ? -1 : 1;
+  for (int k = 0; k < nh; ++k) s -= (htab[hi * nh + k] & 1) ? -1 : 1;
+  mask[r] = (s == ms2) ? 1 : 0;
+}
+
+__global__ void k_cc_den(const double *fd, int o, int rank, const int *htab, long long nhtup, const int *ptab,
+                         long long nptup, double *d) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= nhtup * nptup) return;
+  long long hi = r / nptup, pi = r - hi * nptup;
+  double s = 0.0;
+  for (int k = 0; k < rank; ++k) s += fd[htab[hi * rank + k]] - fd[o + ptab[pi * rank + k]];
+  d[r] = s;
+}
+
+inline unsigned blocks_for(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
+
+void ensure_perm_tables() {
+  static bool done = false;
+  if (done) return;
+  signed char perm[5][24][4] = {};
+  signed char sgn[5][24] = {};
+  int cnt[5] = {};
+  for (int k = 0; k <= 4; ++k) {
+    int a[4] = {0, 1, 2, 3};
+    int c = 0;
+    do {
+      int inv = 0;
+      for (int x = 0; x < k; ++x)
+        for (int y = x + 1; y < k; ++y)
+          if (a[x] > a[y]) ++inv;
+      for (int x = 0; x < 4; ++x) perm[k][c][x] = (signed char)(x < k ? a[x] : 0);
+      sgn[k][c] = (inv & 1) ? -1 : 1;
+      ++c;
+    } while (std::next_permutation(a, a + k));
+    cnt[k] = c;
+  }
+  FNOCC_CUDA(cudaMemcpyToSymbol(c_perm, perm, sizeof(perm)));
+  FNOCC_CUDA(cudaMemcpyToSymbol(c_psign, sgn, sizeof(sgn)));
+  FNOCC_CUDA(cudaMemcpyToSymbol(c_pcount, cnt, sizeof(cnt)));
+  done = true;
+}
+
+inline void post(const Launch &L) {
+  FNOCC_CUDA(cudaGetLastError());
+  if (L.counter) ++*L.counter;
+}
+
+}  // namespace
+
+void gather_gemm(const Launch &L, long long M, long long N, long long K, double alpha, const double *A,
+                 const DMap &arow, const DMap &acol, const double *B, const DMap &brow, const DMap &bcol, double *C,
+                 const DMap &crow, const DMap &ccol, bool accumulate, long long asize, long long bsize,
+                 long long csize) {
+  if (M <= 0 || N <= 0) return;
+  if (arow.maxoff + acol.maxoff >= asize || brow.maxoff + bcol.maxoff >= bsize || crow.maxoff + ccol.maxoff >= csize ||
+      arow.maxoff < 0 || acol.maxoff < 0 || brow.maxoff < 0 || bcol.maxoff < 0 || crow.maxoff < 0 || ccol.maxoff < 0)
+    throw std::runtime_error("gather_gemm: index map exceeds operand bounds");
+  GemmParams p;
+  p.M = M;
+  p.N = N;
+  p.K = K > 0 ? K : 1;
+  p.alpha = alpha;
+  p.A = A;
+  p.B = B;
+  p.C = C;
+  p.arow = arow;
+  p.acol = acol;
+  p.brow = brow;
+  p.bcol = bcol;
+  p.crow = crow;
+  p.ccol = ccol;
+  p.tiles_n = (N + BN - 1) / BN;
+  long long tiles = ((M + BM - 1) / BM) * p.tiles_n;
+  long long ksplit = 1;
+  const long long want = 2 * 152;
+  if (accumulate && tiles < want && p.K >= 4 * BK) {
+    ksplit = (want + tiles - 1) / tiles;
+    ksplit = std::min<long long>(ksplit, (p.K + 4 * BK - 1) / (4 * BK));
+    ksplit = std::min<long long>(ksplit, 65535);
+  }
+  long long kchunk = (p.K + ksplit - 1) / ksplit;
+  kchunk = ((kchunk + BK - 1) / BK) * BK;
+  ksplit = (p.K + kchunk - 1) / kchunk;
+  p.kchunk = kchunk;
+  p.atomic = ksplit > 1 ? 1 : 0;
+  p.accumulate = accumulate ? 1 : 0;
+  if (tiles > 0x7fffffffLL) throw std::runtime_error("gather_gemm: grid too large");
+  dim3 grid((unsigned)tiles, (unsigned)ksplit);
+  k_gather_gemm<<<grid, NT, 0, L.stream>>>(p);
+  post(L);
+}
+
+void gather_axpy(const Launch &L, long long M, double alpha, const double *A, const DMap &arow, double *C,
+                 const DMap &crow, long long asize, long long csize) {
+  if (M <= 0) return;
+  if (arow.maxoff >= asize || crow.maxoff >= csize || arow.maxoff < 0 || crow.maxoff < 0)
+    throw std::runtime_error("gather_axpy: index map exceeds operand bounds");
+  k_gather_axpy<<<blocks_for(M, 256), 256, 0, L.stream>>>(M, alpha, A, arow, C, crow);
+  post(L);
+}
+
+void antisym_pack(const Launch &L, const double *Y, int nh, int np, int o, int v, const int *htab, long long nhtup,
+                  const int *ptab, long long nptup, double *out, double scale, bool accumulate) {
+  ensure_perm_tables();
+  long long n = nhtup * nptup;
+  if (n <= 0) return;
+  k_antisym_pack<<<blocks_for(n, 256), 256, 0, L.stream>>>(Y, nh, np, o, v, htab, nhtup, ptab, nptup, out, scale,
+                                                            accumulate ? 1 : 0);
+  post(L);
+}
+
+void unpack_dense(const Launch &L, const double *packed, int nh, int np, int o, int v, const int *htab,
+                  long long nhtup, const int *ptab, long long nptup, double *dense) {
+  ensure_perm_tables();
+  long long dn = 1;
+  for (int k = 0; k < nh; ++k) dn *= o;
+  for (int k = 0; k < np; ++k) dn *= v;
+  FNOCC_CUDA(cudaMemsetAsync(dense, 0, dn * sizeof(double), L.stream));
+  long long n = nhtup * nptup;
+  if (n <= 0) return;
+  k_unpack_dense<<<blocks_for(n, 256), 256, 0, L.stream>>>(packed, nh, np, o, v, htab, nhtup, ptab, nptup, dense);
+  post(L);
+}
+
+void fill(const Launch &L, double *x, double val, long long n) {
+  if (n <= 0) return;
+  k_fill<<<blocks_for(n, 256), 256, 0, L.stream>>>(x, val, n);
+  post(L);
+}
+
+void axpby(const Launch &L, long long n, double a, const double *x, double b, double *y) {
+  if (n <= 0) return;
+  k_axpby<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, a, x, b, y);
+  post(L);
+}
+
+void scale_mask(const Launch &L, long long n, double *x, const unsigned char *mask) {
+  if (n <= 0) return;
+  k_scale_mask<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, x, mask);
+  post(L);
+}
+
+void jacobi_update(const Launch &L, long long n, const double *r, const double *d, double *t) {
+  if (n <= 0) return;
+  k_jacobi_update<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, r, d, t);
+  post(L);
+}
+
+void precondition(const Launch &L, long long n, const double *r, const double *d, double theta,
+                  const unsigned char *mask, double *out) {
+  if (n <= 0) return;
+  k_precondition<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, r, d, theta, mask, out);
+  post(L);
+}
+
+void multi_dot(const Launch &L, long long n, const double *x, const double *Y, long long ld, int nvec,
+               double *dots_dev, DevBuf &part) {
+  if (nvec <= 0) return;
+  int gx = (int)std::min<long long>(std::max<long long>(1, (n + 256 * 8 - 1) / (256 * 8)), 256);
+  part.reserve(sizeof(double) * (size_t)gx * nvec);
+  dim3 grid(gx, nvec);
+  k_dot_partial<<<grid, 256, 0, L.stream>>>(n, x, Y, ld, part.d());
+  post(L);
+  k_dot_final<<<blocks_for(nvec, 128), 128, 0, L.stream>>>(gx, nvec, part.d(), dots_dev);
+  post(L);
+}
+
+void absmax_sumsq(const Launch &L, long long n, const double *x, double *out2_dev, DevBuf &part) {
+  int gx = (int)std::min<long long>(std::max<long long>(1, (n + 256 * 8 - 1) / (256 * 8)), 256);
+  part.reserve(sizeof(double) * 2 * gx);
+  k_absmax_partial<<<gx, 256, 0, L.stream>>>(n, x, part.d());
+  post(L);
+  k_absmax_final<<<1, 32, 0, L.stream>>>(gx, part.d(), out2_dev);
+  post(L);
+}
+
+void spin_orbital_eri(const Launch &L, const double *eri_sp, int n, double *g) {
+  long long ns = 2LL * n;
+  long long tot = ns * ns * ns * ns;
+  k_spin_eri<<<blocks_for(tot, 256), 256, 0, L.stream>>>(eri_sp, n, g);
+  post(L);
+}
+
+void spin_orbital_h(const Launch &L, const double *h_sp, int n, double *hso) {
+  int ns = 2 * n;
+  k_spin_h<<<blocks_for((long long)ns * ns, 256), 256, 0, L.stream>>>(h_sp, n, hso);
+  post(L);
+}
+
+void normal_order(const Launch &L, const double *h, const double *g, int n, int o, double *f, double *eref2_dev) {
+  k_normal_order<<<blocks_for((long long)n * n, 256), 256, 0, L.stream>>>(h, g, n, o, f);
+  post(L);
+  if (eref2_dev) {
+    k_eref<<<1, 256, 0, L.stream>>>(h, g, n, o, eref2_dev);
+    post(L);
+  }
+}
+
+void t1_transform_mats(const Launch &L, const double *t1, int o, int v, double *Lm, double *Mm) {
+  int n = o + v;
+  k_t1_mats<<<blocks_for((long long)n * n, 256), 256, 0, L.stream>>>(t1, o, v, Lm, Mm);
+  post(L);
+}
+
+void jacobi_eig(const Launch &L, double *A, int n, double *evals, double *V, int *info_dev) {
+  if (n > 128) throw std::runtime_error("jacobi_eig: n > 128");
+  size_t smem = sizeof(double) * (size_t)n * n;
+  static bool attr = false;
+  if (!attr) {
+    FNOCC_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8));
+    attr = true;
+  }
+  k_jacobi_eig<<<1, 512, smem, L.stream>>>(A, n, evals, V, info_dev);
+  post(L);
+}
+
+void permute_columns(const Launch &L, const double *in, int rows, int cols_in, const int *perm, int cols_out,
+                     double *out) {
+  long long tot = (long long)rows * cols_out;
+  if (tot <= 0) return;
+  k_permute_columns<<<blocks_for(tot, 256), 256, 0, L.stream>>>(in, rows, cols_in, perm, cols_out, out);
+  post(L);
+}
+
+void fix_phase(const Launch &L, double *c, int rows, int cols) {
+  if (cols <= 0) return;
+  k_fix_phase<<<blocks_for(cols, 128), 128, 0, L.stream>>>(c, rows, cols);
+  post(L);
+}
+
+void lincomb3(const Launch &L, long long n, double *out, const double *a, double alpha, const double *b,
+              double beta, const double *c) {
+  if (n <= 0) return;
+  k_lincomb3<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, out, a, alpha, b, beta, c);
+  post(L);
+}
+
+void mp2_amplitudes(const Launch &L, const double *g, const double *fdiag, int n, int o, double *t) {
+  long long v = n - o;
+  long long tot = (long long)o * o * v * v;
+  if (tot <= 0) return;
+  k_mp2<<<blocks_for(tot, 256), 256, 0, L.stream>>>(g, fdiag, n, o, t);
+  post(L);
+}
+
+void diag_of(const Launch &L, const double *a, int n, double *d) {
+  k_diag<<<blocks_for(n, 128), 128, 0, L.stream>>>(a, n, d);
+  post(L);
+}
+
+void alpha_block(const Launch &L, const double *in, int nso, double *out) {
+  int m = nso / 2;
+  k_alpha_block<<<blocks_for((long long)m * m, 256), 256, 0, L.stream>>>(in, nso, out);
+  post(L);
+}
+
+void eom_diag(const Launch &L, const double *fdiag, int o, int nh, int np, const int *htab, long long nhtup,
+              const int *ptab, long long nptup, double *d) {
+  long long n = nhtup * nptup;
+  if (n <= 0) return;
+  k_eom_diag<<<blocks_for(n, 256), 256, 0, L.stream>>>(fdiag, o, nh, np, htab, nhtup, ptab, nptup, d);
+  post(L);
+}
+
+void ms_mask(const Launch &L, int nh, int np, const int *htab, long long nhtup, const int *ptab, long long nptup,
+             int ms2, unsigned char *mask) {
+  long long n = nhtup * nptup;
+  if (n <= 0) return;
+  k_ms_mask<<<blocks_for(n, 256), 256, 0, L.stream>>>(nh, np, htab, nhtup, ptab, nptup, ms2, mask);
+  post(L);
+}
+
+void cc_denominators(const Launch &L, const double *fdiag, int o, int rank, const int *htab, long long nhtup,
+                     const int *ptab, long long nptup, double *d) {
+  long long n = nhtup * nptup;
+  if (n <= 0) return;
+  k_cc_den<<<blocks_for(n, 256), 256, 0, L.stream>>>(fdiag, o, rank, htab, nhtup, ptab, nptup, d);
+  post(L);
+}
+
+}  // namespace fnocc
