@@ -1,0 +1,355 @@
+"""Benchmark: seconds per converged EOM-CCSDT solve on one GB300 (FP64 path).
+
+Workload (one step): the seeded synthetic closed-shell Hamiltonian with 10
+electrons in 48 spatial orbitals (synth.hamiltonian(10, 48, seed)), frozen
+natural orbitals kept at occupation >= 1e-4, the CCSDT ground state, and the
+four lowest roots of IP-, EA-, DIP- and DEA-EOM-CCSDT (Davidson, diagonal
+guess, residual 1e-8, |d omega| 1e-10). A step is 4 EOM solves; `value` is
+step time / 4.
+
+  value  device-resident inputs (h, eri already in HBM), device time of the
+         steps from CUDA events on the library's stream.
+  e2e    the same through the host-pointer C ABI call (host->device copy of
+         h and eri and the read-back of every result inside the timed region).
+Between timed steps L2 is flushed by writing a 512 MB buffer.
+
+  python bench.py [--steps K] [--warmup W] [--impl fnocc|reference]
+  torchrun --nproc-per-node N bench.py --gpus N   (independent replicas)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+import numpy as np  # noqa: E402
+
+NE, NORB, THRESHOLD, NROOTS = 10, 48, 1e-4, 4
+VARIANTS = ("ip", "ea", "dip", "dea")
+METRIC = "s per converged EOM-CCSDT solve (FP64)"
+# FP64 FMA issue on this part: 2 FMA per clock per SM (measured), 152 SMs, 2070 MHz max
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def config(threshold, seed):
+    return {"workload": "FNO-EOM-CCSDT, %d electrons / %d orbitals synthetic closed-shell (seed %d), "
+                        "FNO occupation >= %g, CCSDT + IP/EA/DIP/DEA x %d roots" % (NE, NORB, seed, threshold, NROOTS),
+            "electrons": NE, "orbitals": NORB, "fno_threshold": threshold, "roots_per_variant": NROOTS,
+            "variants": list(VARIANTS), "l2": "flushed between timed steps (512 MB write)",
+            "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.samples.append([x.strip() for x in line.split(",")])
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(s) > 4 + k and s[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_traffic():
+    """Per-launch DRAM bytes of the contraction kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    src = os.path.join(HERE, "paper_2509_14157_gb300", "csrc", "kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    path = os.path.join(HERE, "profiles", "k_gather_gemm_fno_eom_c2.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernels\.cu sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram bytes per launch \(bench workload\):\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def cpu_baseline(threshold, gpu_counts, budget_s=20.0):
+    """The oracle, as it stands, on a bounded sample of the workload.
+
+    Sample: the oracle's FNO setup (timed in full), then its Wick-term
+    evaluation of sampled elements of every packed CCSDT residual block and of
+    every sigma block of each variant, at the benchmark's sizes. The
+    per-element times, times the element counts, times the residual
+    evaluations and sigma products one converged GPU step needed (gpu_counts),
+    give the oracle's estimated seconds per converged EOM solve."""
+    import itertools
+
+    import synth
+    from oracle import eom as oeom, fno as ofno, packing, wick
+    t0 = time.time()
+    h, eri = synth.hamiltonian(NE, NORB, seed=0)
+    act = ofno.fno_truncate(h, eri, NE // 2, threshold)
+    t_fno = time.time() - t0
+    f, g, o, v = act["f"], act["g"], act["o"], act["v"]
+    rng = np.random.default_rng(0)
+    amps = {"t%d" % r: packing.unpack(rng.normal(0, 0.01, math.comb(o, r) * math.comb(v, r)), r, r, o, v)
+            for r in (1, 2, 3)}
+    nsamp = 4
+
+    def per_element(terms_by_block, blocks, extra):
+        tot = 0.0
+        for (nh, np_, terms), count in zip(terms_by_block, blocks):
+            hs = list(itertools.combinations(range(o), nh))[:nsamp]
+            ps = list(itertools.combinations(range(v), np_))[:nsamp]
+            tup = np.array([a + b for a, b in zip(hs * nsamp, ps * nsamp)][:nsamp], dtype=int).reshape(-1, nh + np_)
+            t1 = time.time()
+            for tl in terms:
+                wick.evaluate_at(tl, nh, np_, f, g, extra, o, v, tup)
+            tot += (time.time() - t1) / len(tup) * count
+        return tot
+
+    cc_blocks = [(r, r, [wick.cc_terms(r)]) for r in (1, 2, 3)]
+    t_res = per_element(cc_blocks, [math.comb(o, r) * math.comb(v, r) for r in (1, 2, 3)], amps)
+    t_sigma = {}
+    for var in VARIANTS:
+        comps = wick.EOM_SPACES[var]
+        ex = dict(amps)
+        for k, (nh, np_) in enumerate(comps):
+            ex["r%d" % (k + 1)] = packing.unpack(rng.normal(0, 0.1, math.comb(o, nh) * math.comb(v, np_)),
+                                                 nh, np_, o, v)
+        blocks = [(nh, np_, [wick.eom_terms(var, oc, ic) for ic in range(3)]) for oc, (nh, np_) in enumerate(comps)]
+        t_sigma[var] = per_element(blocks, [math.comb(o, nh) * math.comb(v, np_) for nh, np_ in comps], ex)
+        if time.time() - t0 > 4 * budget_s:
+            break
+    est = t_fno + gpu_counts["cc_iters"] * t_res + sum(gpu_counts["sigma"][k] * t_sigma.get(k, 0.0) for k in VARIANTS)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": est / len(VARIANTS), "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": ("oracle FNO setup (%.1f s) plus Wick-term evaluation of %d sampled elements per packed "
+                       "block of the CCSDT residual and of each variant's sigma (residual %.3g s, sigma %s s per full "
+                       "evaluation, extrapolated from the samples), scaled by the %d residual evaluations and %s sigma "
+                       "products of one GPU step; sampling took %.1f s"
+                       % (t_fno, nsamp, t_res, {k: round(x, 3) for k, x in t_sigma.items()}, gpu_counts["cc_iters"],
+                          gpu_counts["sigma"], time.time() - t0))}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # counts of a converged step at this workload (measured on the GPU path; kept fixed so the
+    # reference arm needs no GPU)
+    counts = {"cc_iters": 21, "sigma": {"ip": 139, "ea": 117, "dip": 158, "dea": 143}}
+    t0 = time.time()
+    vals = []
+    for _ in range(max(1, args.steps)):
+        vals.append(cpu_baseline(args.threshold, counts)["value"])
+    base = cpu_baseline(args.threshold, counts)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * value * len(VARIANTS),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args.threshold, 0),
+            "cpu_baseline": dict(base, value=value),
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.time() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def run_sigma_only(args):
+    """FNO setup, random amplitudes, then one sigma product of one variant."""
+    import paper_2509_14157_gb300 as pkg
+    import synth
+    h, eri = synth.hamiltonian(NE, NORB, seed=0)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, NE // 2, args.threshold)
+    rng = np.random.default_rng(0)
+    ctx.set_amplitudes(*[rng.normal(0, 0.01, s) for s in ctx.amp_sizes()])
+    x = rng.normal(0, 0.1, sum(ctx.eom_sizes(args.sigma_only)))
+    t0 = time.perf_counter()
+    ctx.eom_sigma(args.sigma_only, x)
+    print(json.dumps({"sigma_only": args.sigma_only, "seconds": time.perf_counter() - t0,
+                      "flops": ctx.flops}), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fnocc", choices=["fnocc", "reference"])
+    ap.add_argument("--threshold", type=float, default=THRESHOLD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS),
+                    help="one sigma product at the workload's size (profiling case)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.sigma_only:
+        return run_sigma_only(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2509_14157_gb300 as pkg
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    seed = rank  # independent replicas: every rank solves its own seeded system
+    h, eri = synth.hamiltonian(NE, NORB, seed=seed)
+    nocc = NE // 2
+    h_dev = torch.from_numpy(h).to(dev)
+    eri_dev = torch.from_numpy(eri).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)  # 512 MB > L2
+    torch.cuda.synchronize()
+    ctx = pkg.Context(local, stream.cuda_stream)
+
+    counts = {"cc_iters": 0, "sigma": {}}
+
+    def step(device_inputs):
+        if device_inputs:
+            ctx.fno_truncate_dev(h_dev.data_ptr(), eri_dev.data_ptr(), NORB, nocc, args.threshold)
+        else:
+            ctx.fno_truncate(h, eri, nocc, args.threshold)
+        res = ctx.ccsdt_solve()
+        if not res["converged"]:
+            raise RuntimeError("CCSDT did not converge")
+        counts["cc_iters"] = res["iters"]
+        out = {}
+        for var in VARIANTS:
+            r = ctx.eom_solve(var, NROOTS)
+            if not r["converged"]:
+                raise RuntimeError("%s-EOM did not converge" % var)
+            counts["sigma"][var] = r["sigma_calls"]
+            out[var] = r["energies"]
+        return res, out
+
+    for _ in range(args.warmup):
+        step(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile(True)
+    ctx.profile_read()
+    launches0, flops0 = ctx.launches, ctx.flops
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    gemm_ms, gemm_flops, gemm_n = ctx.profile_read()
+    launches = ctx.launches - launches0
+    flops = ctx.flops - flops0
+    ctx.profile(False)
+    clocks = sampler.stop()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+        dist.barrier()
+    # end to end: host buffers through the C ABI, copies and read-back inside
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(False)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    solves = len(VARIANTS) * args.steps * world
+    value = total / solves
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+    traffic = read_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config(args.threshold, seed),
+        "tflops": flops * world / total / 1e12 if total > 0 else None,
+        "roofline": {"bound": "alu", "kernel": "k_gather_gemm (FP64 FMA)", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": traffic,
+                     "launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / total if total else None},
+        "e2e": {"value": e2e_total / solves, "unit": "s",
+                "h2d_bytes_per_step": int(h.nbytes + eri.nbytes),
+                "d2h_bytes_per_step": int(8 * (len(VARIANTS) * NROOTS * 2 + (NORB - nocc)))},
+        "gpu_launches": launches, "clocks": clocks,
+        "solver": {"ccsdt_iters": counts["cc_iters"], "sigma_calls": counts["sigma"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.threshold, counts)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -105,7 +105,7 @@ typedef struct {
   double tol_e;     /* |d omega| per root, default 1e-10 */
   int max_sub;      /* subspace size before collapse, default max(4*nroots, nguess+2*nroots) */
   int maxiter;      /* default 200 */
-  int nguess;       /* guess vectors, default nroots */
+  int nguess;       /* guess vectors, default 2*nroots */
 } eom_options;
 
 typedef struct {
@@ -197,8 +197,46 @@ fnocc_status fnocc_get_block(fnocc_ctx *ctx, int which, int root, double *buf, s
  * library's reading). Returns NaN for npts < 1. Pure host function. */
 double xfno_extrapolate(const double *kept_fraction, const double *energy, int npts);
 
+/* Same as fno_truncate with h and eri already in device memory (device
+ * pointers, read on the context stream). */
+fnocc_status fno_truncate_dev(fnocc_ctx *ctx, const double *h_dev, const double *eri_dev, int n,
+                              int nocc, double occ_threshold, const fno_options *opt,
+                              fno_info *out, double *occ);
+
+/* Text of the term list the library derived for one projected equation
+ * (host only, no GPU needed): kind 0 = CCSDT residual of rank out_comp
+ * (0 = energy, 1..3), with variant and in_comp ignored; kind 1 = EOM product
+ * block sigma_{out_comp} <- R_{in_comp} of `variant` (components 0..2).
+ * Terms are over the T1-similarity-transformed Hamiltonian (f, v) and T2, T3;
+ * each line is "coef factor[...] ...", a representative of an orbit of
+ * output-index permutations whose full antisymmetriser the caller applies.
+ * Writes at most len bytes (NUL-terminated) and returns the full length, or
+ * -1 on bad arguments. */
+long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char *buf, size_t len);
+
+/* Text of the contraction plan the library builds for the same equation
+ * (host only): for every term its GEMM steps with their index groups
+ * (packed or not), operands, intermediates and coefficients, planned with
+ * the cost model at sizes (o, v); amortize > 0 marks R-independent steps as
+ * cached. Same return convention as fnocc_equation_text. */
+long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, int v, double amortize,
+                     char *buf, size_t len);
+
 /* Count of kernel launches issued by the context so far. */
 uint64_t fnocc_launch_count(const fnocc_ctx *ctx);
+
+/* Algorithmic FP64 flops of the contraction steps run so far (CCSDT residuals
+ * and sigma products): sum over planned GEMM steps of 2*M*N*K, where M, N, K
+ * count antisymmetry-unique index tuples. */
+double fnocc_flop_count(const fnocc_ctx *ctx);
+
+/* Contraction-kernel timing: when enabled, every launch of the
+ * gather-GEMM-scatter kernel is bracketed by CUDA events on the context
+ * stream. fnocc_profile_read returns the summed device time (ms), the summed
+ * algorithmic flops of those launches and their number, then resets them. */
+fnocc_status fnocc_profile(fnocc_ctx *ctx, int enable);
+fnocc_status fnocc_profile_read(fnocc_ctx *ctx, double *kernel_ms, double *kernel_flops,
+                                uint64_t *launches);
 
 #ifdef __cplusplus
 }

@@ -17,8 +17,10 @@ non-symmetric Davidson method): orthonormal subspace V, projected matrix
 G = V^T sigma(V), Ritz pairs of G ordered by real part, residual
 r = sigma(x) - theta x, diagonal preconditioner (theta - D)^-1 with D built
 from diag(f), Gram-Schmidt (twice), collapse to the Ritz vectors when the
-subspace exceeds max_sub. Guesses are Koopmans-like unit vectors on the
-lowest diagonal elements of the first component.
+subspace exceeds max_sub. Guesses are 2*nroots unit vectors on the lowest
+diagonal elements (of the first component for the Koopmans guess, of the
+whole space for the diagonal guess); with only nroots guesses a low root of
+weak overlap can be missed.
 
 Parity: sigma pinned to the Fock-space definition for all four variants on
 random T and R; eigenvalues pinned to FCI where the operator space spans the
@@ -110,7 +112,7 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
     n = len(diag)
     allowed = np.where(mask)[0]
     if nguess is None:
-        nguess = nroots
+        nguess = 2 * nroots
     nguess = min(nguess, len(allowed))
     nroots = min(nroots, len(allowed))
     if max_sub is None:

@@ -88,6 +88,15 @@ SIGNATURES = {
     "fnocc_dims": (ctypes.c_int, [_cp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]),
     "fnocc_get_block": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]),
     "xfno_extrapolate": (ctypes.c_double, [_dp, _dp, ctypes.c_int]),
+    "fno_truncate_dev": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.POINTER(FnoOptions), ctypes.POINTER(FnoInfo), _dp]),
+    "fnocc_flop_count": (ctypes.c_double, [_cp]),
+    "fnocc_equation_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_char_p, ctypes.c_size_t]),
+    "fnocc_plan_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
+    "fnocc_profile": (ctypes.c_int, [_cp, ctypes.c_int]),
+    "fnocc_profile_read": (ctypes.c_int, [_cp, _dp, _dp, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 _lib = None
@@ -119,6 +128,30 @@ def xfno_extrapolate(kept_fraction, energy):
     f, fp = _arr(kept_fraction)
     e, ep = _arr(energy)
     return float(lib.xfno_extrapolate(fp, ep, len(f)))
+
+
+def equation_text(kind, variant=0, out_comp=0, in_comp=0):
+    """Term list the library derived (host only); see fnocc_equation_text."""
+    lib = load_library()
+    var = VARIANTS.get(variant, variant)
+    n = lib.fnocc_equation_text(kind, var, out_comp, in_comp, None, 0)
+    if n < 0:
+        raise ValueError("bad equation request")
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.fnocc_equation_text(kind, var, out_comp, in_comp, buf, n + 1)
+    return buf.value.decode()
+
+
+def plan_text(kind, variant=0, out_comp=0, in_comp=0, o=10, v=30, amortize=0.0):
+    """Contraction plan the library builds (host only); see fnocc_plan_text."""
+    lib = load_library()
+    var = VARIANTS.get(variant, variant)
+    n = lib.fnocc_plan_text(kind, var, out_comp, in_comp, o, v, amortize, None, 0)
+    if n < 0:
+        raise ValueError("bad plan request")
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.fnocc_plan_text(kind, var, out_comp, in_comp, o, v, amortize, buf, n + 1)
+    return buf.value.decode()
 
 
 class Context:
@@ -168,6 +201,28 @@ class Context:
                                           ctypes.byref(info), occ.ctypes.data_as(_dp)))
         return dict(e_rhf=info.e_rhf, e_mp2=info.e_mp2, nkept=info.nkept, nvir=info.nvir,
                     kept_fraction=info.kept_fraction, scf_iters=info.scf_iters, occ=occ)
+
+    def fno_truncate_dev(self, h_ptr, eri_ptr, n, nocc, threshold, criterion="abs", nkeep=0):
+        """h_ptr, eri_ptr: device addresses (e.g. torch tensor data_ptr())."""
+        opt = FnoOptions(CRITERIA[criterion], int(nkeep), 200, 1e-12, 1e-10)
+        info = FnoInfo()
+        occ = np.zeros(n - nocc)
+        self._check(self.lib.fno_truncate_dev(self._h, h_ptr, eri_ptr, int(n), int(nocc), float(threshold),
+                                              ctypes.byref(opt), ctypes.byref(info), occ.ctypes.data_as(_dp)))
+        return dict(e_rhf=info.e_rhf, e_mp2=info.e_mp2, nkept=info.nkept, nvir=info.nvir,
+                    kept_fraction=info.kept_fraction, scf_iters=info.scf_iters, occ=occ)
+
+    @property
+    def flops(self):
+        return float(self.lib.fnocc_flop_count(self._h))
+
+    def profile(self, enable=True):
+        self._check(self.lib.fnocc_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        self._check(self.lib.fnocc_profile_read(self._h, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+        return ms.value, fl.value, int(n.value)
 
     def set_mo_hamiltonian(self, h_mo, eri_mo, nocc):
         h, hp = _arr(h_mo)

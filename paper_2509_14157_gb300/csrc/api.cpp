@@ -8,6 +8,7 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -125,7 +126,9 @@ struct fnocc_ctx {
   bool own_stream = false;
   std::string err;
   uint64_t launches = 0;
-  Launch L() { return Launch{stream, &launches}; }
+  GemmProfile prof;
+  double flops_total = 0;
+  Launch L() { return Launch{stream, &launches, &prof}; }
 
   // active Hamiltonian (spin orbitals, bare)
   bool have_ham = false;
@@ -153,6 +156,8 @@ struct fnocc_ctx {
   // EOM
   std::unique_ptr<ExecEquation> eom_eq[4][3][3];
   DevBuf rd[3], sy[3];
+  uint64_t hbar_version = 0;
+  uint64_t eq_seen[4][3][3] = {};  // H-bar version whose cached flops were counted
   int last_variant = -1, last_nroots = 0;
   size_t last_dim = 0;
   DevBuf eom_vecs;
@@ -208,6 +213,11 @@ long long ipow(long long b, int e) {
 
 const int kEom[4][3][2] = {{{1, 0}, {2, 1}, {3, 2}}, {{0, 1}, {1, 2}, {2, 3}}, {{2, 0}, {3, 1}, {4, 2}}, {{0, 2}, {1, 3}, {2, 4}}};
 const int kSectorMs2[4] = {1, 1, 0, 0};
+// R-independent EOM intermediates are cached per H-bar: the planner charges
+// them 1/kSigmaAmortize of their cost (a Davidson solve takes ~100 products);
+// one cached intermediate may hold at most 2^28 doubles (2 GiB).
+const double kSigmaAmortize = 100.0;
+const double kCacheCapDoubles = double(1LL << 28);
 
 // ---- Hamiltonian installation ---------------------------------------------------
 
@@ -316,6 +326,7 @@ double cc_residual_dev(fnocc_ctx *c, const double *tp, double *rp) {
     flops += c->cc_eq[r]->flops();
   }
   c->flops_cc_last = flops;
+  c->flops_total += flops;
   size_t off = 0;
   for (int r = 1; r <= 3; ++r) {
     antisym_pack(L, c->Y[r].d(), r, r, o, v, c->otab[r].dev.as<int>(), c->otab[r].count, c->vtab[r].dev.as<int>(),
@@ -332,6 +343,8 @@ void require_ham(fnocc_ctx *c) {
 
 // ---- EOM sigma --------------------------------------------------------------
 
+uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic);
+
 void eom_sizes(const fnocc_ctx *c, int var, size_t *s) {
   for (int k = 0; k < 3; ++k) s[k] = (size_t)binom_ll(c->o, kEom[var][k][0]) * binom_ll(c->v, kEom[var][k][1]);
 }
@@ -344,7 +357,9 @@ void ensure_eom_plans(fnocc_ctx *c, int var) {
   }
   for (int oc = 0; oc < 3; ++oc)
     for (int ic = 0; ic < 3; ++ic)
-      if (!c->eom_eq[var][oc][ic]) c->eom_eq[var][oc][ic].reset(new ExecEquation(eom_equation(var, oc, ic), c->o, c->v, rd));
+      if (!c->eom_eq[var][oc][ic])
+        c->eom_eq[var][oc][ic].reset(
+            new ExecEquation(eom_equation(var, oc, ic), c->o, c->v, rd, kSigmaAmortize, kCacheCapDoubles));
 }
 
 // prepares dressed operators and dense T2/T3 from the stored amplitudes
@@ -360,7 +375,10 @@ void prepare_hbar(fnocc_ctx *c) {
                c->vtab[2].count, c->t2d.d());
   unpack_dense(L, tp + c->nt[1] + c->nt[2], 3, 3, o, v, c->otab[3].dev.as<int>(), c->otab[3].count,
                c->vtab[3].dev.as<int>(), c->vtab[3].count, c->t3d.d());
+  ++c->hbar_version;
 }
+
+uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic) { return c->eq_seen[var][oc][ic]; }
 
 void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s) {
   Launch L = c->L();
@@ -397,14 +415,18 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s) {
     c->sy[oc].reserve(sizeof(double) * dn);
     FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, c->stream));
     for (int ic = 0; ic < 3; ++ic) {
-      c->eom_eq[var][oc][ic]->run(L, ops, c->sy[oc].d(), dn, c->scratch);
-      flops += c->eom_eq[var][oc][ic]->flops();
+      ExecEquation &eq = *c->eom_eq[var][oc][ic];
+      if (eq.cache_doubles() > 0 && eq_version(c, var, oc, ic) != c->hbar_version) flops += eq.cached_flops();
+      eq.run(L, ops, c->sy[oc].d(), dn, c->scratch, c->hbar_version);
+      eq_version(c, var, oc, ic) = c->hbar_version;
+      flops += eq.flops();
     }
     antisym_pack(L, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
                  c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
     off += sz[oc];
   }
   c->flops_sigma_last = flops;
+  c->flops_total += flops;
 }
 
 // ---- small helpers on device vectors ---------------------------------------------
@@ -603,6 +625,7 @@ void fnocc_destroy(fnocc_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   bool own = c->own_stream;
   cudaStream_t s = c->stream;
+  for (auto ev : c->prof.pool) cudaEventDestroy(ev);
   delete c;
   if (own && s) cudaStreamDestroy(s);
 }
@@ -640,8 +663,8 @@ fnocc_status fnocc_dims(const fnocc_ctx *c, int *o, int *v, double *e_ref) {
   return FNOCC_OK;
 }
 
-fnocc_status fno_truncate(fnocc_ctx *c, const double *h, const double *eri, int n, int nocc, double thr,
-                          const fno_options *opt, fno_info *out, double *occ_out) {
+static fnocc_status fno_truncate_impl(fnocc_ctx *c, const double *h, const double *eri, bool on_device, int n,
+                                      int nocc, double thr, const fno_options *opt, fno_info *out, double *occ_out) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
     if (!h || !eri || n <= 1 || nocc <= 0 || nocc >= n || n > 128) throw StatusError(FNOCC_E_INVALID, "invalid dimensions");
@@ -660,8 +683,15 @@ fnocc_status fno_truncate(fnocc_ctx *c, const double *h, const double *eri, int 
     FNOCC_CUDA(cudaSetDevice(c->device));
     Launch L = c->L();
     const size_t n2 = (size_t)n * n, n4 = n2 * n2;
-    to_dev(c, c->h_ao, h, n2);
-    to_dev(c, c->eri_ao, eri, n4);
+    if (on_device) {
+      c->h_ao.reserve(n2 * sizeof(double));
+      c->eri_ao.reserve(n4 * sizeof(double));
+      FNOCC_CUDA(cudaMemcpyAsync(c->h_ao.p, h, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      FNOCC_CUDA(cudaMemcpyAsync(c->eri_ao.p, eri, n4 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      to_dev(c, c->h_ao, h, n2);
+      to_dev(c, c->eri_ao, eri, n4);
+    }
     c->c_mo.reserve(sizeof(double) * n2);
     c->dens.reserve(sizeof(double) * n2);
     c->fock.reserve(sizeof(double) * n2);
@@ -881,6 +911,48 @@ fnocc_status fno_truncate(fnocc_ctx *c, const double *h, const double *eri, int 
   });
 }
 
+fnocc_status fno_truncate(fnocc_ctx *c, const double *h, const double *eri, int n, int nocc, double thr,
+                          const fno_options *opt, fno_info *out, double *occ_out) {
+  return fno_truncate_impl(c, h, eri, false, n, nocc, thr, opt, out, occ_out);
+}
+
+fnocc_status fno_truncate_dev(fnocc_ctx *c, const double *h, const double *eri, int n, int nocc, double thr,
+                              const fno_options *opt, fno_info *out, double *occ_out) {
+  return fno_truncate_impl(c, h, eri, true, n, nocc, thr, opt, out, occ_out);
+}
+
+double fnocc_flop_count(const fnocc_ctx *c) { return c ? c->flops_total : 0.0; }
+
+fnocc_status fnocc_profile(fnocc_ctx *c, int enable) {
+  if (!c) return FNOCC_E_INVALID;
+  c->prof.enabled = enable != 0;
+  return FNOCC_OK;
+}
+
+fnocc_status fnocc_profile_read(fnocc_ctx *c, double *ms, double *flops, uint64_t *launches) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    GemmProfile &pr = c->prof;
+    FNOCC_CUDA(cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < pr.pairs.size(); ++i) {
+      float t = 0;
+      FNOCC_CUDA(cudaEventElapsedTime(&t, pr.pool[pr.pairs[i].first], pr.pool[pr.pairs[i].second]));
+      pr.ms += t;
+      pr.flop_sum += pr.flops[i];
+      ++pr.launches;
+    }
+    pr.pairs.clear();
+    pr.flops.clear();
+    if (ms) *ms = pr.ms;
+    if (flops) *flops = pr.flop_sum;
+    if (launches) *launches = pr.launches;
+    pr.ms = 0;
+    pr.flop_sum = 0;
+    pr.launches = 0;
+    return FNOCC_OK;
+  });
+}
+
 fnocc_status fnocc_set_amplitudes(fnocc_ctx *c, const double *t1, const double *t2, const double *t3) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
@@ -895,6 +967,8 @@ fnocc_status fnocc_set_amplitudes(fnocc_ctx *c, const double *t1, const double *
                                  c->stream));
     sync(c);
     c->have_amps = true;
+    c->rpk.reserve(sizeof(double) * std::max<size_t>(tot, 1));
+    c->e_corr = cc_residual_dev(c, c->tpk.d(), c->rpk.d());
     return FNOCC_OK;
   });
 }
@@ -1140,7 +1214,7 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
       }
     if (allowed.empty()) throw StatusError(FNOCC_E_INVALID, "empty spin sector");
     int nr = std::min<long long>(nroots, (long long)allowed.size());
-    int ng = o.nguess > 0 ? o.nguess : nr;
+    int ng = o.nguess > 0 ? o.nguess : 2 * nr;
     ng = std::min<long long>(ng, (long long)allowed.size());
     int max_sub = o.max_sub > 0 ? o.max_sub : std::max(4 * nr, ng + 2 * nr);
     if (max_sub < ng + nr) max_sub = ng + nr;
@@ -1330,6 +1404,86 @@ fnocc_status fnocc_get_block(fnocc_ctx *c, int which, int root, double *buf, siz
     }
     throw StatusError(FNOCC_E_INVALID, "unknown block");
   });
+}
+
+long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char *buf, size_t len) {
+  try {
+    std::string s;
+    if (kind == 0) {
+      if (out_comp < 0 || out_comp > 3) return -1;
+      s = equation_to_string(cc_equation(out_comp));
+    } else if (kind == 1) {
+      if (variant < 0 || variant > 3 || out_comp < 0 || out_comp > 2 || in_comp < 0 || in_comp > 2) return -1;
+      s = equation_to_string(eom_equation(variant, out_comp, in_comp));
+    } else {
+      return -1;
+    }
+    if (buf && len > 0) {
+      size_t n = std::min(len - 1, s.size());
+      std::memcpy(buf, s.data(), n);
+      buf[n] = 0;
+    }
+    return (long)s.size();
+  } catch (...) {
+    return -1;
+  }
+}
+
+long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, int v, double amortize, char *buf,
+                     size_t len) {
+  try {
+    if (o <= 0 || v <= 0) return -1;
+    Equation eq;
+    if (kind == 0 && out_comp >= 0 && out_comp <= 3)
+      eq = cc_equation(out_comp);
+    else if (kind == 1 && variant >= 0 && variant <= 3 && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2)
+      eq = eom_equation(variant, out_comp, in_comp);
+    else
+      return -1;
+    std::ostringstream os;
+    os.precision(17);
+    auto groups = [&](const std::vector<DimGroup> &gs) {
+      os << " " << gs.size();
+      for (auto &g : gs) {
+        os << " " << g.space << ":" << g.k << ":" << (g.packed ? 1 : 0) << ":";
+        for (size_t i = 0; i < g.labels.size(); ++i) os << (i ? "," : "") << g.labels[i];
+      }
+    };
+    os << eq.nh << " " << eq.np << " " << eq.terms.size() << "\n";
+    for (auto &t : eq.terms) {
+      TermPlan p = plan_term(t, eq.nh, eq.np, o, v, amortize, double(1LL << 28));
+      os << "TERM " << p.steps.size() << " " << p.inter_dims.size() << "\n";
+      for (size_t i = 0; i < p.inter_dims.size(); ++i) {
+        os << "INTER " << i;
+        groups(p.inter_dims[i]);
+        os << "\n";
+      }
+      for (auto &s : p.steps) {
+        os << "STEP " << s.a.kind << " " << s.a.inter << " " << s.b.kind << " " << s.b.inter << " " << (s.to_output ? 1 : 0)
+           << " " << s.out_inter << " " << (s.constant ? 1 : 0) << " " << s.alpha;
+        os << " A";
+        for (int l : s.a.labels) os << " " << l;
+        os << " B";
+        for (int l : s.b.labels) os << " " << l;
+        os << " M";
+        groups(s.mg);
+        os << " K";
+        groups(s.kg);
+        os << " N";
+        groups(s.ng);
+        os << "\n";
+      }
+    }
+    std::string str = os.str();
+    if (buf && len > 0) {
+      size_t n = std::min(len - 1, str.size());
+      std::memcpy(buf, str.data(), n);
+      buf[n] = 0;
+    }
+    return (long)str.size();
+  } catch (...) {
+    return -1;
+  }
 }
 
 double xfno_extrapolate(const double *f, const double *e, int npts) {

@@ -62,9 +62,20 @@ struct DMap {
   long long maxoff = 0;  // host-side bound: sum over groups of the largest table entry
 };
 
+// Optional event timing of contraction launches (owned by a context).
+struct GemmProfile {
+  bool enabled = false;
+  std::vector<cudaEvent_t> pool;    // events, reused
+  std::vector<std::pair<int, int>> pairs;  // (start, stop) indices into pool
+  std::vector<double> flops;        // per recorded launch
+  double ms = 0, flop_sum = 0;
+  uint64_t launches = 0;
+};
+
 struct Launch {
   cudaStream_t stream;
-  uint64_t *counter;  // incremented per kernel launch
+  uint64_t *counter;      // incremented per kernel launch
+  GemmProfile *prof = nullptr;
 };
 
 // C[crow(m) + ccol(n)] (+)= alpha * sum_k A[arow(m)+acol(k)] * B[brow(k)+bcol(n)]

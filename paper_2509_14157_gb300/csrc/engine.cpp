@@ -39,47 +39,68 @@ void TupleTable::build(int n_, int k_) {
 
 namespace {
 
-// Storage description of an operand: label -> (stride, base offset of its space)
-struct Storage {
+// Storage description of an operand: a list of dimensions, each holding one
+// label (plain index) or a packed group of labels stored as sorted tuples.
+struct SDim {
   std::vector<int> labels;
-  std::vector<long long> stride;
-  std::vector<long long> base;
-  long long find(int lab, long long *st, long long *bs) const {
-    for (size_t i = 0; i < labels.size(); ++i)
-      if (labels[i] == lab) {
-        *st = stride[i];
-        *bs = base[i];
-        return 1;
-      }
-    throw std::runtime_error("engine: label not in operand storage");
+  bool packed = false;
+  long long size = 0, stride = 0, base = 0;  // base: offset of the label's space (full tensors)
+};
+
+struct Storage {
+  std::vector<SDim> dims;
+  long long total() const {
+    long long t = 1;
+    for (auto &d : dims) t *= d.size;
+    return t;
   }
 };
 
+void finish_strides(Storage &s) {
+  long long st = 1;
+  for (int i = (int)s.dims.size() - 1; i >= 0; --i) {
+    s.dims[i].stride = st;
+    st *= s.dims[i].size;
+  }
+}
+
 Storage dense_storage(const std::vector<int> &labels, int o, int v) {
   Storage s;
-  s.labels = labels;
-  s.stride.resize(labels.size());
-  s.base.assign(labels.size(), 0);
-  long long st = 1;
-  for (int i = (int)labels.size() - 1; i >= 0; --i) {
-    s.stride[i] = st;
-    st *= lab_space(labels[i]) == SP_O ? o : v;
+  for (int lab : labels) {
+    SDim d;
+    d.labels = {lab};
+    d.size = lab_space(lab) == SP_O ? o : v;
+    s.dims.push_back(d);
   }
+  finish_strides(s);
   return s;
 }
 
 Storage full_storage(const std::vector<int> &labels, int o, int v) {
-  const long long n = o + v;
   Storage s;
-  s.labels = labels;
-  s.stride.resize(labels.size());
-  s.base.resize(labels.size());
-  long long st = 1;
-  for (int i = (int)labels.size() - 1; i >= 0; --i) {
-    s.stride[i] = st;
-    st *= n;
-    s.base[i] = lab_space(labels[i]) == SP_O ? 0 : o;
+  for (int lab : labels) {
+    SDim d;
+    d.labels = {lab};
+    d.size = o + v;
+    d.base = lab_space(lab) == SP_O ? 0 : o;
+    s.dims.push_back(d);
   }
+  finish_strides(s);
+  return s;
+}
+
+Storage group_storage(const std::vector<DimGroup> &groups, int o, int v) {
+  Storage s;
+  for (auto &g : groups) {
+    int n = g.space == SP_O ? o : v;
+    SDim d;
+    d.labels = g.labels;
+    d.packed = g.packed && g.k >= 2;
+    d.size = d.packed ? binom_ll(n, g.k) : [&] { long long t = 1; for (int j = 0; j < g.k; ++j) t *= n; return t; }();
+    if (!d.packed && g.k != 1) throw std::runtime_error("engine: unpacked multi-label dimension");
+    s.dims.push_back(d);
+  }
+  finish_strides(s);
   return s;
 }
 
@@ -107,36 +128,53 @@ struct TableBuilder {
     for (size_t g = 0; g < groups.size(); ++g) {
       const DimGroup &dg = groups[g];
       int n = dg.space == SP_O ? o : v;
-      std::vector<long long> st(dg.k), bs(dg.k);
-      for (int j = 0; j < dg.k; ++j) s.find(dg.labels[j], &st[j], &bs[j]);
       p.offs.push_back((long long)host.size());
       long long cnt = 0;
-      std::vector<int> cur(dg.k);
-      if (dg.packed) {
-        for (int j = 0; j < dg.k; ++j) cur[j] = j;
-        if (binom_ll(n, dg.k) > 0)
-          while (true) {
-            long long off = 0;
-            for (int j = 0; j < dg.k; ++j) off += st[j] * (bs[j] + cur[j]);
+      // a packed storage dimension is read only as the same packed group
+      const SDim *whole = nullptr;
+      for (auto &d : s.dims)
+        if (d.packed && d.labels == dg.labels) whole = &d;
+      if (whole) {
+        if (!dg.packed) throw std::runtime_error("engine: packed storage read unpacked");
+        for (long long r = 0; r < whole->size; ++r) host.push_back(r * whole->stride);
+        cnt = whole->size;
+      } else {
+        std::vector<long long> st(dg.k), bs(dg.k);
+        for (int j = 0; j < dg.k; ++j) {
+          const SDim *hit = nullptr;
+          for (auto &d : s.dims)
+            if (!d.packed && d.labels.size() == 1 && d.labels[0] == dg.labels[j]) hit = &d;
+          if (!hit) throw std::runtime_error("engine: label not addressable in operand storage");
+          st[j] = hit->stride;
+          bs[j] = hit->base;
+        }
+        std::vector<int> cur(dg.k);
+        if (dg.packed) {
+          for (int j = 0; j < dg.k; ++j) cur[j] = j;
+          if (binom_ll(n, dg.k) > 0)
+            while (true) {
+              long long off = 0;
+              for (int j = 0; j < dg.k; ++j) off += st[j] * (bs[j] + cur[j]);
+              host.push_back(off);
+              ++cnt;
+              int i = dg.k - 1;
+              while (i >= 0 && cur[i] == n - dg.k + i) --i;
+              if (i < 0) break;
+              ++cur[i];
+              for (int j = i + 1; j < dg.k; ++j) cur[j] = cur[j - 1] + 1;
+            }
+        } else {
+          long long tot = 1;
+          for (int j = 0; j < dg.k; ++j) tot *= n;
+          for (long long x = 0; x < tot; ++x) {
+            long long rem = x, off = 0;
+            for (int j = dg.k - 1; j >= 0; --j) {
+              off += st[j] * (bs[j] + rem % n);
+              rem /= n;
+            }
             host.push_back(off);
             ++cnt;
-            int i = dg.k - 1;
-            while (i >= 0 && cur[i] == n - dg.k + i) --i;
-            if (i < 0) break;
-            ++cur[i];
-            for (int j = i + 1; j < dg.k; ++j) cur[j] = cur[j - 1] + 1;
           }
-      } else {
-        long long tot = 1;
-        for (int j = 0; j < dg.k; ++j) tot *= n;
-        for (long long x = 0; x < tot; ++x) {
-          long long rem = x, off = 0;
-          for (int j = dg.k - 1; j >= 0; --j) {
-            off += st[j] * (bs[j] + rem % n);
-            rem /= n;
-          }
-          host.push_back(off);
-          ++cnt;
         }
       }
       map->n[g] = cnt;
@@ -161,22 +199,33 @@ struct TableBuilder {
 
 }  // namespace
 
-ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2])
+ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize,
+                           double cache_cap)
     : nh_(eq.nh), np_(eq.np), o_(o), v_(v) {
   TableBuilder tb;
   Storage outs = output_storage(nh_, np_, o, v);
   terms_.reserve(eq.terms.size());
   for (const Term &t : eq.terms) {
-    TermPlan plan = plan_term(t, nh_, np_, o, v);
+    TermPlan plan = plan_term(t, nh_, np_, o, v, amortize, cache_cap);
     ExecTerm et;
+    std::vector<char> cached(plan.inter_labels.size(), 0);
+    for (const Step &s : plan.steps)
+      if (!s.to_output && s.constant) cached[s.out_inter] = 1;
     long long off = 0;
-    for (auto &labs : plan.inter_labels) {
-      long long sz = 1;
-      for (int lab : labs) sz *= lab_space(lab) == SP_O ? o : v;
-      et.inter_off.push_back(off);
+    std::vector<Storage> inter_store;
+    for (auto &dims : plan.inter_dims) inter_store.push_back(group_storage(dims, o, v));
+    for (size_t i = 0; i < plan.inter_labels.size(); ++i) {
+      long long sz = inter_store[i].total();
+      if (cached[i]) {
+        et.inter_off.push_back(cache_need_);
+        cache_need_ += sz;
+      } else {
+        et.inter_off.push_back(off);
+        off += sz;
+      }
       et.inter_size.push_back(sz);
-      off += sz;
     }
+    et.inter_cached = cached;
     scratch_need_ = std::max(scratch_need_, off);
     auto storage_of = [&](const Operand &op) -> Storage {
       switch (op.kind) {
@@ -184,7 +233,7 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
         case TK_V:
           return full_storage(op.labels, o, v);
         case TK_INTERMEDIATE:
-          return dense_storage(op.labels, o, v);
+          return inter_store.at(op.inter);
         default:
           return dense_storage(op.labels, o, v);
       }
@@ -196,11 +245,12 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
       x.a_inter = s.a.inter;
       x.b_kind = s.b.kind;
       x.b_inter = s.b.inter;
+      x.constant = s.constant;
       x.to_output = s.to_output;
       x.out_inter = s.out_inter;
       x.alpha = s.alpha;
       Storage sa = storage_of(s.a);
-      Storage sc = s.to_output ? outs : dense_storage(plan.inter_labels[s.out_inter], o, v);
+      Storage sc = s.to_output ? outs : inter_store.at(s.out_inter);
       et.steps.push_back(x);
       ExecStep &e = et.steps.back();
       e.M = tb.add(&e.arow, s.mg, sa, o, v);
@@ -211,11 +261,11 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
         tb.add(&e.brow, s.kg, sb, o, v);
         e.N = tb.add(&e.bcol, s.ng, sb, o, v);
         tb.add(&e.ccol, s.ng, sc, o, v);
-        flops_ += 2.0 * double(e.M) * double(e.N) * double(e.K);
+        (s.constant ? cached_flops_ : flops_) += 2.0 * double(e.M) * double(e.N) * double(e.K);
       } else {
         e.N = 1;
         e.K = 1;
-        flops_ += double(e.M);
+        (s.constant ? cached_flops_ : flops_) += double(e.M);
       }
     }
     terms_.push_back(std::move(et));
@@ -224,8 +274,11 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
   tb.upload(tables_);
 }
 
-void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch) const {
+void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch,
+                       uint64_t version) {
   if (scratch_need_ > 0) scratch.reserve(sizeof(double) * (size_t)scratch_need_);
+  const bool refresh = cache_need_ > 0 && version != cache_version_;
+  if (cache_need_ > 0) cache_.reserve(sizeof(double) * (size_t)cache_need_);
   for (const ExecTerm &t : terms_) {
     auto ptr = [&](int kind, int inter) -> const double * {
       switch (kind) {
@@ -236,7 +289,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         case TK_R1: return ops.r[0];
         case TK_R2: return ops.r[1];
         case TK_R3: return ops.r[2];
-        case TK_INTERMEDIATE: return scratch.d() + t.inter_off[inter];
+        case TK_INTERMEDIATE: return (t.inter_cached[inter] ? cache_.d() : scratch.d()) + t.inter_off[inter];
         default: throw std::runtime_error("engine: unknown operand kind");
       }
     };
@@ -254,6 +307,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
       }
     };
     for (const ExecStep &s : t.steps) {
+      if (s.constant && !refresh) continue;  // cached and still valid
       double *C;
       long long csize;
       if (s.to_output) {
@@ -261,7 +315,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         csize = y_size;
       } else {
         csize = t.inter_size[s.out_inter];
-        C = scratch.d() + t.inter_off[s.out_inter];
+        C = (t.inter_cached[s.out_inter] ? cache_.d() : scratch.d()) + t.inter_off[s.out_inter];
         FNOCC_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * t.inter_size[s.out_inter], L.stream));
       }
       const double *A = ptr(s.a_kind, s.a_inter);
@@ -276,6 +330,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
       }
     }
   }
+  if (refresh) cache_version_ = version;
 }
 
 }  // namespace fnocc

@@ -21,6 +21,7 @@ struct Operands {
 
 struct ExecStep {
   int a_kind, a_inter, b_kind, b_inter;
+  bool constant;   // R-independent: run once per H-bar version into the cache
   bool to_output;
   int out_inter;
   long long M, N, K;
@@ -30,19 +31,26 @@ struct ExecStep {
 
 struct ExecTerm {
   std::vector<ExecStep> steps;
-  std::vector<long long> inter_off;   // offsets (doubles) of intermediates in scratch
+  std::vector<long long> inter_off;   // offsets (doubles) in scratch, or in the cache if cached
   std::vector<long long> inter_size;
+  std::vector<char> inter_cached;
 };
 
 // One equation <mu_out| ... |0> compiled for fixed (o, v) and operand shapes.
 class ExecEquation {
  public:
   // rdims: (nh, np) of the three EOM input components (ignored for CC)
-  ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2]);
-  // Y (dense output accumulator [o^nh v^np]) += sum of terms
-  void run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch) const;
+  // amortize > 0: R-independent steps are cached (see plan_term)
+  ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize = 0.0,
+               double cache_cap = 0.0);
+  // Y (dense output accumulator [o^nh v^np]) += sum of terms. version: the
+  // cached R-independent intermediates are recomputed when it changes.
+  void run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch,
+           uint64_t version = 0);
   long long scratch_doubles() const { return scratch_need_; }
-  double flops() const { return flops_; }
+  long long cache_doubles() const { return cache_need_; }
+  double flops() const { return flops_; }              // per run, cached steps excluded
+  double cached_flops() const { return cached_flops_; }  // once per version
   int nh() const { return nh_; }
   int np() const { return np_; }
   size_t nterms() const { return terms_.size(); }
@@ -51,8 +59,10 @@ class ExecEquation {
   int nh_, np_, o_, v_;
   std::vector<ExecTerm> terms_;
   DevBuf tables_;
-  long long scratch_need_ = 0;
-  double flops_ = 0;
+  DevBuf cache_;
+  uint64_t cache_version_ = ~0ULL;
+  long long scratch_need_ = 0, cache_need_ = 0;
+  double flops_ = 0, cached_flops_ = 0;
 };
 
 // Sorted index tuples (lexicographic) of k out of n, as a device int table.

@@ -599,8 +599,37 @@ void gather_gemm(const Launch &L, long long M, long long N, long long K, double 
   p.accumulate = accumulate ? 1 : 0;
   if (tiles > 0x7fffffffLL) throw std::runtime_error("gather_gemm: grid too large");
   dim3 grid((unsigned)tiles, (unsigned)ksplit);
+  GemmProfile *pr = L.prof;
+  int e0 = -1, e1 = -1;
+  if (pr && pr->enabled) {
+    while (pr->pool.size() < 2 * pr->pairs.size() + 2) {
+      cudaEvent_t ev;
+      FNOCC_CUDA(cudaEventCreate(&ev));
+      pr->pool.push_back(ev);
+    }
+    e0 = (int)(2 * pr->pairs.size());
+    e1 = e0 + 1;
+    FNOCC_CUDA(cudaEventRecord(pr->pool[e0], L.stream));
+  }
   k_gather_gemm<<<grid, NT, 0, L.stream>>>(p);
   post(L);
+  if (e0 >= 0) {
+    FNOCC_CUDA(cudaEventRecord(pr->pool[e1], L.stream));
+    pr->pairs.push_back({e0, e1});
+    pr->flops.push_back(2.0 * double(M) * double(N) * double(p.K));
+    if (pr->pairs.size() >= 4096) {  // fold completed pairs to bound the pool
+      FNOCC_CUDA(cudaEventSynchronize(pr->pool[e1]));
+      for (size_t i = 0; i < pr->pairs.size(); ++i) {
+        float t = 0;
+        FNOCC_CUDA(cudaEventElapsedTime(&t, pr->pool[pr->pairs[i].first], pr->pool[pr->pairs[i].second]));
+        pr->ms += t;
+        pr->flop_sum += pr->flops[i];
+        ++pr->launches;
+      }
+      pr->pairs.clear();
+      pr->flops.clear();
+    }
+  }
 }
 
 void gather_axpy(const Launch &L, long long M, double alpha, const double *A, const DMap &arow, double *C,

@@ -462,7 +462,9 @@ namespace {
 
 struct Node {
   Operand op;
-  std::vector<std::vector<int>> anti;  // antisymmetric label groups (size >= 2)
+  std::vector<std::vector<int>> anti;    // antisymmetric label groups (size >= 2)
+  std::vector<std::vector<int>> packed;  // groups stored as sorted tuples (intermediates only)
+  bool variable = false;                 // contains an EOM vector R
 };
 
 std::vector<std::vector<int>> factor_anti_groups(const Factor &f) {
@@ -523,6 +525,7 @@ std::vector<DimGroup> make_groups(const std::vector<int> &labels,
           g.space = lab_space(free[0]);
           g.k = (int)free.size();
           g.packed = true;
+          std::sort(free.begin(), free.end());  // canonical tuple-to-label order
           g.labels = free;
           for (int lab : free) used[std::find(labels.begin(), labels.end(), lab) - labels.begin()] = true;
           *mult *= double(factorial(g.k));
@@ -543,6 +546,26 @@ std::vector<DimGroup> make_groups(const std::vector<int> &labels,
   return out;
 }
 
+// Free dimensions of an intermediate: groups already packed in the operand stay
+// packed; with pack_all every antisymmetric free group is packed as well.
+std::vector<DimGroup> free_groups(const std::vector<int> &labels, const std::vector<std::vector<int>> &anti,
+                                  const std::vector<std::vector<int>> &packed, bool pack_all) {
+  std::vector<std::vector<int>> use = pack_all ? anti : packed;
+  double dummy = 1;
+  std::vector<DimGroup> out = make_groups(labels, use, nullptr, true, &dummy);
+  return out;
+}
+
+bool subset_of_some(const std::vector<int> &g, const std::vector<std::vector<int>> &groups) {
+  for (auto &h : groups) {
+    bool all = true;
+    for (int x : g)
+      if (!contains(h, x)) { all = false; break; }
+    if (all) return true;
+  }
+  return false;
+}
+
 double groups_size(const std::vector<DimGroup> &gs, int o, int v) {
   double s = 1;
   for (auto &g : gs) {
@@ -554,11 +577,12 @@ double groups_size(const std::vector<DimGroup> &gs, int o, int v) {
 
 }  // namespace
 
-TermPlan plan_term(const Term &t, int nh, int np, int o, int v) {
+TermPlan plan_term(const Term &t, int nh, int np, int o, int v, double amortize, double cache_cap) {
   (void)nh; (void)np;
   std::vector<Node> nodes;
   for (auto &f : t.factors) {
     Node n;
+    n.variable = f.kind >= TK_R1 && f.kind <= TK_R3;
     n.op.kind = f.kind;
     for (auto &g : f.groups)
       for (int lab : g) n.op.labels.push_back(lab);
@@ -598,50 +622,82 @@ TermPlan plan_term(const Term &t, int nh, int np, int o, int v) {
         for (int lab : B.op.labels)
           if (!contains(A.op.labels, lab)) fb.push_back(lab);
         if (kl.empty() && cur.size() > 2) continue;  // avoid outer products while others remain
-        bool last = cur.size() == 2;
-        Step s;
-        s.a = A.op;
-        s.b = B.op;
-        double mult = 1;
-        s.kg = make_groups(kl, A.anti, &B.anti, true, &mult);
-        s.mg = make_groups(fa, A.anti, nullptr, last, &mult);
-        s.ng = make_groups(fb, B.anti, nullptr, last, &mult);
-        s.to_output = last;
-        s.alpha = last ? t.coef * mult : mult;
-        double m = groups_size(s.mg, o, v), k = groups_size(s.kg, o, v), n = groups_size(s.ng, o, v);
-        double step_cost = 2.0 * m * n * k + (last ? 0.0 : m * n);
-        TermPlan np2 = plan;
-        Node C;
-        if (!last) {
-          int id = (int)np2.inter_labels.size();
-          s.out_inter = id;
-          std::vector<int> labs;
-          for (auto &g : s.mg) labs.insert(labs.end(), g.labels.begin(), g.labels.end());
-          for (auto &g : s.ng) labs.insert(labs.end(), g.labels.begin(), g.labels.end());
-          np2.inter_labels.push_back(labs);
-          C.op.kind = TK_INTERMEDIATE;
-          C.op.inter = id;
-          C.op.labels = labs;
-          for (auto *src : {&A, &B})
-            for (auto &g : src->anti) {
-              std::vector<int> s2;
-              for (int lab : g)
-                if (contains(labs, lab)) s2.push_back(lab);
-              if (s2.size() >= 2) C.anti.push_back(s2);
-            }
-        }
-        np2.steps.push_back(s);
-        std::vector<Node> nxt;
-        for (size_t q = 0; q < cur.size(); ++q)
-          if (q != i && q != j) nxt.push_back(cur[q]);
-        if (!last) nxt.push_back(C);
-        if (last) {
-          if (best_cost < 0 || cost + step_cost < best_cost) {
-            best = np2;
-            best_cost = cost + step_cost;
+        // a packed group of an operand is either contracted whole with an operand
+        // antisymmetric in it, or stays whole among the free indices
+        bool ok = true;
+        const Node *pairs[2][2] = {{&A, &B}, {&B, &A}};
+        for (auto &pr : pairs) {
+          for (auto &g : pr[0]->packed) {
+            int in = 0;
+            for (int x : g) in += contains(kl, x) ? 1 : 0;
+            if (in != 0 && in != (int)g.size()) ok = false;
+            if (in == (int)g.size() && !subset_of_some(g, pr[1]->anti)) ok = false;
           }
-        } else {
-          rec(nxt, np2, cost + step_cost);
+        }
+        if (!ok) continue;
+        bool last = cur.size() == 2;
+        for (int pack_all = 0; pack_all < (last ? 1 : 2); ++pack_all) {
+          Step s;
+          s.a = A.op;
+          s.b = B.op;
+          double mult = 1;
+          s.kg = make_groups(kl, A.anti, &B.anti, true, &mult);
+          if (last) {
+            s.mg = make_groups(fa, A.anti, nullptr, true, &mult);
+            s.ng = make_groups(fb, B.anti, nullptr, true, &mult);
+          } else {
+            s.mg = free_groups(fa, A.anti, A.packed, pack_all != 0);
+            s.ng = free_groups(fb, B.anti, B.packed, pack_all != 0);
+          }
+          s.to_output = last;
+          s.alpha = last ? t.coef * mult : mult;
+          double m = groups_size(s.mg, o, v), k = groups_size(s.kg, o, v), n = groups_size(s.ng, o, v);
+          double step_cost = 2.0 * m * n * k + (last ? 0.0 : m * n);
+          const bool var = A.variable || B.variable;
+          if (!var && !last && amortize > 0 && m * n <= cache_cap) {
+            s.constant = true;
+            step_cost /= amortize;
+          }
+          TermPlan np2 = plan;
+          Node C;
+          if (!last) {
+            int id = (int)np2.inter_labels.size();
+            s.out_inter = id;
+            std::vector<int> labs;
+            std::vector<DimGroup> dims;
+            for (auto *gs : {&s.mg, &s.ng})
+              for (auto &g : *gs) {
+                labs.insert(labs.end(), g.labels.begin(), g.labels.end());
+                dims.push_back(g);
+                if (g.packed) C.packed.push_back(g.labels);
+              }
+            np2.inter_labels.push_back(labs);
+            np2.inter_dims.push_back(dims);
+            C.op.kind = TK_INTERMEDIATE;
+            C.op.inter = id;
+            C.op.labels = labs;
+            C.variable = var || !s.constant;
+            for (auto *src : {&A, &B})
+              for (auto &g : src->anti) {
+                std::vector<int> s2;
+                for (int lab : g)
+                  if (contains(labs, lab)) s2.push_back(lab);
+                if (s2.size() >= 2) C.anti.push_back(s2);
+              }
+          }
+          np2.steps.push_back(s);
+          std::vector<Node> nxt;
+          for (size_t q = 0; q < cur.size(); ++q)
+            if (q != i && q != j) nxt.push_back(cur[q]);
+          if (!last) nxt.push_back(C);
+          if (last) {
+            if (best_cost < 0 || cost + step_cost < best_cost) {
+              best = np2;
+              best_cost = cost + step_cost;
+            }
+          } else {
+            rec(nxt, np2, cost + step_cost);
+          }
         }
       }
   };

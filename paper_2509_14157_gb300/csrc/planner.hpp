@@ -81,19 +81,27 @@ struct Operand {
 
 struct Step {
   Operand a, b;             // b.kind < 0 for a one-operand (copy) step
+  bool constant = false;    // result independent of R (computed once per H-bar, cached)
   std::vector<DimGroup> mg, kg, ng;  // GEMM dims: rows from a, contraction, columns from b
   bool to_output = false;   // write into the output accumulator
-  int out_inter = -1;       // else the intermediate it creates (layout: mg then ng, unpacked)
+  int out_inter = -1;       // else the intermediate it creates (dims: mg then ng; packed groups
+                            // stored as sorted tuples and only ever consumed whole)
   double alpha = 1.0;       // coefficient incl. packing multiplicities
 };
 
 struct TermPlan {
   std::vector<Step> steps;
-  std::vector<std::vector<int>> inter_labels;  // per intermediate: its labels in storage order
+  std::vector<std::vector<int>> inter_labels;     // per intermediate: its labels in storage order
+  std::vector<std::vector<DimGroup>> inter_dims;  // per intermediate: storage dims (packed groups kept whole)
 };
 
 // Builds the contraction steps of a term for output holes nh, particles np,
 // sized with o and v (used by the cost model that orders contractions).
-TermPlan plan_term(const Term &t, int nh, int np, int o, int v);
+// amortize: steps whose operands do not contain an EOM vector R are computed
+// once and cached, so the cost model charges them 1/amortize of their flops
+// (0 = no caching, every step charged in full). Cached intermediates larger
+// than cache_cap doubles are not cached.
+TermPlan plan_term(const Term &t, int nh, int np, int o, int v, double amortize = 0.0,
+                   double cache_cap = 0.0);
 
 }  // namespace fnocc

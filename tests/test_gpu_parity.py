@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Tolerances (FP64 path): 1e-10 max-abs per packed amplitude or sigma block,
+1e-9 Eh per energy, as fixed for the FP64 path. Sizes span several 64-wide
+GEMM tiles with ragged tails; full-size cases compare sampled elements.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cc, eom, fno, packing, wick
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+AMP_TOL = 1e-10
+E_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2509_14157_gb300 as p
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p.load_library()
+    return p
+
+
+def spin_masked(nh, np_, o, v, seed, scale, ms2=0):
+    x = synth.random_packed(math.comb(o, nh) * math.comb(v, np_), seed, scale)
+    return x * synth.packed_ms_mask(nh, np_, o, v, ms2)
+
+
+def random_amplitudes(o, v, seed=100, scale=0.05):
+    return [spin_masked(r, r, o, v, seed + r, scale) for r in (1, 2, 3)]
+
+
+def random_eom_vector(variant, o, v, seed=7):
+    ms2 = eom.SECTOR_MS2[variant]
+    return np.concatenate([spin_masked(nh, np_, o, v, seed + k, 0.3, ms2)
+                           for k, (nh, np_) in enumerate(wick.EOM_SPACES[variant])])
+
+
+@pytest.mark.parametrize("nocc,n", [(3, 13), (1, 4), (2, 3)])
+def test_ccsdt_residual_random(pkg, nocc, n):
+    """Residuals and Eq. 7 energy for random T1, T2, T3 and a random
+    non-canonical Hamiltonian; (1, 4) has no triples (o = 2), (2, 3) no
+    triple particles (v = 2)."""
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 11 + n)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    ctx = pkg.Context(0)
+    ctx.set_mo_hamiltonian(h, eri, nocc)
+    assert ctx.dims()[:2] == (o, v)
+    assert abs(ctx.dims()[2] - ham["e_ref"]) < 1e-12
+    t = random_amplitudes(o, v)
+    got, e = ctx.ccsdt_residual(*t)
+    ref = cc.residuals_packed(ham["f"], ham["g"], o, v, *t)
+    for a, b in zip(got, ref):
+        assert a.shape == b.shape
+        if b.size:
+            assert np.max(np.abs(a - b)) < AMP_TOL
+    e_ref = cc.energy(ham["f"], ham["g"], o, v, packing.unpack(t[0], 1, 1, o, v), packing.unpack(t[1], 2, 2, o, v))
+    assert abs(e - e_ref) < 1e-12
+    ctx.close()
+
+
+def test_ccsdt_residual_zero_amplitudes(pkg):
+    """T = 0: the residual is <mu|H|Phi_0>: R1 = f_ai, R2 = <ab||ij>, R3 = 0."""
+    h, eri = synth.random_symmetric_mo_hamiltonian(8, 3)
+    ham = fno.mo_hamiltonian(h, eri, 3)
+    o, v = ham["o"], ham["v"]
+    ctx = pkg.Context(0)
+    ctx.set_mo_hamiltonian(h, eri, 3)
+    sizes = ctx.amp_sizes()
+    (r1, r2, r3), e = ctx.ccsdt_residual(*[np.zeros(s) for s in sizes])
+    assert np.max(np.abs(r1 - ham["f"][o:, :o].T.reshape(-1))) < 1e-13
+    assert np.max(np.abs(r2 - packing.pack(ham["g"][o:, o:, :o, :o].transpose(2, 3, 0, 1), 2, 2, o, v))) < 1e-13
+    assert np.max(np.abs(r3)) == 0.0 and e == 0.0
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+def test_eom_sigma_random(pkg, variant):
+    nocc, n = 3, 10
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 29)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    ctx = pkg.Context(0)
+    ctx.set_mo_hamiltonian(h, eri, nocc)
+    t = random_amplitudes(o, v, seed=200)
+    ctx.set_amplitudes(*t)
+    x = random_eom_vector(variant, o, v)
+    got = ctx.eom_sigma(variant, x)
+    td = [packing.unpack(t[r - 1], r, r, o, v) for r in (1, 2, 3)]
+    ref = eom.sigma_packed(variant, ham["f"], ham["g"], o, v, *td, x)
+    assert np.max(np.abs(got - ref)) < AMP_TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("ne,n,thr", [(6, 10, 1e-4), (10, 48, 1e-4), (10, 48, 1e-5), (4, 6, 0.0)])
+def test_fno_truncate(pkg, ne, n, thr):
+    """RHF energy, MP2 energy (Eq. 8-9), natural occupations (Eq. 10),
+    kept count (exact) and kept fraction."""
+    h, eri = synth.hamiltonian(ne, n, seed=0)
+    ref = fno.fno_truncate(h, eri, ne // 2, thr)
+    ctx = pkg.Context(0)
+    got = ctx.fno_truncate(h, eri, ne // 2, thr)
+    assert abs(got["e_rhf"] - ref["e_rhf"]) < E_TOL
+    assert abs(got["e_mp2"] - ref["e_mp2"]) < E_TOL
+    assert got["nkept"] == ref["nkept"]
+    assert np.max(np.abs(got["occ"] - ref["occ"])) < 1e-12
+    assert abs(got["kept_fraction"] - ref["kept_fraction"]) < 1e-12
+    o, v, e_ref = ctx.dims()
+    assert (o, v) == (ref["o"], ref["v"]) and abs(e_ref - ref["e_ref"]) < E_TOL
+    ctx.close()
+
+
+def test_ccsdt_and_eom_small_system(pkg):
+    """Converged CCSDT energy, amplitudes and two roots of every variant for
+    4 electrons in 6 orbitals, against the oracle solved live."""
+    h, eri = synth.hamiltonian(4, 6, seed=0)
+    ref = fno.fno_truncate(h, eri, 2, 0.0)
+    f, g, o, v = ref["f"], ref["g"], ref["o"], ref["v"]
+    rcc = cc.ccsdt(f, g, o, v)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, 2, 0.0)
+    gcc = ctx.ccsdt_solve()
+    assert gcc["converged"]
+    assert abs(gcc["e_corr"] - rcc["e_corr"]) < E_TOL
+    for r in (1, 2, 3):
+        got = ctx.get_block("t%d" % r)
+        assert np.max(np.abs(got - packing.pack(rcc["t%d" % r], r, r, o, v))) < 1e-8
+    for variant in ("ip", "ea", "dip", "dea"):
+        gr = ctx.eom_solve(variant, 2)
+        rr = eom.eom_ccsdt(variant, f, g, o, v, rcc["t1"], rcc["t2"], rcc["t3"], 2)
+        assert gr["converged"] and rr["converged"]
+        assert np.max(np.abs(gr["omegas"] - rr["omega"])) < E_TOL, variant
+    ctx.close()
+
+
+def test_c1_solve_against_oracle_fixture(pkg):
+    """6 electrons / 10 orbitals, FNO 1e-4, CCSDT and three roots of each
+    variant, against values the oracle wrote (tests/golden/make_golden.py)."""
+    path = os.path.join(HERE, "golden", "c1_oracle.json")
+    gold = json.load(open(path))
+    h, eri = synth.hamiltonian(6, 10, seed=0)
+    ctx = pkg.Context(0)
+    info = ctx.fno_truncate(h, eri, 3, 1e-4)
+    assert info["nkept"] == gold["nkept"]
+    assert abs(info["e_rhf"] - gold["e_rhf"]) < E_TOL
+    assert abs(info["e_mp2"] - gold["e_mp2"]) < E_TOL
+    res = ctx.ccsdt_solve()
+    assert res["converged"]
+    assert abs(res["e_corr"] - gold["e_ccsdt_corr"]) < E_TOL
+    for variant, ent in gold["eom"].items():
+        r = ctx.eom_solve(variant, len(ent["omega"]))
+        assert r["converged"]
+        assert np.max(np.abs(r["omegas"] - np.array(ent["omega"]))) < E_TOL, variant
+    ctx.close()
+
+
+def _sample(o, v, nh, np_, count, seed):
+    hs = list(itertools.combinations(range(o), nh))
+    ps = list(itertools.combinations(range(v), np_))
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(hs) * len(ps), size=min(count, len(hs) * len(ps)), replace=False)
+    tuples = np.array([hs[i // len(ps)] + ps[i % len(ps)] for i in idx], dtype=int)
+    return idx, tuples
+
+
+@pytest.fixture(scope="module")
+def c2_system(pkg):
+    h, eri = synth.hamiltonian(10, 48, seed=0)
+    ref = fno.fno_truncate(h, eri, 5, 1e-4)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, 5, 1e-4)
+    yield ref, ctx
+    ctx.close()
+
+
+def test_c2_residual_sampled(c2_system):
+    """10 electrons / 48 orbitals at FNO 1e-4 (the benchmarked workload):
+    residual of random amplitudes at sampled packed elements."""
+    ref, ctx = c2_system
+    f, g, o, v = ref["f"], ref["g"], ref["o"], ref["v"]
+    t = random_amplitudes(o, v, seed=300, scale=0.02)
+    got, e = ctx.ccsdt_residual(*t)
+    amps = {"t%d" % r: packing.unpack(t[r - 1], r, r, o, v) for r in (1, 2, 3)}
+    for r in (1, 2, 3):
+        idx, tup = _sample(o, v, r, r, 48, 17 + r)
+        val = wick.evaluate_at(wick.cc_terms(r), r, r, f, g, amps, o, v, tup)
+        assert np.max(np.abs(got[r - 1][idx] - val)) < AMP_TOL, r
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+def test_c2_sigma_sampled(c2_system, variant):
+    ref, ctx = c2_system
+    f, g, o, v = ref["f"], ref["g"], ref["o"], ref["v"]
+    t = random_amplitudes(o, v, seed=400, scale=0.02)
+    ctx.set_amplitudes(*t)
+    x = random_eom_vector(variant, o, v, seed=50)
+    got = ctx.eom_sigma(variant, x)
+    sizes = ctx.eom_sizes(variant)
+    parts = np.split(x, np.cumsum(sizes)[:-1])
+    comps = wick.EOM_SPACES[variant]
+    amps = {"t%d" % r: packing.unpack(t[r - 1], r, r, o, v) for r in (1, 2, 3)}
+    for k, (nh, np_) in enumerate(comps):
+        amps["r%d" % (k + 1)] = packing.unpack(parts[k], nh, np_, o, v)
+    off = 0
+    for oc, (nh, np_) in enumerate(comps):
+        idx, tup = _sample(o, v, nh, np_, 24, 5 + oc)
+        val = sum(wick.evaluate_at(wick.eom_terms(variant, oc, ic), nh, np_, f, g, amps, o, v, tup)
+                  for ic in range(3))
+        assert np.max(np.abs(got[off + idx] - val)) < AMP_TOL, (variant, oc)
+        off += sizes[oc]

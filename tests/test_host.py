@@ -1,0 +1,144 @@
+"""Host-side tests of libfnocc that need no GPU.
+
+  * the shared library loads and exports every function include/fnocc.h declares;
+  * the equations the library's planner derives (T1-similarity-transformed
+    CCSDT residuals and all twelve EOM product blocks) reproduce the oracle's
+    Wick terms when evaluated on the CPU with T1 = 0;
+  * xfno_extrapolate agrees with the oracle; calls fail with a status, not a
+    crash, when no device is present.
+"""
+import ctypes
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cc, eom, fno, packing, wick, xfno
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+pkg = pytest.importorskip("paper_2509_14157_gb300")
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "fnocc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*[a-zA-Z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "sizeof")))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = pkg.load_library()
+    names = header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding declares a signature for each of them
+    assert set(names) <= set(pkg.SIGNATURES)
+
+
+def test_create_without_device_reports_status():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = pkg.load_library()
+    h = ctypes.c_void_p()
+    st = lib.fnocc_create(ctypes.byref(h), 0, None)
+    assert st != 0 and not h.value
+
+
+def _parse(text):
+    lines = text.strip().splitlines()
+    nh, np_, nt = map(int, lines[0].split())
+    terms = []
+    for ln in lines[1:1 + nt]:
+        parts = ln.split()
+        facs = []
+        for p in parts[1:]:
+            m = re.match(r"(\w+)\[(.*)\]", p)
+            groups = [g.split(",") if g else [] for g in m.group(2).split("|")]
+            facs.append((m.group(1), groups))
+        terms.append((float(parts[0]), facs))
+    return nh, np_, terms
+
+
+def _perm_sign(p):
+    p = list(p)
+    s = 1
+    for a in range(len(p)):
+        while p[a] != a:
+            b = p[a]
+            p[a], p[b] = p[b], p[a]
+            s = -s
+    return s
+
+
+def _evaluate(eq, f, g, amps, o, v):
+    nh, np_, terms = eq
+    letters = "abcdefghijklmnopqrstuvwxyzBCDEFGHJKLMNOPQRSTUVWXYZ"
+    ext = ["I%d" % k for k in range(nh)] + ["A%d" % (nh + k) for k in range(np_)]
+    y = np.zeros((o,) * nh + (v,) * np_)
+    for coef, facs in terms:
+        labs = {e: letters[i] for i, e in enumerate(ext)}
+        subs, ops = [], []
+        for name, groups in facs:
+            flat = [l for gg in groups for l in gg]
+            for l in flat:
+                labs.setdefault(l, letters[len(labs)])
+            subs.append("".join(labs[l] for l in flat))
+            if name in ("f", "v"):
+                sl = tuple(slice(0, o) if l[0] in "Io" else slice(o, None) for l in flat)
+                ops.append((f if name == "f" else g)[sl])
+            else:
+                ops.append(amps[name])
+        y += coef * np.einsum(",".join(subs) + "->" + "".join(labs[e] for e in ext), *ops, optimize=True)
+    out = np.zeros_like(y)
+    for hp in itertools.permutations(range(nh)):
+        for pp in itertools.permutations(range(np_)):
+            out += _perm_sign(hp) * _perm_sign(pp) * np.transpose(y, list(hp) + [nh + x for x in pp])
+    return out
+
+
+@pytest.fixture(scope="module")
+def system():
+    nocc, n = 2, 5
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 7)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    t = {r: packing.unpack(synth.random_packed(packing.packed_size(r, r, o, v), 3 + r, 0.1), r, r, o, v)
+         for r in (2, 3)}
+    return ham, t
+
+
+@pytest.mark.parametrize("rank", [0, 1, 2, 3])
+def test_planner_cc_equations_match_oracle(system, rank):
+    ham, t = system
+    o, v = ham["o"], ham["v"]
+    amps = {"t1": np.zeros((o, v)), "t2": t[2], "t3": t[3]}
+    got = _evaluate(_parse(pkg.equation_text(0, 0, rank)), ham["f"], ham["g"], amps, o, v)
+    ref = wick.evaluate(wick.cc_terms(rank), rank, rank, ham["f"], ham["g"], amps, o, v)
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+def test_planner_eom_equations_match_oracle(system, variant):
+    ham, t = system
+    o, v = ham["o"], ham["v"]
+    comps = wick.EOM_SPACES[variant]
+    rs = [packing.unpack(synth.random_packed(packing.packed_size(nh, np_, o, v), 11 + k, 0.3), nh, np_, o, v)
+          for k, (nh, np_) in enumerate(comps)]
+    amps = {"t1": np.zeros((o, v)), "t2": t[2], "t3": t[3], "r1": rs[0], "r2": rs[1], "r3": rs[2]}
+    ref = eom.sigma_dense(variant, ham["f"], ham["g"], o, v, amps["t1"], t[2], t[3], rs)
+    for oc in range(3):
+        got = sum(_evaluate(_parse(pkg.equation_text(1, variant, oc, ic)), ham["f"], ham["g"], amps, o, v)
+                  for ic in range(3))
+        assert np.max(np.abs(got - ref[oc])) < 1e-12, (variant, oc)
+
+
+def test_xfno_matches_oracle():
+    f = [0.999, 0.9975, 0.995]
+    e = [-1.2001, -1.2004, -1.2011]
+    assert abs(pkg.xfno_extrapolate(f, e) - xfno.extrapolate(f, e)) < 1e-14
+    assert abs(pkg.xfno_extrapolate([1.0], [-3.0]) + 3.0) < 1e-15

@@ -1,0 +1,275 @@
+"""Pins of the CPU oracle against quantities fixed by the paper's definitions
+and by mathematics, independent of the oracle's own formulas.
+
+  * CC residuals (Eq. 6) and energy (Eq. 7), and the EOM products of Eq. 1-4,
+    against the Fock-space definition on random amplitudes (oracle/detspace.py);
+  * CCSDT = FCI for three electrons; EOM-CCSDT = FCI for every root where
+    the operator space spans the whole (N +- m) sector (IP, EA, DEA from two
+    electrons, DIP from four);
+  * MP2 energy and virtual-virtual density (Eq. 8-10) against second-order
+    perturbation theory written out in determinant space;
+  * RHF stationarity; invariance of CCSDT under the FNO rotation at
+    threshold 0; size-extensivity; the non-interacting (Koopmans) limit;
+  * XFNO exactness on linear data; truncation rules.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cc, detspace, eom, fno, packing, wick, xfno
+
+
+def spin_masked(nh, np_, o, v, seed, scale, ms2=0):
+    x = synth.random_packed(math.comb(o, nh) * math.comb(v, np_), seed, scale)
+    return x * synth.packed_ms_mask(nh, np_, o, v, ms2)
+
+
+@pytest.fixture(scope="module")
+def small_system():
+    nocc, n = 2, 5
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 21)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    amps = {r: packing.unpack(spin_masked(r, r, o, v, 40 + r, 0.1), r, r, o, v) for r in (1, 2, 3)}
+    dso = detspace.DefinitionOracle(ham["hso"], ham["g"], o)
+    return ham, amps, dso
+
+
+def test_packing_roundtrip_and_signs():
+    o, v = 5, 6
+    for nh, np_ in [(1, 0), (0, 2), (2, 2), (3, 2), (2, 4), (4, 2)]:
+        x = np.random.default_rng(nh * 10 + np_).normal(size=packing.packed_size(nh, np_, o, v))
+        d = packing.unpack(x, nh, np_, o, v)
+        assert np.array_equal(packing.pack(d, nh, np_, o, v), x)
+        if nh >= 2:  # antisymmetric under a hole swap, zero on repeated holes
+            assert np.allclose(d, -np.swapaxes(d, 0, 1))
+            assert np.all(d[0, 0] == 0)
+        if np_ >= 2:
+            assert np.allclose(d, -np.swapaxes(d, nh, nh + 1))
+
+
+@pytest.mark.parametrize("rank", [1, 2, 3])
+def test_cc_residual_equals_definition(small_system, rank):
+    ham, amps, dso = small_system
+    o, v = ham["o"], ham["v"]
+    a = {"t1": amps[1], "t2": amps[2], "t3": amps[3]}
+    got = wick.evaluate(wick.cc_terms(rank), rank, rank, ham["f"], ham["g"], a, o, v)
+    ref = dso.cc_residual(amps, rank)
+    assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_cc_energy_equals_definition(small_system):
+    ham, amps, dso = small_system
+    o, v = ham["o"], ham["v"]
+    e = cc.energy(ham["f"], ham["g"], o, v, amps[1], amps[2], amps[3])
+    assert abs(e - dso.cc_energy(amps, ham["e_ref"])) < 1e-12
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+def test_eom_sigma_equals_definition(small_system, variant):
+    ham, amps, dso = small_system
+    o, v = ham["o"], ham["v"]
+    comps = wick.EOM_SPACES[variant]
+    rs = [packing.unpack(synth.random_packed(packing.packed_size(nh, np_, o, v), 90 + k, 0.3), nh, np_, o, v)
+          for k, (nh, np_) in enumerate(comps)]
+    got = eom.sigma_dense(variant, ham["f"], ham["g"], o, v, amps[1], amps[2], amps[3], rs)
+    for oc, (nh, np_) in enumerate(comps):
+        ref = dso.eom_sigma(amps, [(rs[k],) + comps[k] for k in range(3)], nh, np_)
+        assert np.max(np.abs(got[oc] - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref))), (variant, oc)
+
+
+def _so_hamiltonian(h, eri):
+    g = fno.spin_orbital_integrals(eri)
+    hso = fno.spin_orbital_one_body(h)
+    return hso, g
+
+
+def test_ccsdt_three_electrons_is_fci():
+    # open-shell 3-electron reference (0a, 0b, 1a) in 5 spatial orbitals
+    h, eri = synth.random_symmetric_mo_hamiltonian(5, 3, scale_h=0.1, scale_eri=0.03)
+    hso, g = _so_hamiltonian(h, eri)
+    o = 3
+    f, e_ref = fno.fock_from_bare(hso, g, o)
+    res = cc.ccsdt(f, g, o, hso.shape[0] - o)
+    assert res["converged"]
+    e_fci = detspace.fci_energies(hso, g, 3, 1)
+    assert abs(e_ref + res["e_corr"] - e_fci[0]) < 1e-9
+
+
+def _dense_roots(variant, act, res, k):
+    f, g, o, v = act["f"], act["g"], act["o"], act["v"]
+    m = eom.sigma_matrix(variant, f, g, o, v, res["t1"], res["t2"], res["t3"])
+    w = np.sort(np.linalg.eigvals(m).real)
+    return act["e_ref"] + res["e_corr"] + w[:k], m.shape[0]
+
+
+@pytest.fixture(scope="module")
+def two_electron():
+    h, eri = synth.hamiltonian(2, 5, seed=36)
+    act = fno.fno_truncate(h, eri, 1, 0.0)
+    res = cc.ccsdt(act["f"], act["g"], act["o"], act["v"])
+    return act, res
+
+
+def test_ccsdt_two_electrons_is_fci(two_electron):
+    act, res = two_electron
+    assert res["converged"]
+    e_fci = detspace.fci_energies(act["hso"], act["g"], 2, 0)
+    assert abs(act["e_ref"] + res["e_corr"] - e_fci[0]) < 1e-9
+
+
+@pytest.mark.parametrize("variant,nelec,ms2", [("ip", 1, 1), ("ea", 3, 1), ("dea", 4, 0)])
+def test_eom_two_electron_reference_is_fci(two_electron, variant, nelec, ms2):
+    act, res = two_electron
+    fci = detspace.fci_energies(act["hso"], act["g"], nelec, ms2)
+    roots, dim = _dense_roots(variant, act, res, len(fci))
+    assert dim == len(fci)  # the operator space spans the whole sector
+    assert np.max(np.abs(roots - fci)) < 1e-8
+
+
+def test_dip_four_electron_reference_is_fci():
+    h, eri = synth.hamiltonian(4, 5, seed=2)
+    act = fno.fno_truncate(h, eri, 2, 0.0)
+    res = cc.ccsdt(act["f"], act["g"], act["o"], act["v"])
+    assert res["converged"]
+    assert np.max(np.abs(res["t3"])) > 1e-6  # triples are active here
+    fci = detspace.fci_energies(act["hso"], act["g"], 2, 0)
+    roots, dim = _dense_roots("dip", act, res, len(fci))
+    assert dim == len(fci)
+    assert np.max(np.abs(roots - fci)) < 1e-8
+
+
+def test_davidson_matches_dense_diagonalisation():
+    h, eri = synth.hamiltonian(4, 5, seed=2)
+    act = fno.fno_truncate(h, eri, 2, 0.0)
+    f, g, o, v = act["f"], act["g"], act["o"], act["v"]
+    res = cc.ccsdt(f, g, o, v)
+    for variant in ("ip", "dea"):
+        dense, _ = _dense_roots(variant, act, res, 3)
+        out = eom.eom_ccsdt(variant, f, g, o, v, res["t1"], res["t2"], res["t3"], 3, tol_res=1e-9)
+        assert out["converged"]
+        got = act["e_ref"] + res["e_corr"] + out["omega"]
+        assert np.max(np.abs(got - dense)) < 1e-9, (variant, got, dense)
+
+
+def test_mp2_energy_and_density_from_perturbation_theory():
+    h, eri = synth.hamiltonian(4, 5, seed=2)
+    scf = fno.rhf(h, eri, 2)
+    c, eps = scf["c"], scf["eps"]
+    act = fno.active_hamiltonian(h, eri, c, 2)
+    hso, g, o = act["hso"], act["g"], act["o"]
+    # oracle formulas (Eq. 8-10)
+    t2 = fno.mp2_amplitudes(act["f"], g, o)
+    e2 = fno.mp2_energy(g, t2, o)
+    d = fno.mp2_vv_density(act["f"], g, o)
+    # determinant space: |psi1> = -sum_D |D><D|H|0> / (E_D - E_0), H0 = sum eps_p n_p
+    fs = detspace.FockSpace(hso.shape[0])
+    hmat = fs.hamiltonian(hso, g)
+    ref = fs.vacuum(range(o))
+    eso = np.repeat(eps, 2)
+    occ_energy = np.array([eso[[p for p in range(len(eso)) if (s >> p) & 1]].sum() for s in fs.states])
+    hv = hmat @ ref
+    e0 = occ_energy[int(np.argmax(ref))]
+    n_e = np.bitwise_count(fs.states)
+    psi1 = np.zeros(fs.dim)
+    sel = (n_e == o) & (ref == 0) & (np.abs(hv) > 0)
+    psi1[sel] = -hv[sel] / (occ_energy[sel] - e0)
+    assert abs(ref @ hmat @ psi1 - e2) < 1e-12
+    vir = list(range(o, hso.shape[0]))
+    dd = np.array([[psi1 @ (fs.string([(a, True), (b, False)]) @ psi1) for b in vir] for a in vir])
+    assert np.max(np.abs(dd - d)) < 1e-10 * np.max(np.abs(d))
+
+
+def test_rhf_is_stationary_and_matches_determinant_energy():
+    h, eri = synth.hamiltonian(6, 10, seed=0)
+    scf = fno.rhf(h, eri, 3)
+    act = fno.active_hamiltonian(h, eri, scf["c"], 3)
+    o = act["o"]
+    assert np.max(np.abs(act["f"][:o, o:])) < 1e-9               # Brillouin
+    assert abs(act["e_ref"] - scf["e"]) < 1e-10                    # <Phi0|H|Phi0>
+    assert np.max(np.abs(np.diag(act["f"]) - np.repeat(scf["eps"], 2))) < 1e-9
+    assert np.max(np.abs(scf["d"] @ scf["d"] - scf["d"])) < 1e-12  # idempotent
+
+
+def test_threshold_zero_reproduces_untruncated_ccsdt():
+    h, eri = synth.hamiltonian(4, 6, seed=0)
+    trunc = fno.fno_truncate(h, eri, 2, 0.0)
+    assert trunc["nkept"] == 4 and abs(trunc["kept_fraction"] - 1.0) < 1e-15
+    scf = fno.rhf(h, eri, 2)
+    canon = fno.active_hamiltonian(h, eri, scf["c"], 2)
+    e1 = cc.ccsdt(trunc["f"], trunc["g"], trunc["o"], trunc["v"])["e_corr"]
+    e2 = cc.ccsdt(canon["f"], canon["g"], canon["o"], canon["v"])["e_corr"]
+    assert abs(e1 - e2) < 1e-10
+
+
+def test_size_extensivity_of_ccsdt():
+    ha, ea = synth.random_symmetric_mo_hamiltonian(3, 5, scale_h=0.1, scale_eri=0.05)
+    hb, eb = synth.random_symmetric_mo_hamiltonian(3, 6, scale_h=0.1, scale_eri=0.05)
+    # well-separated occupied / virtual levels so that each fragment has a clear reference
+    ha[np.diag_indices(3)] = [-1.1, 0.6, 1.4]
+    hb[np.diag_indices(3)] = [-0.9, 0.8, 1.2]
+    # combined orbital order: occupied A, occupied B, virtuals A, virtuals B
+    order = [("a", 0), ("b", 0), ("a", 1), ("a", 2), ("b", 1), ("b", 2)]
+    n = len(order)
+    h = np.zeros((n, n))
+    eri = np.zeros((n,) * 4)
+    for p, (sp, ip) in enumerate(order):
+        for q, (sq, iq) in enumerate(order):
+            if sp == sq:
+                h[p, q] = (ha if sp == "a" else hb)[ip, iq]
+    for idx in itertools.product(range(n), repeat=4):
+        sys_ = {order[k][0] for k in idx}
+        if len(sys_) == 1:
+            src = ea if "a" in sys_ else eb
+            eri[idx] = src[tuple(order[k][1] for k in idx)]
+    e = {}
+    for name, (hh, ee, nocc) in {"a": (ha, ea, 1), "b": (hb, eb, 1), "ab": (h, eri, 2)}.items():
+        ham = fno.mo_hamiltonian(hh, ee, nocc)
+        res = cc.ccsdt(ham["f"], ham["g"], ham["o"], ham["v"], tol_res=1e-12, tol_e=1e-14)
+        assert res["converged"]
+        e[name] = res["e_corr"]
+    assert abs(e["ab"] - e["a"] - e["b"]) < 1e-10
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+def test_noninteracting_limit_is_koopmans(variant):
+    n, nocc = 5, 2
+    eps = np.array([-1.3, -0.7, 0.4, 0.9, 1.6])
+    ham = fno.mo_hamiltonian(np.diag(eps), np.zeros((n,) * 4), nocc)
+    f, g, o, v = ham["f"], ham["g"], ham["o"], ham["v"]
+    res = cc.ccsdt(f, g, o, v)
+    assert abs(res["e_corr"]) < 1e-14
+    out = eom.eom_ccsdt(variant, f, g, o, v, res["t1"], res["t2"], res["t3"], 3)
+    eso = np.repeat(eps, 2)
+    occ, vir = list(range(o)), list(range(o, 2 * n))
+    spin = lambda p: 1 if p % 2 == 0 else -1
+    vals = []
+    for nh, np_ in wick.EOM_SPACES[variant]:
+        for hs in itertools.combinations(occ, nh):
+            for ps in itertools.combinations(vir, np_):
+                if sum(spin(a) for a in ps) - sum(spin(i) for i in hs) == eom.SECTOR_MS2[variant]:
+                    vals.append(sum(eso[a] for a in ps) - sum(eso[i] for i in hs))
+    assert np.max(np.abs(np.sort(out["omega"]) - np.sort(vals)[:3])) < 1e-10
+
+
+def test_xfno_is_exact_on_linear_data():
+    f = np.array([0.999, 0.9975, 0.995])
+    e = -1.5 + 0.3 * (1 - f)
+    assert abs(xfno.extrapolate(f, e) + 1.5) < 1e-14
+    assert abs(xfno.extrapolate([1.0, 1.0], [-2.0, -2.0]) + 2.0) < 1e-15
+
+
+def test_truncation_rules():
+    occ = np.array([1e-2, 5e-3, 1e-4, 1e-4, 5e-5, 1e-6])
+    assert fno.choose_kept(occ, 1e-4) == 4
+    assert fno.choose_kept(occ, 0.0) == 6
+    assert fno.choose_kept(occ, 1.0) == 0
+    assert fno.choose_kept(occ, 0.5, nkeep=2) == 2
+    tot = occ.sum()
+    assert fno.choose_kept(occ, (occ[0] + occ[1]) / tot, criterion="occt") == 2
+    # a degenerate pair straddling the cut is kept whole
+    occ2 = np.array([1e-2, 2e-3, 2e-3, 1e-5])
+    assert fno.choose_kept(occ2, (occ2[0] + occ2[1]) / occ2.sum(), criterion="occt") == 3
