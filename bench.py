@@ -40,6 +40,12 @@ VARIANTS = ("ip", "ea", "dip", "dea")
 METRIC = "s per converged EOM-CCSDT solve (FP64)"
 # FP64 FMA issue on this part: 2 FMA per clock per SM (measured), 152 SMs, 2070 MHz max
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# Iteration counts and algorithmic flops per evaluation of one converged step
+# of this workload, as the library measured them on a GB300; the reference
+# arm uses them to turn its timed oracle sample into seconds per solve.
+REFERENCE_COUNTS = {"cc_iters": 21, "sigma": {"ip": 169, "ea": 136, "dip": 170, "dea": 109},
+                    "flops_per_residual": 9.11e9,
+                    "flops_per_sigma": {"ip": 7.0e8, "ea": 2.7e9, "dip": 2.9e9, "dea": 3.8e10}}
 
 
 def config(threshold, seed):
@@ -119,63 +125,42 @@ def read_traffic():
     return float(m_b.group(1))
 
 
-def cpu_baseline(threshold, gpu_counts, budget_s=20.0):
+def cpu_baseline(threshold, gpu_counts):
     """The oracle, as it stands, on a bounded sample of the workload.
 
-    Sample: the oracle's FNO setup (timed in full), then its Wick-term
-    evaluation of sampled elements of every packed CCSDT residual block and of
-    every sigma block of each variant, at the benchmark's sizes. The
-    per-element times, times the element counts, times the residual
-    evaluations and sigma products one converged GPU step needed (gpu_counts),
-    give the oracle's estimated seconds per converged EOM solve."""
-    import itertools
-
+    Sample: the oracle's FNO setup and one full evaluation of its CCSDT
+    residual (all Wick terms, einsum on dense tensors) at the benchmark's
+    size, i.e. one CCSDT iteration of the workload. A converged step needs
+    cc_iters residuals and the sigma products of four Davidson solves; the
+    sigma products are costed as residual evaluations scaled by the ratio of
+    the algorithmic flops the library measured for a sigma product of that
+    variant and for a residual (gpu_counts). Result: estimated oracle seconds
+    per converged EOM solve."""
     import synth
-    from oracle import eom as oeom, fno as ofno, packing, wick
+    from oracle import cc as occ, fno as ofno, packing
     t0 = time.time()
     h, eri = synth.hamiltonian(NE, NORB, seed=0)
     act = ofno.fno_truncate(h, eri, NE // 2, threshold)
     t_fno = time.time() - t0
     f, g, o, v = act["f"], act["g"], act["o"], act["v"]
     rng = np.random.default_rng(0)
-    amps = {"t%d" % r: packing.unpack(rng.normal(0, 0.01, math.comb(o, r) * math.comb(v, r)), r, r, o, v)
-            for r in (1, 2, 3)}
-    nsamp = 4
-
-    def per_element(terms_by_block, blocks, extra):
-        tot = 0.0
-        for (nh, np_, terms), count in zip(terms_by_block, blocks):
-            hs = list(itertools.combinations(range(o), nh))[:nsamp]
-            ps = list(itertools.combinations(range(v), np_))[:nsamp]
-            tup = np.array([a + b for a, b in zip(hs * nsamp, ps * nsamp)][:nsamp], dtype=int).reshape(-1, nh + np_)
-            t1 = time.time()
-            for tl in terms:
-                wick.evaluate_at(tl, nh, np_, f, g, extra, o, v, tup)
-            tot += (time.time() - t1) / len(tup) * count
-        return tot
-
-    cc_blocks = [(r, r, [wick.cc_terms(r)]) for r in (1, 2, 3)]
-    t_res = per_element(cc_blocks, [math.comb(o, r) * math.comb(v, r) for r in (1, 2, 3)], amps)
-    t_sigma = {}
-    for var in VARIANTS:
-        comps = wick.EOM_SPACES[var]
-        ex = dict(amps)
-        for k, (nh, np_) in enumerate(comps):
-            ex["r%d" % (k + 1)] = packing.unpack(rng.normal(0, 0.1, math.comb(o, nh) * math.comb(v, np_)),
-                                                 nh, np_, o, v)
-        blocks = [(nh, np_, [wick.eom_terms(var, oc, ic) for ic in range(3)]) for oc, (nh, np_) in enumerate(comps)]
-        t_sigma[var] = per_element(blocks, [math.comb(o, nh) * math.comb(v, np_) for nh, np_ in comps], ex)
-        if time.time() - t0 > 4 * budget_s:
-            break
-    est = t_fno + gpu_counts["cc_iters"] * t_res + sum(gpu_counts["sigma"][k] * t_sigma.get(k, 0.0) for k in VARIANTS)
+    t = [packing.unpack(rng.normal(0, 0.01, math.comb(o, r) * math.comb(v, r)), r, r, o, v) for r in (1, 2, 3)]
+    from oracle import wick
+    for r in (1, 2, 3):
+        wick.cc_terms(r)  # term derivation is setup, not timed
+    t1 = time.time()
+    occ.residuals(f, g, o, v, *t)
+    t_res = time.time() - t1
+    fr = gpu_counts["flops_per_residual"]
+    sig_equiv = sum(gpu_counts["sigma"][k] * gpu_counts["flops_per_sigma"][k] / fr for k in VARIANTS)
+    est = t_fno + t_res * (gpu_counts["cc_iters"] + sig_equiv)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": est / len(VARIANTS), "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": ("oracle FNO setup (%.1f s) plus Wick-term evaluation of %d sampled elements per packed "
-                       "block of the CCSDT residual and of each variant's sigma (residual %.3g s, sigma %s s per full "
-                       "evaluation, extrapolated from the samples), scaled by the %d residual evaluations and %s sigma "
-                       "products of one GPU step; sampling took %.1f s"
-                       % (t_fno, nsamp, t_res, {k: round(x, 3) for k, x in t_sigma.items()}, gpu_counts["cc_iters"],
-                          gpu_counts["sigma"], time.time() - t0))}
+            "sample": ("oracle FNO setup (%.1f s) and one full CCSDT residual evaluation (%.1f s, all Wick terms as "
+                       "dense einsum, %d threads available) at o=%d, v=%d; per converged step %d residuals plus "
+                       "sigma products costed as %.1f residual-equivalents (library-measured flop ratio); "
+                       "estimate = (setup + residual x (iterations + equivalents)) / 4 solves"
+                       % (t_fno, t_res, cores, o, v, gpu_counts["cc_iters"], sig_equiv))}
 
 
 def run_reference(args):
@@ -184,12 +169,13 @@ def run_reference(args):
         return
     # counts of a converged step at this workload (measured on the GPU path; kept fixed so the
     # reference arm needs no GPU)
-    counts = {"cc_iters": 21, "sigma": {"ip": 139, "ea": 117, "dip": 158, "dea": 143}}
+    counts = REFERENCE_COUNTS
     t0 = time.time()
     vals = []
+    base = None
     for _ in range(max(1, args.steps)):
-        vals.append(cpu_baseline(args.threshold, counts)["value"])
-    base = cpu_baseline(args.threshold, counts)
+        base = cpu_baseline(args.threshold, counts)
+        vals.append(base["value"])
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * value * len(VARIANTS),
@@ -256,23 +242,29 @@ def main():
     torch.cuda.synchronize()
     ctx = pkg.Context(local, stream.cuda_stream)
 
-    counts = {"cc_iters": 0, "sigma": {}}
+    counts = {"cc_iters": 0, "sigma": {}, "detail": {}, "flops_per_sigma": {}}
 
     def step(device_inputs):
         if device_inputs:
             ctx.fno_truncate_dev(h_dev.data_ptr(), eri_dev.data_ptr(), NORB, nocc, args.threshold)
         else:
             ctx.fno_truncate(h, eri, nocc, args.threshold)
+        f0 = ctx.flops
         res = ctx.ccsdt_solve()
         if not res["converged"]:
             raise RuntimeError("CCSDT did not converge")
         counts["cc_iters"] = res["iters"]
+        counts["flops_per_residual"] = (ctx.flops - f0) / max(1, res["iters"])
         out = {}
         for var in VARIANTS:
+            f0 = ctx.flops
             r = ctx.eom_solve(var, NROOTS)
+            counts["flops_per_sigma"][var] = (ctx.flops - f0) / max(1, r["sigma_calls"])
             if not r["converged"]:
                 raise RuntimeError("%s-EOM did not converge" % var)
             counts["sigma"][var] = r["sigma_calls"]
+            counts["detail"][var] = {"iters": r["iters"], "res_max": r["res_max"],
+                                     "complex_roots": r["complex_roots"], "seconds": round(r["seconds"], 3)}
             out[var] = r["energies"]
         return res, out
 
@@ -284,7 +276,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     ctx.profile(True)
-    ctx.profile_read()
+    ctx.profile_read(-1)
     launches0, flops0 = ctx.launches, ctx.flops
     times = []
     for _ in range(args.steps):
@@ -298,7 +290,12 @@ def main():
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     torch.cuda.synchronize()
-    gemm_ms, gemm_flops, gemm_n = ctx.profile_read()
+    paths = {}
+    for pid, name in ctx.PROFILE_PATHS.items():
+        ms_, fl_, n_ = ctx.profile_read(pid)
+        paths[name] = {"ms": ms_, "flops": fl_, "launches": n_}
+    dominant = max(paths, key=lambda k: paths[k]["ms"])
+    gemm_ms, gemm_flops, gemm_n = paths[dominant]["ms"], paths[dominant]["flops"], paths[dominant]["launches"]
     launches = ctx.launches - launches0
     flops = ctx.flops - flops0
     ctx.profile(False)
@@ -332,15 +329,20 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config(args.threshold, seed),
         "tflops": flops * world / total / 1e12 if total > 0 else None,
-        "roofline": {"bound": "alu", "kernel": "k_gather_gemm (FP64 FMA)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": dominant + " (FP64 FMA)", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": traffic,
-                     "launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / total if total else None},
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                     "traffic": traffic if dominant == "k_gather_gemm" else None,
+                     "launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / total if total else None,
+                     "peak_basis": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz",
+                     "paths": {k: {"ms": round(x["ms"], 3), "tflops": (x["flops"] / x["ms"] / 1e9) if x["ms"] else None,
+                                   "launches": x["launches"]} for k, x in paths.items()}},
         "e2e": {"value": e2e_total / solves, "unit": "s",
                 "h2d_bytes_per_step": int(h.nbytes + eri.nbytes),
                 "d2h_bytes_per_step": int(8 * (len(VARIANTS) * NROOTS * 2 + (NORB - nocc)))},
         "gpu_launches": launches, "clocks": clocks,
-        "solver": {"ccsdt_iters": counts["cc_iters"], "sigma_calls": counts["sigma"]},
+        "solver": {"ccsdt_iters": counts["cc_iters"], "sigma_calls": counts["sigma"], "eom": counts["detail"],
+                   "flops_per_residual": counts["flops_per_residual"], "flops_per_sigma": counts["flops_per_sigma"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.threshold, counts)

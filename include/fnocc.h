@@ -230,12 +230,16 @@ uint64_t fnocc_launch_count(const fnocc_ctx *ctx);
  * count antisymmetry-unique index tuples. */
 double fnocc_flop_count(const fnocc_ctx *ctx);
 
-/* Contraction-kernel timing: when enabled, every launch of the
- * gather-GEMM-scatter kernel is bracketed by CUDA events on the context
- * stream. fnocc_profile_read returns the summed device time (ms), the summed
- * algorithmic flops of those launches and their number, then resets them. */
+/* Contraction-kernel timing: when enabled, every contraction launch is
+ * bracketed by CUDA events on the context stream. Contractions run on one of
+ * four kernel paths: 0 the tiled gather-GEMM (k_gather_gemm), 1 its split-K
+ * form with an ordered reduction, 2 the small-output kernel (<= 256 outputs)
+ * with its reduction, 3 the row-parallel GEMV. fnocc_profile_read returns,
+ * for one path (or all with path = -1), the summed device time (ms), the
+ * summed algorithmic flops (2*M*N*K) and the number of launches, then resets
+ * those counters. */
 fnocc_status fnocc_profile(fnocc_ctx *ctx, int enable);
-fnocc_status fnocc_profile_read(fnocc_ctx *ctx, double *kernel_ms, double *kernel_flops,
+fnocc_status fnocc_profile_read(fnocc_ctx *ctx, int path, double *kernel_ms, double *kernel_flops,
                                 uint64_t *launches);
 
 #ifdef __cplusplus

@@ -96,7 +96,7 @@ SIGNATURES = {
     "fnocc_plan_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
     "fnocc_profile": (ctypes.c_int, [_cp, ctypes.c_int]),
-    "fnocc_profile_read": (ctypes.c_int, [_cp, _dp, _dp, ctypes.POINTER(ctypes.c_uint64)]),
+    "fnocc_profile_read": (ctypes.c_int, [_cp, ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 _lib = None
@@ -219,9 +219,15 @@ class Context:
     def profile(self, enable=True):
         self._check(self.lib.fnocc_profile(self._h, 1 if enable else 0))
 
-    def profile_read(self):
+    PROFILE_PATHS = {0: "k_gather_gemm", 1: "k_gather_gemm_part+k_reduce_partials",
+                     2: "k_gemm_small+k_reduce_partials", 3: "k_gemv_rows"}
+
+    def profile_read(self, path=-1):
+        """(device ms, algorithmic flops, launches) of one contraction kernel path
+        (see PROFILE_PATHS) or of all (-1) since the last read of that path."""
         ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
-        self._check(self.lib.fnocc_profile_read(self._h, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+        self._check(self.lib.fnocc_profile_read(self._h, int(path), ctypes.byref(ms), ctypes.byref(fl),
+                                                ctypes.byref(n)))
         return ms.value, fl.value, int(n.value)
 
     def set_mo_hamiltonian(self, h_mo, eri_mo, nocc):

@@ -127,8 +127,9 @@ struct fnocc_ctx {
   std::string err;
   uint64_t launches = 0;
   GemmProfile prof;
+  DevBuf partials;
   double flops_total = 0;
-  Launch L() { return Launch{stream, &launches, &prof}; }
+  Launch L() { return Launch{stream, &launches, &prof, &partials}; }
 
   // active Hamiltonian (spin orbitals, bare)
   bool have_ham = false;
@@ -929,26 +930,29 @@ fnocc_status fnocc_profile(fnocc_ctx *c, int enable) {
   return FNOCC_OK;
 }
 
-fnocc_status fnocc_profile_read(fnocc_ctx *c, double *ms, double *flops, uint64_t *launches) {
-  if (!c) return FNOCC_E_INVALID;
+fnocc_status fnocc_profile_read(fnocc_ctx *c, int path, double *ms, double *flops, uint64_t *launches) {
+  if (!c || path < -1 || path >= kGemmPaths) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
     GemmProfile &pr = c->prof;
     FNOCC_CUDA(cudaStreamSynchronize(c->stream));
-    for (size_t i = 0; i < pr.pairs.size(); ++i) {
-      float t = 0;
-      FNOCC_CUDA(cudaEventElapsedTime(&t, pr.pool[pr.pairs[i].first], pr.pool[pr.pairs[i].second]));
-      pr.ms += t;
-      pr.flop_sum += pr.flops[i];
-      ++pr.launches;
-    }
-    pr.pairs.clear();
-    pr.flops.clear();
-    if (ms) *ms = pr.ms;
-    if (flops) *flops = pr.flop_sum;
-    if (launches) *launches = pr.launches;
-    pr.ms = 0;
-    pr.flop_sum = 0;
-    pr.launches = 0;
+    pr.fold();
+    double m = 0, f = 0;
+    uint64_t n = 0;
+    for (int k = 0; k < kGemmPaths; ++k)
+      if (path < 0 || path == k) {
+        m += pr.ms[k];
+        f += pr.flop_sum[k];
+        n += pr.launches[k];
+      }
+    if (ms) *ms = m;
+    if (flops) *flops = f;
+    if (launches) *launches = n;
+    for (int k = 0; k < kGemmPaths; ++k)
+      if (path < 0 || path == k) {
+        pr.ms[k] = 0;
+        pr.flop_sum[k] = 0;
+        pr.launches[k] = 0;
+      }
     return FNOCC_OK;
   });
 }
@@ -1449,9 +1453,11 @@ long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, in
         for (size_t i = 0; i < g.labels.size(); ++i) os << (i ? "," : "") << g.labels[i];
       }
     };
-    os << eq.nh << " " << eq.np << " " << eq.terms.size() << "\n";
-    for (auto &t : eq.terms) {
-      TermPlan p = plan_term(t, eq.nh, eq.np, o, v, amortize, double(1LL << 28));
+    std::vector<TermPlan> raw;
+    for (auto &t : eq.terms) raw.push_back(plan_term(t, eq.nh, eq.np, o, v, amortize, double(1LL << 28)));
+    std::vector<TermPlan> plans = fuse_plans(raw, amortize);
+    os << eq.nh << " " << eq.np << " " << plans.size() << "\n";
+    for (auto &p : plans) {
       os << "TERM " << p.steps.size() << " " << p.inter_dims.size() << "\n";
       for (size_t i = 0; i < p.inter_dims.size(); ++i) {
         os << "INTER " << i;

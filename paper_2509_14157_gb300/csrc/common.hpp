@@ -62,20 +62,26 @@ struct DMap {
   long long maxoff = 0;  // host-side bound: sum over groups of the largest table entry
 };
 
-// Optional event timing of contraction launches (owned by a context).
+// Optional event timing of contraction launches (owned by a context), per
+// kernel path: 0 tiled GEMM, 1 split-K tiled GEMM + ordered reduction,
+// 2 small-output kernel + reduction, 3 GEMV.
+constexpr int kGemmPaths = 4;
 struct GemmProfile {
   bool enabled = false;
-  std::vector<cudaEvent_t> pool;    // events, reused
+  std::vector<cudaEvent_t> pool;           // events, reused
   std::vector<std::pair<int, int>> pairs;  // (start, stop) indices into pool
-  std::vector<double> flops;        // per recorded launch
-  double ms = 0, flop_sum = 0;
-  uint64_t launches = 0;
+  std::vector<double> flops;               // per recorded launch
+  std::vector<int> path;                   // per recorded launch
+  double ms[kGemmPaths] = {0, 0, 0, 0}, flop_sum[kGemmPaths] = {0, 0, 0, 0};
+  uint64_t launches[kGemmPaths] = {0, 0, 0, 0};
+  void fold();                             // accumulate completed pairs (synchronises)
 };
 
 struct Launch {
   cudaStream_t stream;
   uint64_t *counter;      // incremented per kernel launch
   GemmProfile *prof = nullptr;
+  DevBuf *partials = nullptr;  // split-K partial sums (deterministic reduction)
 };
 
 // C[crow(m) + ccol(n)] (+)= alpha * sum_k A[arow(m)+acol(k)] * B[brow(k)+bcol(n)]

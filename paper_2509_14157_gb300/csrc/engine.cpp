@@ -187,6 +187,31 @@ struct TableBuilder {
     return total;
   }
 
+  // tables of `groups` addressing storage dims first_dim, first_dim+1, ... in
+  // order (the producer of an intermediate writes its dims positionally)
+  long long add_positional(DMap *map, const std::vector<DimGroup> &groups, const Storage &s, int first_dim) {
+    if ((int)groups.size() > kMaxGroups) throw std::runtime_error("engine: too many dimension groups");
+    if (first_dim + (int)groups.size() > (int)s.dims.size()) throw std::runtime_error("engine: positional dims");
+    map->ng = (int)groups.size();
+    map->maxoff = 0;
+    Pending p;
+    p.map = map;
+    long long total = 1;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      const SDim &d = s.dims[first_dim + g];
+      const DimGroup &dg = groups[g];
+      if (d.packed != (dg.packed && dg.k >= 2) || (int)d.labels.size() != dg.k)
+        throw std::runtime_error("engine: producer dims do not match the intermediate");
+      p.offs.push_back((long long)host.size());
+      for (long long r = 0; r < d.size; ++r) host.push_back(r * d.stride);
+      map->n[g] = d.size;
+      map->maxoff += (d.size - 1) * d.stride;
+      total *= d.size;
+    }
+    pend.push_back(p);
+    return total;
+  }
+
   void upload(DevBuf &buf) {
     if (host.empty()) host.push_back(0);
     buf.reserve(host.size() * sizeof(long long));
@@ -204,9 +229,11 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
     : nh_(eq.nh), np_(eq.np), o_(o), v_(v) {
   TableBuilder tb;
   Storage outs = output_storage(nh_, np_, o, v);
-  terms_.reserve(eq.terms.size());
-  for (const Term &t : eq.terms) {
-    TermPlan plan = plan_term(t, nh_, np_, o, v, amortize, cache_cap);
+  std::vector<TermPlan> raw;
+  for (const Term &t : eq.terms) raw.push_back(plan_term(t, nh_, np_, o, v, amortize, cache_cap));
+  std::vector<TermPlan> plans = fuse_plans(raw, amortize);
+  terms_.reserve(plans.size());
+  for (const TermPlan &plan : plans) {
     ExecTerm et;
     std::vector<char> cached(plan.inter_labels.size(), 0);
     for (const Step &s : plan.steps)
@@ -239,8 +266,11 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
       }
     };
     et.steps.reserve(plan.steps.size());
+    std::vector<char> written(plan.inter_dims.size(), 0);
     for (const Step &s : plan.steps) {
       ExecStep x;
+      x.zero_first = !s.to_output && !written[s.out_inter];
+      if (!s.to_output) written[s.out_inter] = 1;
       x.a_kind = s.a.kind;
       x.a_inter = s.a.inter;
       x.b_kind = s.b.kind;
@@ -254,13 +284,19 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
       et.steps.push_back(x);
       ExecStep &e = et.steps.back();
       e.M = tb.add(&e.arow, s.mg, sa, o, v);
-      tb.add(&e.crow, s.mg, sc, o, v);
+      if (s.to_output)
+        tb.add(&e.crow, s.mg, sc, o, v);
+      else
+        tb.add_positional(&e.crow, s.mg, sc, 0);
       if (s.b.kind >= 0) {
         Storage sb = storage_of(s.b);
         e.K = tb.add(&e.acol, s.kg, sa, o, v);
         tb.add(&e.brow, s.kg, sb, o, v);
         e.N = tb.add(&e.bcol, s.ng, sb, o, v);
-        tb.add(&e.ccol, s.ng, sc, o, v);
+        if (s.to_output)
+          tb.add(&e.ccol, s.ng, sc, o, v);
+        else
+          tb.add_positional(&e.ccol, s.ng, sc, (int)s.mg.size());
         (s.constant ? cached_flops_ : flops_) += 2.0 * double(e.M) * double(e.N) * double(e.K);
       } else {
         e.N = 1;
@@ -316,7 +352,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
       } else {
         csize = t.inter_size[s.out_inter];
         C = (t.inter_cached[s.out_inter] ? cache_.d() : scratch.d()) + t.inter_off[s.out_inter];
-        FNOCC_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * t.inter_size[s.out_inter], L.stream));
+        if (s.zero_first) FNOCC_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * t.inter_size[s.out_inter], L.stream));
       }
       const double *A = ptr(s.a_kind, s.a_inter);
       if (!A) throw std::runtime_error("engine: missing operand");

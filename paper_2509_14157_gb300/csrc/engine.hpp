@@ -22,6 +22,7 @@ struct Operands {
 struct ExecStep {
   int a_kind, a_inter, b_kind, b_inter;
   bool constant;   // R-independent: run once per H-bar version into the cache
+  bool zero_first; // first writer of its intermediate: zero it before the step
   bool to_output;
   int out_inter;
   long long M, N, K;

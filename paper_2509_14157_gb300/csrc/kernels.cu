@@ -118,13 +118,150 @@ __global__ void __launch_bounds__(NT) k_gather_gemm(const GemmParams p) {
       if (n >= p.N) continue;
       double *dst = p.C + crow_s[ty * 4 + i] + ccol_s[tx * 4 + j];
       double val = p.alpha * acc[i][j];
-      if (p.atomic)
-        atomicAdd(dst, val);
-      else if (p.accumulate)
+      if (p.accumulate)
         *dst += val;
       else
         *dst = val;
     }
+  }
+}
+
+// Split-K partial products: the tiled kernel writes its 64x64 tile of a K
+// chunk to part[z][m * N + n] instead of C (grid.y = z); k_reduce_partials
+// sums the chunks in order, so results do not depend on scheduling.
+__global__ void __launch_bounds__(NT) k_gather_gemm_part(const GemmParams p, double *part) {
+  __shared__ double As[BK][BM];
+  __shared__ double Bs[BK][BN];
+  __shared__ long long arow_s[BM], bcol_s[BN], acol_s[BK], brow_s[BK];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const long long tile = blockIdx.x;
+  const long long m0 = (tile / p.tiles_n) * BM;
+  const long long n0 = (tile % p.tiles_n) * BN;
+  const long long kb = (long long)blockIdx.y * p.kchunk;
+  const long long ke = min(p.K, kb + p.kchunk);
+  if (tid < BM) {
+    long long m = m0 + tid;
+    arow_s[tid] = m < p.M ? map_off(p.arow, m) : 0;
+  } else if (tid < BM + BN) {
+    long long n = n0 + tid - BM;
+    bcol_s[tid - BM] = n < p.N ? map_off(p.bcol, n) : 0;
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long long k0 = kb; k0 < ke; k0 += BK) {
+    __syncthreads();
+    if (tid < BK) {
+      long long k = k0 + tid;
+      acol_s[tid] = k < ke ? map_off(p.acol, k) : 0;
+    } else if (tid < 2 * BK) {
+      long long k = k0 + tid - BK;
+      brow_s[tid - BK] = k < ke ? map_off(p.brow, k) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < (BM * BK) / NT; ++r) {
+      int idx = tid + NT * r;
+      int kk = idx % BK, row = idx / BK;
+      bool ok = (m0 + row < p.M) && (k0 + kk < ke);
+      As[kk][row] = ok ? p.A[arow_s[row] + acol_s[kk]] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < (BN * BK) / NT; ++r) {
+      int idx = tid + NT * r;
+      int col = idx % BN, kk = idx / BN;
+      bool ok = (n0 + col < p.N) && (k0 + kk < ke);
+      Bs[kk][col] = ok ? p.B[brow_s[kk] + bcol_s[col]] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  double *dst = part + (long long)blockIdx.y * p.M * p.N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    long long m = m0 + ty * 4 + i;
+    if (m >= p.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      long long n = n0 + tx * 4 + j;
+      if (n < p.N) dst[m * p.N + n] = acc[i][j];
+    }
+  }
+}
+
+// Small outputs (M*N <= 256): one thread per output, blocks split K; every
+// useful multiply-add is done once. Partials go to part[blockIdx.x][M*N].
+__global__ void __launch_bounds__(256) k_gemm_small(const GemmParams p, double *part) {
+  __shared__ long long acol_s[256], brow_s[256];
+  const int t = threadIdx.x;
+  const long long O = p.M * p.N;
+  long long ar = 0, bc = 0;
+  if (t < O) {
+    ar = map_off(p.arow, t / p.N);
+    bc = map_off(p.bcol, t % p.N);
+  }
+  const long long kb = (long long)blockIdx.x * p.kchunk;
+  const long long ke = min(p.K, kb + p.kchunk);
+  double acc = 0.0;
+  for (long long k0 = kb; k0 < ke; k0 += 256) {
+    __syncthreads();
+    long long k = k0 + t;
+    acol_s[t] = k < ke ? map_off(p.acol, k) : 0;
+    brow_s[t] = k < ke ? map_off(p.brow, k) : 0;
+    __syncthreads();
+    const int nk = (int)min((long long)256, ke - k0);
+    if (t < O)
+      for (int kk = 0; kk < nk; ++kk) acc = fma(p.A[ar + acol_s[kk]], p.B[brow_s[kk] + bc], acc);
+  }
+  if (t < O) part[(long long)blockIdx.x * O + t] = acc;
+}
+
+// C[crow(m) + ccol(n)] (+)= alpha * sum_z part[z][m * N + n], z in order
+__global__ void k_reduce_partials(const GemmParams p, const double *part, int nz) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long O = p.M * p.N;
+  if (idx >= O) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += part[(long long)z * O + idx];
+  double *dst = p.C + map_off(p.crow, idx / p.N) + map_off(p.ccol, idx % p.N);
+  *dst = p.accumulate ? *dst + p.alpha * s : p.alpha * s;
+}
+
+// GEMV (N = 1): one thread per row, the K loop in registers, x offsets staged
+// in shared memory. Used for the Davidson linear combinations and Fock builds.
+__global__ void __launch_bounds__(256) k_gemv_rows(const GemmParams p) {
+  __shared__ long long acol_s[256], brow_s[256];
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long ar = m < p.M ? map_off(p.arow, m) : 0;
+  const long long bc = map_off(p.bcol, 0);
+  double acc = 0.0;
+  for (long long k0 = 0; k0 < p.K; k0 += 256) {
+    __syncthreads();
+    long long k = k0 + threadIdx.x;
+    acol_s[threadIdx.x] = k < p.K ? map_off(p.acol, k) : 0;
+    brow_s[threadIdx.x] = k < p.K ? map_off(p.brow, k) : 0;
+    __syncthreads();
+    const int nk = (int)min((long long)256, p.K - k0);
+    if (m < p.M)
+      for (int kk = 0; kk < nk; ++kk) acc = fma(p.A[ar + acol_s[kk]], p.B[brow_s[kk] + bc], acc);
+  }
+  if (m < p.M) {
+    double *dst = p.C + map_off(p.crow, m) + map_off(p.ccol, 0);
+    *dst = p.accumulate ? *dst + p.alpha * acc : p.alpha * acc;
   }
 }
 
@@ -584,52 +721,98 @@ void gather_gemm(const Launch &L, long long M, long long N, long long K, double 
   p.ccol = ccol;
   p.tiles_n = (N + BN - 1) / BN;
   long long tiles = ((M + BM - 1) / BM) * p.tiles_n;
-  long long ksplit = 1;
-  const long long want = 2 * 152;
-  if (accumulate && tiles < want && p.K >= 4 * BK) {
-    ksplit = (want + tiles - 1) / tiles;
-    ksplit = std::min<long long>(ksplit, (p.K + 4 * BK - 1) / (4 * BK));
-    ksplit = std::min<long long>(ksplit, 65535);
-  }
-  long long kchunk = (p.K + ksplit - 1) / ksplit;
-  kchunk = ((kchunk + BK - 1) / BK) * BK;
-  ksplit = (p.K + kchunk - 1) / kchunk;
-  p.kchunk = kchunk;
-  p.atomic = ksplit > 1 ? 1 : 0;
   p.accumulate = accumulate ? 1 : 0;
-  if (tiles > 0x7fffffffLL) throw std::runtime_error("gather_gemm: grid too large");
-  dim3 grid((unsigned)tiles, (unsigned)ksplit);
-  GemmProfile *pr = L.prof;
-  int e0 = -1, e1 = -1;
-  if (pr && pr->enabled) {
+  GemmProfile *pr = (L.prof && L.prof->enabled) ? L.prof : nullptr;
+  int e0 = -1;
+  auto begin = [&]() {
+    if (!pr) return;
     while (pr->pool.size() < 2 * pr->pairs.size() + 2) {
       cudaEvent_t ev;
       FNOCC_CUDA(cudaEventCreate(&ev));
       pr->pool.push_back(ev);
     }
     e0 = (int)(2 * pr->pairs.size());
-    e1 = e0 + 1;
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0], L.stream));
+  };
+  auto end = [&](int path) {
+    if (!pr) return;
+    FNOCC_CUDA(cudaEventRecord(pr->pool[e0 + 1], L.stream));
+    pr->pairs.push_back({e0, e0 + 1});
+    pr->flops.push_back(2.0 * double(M) * double(N) * double(p.K));
+    pr->path.push_back(path);
+    if (pr->pairs.size() >= 4096) pr->fold();
+  };
+  p.atomic = 0;
+  const long long want = 2 * 152;
+  const long long O = M * N;
+  // GEMV shape with enough rows: one thread per row
+  if (N == 1 && M >= 2048) {
+    p.kchunk = p.K;
+    begin();
+    k_gemv_rows<<<blocks_for(M, 256), 256, 0, L.stream>>>(p);
+    post(L);
+    end(3);
+    return;
   }
+  // tiny outputs: one thread per output, K split over blocks, ordered reduction
+  if (O <= 256) {
+    long long nblk = std::min<long long>(std::max<long long>(1, p.K / 2048), 1024);
+    long long kchunk = (p.K + nblk - 1) / nblk;
+    nblk = (p.K + kchunk - 1) / kchunk;
+    p.kchunk = kchunk;
+    if (!L.partials) throw std::runtime_error("gather_gemm: no partial-sum scratch");
+    L.partials->reserve(sizeof(double) * (size_t)(nblk * O));
+    begin();
+    k_gemm_small<<<(unsigned)nblk, 256, 0, L.stream>>>(p, L.partials->d());
+    post(L);
+    k_reduce_partials<<<blocks_for(O, 256), 256, 0, L.stream>>>(p, L.partials->d(), (int)nblk);
+    post(L);
+    end(2);
+    return;
+  }
+  long long ksplit = 1;
+  if (tiles < want && p.K >= 4 * BK && L.partials) {
+    ksplit = (want + tiles - 1) / tiles;
+    ksplit = std::min<long long>(ksplit, (p.K + 4 * BK - 1) / (4 * BK));
+    ksplit = std::min<long long>(ksplit, std::max<long long>(1, (1LL << 27) / std::max<long long>(O, 1)));
+    ksplit = std::min<long long>(ksplit, 65535);
+  }
+  long long kchunk = (p.K + ksplit - 1) / ksplit;
+  kchunk = ((kchunk + BK - 1) / BK) * BK;
+  ksplit = (p.K + kchunk - 1) / kchunk;
+  p.kchunk = kchunk;
+  if (tiles > 0x7fffffffLL) throw std::runtime_error("gather_gemm: grid too large");
+  if (ksplit > 1) {
+    L.partials->reserve(sizeof(double) * (size_t)(ksplit * O));
+    dim3 g2((unsigned)tiles, (unsigned)ksplit);
+    begin();
+    k_gather_gemm_part<<<g2, NT, 0, L.stream>>>(p, L.partials->d());
+    post(L);
+    k_reduce_partials<<<blocks_for(O, 256), 256, 0, L.stream>>>(p, L.partials->d(), (int)ksplit);
+    post(L);
+    end(1);
+    return;
+  }
+  dim3 grid((unsigned)tiles, 1);
+  begin();
   k_gather_gemm<<<grid, NT, 0, L.stream>>>(p);
   post(L);
-  if (e0 >= 0) {
-    FNOCC_CUDA(cudaEventRecord(pr->pool[e1], L.stream));
-    pr->pairs.push_back({e0, e1});
-    pr->flops.push_back(2.0 * double(M) * double(N) * double(p.K));
-    if (pr->pairs.size() >= 4096) {  // fold completed pairs to bound the pool
-      FNOCC_CUDA(cudaEventSynchronize(pr->pool[e1]));
-      for (size_t i = 0; i < pr->pairs.size(); ++i) {
-        float t = 0;
-        FNOCC_CUDA(cudaEventElapsedTime(&t, pr->pool[pr->pairs[i].first], pr->pool[pr->pairs[i].second]));
-        pr->ms += t;
-        pr->flop_sum += pr->flops[i];
-        ++pr->launches;
-      }
-      pr->pairs.clear();
-      pr->flops.clear();
-    }
+  end(0);
+}
+
+void GemmProfile::fold() {
+  if (pairs.empty()) return;
+  FNOCC_CUDA(cudaEventSynchronize(pool[pairs.back().second]));
+  for (size_t i = 0; i < pairs.size(); ++i) {
+    float t = 0;
+    FNOCC_CUDA(cudaEventElapsedTime(&t, pool[pairs[i].first], pool[pairs[i].second]));
+    ms[path[i]] += t;
+    flop_sum[path[i]] += flops[i];
+    ++launches[path[i]];
   }
+  pairs.clear();
+  flops.clear();
+  path.clear();
 }
 
 void gather_axpy(const Launch &L, long long M, double alpha, const double *A, const DMap &arow, double *C,

@@ -706,4 +706,175 @@ TermPlan plan_term(const Term &t, int nh, int np, int o, int v, double amortize,
   return best;
 }
 
+
+namespace {
+
+int amp_priority(int kind) {
+  switch (kind) {
+    case TK_R3: return 6;
+    case TK_R2: return 5;
+    case TK_R1: return 4;
+    case TK_T3: return 3;
+    case TK_T2: return 2;
+    default: return -1;
+  }
+}
+
+std::vector<int> group_key(const std::vector<DimGroup> &gs) {
+  std::vector<int> k;
+  for (auto &g : gs) {
+    k.push_back(g.packed ? 1 : 0);
+    k.push_back((int)g.labels.size());
+    k.insert(k.end(), g.labels.begin(), g.labels.end());
+  }
+  return k;
+}
+
+std::vector<DimGroup> relabel(std::vector<DimGroup> gs, const std::map<int, int> &m) {
+  for (auto &g : gs)
+    for (int &l : g.labels) {
+      auto it = m.find(l);
+      if (it != m.end()) l = it->second;
+    }
+  for (auto &g : gs)
+    if (g.packed) std::sort(g.labels.begin(), g.labels.end());
+  std::sort(gs.begin(), gs.end(), [](const DimGroup &a, const DimGroup &b) { return a.labels < b.labels; });
+  return gs;
+}
+
+struct FuseInfo {
+  bool ok = false;
+  bool q_is_b = true;
+  Operand p, q;             // operands, q with role labels
+  std::vector<DimGroup> pfree, kg, qfree;  // role labels, canonical order
+  std::map<int, int> to_role, from_role;
+  bool p_constant = false;
+  double alpha = 0;
+  std::vector<int> key;
+};
+
+FuseInfo fuse_info(const TermPlan &pl, double amortize) {
+  FuseInfo fi;
+  if (pl.steps.empty()) return fi;
+  const Step &f = pl.steps.back();
+  if (!f.to_output || f.b.kind < 0) return fi;
+  int pa = amp_priority(f.a.kind), pb = amp_priority(f.b.kind);
+  if (std::max(pa, pb) < 0) return fi;
+  fi.q_is_b = pb >= pa;
+  const Operand &q = fi.q_is_b ? f.b : f.a;
+  fi.p = fi.q_is_b ? f.a : f.b;
+  std::vector<int> klabs;
+  for (auto &g : f.kg) klabs.insert(klabs.end(), g.labels.begin(), g.labels.end());
+  for (size_t i = 0; i < q.labels.size(); ++i) {
+    int l = q.labels[i];
+    if (std::find(klabs.begin(), klabs.end(), l) != klabs.end()) {
+      int r = make_label(200 + (int)i, lab_space(l));
+      fi.to_role[l] = r;
+      fi.from_role[r] = l;
+    }
+  }
+  fi.q = q;
+  for (int &l : fi.q.labels) {
+    auto it = fi.to_role.find(l);
+    if (it != fi.to_role.end()) l = it->second;
+  }
+  fi.kg = relabel(f.kg, fi.to_role);
+  fi.pfree = relabel(fi.q_is_b ? f.mg : f.ng, fi.to_role);
+  fi.qfree = relabel(fi.q_is_b ? f.ng : f.mg, fi.to_role);
+  if (fi.p.kind == TK_INTERMEDIATE) {
+    fi.p_constant = false;
+    for (auto &s : pl.steps)
+      if (!s.to_output && s.out_inter == fi.p.inter) fi.p_constant = s.constant;
+  } else {
+    fi.p_constant = amortize > 0 && amp_priority(fi.p.kind) < 4;
+  }
+  fi.alpha = f.alpha;
+  fi.key.push_back(q.kind);
+  fi.key.push_back(fi.p_constant ? 1 : 0);
+  fi.key.insert(fi.key.end(), fi.q.labels.begin(), fi.q.labels.end());
+  fi.key.push_back(-1);
+  for (auto *gs : {&fi.kg, &fi.pfree, &fi.qfree}) {
+    auto k = group_key(*gs);
+    fi.key.insert(fi.key.end(), k.begin(), k.end());
+    fi.key.push_back(-2);
+  }
+  fi.ok = true;
+  return fi;
+}
+
+}  // namespace
+
+std::vector<TermPlan> fuse_plans(const std::vector<TermPlan> &plans, double amortize) {
+  std::vector<FuseInfo> info;
+  for (auto &p : plans) info.push_back(fuse_info(p, amortize));
+  std::vector<TermPlan> out;
+  std::vector<bool> used(plans.size(), false);
+  for (size_t i = 0; i < plans.size(); ++i) {
+    if (used[i]) continue;
+    std::vector<size_t> members = {i};
+    if (info[i].ok)
+      for (size_t j = i + 1; j < plans.size(); ++j)
+        if (!used[j] && info[j].ok && info[j].key == info[i].key) members.push_back(j);
+    if (members.size() < 2) {
+      out.push_back(plans[i]);
+      used[i] = true;
+      continue;
+    }
+    const FuseInfo &fi0 = info[i];
+    TermPlan fused;
+    std::vector<DimGroup> fdims = fi0.pfree;
+    fdims.insert(fdims.end(), fi0.kg.begin(), fi0.kg.end());
+    std::vector<int> flabs;
+    for (auto &g : fdims) flabs.insert(flabs.end(), g.labels.begin(), g.labels.end());
+    fused.inter_dims.push_back(fdims);
+    fused.inter_labels.push_back(flabs);
+    for (size_t m : members) {
+      used[m] = true;
+      const TermPlan &pl = plans[m];
+      const FuseInfo &fi = info[m];
+      const int base = (int)fused.inter_dims.size();
+      fused.inter_dims.insert(fused.inter_dims.end(), pl.inter_dims.begin(), pl.inter_dims.end());
+      fused.inter_labels.insert(fused.inter_labels.end(), pl.inter_labels.begin(), pl.inter_labels.end());
+      auto shift = [&](Operand o) {
+        if (o.kind == TK_INTERMEDIATE) o.inter += base;
+        return o;
+      };
+      for (size_t k = 0; k + 1 < pl.steps.size(); ++k) {
+        Step s = pl.steps[k];
+        s.a = shift(s.a);
+        s.b = shift(s.b);
+        if (!s.to_output) s.out_inter += base;
+        fused.steps.push_back(s);
+      }
+      Step ax;
+      ax.a = shift(fi.p);
+      ax.b.kind = -1;
+      ax.to_output = false;
+      ax.out_inter = 0;
+      ax.alpha = fi.alpha;
+      ax.constant = fi.p_constant;
+      ax.mg = fdims;
+      for (auto &g : ax.mg)
+        for (int &l : g.labels) {
+          auto it = fi.from_role.find(l);
+          if (it != fi.from_role.end()) l = it->second;
+        }
+      fused.steps.push_back(ax);
+    }
+    Step fin;
+    fin.a.kind = TK_INTERMEDIATE;
+    fin.a.inter = 0;
+    fin.a.labels = flabs;
+    fin.b = fi0.q;
+    fin.mg = fi0.pfree;
+    fin.kg = fi0.kg;
+    fin.ng = fi0.qfree;
+    fin.to_output = true;
+    fin.alpha = 1.0;
+    fused.steps.push_back(fin);
+    out.push_back(fused);
+  }
+  return out;
+}
+
 }  // namespace fnocc

@@ -104,4 +104,11 @@ struct TermPlan {
 TermPlan plan_term(const Term &t, int nh, int np, int o, int v, double amortize = 0.0,
                    double cache_cap = 0.0);
 
+// Fuses terms whose last GEMM contracts the same amplitude operand Q (T2, T3
+// or an EOM component R) in the same way: their other operands P_t are summed
+// into one intermediate F = sum_t alpha_t P_t (the H-bar element) and one GEMM
+// F x Q replaces the per-term GEMMs. amortize > 0 marks F as cached when every
+// P_t is R-independent.
+std::vector<TermPlan> fuse_plans(const std::vector<TermPlan> &plans, double amortize);
+
 }  // namespace fnocc

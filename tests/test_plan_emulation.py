@@ -63,7 +63,7 @@ def parse_plan(text):
             kg, j = _groups(tok, j + 1)
             ng, j = _groups(tok, j + 1)
             steps.append(dict(a=(ak, ai, alab), b=(bk, bi, blab), to_out=to_out, out=oi, alpha=alpha,
-                              mg=mg, kg=kg, ng=ng))
+                              mg=mg, kg=kg, ng=ng, constant=const))
         terms.append((inters, steps))
     return nh, np_, terms
 
@@ -136,18 +136,25 @@ class Emulator:
                             a = {**r, **c}
                             y[tuple(a[(e << 1) | (0 if e < nh else 1)] for e in range(nh + np_))] += cmat[i, j]
                 else:
+                    # the producer writes the intermediate's dims positionally: mg groups, then ng groups
                     dims = inter_dims[s["out"]]
-                    shape = [len(_tuples(d, o, v)) for d in dims]
-                    arr = np.zeros(shape)
-                    inters[s["out"]] = (arr, dims)
+                    if s["out"] not in inters:
+                        shape = [len(_tuples(d, o, v)) for d in dims]
+                        inters[s["out"]] = (np.zeros(shape), dims)
+                    arr = inters[s["out"]][0]
+                    wgroups = s["mg"] + s["ng"]
+                    assert len(wgroups) == len(dims)
                     for i, r in enumerate(rows):
                         for j, c in enumerate(cols):
                             a = {**r, **c}
                             idx = []
-                            for d in dims:
-                                vals = tuple(a[l] for l in d[3])
-                                idx.append(list(itertools.combinations(range(o if d[0] == 0 else v, ), d[1])).index(vals)
-                                           if d[2] else vals[0])
+                            for d, wg in zip(dims, wgroups):
+                                vals = tuple(a[l] for l in wg[3])
+                                if d[2]:
+                                    n = o if d[0] == 0 else v
+                                    idx.append(list(itertools.combinations(range(n), d[1])).index(vals))
+                                else:
+                                    idx.append(vals[0])
                             arr[tuple(idx)] += cmat[i, j]
         out = np.zeros_like(y)
         for hp in itertools.permutations(range(nh)):
