@@ -187,6 +187,13 @@ fnocc_status fnocc_set_amplitudes(fnocc_ctx *ctx, const double *t1, const double
  * reference energy. */
 fnocc_status fnocc_dims(const fnocc_ctx *ctx, int *o, int *v, double *e_ref);
 
+/* Davidson projection: dots[j] = sum_i x[i] * Y[j*ld + i] for j < nvec
+ * (device pointers; dots is a device array of nvec doubles), computed with a
+ * deterministic two-pass reduction on the context stream; returns after the
+ * result is in dots. Scratch for the partial sums comes from the context. */
+fnocc_status fnocc_multi_dot(fnocc_ctx *ctx, const double *x, const double *Y, size_t n, size_t ld,
+                             int nvec, double *dots);
+
 /* Copies a packed block to the host. which: 1..3 = T1..T3 of the ground
  * state; 11..13 = R1..R3 of EOM root `root` of the last eom_ccsdt_solve.
  * len must equal the block's packed size. */

@@ -91,6 +91,7 @@ SIGNATURES = {
     "fno_truncate_dev": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(FnoOptions), ctypes.POINTER(FnoInfo), _dp]),
     "fnocc_flop_count": (ctypes.c_double, [_cp]),
+    "fnocc_multi_dot": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp]),
     "fnocc_equation_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_char_p, ctypes.c_size_t]),
     "fnocc_plan_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -265,6 +266,10 @@ class Context:
     def set_amplitudes(self, t1, t2, t3):
         ins = [_arr(t) for t in (t1, t2, t3)]
         self._check(self.lib.fnocc_set_amplitudes(self._h, ins[0][1], ins[1][1], ins[2][1]))
+
+    def multi_dot_dev(self, x_ptr, y_ptr, n, ld, nvec, dots_ptr):
+        """dots[j] = x . Y[j] on the device (all device addresses)."""
+        self._check(self.lib.fnocc_multi_dot(self._h, x_ptr, y_ptr, int(n), int(ld), int(nvec), dots_ptr))
 
     def eom_sizes(self, variant):
         sz = (ctypes.c_size_t * 3)()

@@ -1384,6 +1384,18 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
   });
 }
 
+fnocc_status fnocc_multi_dot(fnocc_ctx *c, const double *x, const double *Y, size_t n, size_t ld, int nvec,
+                             double *dots) {
+  if (!c) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (!x || !Y || !dots || nvec <= 0 || n == 0 || ld < n) throw StatusError(FNOCC_E_INVALID, "bad multi_dot arguments");
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    multi_dot(c->L(), (long long)n, x, Y, (long long)ld, nvec, dots, c->red);
+    sync(c);
+    return FNOCC_OK;
+  });
+}
+
 fnocc_status fnocc_get_block(fnocc_ctx *c, int which, int root, double *buf, size_t len) {
   if (!c || !buf) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
