@@ -194,6 +194,27 @@ fnocc_status fnocc_dims(const fnocc_ctx *ctx, int *o, int *v, double *e_ref);
 fnocc_status fnocc_multi_dot(fnocc_ctx *ctx, const double *x, const double *Y, size_t n, size_t ld,
                              int nvec, double *dots);
 
+/* fnocc_multi_dot without any device allocation (the paper has no
+ * counterpart; this is a library facility). For callers that cannot allocate
+ * device memory: a process whose device memory is owned by another allocator
+ * (a framework's caching allocator, a pool sized in advance) must not call
+ * cudaMalloc/cudaFree behind its back, and cudaFree synchronises the device.
+ * No context is needed; the caller passes the inputs x, Y and the output dots
+ * (all device pointers, same meaning as fnocc_multi_dot) and a stream (NULL =
+ * the default stream), and the call returns after dots is written.
+ * Scratch: a fixed array of 256 x 64 doubles (128 KiB) in the library's own
+ * device memory, held on every GPU that loads the library until the process
+ * exits. Limit: nvec <= 64; larger nvec (or nvec < 1, n = 0, ld < n, a NULL
+ * pointer) returns FNOCC_E_INVALID without touching the GPU.
+ * The first call on a device, with that device current, looks up the
+ * scratch's device address; make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The array keeps the last call's partial sums; each call overwrites every
+ * element it reads, so nothing needs clearing. */
+fnocc_status fnocc_multi_dot_noalloc(const double *x, const double *Y, size_t n, size_t ld, int nvec,
+                                     double *dots, void *stream);
+
 /* Copies a packed block to the host. which: 1..3 = T1..T3 of the ground
  * state; 11..13 = R1..R3 of EOM root `root` of the last eom_ccsdt_solve.
  * len must equal the block's packed size. */

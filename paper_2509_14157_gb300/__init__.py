@@ -92,6 +92,7 @@ SIGNATURES = {
                                         ctypes.POINTER(FnoOptions), ctypes.POINTER(FnoInfo), _dp]),
     "fnocc_flop_count": (ctypes.c_double, [_cp]),
     "fnocc_multi_dot": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp]),
+    "fnocc_multi_dot_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp, _vp]),
     "fnocc_equation_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_char_p, ctypes.c_size_t]),
     "fnocc_plan_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,

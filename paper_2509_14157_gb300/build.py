@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfnocc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "engine.cpp", "planner.cpp", "linalg.cpp", "api.cpp"]
+SOURCES = ["kernels.cu", "engine.cpp", "planner.cpp", "linalg.cpp", "api.cpp", "noalloc.cu"]
 
 
 def _nvcc():
