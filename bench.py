@@ -37,7 +37,7 @@ import numpy as np  # noqa: E402
 
 NE, NORB, THRESHOLD, NROOTS = 10, 48, 1e-4, 4
 VARIANTS = ("ip", "ea", "dip", "dea")
-METRIC = "s per converged EOM-CCSDT solve (FP64)"
+METRIC = "s per converged EOM-CCSDT solve"
 # FP64 FMA issue on this part: 2 FMA per clock per SM (measured), 152 SMs, 2070 MHz max
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # Iteration counts and algorithmic flops per evaluation of one converged step
@@ -196,11 +196,12 @@ def run_sigma_only(args):
     ctx.fno_truncate(h, eri, NE // 2, args.threshold)
     rng = np.random.default_rng(0)
     ctx.set_amplitudes(*[rng.normal(0, 0.01, s) for s in ctx.amp_sizes()])
+    ctx.set_precision(args.precision)
     x = rng.normal(0, 0.1, sum(ctx.eom_sizes(args.sigma_only)))
     t0 = time.perf_counter()
     ctx.eom_sigma(args.sigma_only, x)
-    print(json.dumps({"sigma_only": args.sigma_only, "seconds": time.perf_counter() - t0,
-                      "flops": ctx.flops}), flush=True)
+    print(json.dumps({"sigma_only": args.sigma_only, "precision": args.precision,
+                      "seconds": time.perf_counter() - t0, "flops": ctx.flops}), flush=True)
     ctx.close()
 
 
@@ -212,6 +213,8 @@ def main():
     ap.add_argument("--impl", default="fnocc", choices=["fnocc", "reference"])
     ap.add_argument("--threshold", type=float, default=THRESHOLD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="mixed: BF16 three-slice tensor-core contractions, then FP64 refinement")
     ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS),
                     help="one sigma product at the workload's size (profiling case)")
     args = ap.parse_args()
@@ -250,7 +253,7 @@ def main():
         else:
             ctx.fno_truncate(h, eri, nocc, args.threshold)
         f0 = ctx.flops
-        res = ctx.ccsdt_solve()
+        res = ctx.ccsdt_solve(precision=args.precision)
         if not res["converged"]:
             raise RuntimeError("CCSDT did not converge")
         counts["cc_iters"] = res["iters"]
@@ -258,7 +261,7 @@ def main():
         out = {}
         for var in VARIANTS:
             f0 = ctx.flops
-            r = ctx.eom_solve(var, NROOTS)
+            r = ctx.eom_solve(var, NROOTS, precision=args.precision)
             counts["flops_per_sigma"][var] = (ctx.flops - f0) / max(1, r["sigma_calls"])
             if not r["converged"]:
                 raise RuntimeError("%s-EOM did not converge" % var)
@@ -326,8 +329,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config(args.threshold, seed),
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "bf16x3->f32, f64 refinement",
+        "data": "synthetic", "config": dict(config(args.threshold, seed), precision=args.precision),
         "tflops": flops * world / total / 1e12 if total > 0 else None,
         "roofline": {"bound": "alu", "kernel": dominant + " (FP64 FMA)", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

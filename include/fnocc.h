@@ -60,6 +60,13 @@ typedef enum {
 typedef enum { FNOCC_IP = 0, FNOCC_EA = 1, FNOCC_DIP = 2, FNOCC_DEA = 3 } fnocc_variant;
 typedef enum { FNOCC_GUESS_KOOPMANS = 0, FNOCC_GUESS_DIAGONAL = 1 } fnocc_guess;
 typedef enum { FNOCC_CRIT_ABS = 0, FNOCC_CRIT_OCCT = 1 } fnocc_criterion;
+/* Arithmetic of the contractions (the single- and double-precision
+ * algorithms of Sec. 1). MIXED runs the large contractions as BF16
+ * three-slice split products on the tensor cores with FP32 accumulation
+ * until the residual falls below switch_tol, then refines in FP64;
+ * DIIS, Davidson orthogonalisation, the subspace problem and norms are
+ * always FP64. */
+typedef enum { FNOCC_FP64 = 0, FNOCC_MIXED_BF16X3 = 1 } fnocc_precision;
 
 typedef struct fnocc_ctx fnocc_ctx;
 
@@ -89,6 +96,8 @@ typedef struct {
   double tol_e;     /* |dE| for convergence, default 1e-12 */
   int maxiter;      /* default 200 */
   int diis;         /* DIIS history length, default 8 (0 = plain Jacobi) */
+  int precision;    /* fnocc_precision, default FP64 */
+  double switch_tol;/* MIXED: switch to FP64 below this max |residual| (default 1e-6; 0 = never) */
 } ccsdt_options;
 
 typedef struct {
@@ -98,14 +107,18 @@ typedef struct {
   double res_max;   /* max |residual| of the last iteration */
   double seconds;   /* wall time of the solve */
   double seconds_per_iter;
+  int iters_mixed;  /* iterations run in MIXED precision */
 } ccsdt_info;
 
 typedef struct {
   double tol_res;   /* residual 2-norm per root, default 1e-8 */
   double tol_e;     /* |d omega| per root, default 1e-10 */
-  int max_sub;      /* subspace size before collapse, default max(4*nroots, nguess+2*nroots) */
+  int max_sub;      /* subspace size before a thick restart (keeps the 2*nroots lowest Ritz
+                       vectors), default max(6*nroots, nguess+3*nroots) */
   int maxiter;      /* default 200 */
   int nguess;       /* guess vectors, default 2*nroots */
+  int precision;    /* fnocc_precision, default FP64 */
+  double switch_tol;/* MIXED: FP64 once every residual norm is below this (default 1e-5; 0 = never) */
 } eom_options;
 
 typedef struct {
@@ -115,6 +128,7 @@ typedef struct {
   double seconds_per_iter;
   int complex_roots;      /* roots whose Ritz value had |Im| > 1e-8 */
   double res_max;         /* max residual norm over roots at exit */
+  int sigma_calls_mixed;  /* products evaluated in MIXED precision */
 } eom_info;
 
 /* Context ---------------------------------------------------------------- */
@@ -171,7 +185,15 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *ctx, int variant, int nroots, int guess,
                              const eom_options *opt, double *energies, double *omegas,
                              eom_info *out);
 
-/* sigma = (H-bar R)_c for a packed EOM vector (host pointers). */
+/* Arithmetic of standalone ccsdt_residual / eom_sigma calls (fnocc_precision;
+ * default FP64). The solvers take theirs from their options. */
+fnocc_status fnocc_set_precision(fnocc_ctx *ctx, int precision);
+
+/* sigma = (H-bar R)_c for a packed EOM vector (host pointers). R is taken in
+ * the variant's target spin sector (2*dM_s = +1 for IP/EA, 0 for DIP/DEA):
+ * components outside it do not contribute, and sigma is returned in that
+ * sector (zero elsewhere). Likewise every call treats ground-state amplitudes
+ * as M_s-conserving. */
 fnocc_status eom_sigma(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
 fnocc_status eom_sigma_dev(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
 
@@ -219,6 +241,38 @@ fnocc_status fnocc_multi_dot_noalloc(const double *x, const double *Y, size_t n,
  * state; 11..13 = R1..R3 of EOM root `root` of the last eom_ccsdt_solve.
  * len must equal the block's packed size. */
 fnocc_status fnocc_get_block(fnocc_ctx *ctx, int which, int root, double *buf, size_t len);
+
+/* Batched solves ----------------------------------------------------------
+ * Many independent systems (not in the paper; the batching extension): each
+ * runs the whole path (fno_truncate, ccsdt_solve, eom_ccsdt_solve for every
+ * requested variant) on its own context and CUDA stream, nworkers systems at
+ * a time on device `device`, largest first, so that the GPU work of small
+ * systems overlaps. omegas[(s * nvariants + k) * nroots + r] receives the
+ * ionization / attachment energy omega of root r of variants[k] for system s
+ * (total energy = results[s].e_ccsdt + omega); results[s] (optional) its
+ * status, energies and timings. Host arrays are read during the call only.
+ * Returns FNOCC_OK when every system succeeded, else the first error status
+ * met (or FNOCC_NOT_CONVERGED); every system is attempted. */
+typedef struct {
+  const double *h;       /* n*n, host */
+  const double *eri;     /* n^4 chemists' (pq|rs), host */
+  int n, nocc;
+  double occ_threshold;  /* ABS criterion */
+  int nkeep;             /* > 0: keep exactly nkeep natural virtuals */
+} fnocc_system;
+
+typedef struct {
+  int status;            /* fnocc_status of this system */
+  int nkept;
+  double e_rhf, e_ccsdt;
+  int ccsdt_iters, sigma_calls;
+  double seconds;        /* wall time of this system's pipeline */
+} fnocc_system_result;
+
+fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems, int nvariants,
+                               const int *variants, int nroots, const ccsdt_options *cc_opt,
+                               const eom_options *eom_opt, int nworkers, double *omegas,
+                               fnocc_system_result *results);
 
 /* XFNO (Sec. 2): least-squares line E(f) through (kept_fraction, energy)
  * points evaluated at f = 1 (the paper prints no formula; this is the

@@ -16,8 +16,8 @@ Davidson (the paper names no eigensolver; this follows the standard
 non-symmetric Davidson method): orthonormal subspace V, projected matrix
 G = V^T sigma(V), Ritz pairs of G ordered by real part, residual
 r = sigma(x) - theta x, diagonal preconditioner (theta - D)^-1 with D built
-from diag(f), Gram-Schmidt (twice), collapse to the Ritz vectors when the
-subspace exceeds max_sub. Guesses are 2*nroots unit vectors on the lowest
+from diag(f), Gram-Schmidt (twice), and a thick restart from the 2*nroots
+lowest Ritz vectors when the subspace exceeds max_sub. Guesses are 2*nroots unit vectors on the lowest
 diagonal elements (of the first component for the Koopmans guess, of the
 whole space for the diagonal guess); with only nroots guesses a low root of
 weak overlap can be missed.
@@ -108,7 +108,9 @@ def _orthonormalise(vec, basis, tol=1e-10):
 def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
              maxiter=200, nguess=None, guess_mask=None):
     """Lowest-Re roots of a non-symmetric operator restricted to `mask`.
-    Guess unit vectors sit on the lowest `diag` entries inside guess_mask."""
+    Guess unit vectors sit on the lowest `diag` entries inside guess_mask.
+    When the subspace would exceed max_sub it is restarted from the 2*nroots
+    lowest Ritz vectors, whose products follow as the same combinations."""
     n = len(diag)
     allowed = np.where(mask)[0]
     if nguess is None:
@@ -116,31 +118,47 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
     nguess = min(nguess, len(allowed))
     nroots = min(nroots, len(allowed))
     if max_sub is None:
-        max_sub = max(4 * nroots, nguess + 2 * nroots)
+        max_sub = max(6 * nroots, nguess + 3 * nroots)
+    max_sub = max(max_sub, max(nguess, 2 * nroots) + nroots)
     pref = allowed if guess_mask is None else np.where(mask & guess_mask)[0]
     rest = np.setdiff1d(allowed, pref)
     order = np.concatenate([pref[np.argsort(diag[pref], kind="stable")],
                             rest[np.argsort(diag[rest], kind="stable")]])[:nguess]
     basis, sig = [], []
+
+    def add(vec, svec=None):
+        vec = vec * mask
+        if svec is not None:
+            svec = svec * mask
+        for _ in range(2):
+            for b, sb in zip(basis, sig):
+                c = b @ vec
+                vec = vec - c * b
+                if svec is not None:
+                    svec = svec - c * sb
+        nrm = np.linalg.norm(vec)
+        if nrm < 1e-10:
+            return
+        basis.append(vec / nrm)
+        sig.append(svec / nrm if svec is not None else apply(vec / nrm) * mask)
+
     for k in order:
         e = np.zeros(n)
         e[k] = 1.0
-        basis.append(e)
-        sig.append(apply(e) * mask)
+        add(e)
     theta_old = None
     for it in range(1, maxiter + 1):
         vmat = np.array(basis)
         smat = np.array(sig)
         gmat = vmat @ smat.T
-        w, y = np.linalg.eig(gmat)
-        srt = np.argsort(w.real, kind="stable")
-        w = w[srt][:nroots]
-        y = y[:, srt][:, :nroots]
+        w_all, y_all = np.linalg.eig(gmat)
+        srt = np.argsort(w_all.real, kind="stable")
+        w = w_all[srt][:nroots]
+        yr = np.real(y_all[:, srt])
         theta = w.real
-        yr = np.real(y)
         xs, res, norms = [], [], []
         for r in range(nroots):
-            yv = yr[:, r] / np.linalg.norm(vmat.T @ yr[:, r])
+            yv = yr[:, r] / np.linalg.norm(yr[:, r])
             x = vmat.T @ yv
             rv = smat.T @ yv - theta[r] * x
             xs.append(x)
@@ -160,18 +178,16 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
             den = np.where(np.abs(den) < 1e-8, 1e-8, den)
             new.append((res[r] / den) * mask)
         if len(basis) + len(new) > max_sub:
-            nb = []
-            for x in xs:
-                q = _orthonormalise(x, nb)
-                if q is not None:
-                    nb.append(q)
-            basis = nb
-            sig = [apply(b) * mask for b in basis]
+            nkeep = min(len(basis), 2 * nroots)
+            keep = []
+            for q in range(nkeep):
+                yv = yr[:, q] / np.linalg.norm(yr[:, q])
+                keep.append((vmat.T @ yv, smat.T @ yv))
+            basis, sig = [], []
+            for x, sx in keep:
+                add(x, sx)
         for d in new:
-            q = _orthonormalise(d, basis)
-            if q is not None:
-                basis.append(q)
-                sig.append(apply(q) * mask)
+            add(d)
     return dict(omega=theta, vectors=np.array(xs), iters=maxiter, res=np.array(norms),
                 converged=False, imag=np.abs(w.imag))
 

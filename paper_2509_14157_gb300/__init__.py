@@ -18,6 +18,7 @@ IP, EA, DIP, DEA = 0, 1, 2, 3
 VARIANTS = {"ip": IP, "ea": EA, "dip": DIP, "dea": DEA}
 GUESS = {"koopmans": 0, "diagonal": 1}
 CRITERIA = {"abs": 0, "occt": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "E_INVALID", -2: "E_NOMEM", -3: "E_CUDA",
           -4: "E_STATE", -5: "E_NUMERIC", -6: "E_TIMEOUT"}
 # (holes, particles) of R1, R2, R3 per variant
@@ -43,24 +44,37 @@ class FnoInfo(ctypes.Structure):
 
 class CcsdtOptions(ctypes.Structure):
     _fields_ = [("tol_res", ctypes.c_double), ("tol_e", ctypes.c_double), ("maxiter", ctypes.c_int),
-                ("diis", ctypes.c_int)]
+                ("diis", ctypes.c_int), ("precision", ctypes.c_int), ("switch_tol", ctypes.c_double)]
 
 
 class CcsdtInfo(ctypes.Structure):
     _fields_ = [("e_corr", ctypes.c_double), ("e_tot", ctypes.c_double), ("iters", ctypes.c_int),
                 ("res_max", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("seconds_per_iter", ctypes.c_double)]
+                ("seconds_per_iter", ctypes.c_double), ("iters_mixed", ctypes.c_int)]
 
 
 class EomOptions(ctypes.Structure):
     _fields_ = [("tol_res", ctypes.c_double), ("tol_e", ctypes.c_double), ("max_sub", ctypes.c_int),
-                ("maxiter", ctypes.c_int), ("nguess", ctypes.c_int)]
+                ("maxiter", ctypes.c_int), ("nguess", ctypes.c_int), ("precision", ctypes.c_int),
+                ("switch_tol", ctypes.c_double)]
 
 
 class EomInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("sigma_calls", ctypes.c_int), ("seconds", ctypes.c_double),
                 ("seconds_per_iter", ctypes.c_double), ("complex_roots", ctypes.c_int),
-                ("res_max", ctypes.c_double)]
+                ("res_max", ctypes.c_double), ("sigma_calls_mixed", ctypes.c_int)]
+
+
+class System(ctypes.Structure):
+    _fields_ = [("h", ctypes.POINTER(ctypes.c_double)), ("eri", ctypes.POINTER(ctypes.c_double)),
+                ("n", ctypes.c_int), ("nocc", ctypes.c_int), ("occ_threshold", ctypes.c_double),
+                ("nkeep", ctypes.c_int)]
+
+
+class SystemResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nkept", ctypes.c_int), ("e_rhf", ctypes.c_double),
+                ("e_ccsdt", ctypes.c_double), ("ccsdt_iters", ctypes.c_int), ("sigma_calls", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -91,6 +105,7 @@ SIGNATURES = {
     "fno_truncate_dev": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(FnoOptions), ctypes.POINTER(FnoInfo), _dp]),
     "fnocc_flop_count": (ctypes.c_double, [_cp]),
+    "fnocc_set_precision": (ctypes.c_int, [_cp, ctypes.c_int]),
     "fnocc_multi_dot": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp]),
     "fnocc_multi_dot_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp, _vp]),
     "fnocc_equation_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -98,6 +113,10 @@ SIGNATURES = {
     "fnocc_plan_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
     "fnocc_profile": (ctypes.c_int, [_cp, ctypes.c_int]),
+    "fnocc_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(System), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                         ctypes.POINTER(CcsdtOptions), ctypes.POINTER(EomOptions), ctypes.c_int,
+                                         _dp, ctypes.POINTER(SystemResult)]),
     "fnocc_profile_read": (ctypes.c_int, [_cp, ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
@@ -130,6 +149,38 @@ def xfno_extrapolate(kept_fraction, energy):
     f, fp = _arr(kept_fraction)
     e, ep = _arr(energy)
     return float(lib.xfno_extrapolate(fp, ep, len(f)))
+
+
+def batch_solve(systems, variants, nroots, device=0, nworkers=4, cc_tol_res=1e-10, cc_tol_e=1e-12,
+                eom_tol_res=1e-8, eom_tol_e=1e-10, precision="fp64"):
+    """Independent systems through the whole path, nworkers at a time (one
+    context and stream each); see fnocc_batch_solve.
+
+    systems: list of dicts with h, eri, nocc and threshold or nkeep.
+    Returns (omegas[nsys, len(variants), nroots], list of per-system dicts);
+    a system that failed carries its status in its dict."""
+    lib = load_library()
+    keep = []
+    arr = (System * len(systems))()
+    for i, sy in enumerate(systems):
+        h, hp = _arr(sy["h"])
+        e, ep = _arr(sy["eri"])
+        keep += [h, e]
+        arr[i] = System(hp, ep, h.shape[0], int(sy["nocc"]), float(sy.get("threshold", 0.0)),
+                        int(sy.get("nkeep", 0)))
+    vs = [VARIANTS.get(v, v) for v in variants]
+    var = (ctypes.c_int * len(vs))(*vs)
+    cc = CcsdtOptions(cc_tol_res, cc_tol_e, 200, 8, PRECISION[precision], 1e-6)
+    eo = EomOptions(eom_tol_res, eom_tol_e, 0, 200, 0, PRECISION[precision], 1e-5)
+    om = np.zeros((len(systems), len(vs), nroots))
+    res = (SystemResult * len(systems))()
+    st = lib.fnocc_batch_solve(int(device), len(systems), arr, len(vs), var, int(nroots), ctypes.byref(cc),
+                               ctypes.byref(eo), int(nworkers), om.ctypes.data_as(_dp), res)
+    if st == -1:
+        raise FnoccError(st, "invalid batch request")
+    out = [dict(status=r.status, nkept=r.nkept, e_rhf=r.e_rhf, e_ccsdt=r.e_ccsdt, ccsdt_iters=r.ccsdt_iters,
+                sigma_calls=r.sigma_calls, seconds=r.seconds) for r in res]
+    return om, out
 
 
 def equation_text(kind, variant=0, out_comp=0, in_comp=0):
@@ -214,6 +265,10 @@ class Context:
         return dict(e_rhf=info.e_rhf, e_mp2=info.e_mp2, nkept=info.nkept, nvir=info.nvir,
                     kept_fraction=info.kept_fraction, scf_iters=info.scf_iters, occ=occ)
 
+    def set_precision(self, precision):
+        """Arithmetic of standalone residual / sigma calls: 'fp64' or 'mixed'."""
+        self._check(self.lib.fnocc_set_precision(self._h, PRECISION[precision]))
+
     @property
     def flops(self):
         return float(self.lib.fnocc_flop_count(self._h))
@@ -237,12 +292,13 @@ class Context:
         e, ep = _arr(eri_mo)
         self._check(self.lib.fnocc_set_mo_hamiltonian(self._h, hp, ep, h.shape[0], int(nocc)))
 
-    def ccsdt_solve(self, tol_res=1e-10, tol_e=1e-12, maxiter=200, diis=8):
-        opt = CcsdtOptions(tol_res, tol_e, maxiter, diis)
+    def ccsdt_solve(self, tol_res=1e-10, tol_e=1e-12, maxiter=200, diis=8, precision="fp64", switch_tol=1e-6):
+        opt = CcsdtOptions(tol_res, tol_e, maxiter, diis, PRECISION[precision], switch_tol)
         info = CcsdtInfo()
         st = self._check(self.lib.ccsdt_solve(self._h, ctypes.byref(opt), ctypes.byref(info)), allow=(0, 1))
         return dict(e_corr=info.e_corr, e_tot=info.e_tot, iters=info.iters, res_max=info.res_max,
-                    seconds=info.seconds, seconds_per_iter=info.seconds_per_iter, converged=(st == 0))
+                    seconds=info.seconds, seconds_per_iter=info.seconds_per_iter, converged=(st == 0),
+                    iters_mixed=info.iters_mixed)
 
     def amp_sizes(self):
         from math import comb
@@ -288,10 +344,10 @@ class Context:
         self._check(self.lib.eom_sigma_dev(self._h, VARIANTS.get(variant, variant), r_ptr, s_ptr))
 
     def eom_solve(self, variant, nroots, guess="diagonal", tol_res=1e-8, tol_e=1e-10, max_sub=0,
-                  maxiter=200, nguess=0):
+                  maxiter=200, nguess=0, precision="fp64", switch_tol=1e-5):
         var = VARIANTS.get(variant, variant)
         self._last_sizes = self.eom_sizes(var)
-        opt = EomOptions(tol_res, tol_e, max_sub, maxiter, nguess)
+        opt = EomOptions(tol_res, tol_e, max_sub, maxiter, nguess, PRECISION[precision], switch_tol)
         info = EomInfo()
         en = np.zeros(nroots)
         om = np.zeros(nroots)
@@ -300,7 +356,8 @@ class Context:
                                                   ctypes.byref(info)), allow=(0, 1))
         return dict(energies=en, omegas=om, iters=info.iters, sigma_calls=info.sigma_calls,
                     seconds=info.seconds, seconds_per_iter=info.seconds_per_iter,
-                    complex_roots=info.complex_roots, res_max=info.res_max, converged=(st == 0))
+                    complex_roots=info.complex_roots, res_max=info.res_max, converged=(st == 0),
+                    sigma_calls_mixed=info.sigma_calls_mixed)
 
     def get_block(self, which, root=0):
         """which: 't1','t2','t3' or ('r', k) for component k=1..3 of EOM root `root`."""

@@ -2,7 +2,9 @@
 #include "../../include/fnocc.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -129,7 +131,9 @@ struct fnocc_ctx {
   GemmProfile prof;
   DevBuf partials;
   double flops_total = 0;
-  Launch L() { return Launch{stream, &launches, &prof, &partials}; }
+  int precision = 0;          // fnocc_precision of the contractions currently issued
+  int default_precision = 0;  // for standalone residual / sigma calls
+  Launch L() { return Launch{stream, &launches, &prof, &partials, precision}; }
 
   // active Hamiltonian (spin orbitals, bare)
   bool have_ham = false;
@@ -257,6 +261,7 @@ void install_hamiltonian(fnocc_ctx *c, int nocc, int nact_spatial) {
 
 void dress(fnocc_ctx *c, const double *t1) {
   Launch L = c->L();
+  L.precision = FNOCC_FP64;  // the T1 transformation and reference energy stay FP64
   const int n = c->n;
   const size_t n4 = (size_t)n * n * n * n;
   c->Lm.reserve(sizeof(double) * n * n);
@@ -360,7 +365,8 @@ void ensure_eom_plans(fnocc_ctx *c, int var) {
     for (int ic = 0; ic < 3; ++ic)
       if (!c->eom_eq[var][oc][ic])
         c->eom_eq[var][oc][ic].reset(
-            new ExecEquation(eom_equation(var, oc, ic), c->o, c->v, rd, kSigmaAmortize, kCacheCapDoubles));
+            new ExecEquation(eom_equation(var, oc, ic), c->o, c->v, rd, kSigmaAmortize, kCacheCapDoubles,
+                             kSectorMs2[var]));
 }
 
 // prepares dressed operators and dense T2/T3 from the stored amplitudes
@@ -994,7 +1000,9 @@ fnocc_status ccsdt_residual_dev(fnocc_ctx *c, const double *t1, const double *t2
     cp(tin.d(), t1, c->nt[1]);
     cp(tin.d() + c->nt[1], t2, c->nt[2]);
     cp(tin.d() + c->nt[1] + c->nt[2], t3, c->nt[3]);
+    c->precision = c->default_precision;
     double e = cc_residual_dev(c, tin.d(), c->rpk.d());
+    c->precision = FNOCC_FP64;
     cp(r1, c->rpk.d(), c->nt[1]);
     cp(r2, c->rpk.d() + c->nt[1], c->nt[2]);
     cp(r3, c->rpk.d() + c->nt[1] + c->nt[2], c->nt[3]);
@@ -1020,7 +1028,9 @@ fnocc_status ccsdt_residual(fnocc_ctx *c, const double *t1, const double *t2, co
     if (c->nt[3])
       FNOCC_CUDA(cudaMemcpyAsync(tin.d() + c->nt[1] + c->nt[2], t3, sizeof(double) * c->nt[3], cudaMemcpyHostToDevice,
                                  c->stream));
+    c->precision = c->default_precision;
     double e = cc_residual_dev(c, tin.d(), rout.d());
+    c->precision = FNOCC_FP64;
     FNOCC_CUDA(cudaMemcpyAsync(r1, rout.d(), sizeof(double) * c->nt[1], cudaMemcpyDeviceToHost, c->stream));
     FNOCC_CUDA(cudaMemcpyAsync(r2, rout.d() + c->nt[1], sizeof(double) * c->nt[2], cudaMemcpyDeviceToHost, c->stream));
     if (c->nt[3])
@@ -1038,8 +1048,17 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     Timer timer;
-    ccsdt_options o{1e-10, 1e-12, 200, 8};
+    ccsdt_options o{1e-10, 1e-12, 200, 8, FNOCC_FP64, 1e-6};
     if (opt) o = *opt;
+    if (o.precision != FNOCC_FP64 && o.precision != FNOCC_MIXED_BF16X3)
+      throw StatusError(FNOCC_E_INVALID, "bad precision");
+    if (o.switch_tol < 0) o.switch_tol = 0;
+    struct PrecisionGuard {
+      fnocc_ctx *c;
+      ~PrecisionGuard() { c->precision = FNOCC_FP64; }
+    } guard{c};
+    c->precision = o.precision;
+    int iters_mixed = 0;
     if (o.tol_res <= 0) o.tol_res = 1e-10;
     if (o.tol_e <= 0) o.tol_e = 1e-12;
     if (o.maxiter <= 0) o.maxiter = 200;
@@ -1079,9 +1098,16 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
     bool conv = false;
     int it;
     for (it = 1; it <= o.maxiter; ++it) {
+      if (c->precision == FNOCC_MIXED_BF16X3) ++iters_mixed;
       e = cc_residual_dev(c, c->tpk.d(), c->rpk.d());
       absmax_dev(c, tot, c->rpk.d(), &rmax, &rn);
       if (!std::isfinite(e) || !std::isfinite(rmax)) throw StatusError(FNOCC_E_NUMERIC, "NaN/Inf in CCSDT iterations");
+      if (c->precision == FNOCC_MIXED_BF16X3 && o.switch_tol > 0 && rmax < o.switch_tol) {
+        // refinement: from here on every contraction is FP64; the iterate is kept
+        c->precision = FNOCC_FP64;
+        e_old = e;
+        continue;
+      }
       if (it > 1 && rmax < o.tol_res && std::fabs(e - e_old) < o.tol_e) {
         conv = true;
         break;
@@ -1128,9 +1154,16 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
       out->res_max = rmax;
       out->seconds = secs;
       out->seconds_per_iter = secs / std::max(1, conv ? it : o.maxiter);
+      out->iters_mixed = iters_mixed;
     }
     return conv ? FNOCC_OK : FNOCC_NOT_CONVERGED;
   });
+}
+
+fnocc_status fnocc_set_precision(fnocc_ctx *c, int precision) {
+  if (!c || (precision != FNOCC_FP64 && precision != FNOCC_MIXED_BF16X3)) return FNOCC_E_INVALID;
+  c->default_precision = precision;
+  return FNOCC_OK;
 }
 
 fnocc_status fnocc_eom_sizes(const fnocc_ctx *c, int variant, size_t *sizes) {
@@ -1147,7 +1180,9 @@ fnocc_status eom_sigma_dev(fnocc_ctx *c, int variant, const double *r, double *s
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     prepare_hbar(c);
+    c->precision = c->default_precision;
     sigma_dev(c, variant, r, s);
+    c->precision = FNOCC_FP64;
     sync(c);
     return FNOCC_OK;
   });
@@ -1167,7 +1202,9 @@ fnocc_status eom_sigma(fnocc_ctx *c, int variant, const double *r, double *s) {
     y.reserve(sizeof(double) * dim);
     FNOCC_CUDA(cudaMemcpyAsync(x.p, r, sizeof(double) * dim, cudaMemcpyHostToDevice, c->stream));
     prepare_hbar(c);
+    c->precision = c->default_precision;
     sigma_dev(c, variant, x.d(), y.d());
+    c->precision = FNOCC_FP64;
     FNOCC_CUDA(cudaMemcpyAsync(s, y.p, sizeof(double) * dim, cudaMemcpyDeviceToHost, c->stream));
     sync(c);
     return FNOCC_OK;
@@ -1184,13 +1221,23 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     Timer timer;
-    eom_options o{1e-8, 1e-10, 0, 200, 0};
+    eom_options o{1e-8, 1e-10, 0, 200, 0, FNOCC_FP64, 1e-5};
     if (opt) o = *opt;
+    if (o.precision != FNOCC_FP64 && o.precision != FNOCC_MIXED_BF16X3)
+      throw StatusError(FNOCC_E_INVALID, "bad precision");
+    if (o.switch_tol < 0) o.switch_tol = 0;
+    struct PrecisionGuard {
+      fnocc_ctx *c;
+      ~PrecisionGuard() { c->precision = FNOCC_FP64; }
+    } guard{c};
     if (o.tol_res <= 0) o.tol_res = 1e-8;
     if (o.tol_e <= 0) o.tol_e = 1e-10;
     if (o.maxiter <= 0) o.maxiter = 200;
     Launch L = c->L();
-    prepare_hbar(c);
+    c->precision = FNOCC_FP64;
+    prepare_hbar(c);  // T1 dressing and amplitude unpacking stay FP64
+    c->precision = o.precision;
+    int sigma_calls_mixed = 0;
     size_t sz[3];
     eom_sizes(c, variant, sz);
     const long long dim = (long long)(sz[0] + sz[1] + sz[2]);
@@ -1220,8 +1267,8 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
     int nr = std::min<long long>(nroots, (long long)allowed.size());
     int ng = o.nguess > 0 ? o.nguess : 2 * nr;
     ng = std::min<long long>(ng, (long long)allowed.size());
-    int max_sub = o.max_sub > 0 ? o.max_sub : std::max(4 * nr, ng + 2 * nr);
-    if (max_sub < ng + nr) max_sub = ng + nr;
+    int max_sub = o.max_sub > 0 ? o.max_sub : std::max(6 * nr, ng + 3 * nr);
+    if (max_sub < std::max(ng, 2 * nr) + nr) max_sub = std::max(ng, 2 * nr) + nr;
     auto by_diag = [&](long long a, long long b) { return dgh[a] < dgh[b] || (dgh[a] == dgh[b] && a < b); };
     std::stable_sort(pref.begin(), pref.end(), by_diag);
     std::vector<long long> rest;
@@ -1248,25 +1295,37 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
     std::vector<double> G;  // kb x kb, row-major, G[i][j] = V_i . S_j
     auto vrow = [&](int i) { return Vb.d() + (size_t)i * dim; };
     auto srow = [&](int i) { return Sb.d() + (size_t)i * dim; };
-    auto add_vector = [&](const double *src) -> bool {
-      // orthonormalise src against the basis (twice), append V and sigma(V)
+    // Appends src, orthonormalised against the basis (Gram-Schmidt twice), and
+    // its product: computed, or (restart) carried along linearly from sig_src.
+    auto add_vector = [&](const double *src, const double *sig_src = nullptr) -> bool {
       double *dst = vrow(kb);
+      double *sdst = srow(kb);
       FNOCC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
       scale_mask(L, dim, dst, mask);
+      if (sig_src) {
+        FNOCC_CUDA(cudaMemcpyAsync(sdst, sig_src, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
+        scale_mask(L, dim, sdst, mask);
+      }
       for (int pass = 0; pass < 2 && kb > 0; ++pass) {
         c->small.reserve(sizeof(double) * std::max(64, kb));
         multi_dot(L, dim, dst, Vb.d(), dim, kb, c->small.d(), c->red);
         auto d = to_host(c, c->small.d(), kb);
         for (auto &x : d) x = -x;
         combine_rows(c, dim, Vb.d(), kb, d, dst, true);
+        if (sig_src) combine_rows(c, dim, Sb.d(), kb, d, sdst, true);
       }
       double amax, nrm;
       absmax_dev(c, dim, dst, &amax, &nrm);
       if (!(nrm > 1e-10)) return false;
       axpby(L, dim, 0.0, dst, 1.0 / nrm, dst);
-      sigma_dev(c, variant, dst, srow(kb));
-      scale_mask(L, dim, srow(kb), mask);
-      ++sigma_calls;
+      if (sig_src) {
+        axpby(L, dim, 0.0, sdst, 1.0 / nrm, sdst);
+      } else {
+        sigma_dev(c, variant, dst, sdst);
+        scale_mask(L, dim, sdst, mask);
+        ++sigma_calls;
+        if (c->precision == FNOCC_MIXED_BF16X3) ++sigma_calls_mixed;
+      }
       // extend G
       int k1 = kb + 1;
       std::vector<double> Gn((size_t)k1 * k1, 0.0);
@@ -1326,10 +1385,29 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
         if (!std::isfinite(nrm)) throw StatusError(FNOCC_E_NUMERIC, "NaN in Davidson residual");
         norms[r] = nrm;
       }
+      if (c->precision == FNOCC_MIXED_BF16X3 && o.switch_tol > 0) {
+        double mx = 0;
+        for (double x : norms) mx = std::max(mx, x);
+        if (mx < o.switch_tol) {
+          // refinement: FP64 from here on; rebuild the subspace from the Ritz
+          // vectors with FP64 products (cached H-bar pieces recomputed too)
+          c->precision = FNOCC_FP64;
+          ++c->hbar_version;
+          DevBuf keep;
+          keep.reserve(sizeof(double) * dim * nr);
+          FNOCC_CUDA(cudaMemcpyAsync(keep.p, xr.p, sizeof(double) * dim * nr, cudaMemcpyDeviceToDevice, c->stream));
+          kb = 0;
+          G.clear();
+          for (int r = 0; r < nr; ++r) add_vector(keep.d() + (size_t)r * dim);
+          have_old = false;
+          continue;
+        }
+      }
+      const bool may_stop = c->precision == FNOCC_FP64 || o.switch_tol == 0;
       std::vector<bool> done(nr);
       bool all = true;
       for (int r = 0; r < nr; ++r) {
-        done[r] = norms[r] < o.tol_res && have_old && std::fabs(theta[r] - theta_old[r]) < o.tol_e;
+        done[r] = may_stop && norms[r] < o.tol_res && have_old && std::fabs(theta[r] - theta_old[r]) < o.tol_e;
         all = all && done[r];
       }
       if (all) {
@@ -1342,13 +1420,27 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
       for (int r = 0; r < nr; ++r)
         if (!done[r]) ++nnew;
       if (kb + nnew > max_sub) {
-        // collapse onto the current Ritz vectors
-        DevBuf keep;
-        keep.reserve(sizeof(double) * dim * nr);
-        FNOCC_CUDA(cudaMemcpyAsync(keep.p, xr.p, sizeof(double) * dim * nr, cudaMemcpyDeviceToDevice, c->stream));
+        // thick restart: keep the lowest nkeep Ritz vectors with their
+        // products, formed as the same linear combinations (no new products)
+        const int nkeep = std::min(kb, 2 * nr);
+        DevBuf kx, ks;
+        kx.reserve(sizeof(double) * dim * nkeep);
+        ks.reserve(sizeof(double) * dim * nkeep);
+        for (int q = 0; q < nkeep; ++q) {
+          int j = idx[q];
+          std::vector<double> y(kb);
+          for (int i = 0; i < kb; ++i) y[i] = Y[(size_t)i * kb + j].real();
+          double nn = 0;
+          for (double t : y) nn += t * t;
+          nn = std::sqrt(nn);
+          if (nn == 0) nn = 1;
+          for (double &t : y) t /= nn;
+          combine_rows(c, dim, Vb.d(), kb, y, kx.d() + (size_t)q * dim, false);
+          combine_rows(c, dim, Sb.d(), kb, y, ks.d() + (size_t)q * dim, false);
+        }
         kb = 0;
         G.clear();
-        for (int r = 0; r < nr; ++r) add_vector(keep.d() + (size_t)r * dim);
+        for (int q = 0; q < nkeep; ++q) add_vector(kx.d() + (size_t)q * dim, ks.d() + (size_t)q * dim);
       }
       for (int r = 0; r < nr; ++r) {
         if (done[r]) continue;
@@ -1379,6 +1471,7 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
       double mx = 0;
       for (double x : norms) mx = std::max(mx, x);
       out->res_max = mx;
+      out->sigma_calls_mixed = sigma_calls_mixed;
     }
     return conv ? FNOCC_OK : FNOCC_NOT_CONVERGED;
   });
@@ -1420,6 +1513,74 @@ fnocc_status fnocc_get_block(fnocc_ctx *c, int which, int root, double *buf, siz
     }
     throw StatusError(FNOCC_E_INVALID, "unknown block");
   });
+}
+
+fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems, int nvariants, const int *variants,
+                               int nroots, const ccsdt_options *cc_opt, const eom_options *eom_opt, int nworkers,
+                               double *omegas, fnocc_system_result *results) {
+  if (nsys <= 0 || !systems || nvariants <= 0 || !variants || nroots <= 0 || !omegas) return FNOCC_E_INVALID;
+  for (int k = 0; k < nvariants; ++k)
+    if (variants[k] < 0 || variants[k] > 3) return FNOCC_E_INVALID;
+  for (int s = 0; s < nsys; ++s)
+    if (!systems[s].h || !systems[s].eri || systems[s].n <= 1 || systems[s].nocc <= 0 || systems[s].nocc >= systems[s].n)
+      return FNOCC_E_INVALID;
+  if (nworkers <= 0) nworkers = 4;
+  nworkers = std::min(nworkers, nsys);
+  // largest systems first (cost grows steeply with the orbital count)
+  std::vector<int> order(nsys);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return systems[a].n > systems[b].n; });
+  std::atomic<int> next(0);
+  std::vector<fnocc_status> st(nsys, FNOCC_OK);
+  auto worker = [&]() {
+    fnocc_ctx *c = nullptr;
+    if (fnocc_create(&c, device, nullptr) != FNOCC_OK) {
+      for (int q; (q = next.fetch_add(1)) < nsys;) st[order[q]] = FNOCC_E_CUDA;
+      return;
+    }
+    for (int q; (q = next.fetch_add(1)) < nsys;) {
+      const int s = order[q];
+      const fnocc_system &sys = systems[s];
+      Timer timer;
+      fno_options fo{FNOCC_CRIT_ABS, sys.nkeep, 200, 1e-12, 1e-10};
+      fno_info fi{};
+      ccsdt_info ci{};
+      fnocc_status worst = fno_truncate(c, sys.h, sys.eri, sys.n, sys.nocc, sys.occ_threshold, &fo, &fi, nullptr);
+      int sig = 0;
+      if (worst >= 0) {
+        fnocc_status cs = ccsdt_solve(c, cc_opt, &ci);
+        if (cs != FNOCC_OK) worst = cs;
+        if (cs >= 0)
+          for (int k = 0; k < nvariants; ++k) {
+            eom_info ei{};
+            std::vector<double> en(nroots);
+            fnocc_status es = eom_ccsdt_solve(c, variants[k], nroots, FNOCC_GUESS_DIAGONAL, eom_opt, en.data(),
+                                              omegas + ((size_t)s * nvariants + k) * nroots, &ei);
+            sig += ei.sigma_calls;
+            if (es < 0 || (es != FNOCC_OK && worst >= 0)) worst = es;
+          }
+      }
+      st[s] = worst;
+      if (results) {
+        results[s].status = worst;
+        results[s].nkept = fi.nkept;
+        results[s].e_rhf = fi.e_rhf;
+        results[s].e_ccsdt = ci.e_tot;
+        results[s].ccsdt_iters = ci.iters;
+        results[s].sigma_calls = sig;
+        results[s].seconds = timer.s();
+      }
+    }
+    fnocc_destroy(c);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nworkers; ++w) pool.emplace_back(worker);
+  for (auto &t : pool) t.join();
+  fnocc_status out = FNOCC_OK;
+  for (int s = 0; s < nsys; ++s)
+    if (st[s] < 0) return st[s];
+    else if (st[s] != FNOCC_OK) out = st[s];
+  return out;
 }
 
 long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char *buf, size_t len) {

@@ -82,17 +82,22 @@ struct Launch {
   uint64_t *counter;      // incremented per kernel launch
   GemmProfile *prof = nullptr;
   DevBuf *partials = nullptr;  // split-K partial sums (deterministic reduction)
+  int precision = 0;           // 0 FP64; 1 BF16 three-slice split on tensor cores (tiled path)
 };
 
 // C[crow(m) + ccol(n)] (+)= alpha * sum_k A[arow(m)+acol(k)] * B[brow(k)+bcol(n)]
 // asize, bsize, csize: element counts of the buffers; every launch checks on
 // the host that maxoff(row) + maxoff(col) < size for each operand, so a wrong
 // table is reported as an error instead of reaching the device.
-void gather_gemm(const Launch &L, long long M, long long N, long long K, double alpha,
-                 const double *A, const DMap &arow, const DMap &acol, const double *B,
-                 const DMap &brow, const DMap &bcol, double *C, const DMap &crow,
-                 const DMap &ccol, bool accumulate, long long asize, long long bsize,
-                 long long csize);
+// shape: micro-tile of the FP64 tiled path (0..kTileShapes-1), or -1 for the
+// shape with the least padding. Returns the shape used (-1 for the GEMV,
+// small-output and mixed-precision paths, whose tiles are fixed).
+constexpr int kTileShapes = 5;
+int gather_gemm(const Launch &L, long long M, long long N, long long K, double alpha,
+                const double *A, const DMap &arow, const DMap &acol, const double *B,
+                const DMap &brow, const DMap &bcol, double *C, const DMap &crow,
+                const DMap &ccol, bool accumulate, long long asize, long long bsize,
+                long long csize, int shape = -1);
 // C[crow(m)] += alpha * A[arow(m)]
 void gather_axpy(const Launch &L, long long M, double alpha, const double *A, const DMap &arow,
                  double *C, const DMap &crow, long long asize, long long csize);

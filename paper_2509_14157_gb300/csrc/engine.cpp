@@ -3,7 +3,9 @@
 #include "engine.hpp"
 
 #include <algorithm>
+#include <functional>
 #include <map>
+#include <mutex>
 
 namespace fnocc {
 
@@ -44,6 +46,7 @@ namespace {
 struct SDim {
   std::vector<int> labels;
   bool packed = false;
+  bool positional = false;  // intermediate: indexed by position in the canonical tuple order
   long long size = 0, stride = 0, base = 0;  // base: offset of the label's space (full tensors)
 };
 
@@ -97,6 +100,7 @@ Storage group_storage(const std::vector<DimGroup> &groups, int o, int v) {
     d.labels = g.labels;
     d.packed = g.packed && g.k >= 2;
     d.size = d.packed ? binom_ll(n, g.k) : [&] { long long t = 1; for (int j = 0; j < g.k; ++j) t *= n; return t; }();
+    d.positional = true;
     if (!d.packed && g.k != 1) throw std::runtime_error("engine: unpacked multi-label dimension");
     s.dims.push_back(d);
   }
@@ -110,6 +114,68 @@ Storage output_storage(int nh, int np, int o, int v) {
   for (int k = 0; k < nh; ++k) labs.push_back(make_label(k, SP_O));
   for (int k = 0; k < np; ++k) labs.push_back(make_label(nh + k, SP_V));
   return dense_storage(labs, o, v);
+}
+
+// Canonical tuple order of an index group: tuples (strictly increasing if
+// packed) sorted by spin sum (alpha = even index +1, beta = odd -1), then
+// lexicographically. Every table, every intermediate dimension and every
+// spin segment uses this order.
+struct GroupEnum {
+  std::vector<int> flat;  // count * k indices
+  std::vector<std::tuple<int, long long, long long>> segs;  // (spin sum, start, length)
+  long long count = 0;
+};
+
+const GroupEnum &enumerate_group(int n, int k, bool packed) {
+  // shared by all contexts (host threads): entries are never erased, so the
+  // returned references stay valid
+  static std::map<std::tuple<int, int, bool>, GroupEnum> cache;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_tuple(n, k, packed);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  std::vector<std::vector<int>> tup;
+  std::vector<int> cur(k);
+  if (packed) {
+    for (int j = 0; j < k; ++j) cur[j] = j;
+    if (binom_ll(n, k) > 0)
+      while (true) {
+        tup.push_back(cur);
+        int i = k - 1;
+        while (i >= 0 && cur[i] == n - k + i) --i;
+        if (i < 0) break;
+        ++cur[i];
+        for (int j = i + 1; j < k; ++j) cur[j] = cur[j - 1] + 1;
+      }
+  } else {
+    long long tot = 1;
+    for (int j = 0; j < k; ++j) tot *= n;
+    for (long long x = 0; x < tot; ++x) {
+      long long rem = x;
+      for (int j = k - 1; j >= 0; --j) {
+        cur[j] = (int)(rem % n);
+        rem /= n;
+      }
+      tup.push_back(cur);
+    }
+  }
+  auto spin = [](const std::vector<int> &t) {
+    int sm = 0;
+    for (int x : t) sm += (x % 2 == 0) ? 1 : -1;
+    return sm;
+  };
+  std::stable_sort(tup.begin(), tup.end(),
+                   [&](const std::vector<int> &a, const std::vector<int> &b) { return spin(a) < spin(b); });
+  GroupEnum ge;
+  ge.count = (long long)tup.size();
+  for (long long r = 0; r < ge.count; ++r) {
+    ge.flat.insert(ge.flat.end(), tup[r].begin(), tup[r].end());
+    int sm = spin(tup[r]);
+    if (ge.segs.empty() || std::get<0>(ge.segs.back()) != sm) ge.segs.emplace_back(sm, r, 0);
+    ++std::get<2>(ge.segs.back());
+  }
+  return cache.emplace(key, std::move(ge)).first->second;
 }
 
 struct TableBuilder {
@@ -130,16 +196,21 @@ struct TableBuilder {
       int n = dg.space == SP_O ? o : v;
       p.offs.push_back((long long)host.size());
       long long cnt = 0;
-      // a packed storage dimension is read only as the same packed group
+      // a packed or intermediate (positional) storage dimension is read only
+      // as the same group, by canonical position
       const SDim *whole = nullptr;
       for (auto &d : s.dims)
-        if (d.packed && d.labels == dg.labels) whole = &d;
+        if ((d.packed || d.positional) && d.labels == dg.labels) whole = &d;
+      const GroupEnum &ge = enumerate_group(n, dg.k, dg.packed && dg.k >= 2);
       if (whole) {
-        if (!dg.packed) throw std::runtime_error("engine: packed storage read unpacked");
+        if (whole->packed != (dg.packed && dg.k >= 2)) throw std::runtime_error("engine: storage packing mismatch");
         for (long long r = 0; r < whole->size; ++r) host.push_back(r * whole->stride);
         cnt = whole->size;
       } else {
+        // label by label: a dense dimension by index value; a single-label
+        // intermediate dimension by the index's canonical position
         std::vector<long long> st(dg.k), bs(dg.k);
+        std::vector<std::vector<long long>> pos(dg.k);
         for (int j = 0; j < dg.k; ++j) {
           const SDim *hit = nullptr;
           for (auto &d : s.dims)
@@ -147,35 +218,21 @@ struct TableBuilder {
           if (!hit) throw std::runtime_error("engine: label not addressable in operand storage");
           st[j] = hit->stride;
           bs[j] = hit->base;
-        }
-        std::vector<int> cur(dg.k);
-        if (dg.packed) {
-          for (int j = 0; j < dg.k; ++j) cur[j] = j;
-          if (binom_ll(n, dg.k) > 0)
-            while (true) {
-              long long off = 0;
-              for (int j = 0; j < dg.k; ++j) off += st[j] * (bs[j] + cur[j]);
-              host.push_back(off);
-              ++cnt;
-              int i = dg.k - 1;
-              while (i >= 0 && cur[i] == n - dg.k + i) --i;
-              if (i < 0) break;
-              ++cur[i];
-              for (int j = i + 1; j < dg.k; ++j) cur[j] = cur[j - 1] + 1;
-            }
-        } else {
-          long long tot = 1;
-          for (int j = 0; j < dg.k; ++j) tot *= n;
-          for (long long x = 0; x < tot; ++x) {
-            long long rem = x, off = 0;
-            for (int j = dg.k - 1; j >= 0; --j) {
-              off += st[j] * (bs[j] + rem % n);
-              rem /= n;
-            }
-            host.push_back(off);
-            ++cnt;
+          if (hit->positional) {
+            const GroupEnum &g1 = enumerate_group(n, 1, false);
+            pos[j].assign(n, 0);
+            for (long long r = 0; r < g1.count; ++r) pos[j][g1.flat[r]] = r;
           }
         }
+        for (long long r = 0; r < ge.count; ++r) {
+          long long off = 0;
+          for (int j = 0; j < dg.k; ++j) {
+            const int x = ge.flat[r * dg.k + j];
+            off += st[j] * (bs[j] + (pos[j].empty() ? x : pos[j][x]));
+          }
+          host.push_back(off);
+        }
+        cnt = ge.count;
       }
       map->n[g] = cnt;
       long long mx = 0;
@@ -224,8 +281,48 @@ struct TableBuilder {
 
 }  // namespace
 
+namespace {
+
+// Spin bookkeeping of an operand: the sign each label carries in its charge
+// (particle-like / creator +1, hole-like / annihilator -1) and the charge
+// sum_labels sign * spin, conserved by every tensor of the method.
+struct SpinInfo {
+  std::map<int, int> sign;
+  int charge = 0;
+};
+
+SpinInfo input_spin(const Operand &op, int r_charge) {
+  SpinInfo si;
+  for (size_t i = 0; i < op.labels.size(); ++i) {
+    int sg;
+    if (op.kind == TK_F)
+      sg = i == 0 ? 1 : -1;
+    else if (op.kind == TK_V)
+      sg = i < 2 ? 1 : -1;
+    else
+      sg = lab_space(op.labels[i]) == SP_V ? 1 : -1;
+    si.sign[op.labels[i]] = sg;
+  }
+  si.charge = (op.kind >= TK_R1 && op.kind <= TK_R3) ? r_charge : 0;
+  return si;
+}
+
+// group sign in an operand, 0 if its labels disagree or are unknown
+int group_sign(const DimGroup &g, const SpinInfo &si) {
+  int sg = 0;
+  for (int l : g.labels) {
+    auto it = si.sign.find(l);
+    if (it == si.sign.end()) return 0;
+    if (sg == 0) sg = it->second;
+    if (sg != it->second) return 0;
+  }
+  return sg;
+}
+
+}  // namespace
+
 ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize,
-                           double cache_cap)
+                           double cache_cap, int r_charge)
     : nh_(eq.nh), np_(eq.np), o_(o), v_(v) {
   TableBuilder tb;
   Storage outs = output_storage(nh_, np_, o, v);
@@ -265,6 +362,12 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
           return dense_storage(op.labels, o, v);
       }
     };
+    std::vector<SpinInfo> inter_spin(plan.inter_dims.size());
+    std::vector<char> inter_spin_set(plan.inter_dims.size(), 0);
+    auto spin_of = [&](const Operand &op) -> SpinInfo {
+      if (op.kind == TK_INTERMEDIATE) return inter_spin.at(op.inter);
+      return input_spin(op, r_charge);
+    };
     et.steps.reserve(plan.steps.size());
     std::vector<char> written(plan.inter_dims.size(), 0);
     for (const Step &s : plan.steps) {
@@ -288,7 +391,8 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
         tb.add(&e.crow, s.mg, sc, o, v);
       else
         tb.add_positional(&e.crow, s.mg, sc, 0);
-      if (s.b.kind >= 0) {
+      const bool binary = s.b.kind >= 0;
+      if (binary) {
         Storage sb = storage_of(s.b);
         e.K = tb.add(&e.acol, s.kg, sa, o, v);
         tb.add(&e.brow, s.kg, sb, o, v);
@@ -297,17 +401,116 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
           tb.add(&e.ccol, s.ng, sc, o, v);
         else
           tb.add_positional(&e.ccol, s.ng, sc, (int)s.mg.size());
-        (s.constant ? cached_flops_ : flops_) += 2.0 * double(e.M) * double(e.N) * double(e.K);
       } else {
         e.N = 1;
         e.K = 1;
-        (s.constant ? cached_flops_ : flops_) += double(e.M);
       }
+      // spin: charges and group signs; the result's spin info for intermediates
+      SpinInfo sa_spin = spin_of(s.a), sb_spin;
+      if (binary) sb_spin = spin_of(s.b);
+      if (!s.to_output && !inter_spin_set[s.out_inter]) {
+        // the producer writes the intermediate's dims positionally (mg, then ng):
+        // dim d takes the signs of the producer's group d
+        SpinInfo r;
+        const auto &dims = plan.inter_dims.at(s.out_inter);
+        size_t d = 0;
+        for (int side = 0; side < 2; ++side) {
+          const auto &gs = side == 0 ? s.mg : s.ng;
+          const SpinInfo &src = side == 0 ? sa_spin : sb_spin;
+          for (auto &g : gs) {
+            if (d >= dims.size() || dims[d].labels.size() != g.labels.size())
+              throw std::runtime_error("engine: producer groups do not match the intermediate");
+            for (size_t j = 0; j < g.labels.size(); ++j) {
+              auto it = src.sign.find(g.labels[j]);
+              r.sign[dims[d].labels[j]] = it == src.sign.end() ? 0 : it->second;
+            }
+            ++d;
+          }
+        }
+        r.charge = sa_spin.charge + (binary ? sb_spin.charge : 0);
+        inter_spin[s.out_inter] = r;
+        inter_spin_set[s.out_inter] = 1;
+      }
+      // spin-allowed sub-GEMMs of large steps
+      const double full = binary ? 2.0 * double(e.M) * double(e.N) * double(e.K) : double(e.M);
+      std::vector<const DimGroup *> groups;
+      std::vector<int> sig_a, sig_b;
+      for (auto &g : s.mg) {
+        groups.push_back(&g);
+        sig_a.push_back(group_sign(g, sa_spin));
+        sig_b.push_back(0);
+      }
+      if (binary) {
+        for (auto &g : s.kg) {
+          groups.push_back(&g);
+          sig_a.push_back(group_sign(g, sa_spin));
+          sig_b.push_back(group_sign(g, sb_spin));
+        }
+        for (auto &g : s.ng) {
+          groups.push_back(&g);
+          sig_a.push_back(0);
+          sig_b.push_back(group_sign(g, sb_spin));
+        }
+      }
+      bool signs_ok = true;
+      for (size_t gi = 0; gi < groups.size(); ++gi) {
+        bool in_a = gi < s.mg.size() + (binary ? s.kg.size() : 0);
+        bool in_b = binary && gi >= s.mg.size();
+        if ((in_a && sig_a[gi] == 0) || (in_b && sig_b[gi] == 0)) signs_ok = false;
+      }
+      double done_flops = full;
+      if (signs_ok && full >= 1e7) {
+        std::vector<const GroupEnum *> ge;
+        for (auto *g : groups) ge.push_back(&enumerate_group(g->space == SP_O ? o : v, g->k, g->packed && g->k >= 2));
+        std::vector<int> pick(groups.size(), 0);
+        const size_t nm = s.mg.size(), nk = binary ? s.kg.size() : 0;
+        double blocked_flops = 0;
+        std::function<void(size_t, int, int)> rec = [&](size_t gi, int ca, int cb) {
+          if (gi == groups.size()) {
+            if (ca != sa_spin.charge) return;
+            if (binary && cb != sb_spin.charge) return;
+            SubGemm b;
+            b.M = b.N = b.K = 1;
+            for (size_t q = 0; q < groups.size(); ++q) {
+              auto &sg = ge[q]->segs[pick[q]];
+              std::pair<long long, long long> seg(std::get<1>(sg), std::get<2>(sg));
+              if (q < nm) {
+                b.mseg.push_back(seg);
+                b.M *= seg.second;
+              } else if (q < nm + nk) {
+                b.kseg.push_back(seg);
+                b.K *= seg.second;
+              } else {
+                b.nseg.push_back(seg);
+                b.N *= seg.second;
+              }
+            }
+            blocked_flops += binary ? 2.0 * double(b.M) * double(b.N) * double(b.K) : double(b.M);
+            e.blocks.push_back(b);
+            return;
+          }
+          for (size_t k = 0; k < ge[gi]->segs.size(); ++k) {
+            pick[gi] = (int)k;
+            int sv = std::get<0>(ge[gi]->segs[k]);
+            rec(gi + 1, ca + sig_a[gi] * sv, cb + sig_b[gi] * sv);
+          }
+        };
+        rec(0, 0, 0);
+        e.blocked = true;
+        done_flops = blocked_flops;
+      }
+      (s.constant ? cached_flops_ : flops_) += done_flops;
     }
     terms_.push_back(std::move(et));
   }
   (void)rdims;
   tb.upload(tables_);
+}
+
+bool ExecEquation::autotune = true;
+
+ExecEquation::~ExecEquation() {
+  for (auto ev : tune_events_) cudaEventDestroy(ev);
 }
 
 void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch,
@@ -356,13 +559,80 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
       }
       const double *A = ptr(s.a_kind, s.a_inter);
       if (!A) throw std::runtime_error("engine: missing operand");
+      auto sub_map = [](const DMap &full, const std::vector<std::pair<long long, long long>> &seg) {
+        DMap m = full;
+        for (size_t g = 0; g < seg.size(); ++g) {
+          m.tab[g] = full.tab[g] + seg[g].first;
+          m.n[g] = seg[g].second;
+        }
+        return m;
+      };
+      if (s.blocked) {
+        for (const SubGemm &b : s.blocks) {
+          if (b.M == 0 || b.N == 0 || b.K == 0) continue;
+          DMap arow = sub_map(s.arow, b.mseg), crow = sub_map(s.crow, b.mseg);
+          if (s.b_kind < 0) {
+            gather_axpy(L, b.M, s.alpha, A, arow, C, crow, size(s.a_kind, s.a_inter), csize);
+            continue;
+          }
+          const double *B = ptr(s.b_kind, s.b_inter);
+          DMap acol = sub_map(s.acol, b.kseg), brow = sub_map(s.brow, b.kseg);
+          DMap bcol = sub_map(s.bcol, b.nseg), ccol = sub_map(s.ccol, b.nseg);
+          gather_gemm(L, b.M, b.N, b.K, s.alpha, A, arow, acol, B, brow, bcol, C, crow, ccol, true,
+                      size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize);
+        }
+        continue;
+      }
       if (s.b_kind < 0) {
         gather_axpy(L, s.M, s.alpha, A, s.arow, C, s.crow, size(s.a_kind, s.a_inter), csize);
       } else {
         const double *B = ptr(s.b_kind, s.b_inter);
         if (!B) throw std::runtime_error("engine: missing operand");
-        gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol, true,
-                    size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize);
+        ExecStep &ms = const_cast<ExecStep &>(s);
+        const bool tune = autotune && L.precision == 0 && ms.tuned_shape < 0 &&
+                          2.0 * double(s.M) * double(s.N) * double(s.K) >= 2e8;
+        if (!tune) {
+          const int shape = (ms.tuned_shape >= 0 && ms.tuned_shape < kTileShapes) ? ms.tuned_shape : -1;
+          gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol, true,
+                      size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize, shape);
+          continue;
+        }
+        if (ms.pending < 0) {  // first use: an event pair of its own
+          ms.pending = tune_count_++;
+          while ((int)tune_events_.size() < 2 * tune_count_) {
+            cudaEvent_t ev;
+            FNOCC_CUDA(cudaEventCreate(&ev));
+            tune_events_.push_back(ev);
+          }
+        }
+        cudaEvent_t e0 = tune_events_[2 * ms.pending], e1 = tune_events_[2 * ms.pending + 1];
+        for (int k = 0; k < kTileShapes; ++k)
+          if (ms.trial_ms[k] < 0) {  // the trial of the previous run
+            FNOCC_CUDA(cudaEventSynchronize(e1));
+            float t = 0;
+            FNOCC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            ms.trial_ms[k] = std::max(t, 1e-6f);
+          }
+        int next = -1;
+        for (int k = 0; k < kTileShapes && next < 0; ++k)
+          if (ms.trial_ms[k] == 0) next = k;
+        if (next < 0) {
+          int best = 0;
+          for (int k = 1; k < kTileShapes; ++k)
+            if (ms.trial_ms[k] < ms.trial_ms[best]) best = k;
+          ms.tuned_shape = best;
+          gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol, true,
+                      size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize, best);
+          continue;
+        }
+        FNOCC_CUDA(cudaEventRecord(e0, L.stream));
+        int used = gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol,
+                               true, size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize, next);
+        FNOCC_CUDA(cudaEventRecord(e1, L.stream));
+        if (used < 0)
+          ms.tuned_shape = kTileShapes;  // not a tiled launch: nothing to tune
+        else
+          ms.trial_ms[next] = -1.f;       // in flight; read on the next run
       }
     }
   }

@@ -19,8 +19,17 @@ struct Operands {
   long long f_size = 0, v_size = 0, t2_size = 0, t3_size = 0, r_size[3] = {0, 0, 0};
 };
 
+// One spin-allowed block of a step: for every M, K and N group a contiguous
+// segment (start, length) of its spin-sorted tuple list.
+struct SubGemm {
+  std::vector<std::pair<long long, long long>> mseg, kseg, nseg;
+  long long M = 0, N = 0, K = 0;
+};
+
 struct ExecStep {
   int a_kind, a_inter, b_kind, b_inter;
+  bool blocked = false;          // run as spin-allowed sub-GEMMs
+  std::vector<SubGemm> blocks;
   bool constant;   // R-independent: run once per H-bar version into the cache
   bool zero_first; // first writer of its intermediate: zero it before the step
   bool to_output;
@@ -28,6 +37,11 @@ struct ExecStep {
   long long M, N, K;
   double alpha;
   DMap arow, acol, brow, bcol, crow, ccol;
+  // tile-shape autotuning of large FP64 steps: every shape is timed once,
+  // then the fastest is kept
+  int tuned_shape = -1;  // -1 untuned, kTileShapes: not a tiled launch
+  float trial_ms[kTileShapes] = {0, 0, 0, 0, 0};  // 0 untimed, < 0 in flight
+  int pending = -1;      // index of this step's event pair, -1 none yet
 };
 
 struct ExecTerm {
@@ -42,8 +56,9 @@ class ExecEquation {
  public:
   // rdims: (nh, np) of the three EOM input components (ignored for CC)
   // amortize > 0: R-independent steps are cached (see plan_term)
+  // r_charge: 2*M_s change of the EOM vectors (their spin sector); 0 for CC.
   ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize = 0.0,
-               double cache_cap = 0.0);
+               double cache_cap = 0.0, int r_charge = 0);
   // Y (dense output accumulator [o^nh v^np]) += sum of terms. version: the
   // cached R-independent intermediates are recomputed when it changes.
   void run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch,
@@ -52,6 +67,9 @@ class ExecEquation {
   long long cache_doubles() const { return cache_need_; }
   double flops() const { return flops_; }              // per run, cached steps excluded
   double cached_flops() const { return cached_flops_; }  // once per version
+  ~ExecEquation();
+  // autotuning switch for all equations (on by default)
+  static bool autotune;
   int nh() const { return nh_; }
   int np() const { return np_; }
   size_t nterms() const { return terms_.size(); }
@@ -61,6 +79,8 @@ class ExecEquation {
   std::vector<ExecTerm> terms_;
   DevBuf tables_;
   DevBuf cache_;
+  std::vector<cudaEvent_t> tune_events_;  // two per tuned step
+  int tune_count_ = 0;
   uint64_t cache_version_ = ~0ULL;
   long long scratch_need_ = 0, cache_need_ = 0;
   double flops_ = 0, cached_flops_ = 0;

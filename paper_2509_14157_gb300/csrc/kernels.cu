@@ -10,16 +10,18 @@
 // K staged through shared memory 16 at a time.
 #include "common.hpp"
 
+#include <cuda_bf16.h>
 #include <math_constants.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace fnocc {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
 struct GemmParams {
   long long M, N, K;
@@ -45,31 +47,38 @@ __device__ __forceinline__ long long map_off(const DMap &mp, long long m) {
   return off;
 }
 
-__global__ void __launch_bounds__(NT) k_gather_gemm(const GemmParams p) {
-  __shared__ double As[BK][BM];
-  __shared__ double Bs[BK][BN];
-  __shared__ long long arow_s[BM], crow_s[BM], bcol_s[BN], ccol_s[BN], acol_s[BK], brow_s[BK];
+// Tiled FP64 gather-GEMM. 256 threads as 16 x 16, each computing a TM x TN
+// micro-tile, so a block covers 16*TM rows and 16*TN columns; K is
+// staged through shared memory 16 at a time. PART: write the block's partial
+// product of one K chunk (grid.y) to part[z][m * N + n] for an ordered
+// split-K reduction instead of updating C.
+template <int TM, int TN, bool PART>
+__global__ void __launch_bounds__(NT) k_gather_gemm(const GemmParams p, double *part) {
+  constexpr int TBM = 16 * TM, TBN = 16 * TN;
+  __shared__ double As[BK][TBM];
+  __shared__ double Bs[BK][TBN];
+  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[BK], brow_s[BK];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const long long tile = blockIdx.x;
-  const long long m0 = (tile / p.tiles_n) * BM;
-  const long long n0 = (tile % p.tiles_n) * BN;
+  const long long m0 = (tile / p.tiles_n) * TBM;
+  const long long n0 = (tile % p.tiles_n) * TBN;
   const long long kb = (long long)blockIdx.y * p.kchunk;
   const long long ke = min(p.K, kb + p.kchunk);
-  if (tid < BM) {
+  if (tid < TBM) {
     long long m = m0 + tid;
     arow_s[tid] = m < p.M ? map_off(p.arow, m) : 0;
-    crow_s[tid] = m < p.M ? map_off(p.crow, m) : 0;
-  } else if (tid < BM + BN) {
-    long long n = n0 + tid - BM;
-    bcol_s[tid - BM] = n < p.N ? map_off(p.bcol, n) : 0;
-    ccol_s[tid - BM] = n < p.N ? map_off(p.ccol, n) : 0;
+    if (!PART) crow_s[tid] = m < p.M ? map_off(p.crow, m) : 0;
+  } else if (tid < TBM + TBN) {
+    long long n = n0 + tid - TBM;
+    bcol_s[tid - TBM] = n < p.N ? map_off(p.bcol, n) : 0;
+    if (!PART) ccol_s[tid - TBM] = n < p.N ? map_off(p.ccol, n) : 0;
   }
-  double acc[4][4];
+  double acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
   for (long long k0 = kb; k0 < ke; k0 += BK) {
     __syncthreads();
     if (tid < BK) {
@@ -81,142 +90,212 @@ __global__ void __launch_bounds__(NT) k_gather_gemm(const GemmParams p) {
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < (BM * BK) / NT; ++r) {
+    for (int r = 0; r < TM; ++r) {  // TBM * BK / NT = TM elements per thread
       int idx = tid + NT * r;
       int kk = idx % BK, row = idx / BK;
       bool ok = (m0 + row < p.M) && (k0 + kk < ke);
       As[kk][row] = ok ? p.A[arow_s[row] + acol_s[kk]] : 0.0;
     }
 #pragma unroll
-    for (int r = 0; r < (BN * BK) / NT; ++r) {
+    for (int r = 0; r < TN; ++r) {
       int idx = tid + NT * r;
-      int col = idx % BN, kk = idx / BN;
+      int col = idx % TBN, kk = idx / TBN;
       bool ok = (n0 + col < p.N) && (k0 + kk < ke);
       Bs[kk][col] = ok ? p.B[brow_s[kk] + bcol_s[col]] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
   }
+  double *dst_part = PART ? part + (long long)blockIdx.y * p.M * p.N : nullptr;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    long long m = m0 + ty * 4 + i;
+  for (int i = 0; i < TM; ++i) {
+    long long m = m0 + ty * TM + i;
     if (m >= p.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      long long n = n0 + tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      long long n = n0 + tx * TN + j;
       if (n >= p.N) continue;
-      double *dst = p.C + crow_s[ty * 4 + i] + ccol_s[tx * 4 + j];
-      double val = p.alpha * acc[i][j];
-      if (p.accumulate)
-        *dst += val;
-      else
-        *dst = val;
+      if (PART) {
+        dst_part[m * p.N + n] = acc[i][j];
+      } else {
+        double *dst = p.C + crow_s[ty * TM + i] + ccol_s[tx * TN + j];
+        double val = p.alpha * acc[i][j];
+        if (p.accumulate)
+          *dst += val;
+        else
+          *dst = val;
+      }
     }
   }
 }
 
-// Split-K partial products: the tiled kernel writes its 64x64 tile of a K
-// chunk to part[z][m * N + n] instead of C (grid.y = z); k_reduce_partials
-// sums the chunks in order, so results do not depend on scheduling.
-__global__ void __launch_bounds__(NT) k_gather_gemm_part(const GemmParams p, double *part) {
-  __shared__ double As[BK][BM];
-  __shared__ double Bs[BK][BN];
-  __shared__ long long arow_s[BM], bcol_s[BN], acol_s[BK], brow_s[BK];
+// BF16 three-slice split GEMM on the tensor cores (mixed precision). Each
+// gathered FP64 operand element is rounded to FP32 and split exactly into
+// three BF16 slices x = x0 + x1 + x2 (8 significant bits each, 24 in all);
+// the six slice products with i + j <= 2 are accumulated in FP32 by
+// mma.sync m16n8k16 (the products themselves are exact). Block tile 64 x 64,
+// K tile 32, 8 warps as 2 x 4, each warp 32 x 16 outputs (2 x 2 MMA tiles).
+// Relative error about 1e-7 of the summed magnitudes; the solvers finish in
+// FP64.
+template <bool PART>
+__global__ void __launch_bounds__(NT) k_gather_gemm_bf16x3(const GemmParams p, double *part) {
+  constexpr int TBM = 64, TBN = 64, TBK = 32, LDS = 40;  // padded row stride (bf16) avoids bank conflicts
+  __shared__ __align__(16) __nv_bfloat16 As[3][TBM][LDS];
+  __shared__ __align__(16) __nv_bfloat16 Bs[3][TBN][LDS];
+  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[TBK], brow_s[TBK];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 2, wn = warp & 3;
+  const int g = lane >> 2, tg = lane & 3;
   const long long tile = blockIdx.x;
-  const long long m0 = (tile / p.tiles_n) * BM;
-  const long long n0 = (tile % p.tiles_n) * BN;
+  const long long m0 = (tile / p.tiles_n) * TBM;
+  const long long n0 = (tile % p.tiles_n) * TBN;
   const long long kb = (long long)blockIdx.y * p.kchunk;
   const long long ke = min(p.K, kb + p.kchunk);
-  if (tid < BM) {
+  if (tid < TBM) {
     long long m = m0 + tid;
     arow_s[tid] = m < p.M ? map_off(p.arow, m) : 0;
-  } else if (tid < BM + BN) {
-    long long n = n0 + tid - BM;
-    bcol_s[tid - BM] = n < p.N ? map_off(p.bcol, n) : 0;
+    crow_s[tid] = (!PART && m < p.M) ? map_off(p.crow, m) : 0;
+  } else if (tid < TBM + TBN) {
+    long long n = n0 + tid - TBM;
+    bcol_s[tid - TBM] = n < p.N ? map_off(p.bcol, n) : 0;
+    ccol_s[tid - TBM] = (!PART && n < p.N) ? map_off(p.ccol, n) : 0;
   }
-  double acc[4][4];
+  float acc[2][2][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (long long k0 = kb; k0 < ke; k0 += BK) {
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  for (long long k0 = kb; k0 < ke; k0 += TBK) {
     __syncthreads();
-    if (tid < BK) {
+    if (tid < TBK) {
       long long k = k0 + tid;
       acol_s[tid] = k < ke ? map_off(p.acol, k) : 0;
-    } else if (tid < 2 * BK) {
-      long long k = k0 + tid - BK;
-      brow_s[tid - BK] = k < ke ? map_off(p.brow, k) : 0;
+    } else if (tid < 2 * TBK) {
+      long long k = k0 + tid - TBK;
+      brow_s[tid - TBK] = k < ke ? map_off(p.brow, k) : 0;
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < (BM * BK) / NT; ++r) {
+    for (int r = 0; r < (TBM * TBK) / NT; ++r) {
       int idx = tid + NT * r;
-      int kk = idx % BK, row = idx / BK;
+      int kk = idx % TBK, row = idx / TBK;
       bool ok = (m0 + row < p.M) && (k0 + kk < ke);
-      As[kk][row] = ok ? p.A[arow_s[row] + acol_s[kk]] : 0.0;
+      float xf = ok ? (float)p.A[arow_s[row] + acol_s[kk]] : 0.f;
+      __nv_bfloat16 h = __float2bfloat16_rn(xf);
+      float r1 = xf - __bfloat162float(h);
+      __nv_bfloat16 md = __float2bfloat16_rn(r1);
+      float r2 = r1 - __bfloat162float(md);
+      As[0][row][kk] = h;
+      As[1][row][kk] = md;
+      As[2][row][kk] = __float2bfloat16_rn(r2);
     }
 #pragma unroll
-    for (int r = 0; r < (BN * BK) / NT; ++r) {
+    for (int r = 0; r < (TBN * TBK) / NT; ++r) {
       int idx = tid + NT * r;
-      int col = idx % BN, kk = idx / BN;
+      int col = idx % TBN, kk = idx / TBN;
       bool ok = (n0 + col < p.N) && (k0 + kk < ke);
-      Bs[kk][col] = ok ? p.B[brow_s[kk] + bcol_s[col]] : 0.0;
+      float xf = ok ? (float)p.B[brow_s[kk] + bcol_s[col]] : 0.f;
+      __nv_bfloat16 h = __float2bfloat16_rn(xf);
+      float r1 = xf - __bfloat162float(h);
+      __nv_bfloat16 md = __float2bfloat16_rn(r1);
+      float r2 = r1 - __bfloat162float(md);
+      Bs[0][col][kk] = h;
+      Bs[1][col][kk] = md;
+      Bs[2][col][kk] = __float2bfloat16_rn(r2);
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+    for (int ks = 0; ks < TBK; ks += 16) {
+      unsigned a[3][2][4], b[3][2][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int s = 0; s < 3; ++s) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+        for (int mt = 0; mt < 2; ++mt) {
+          const int r0 = wm * 32 + mt * 16 + g;
+          const int c0 = ks + 2 * tg;
+          a[s][mt][0] = *reinterpret_cast<const unsigned *>(&As[s][r0][c0]);
+          a[s][mt][1] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0]);
+          a[s][mt][2] = *reinterpret_cast<const unsigned *>(&As[s][r0][c0 + 8]);
+          a[s][mt][3] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0 + 8]);
+        }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int nt = 0; nt < 2; ++nt) {
+          const int n = wn * 16 + nt * 8 + g;
+          b[s][nt][0] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg]);
+          b[s][nt][1] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg + 8]);
+        }
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3 - i; ++j)
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+              asm volatile(
+                  "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                  "{%0,%1,%2,%3};\n"
+                  : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
+                  : "r"(a[i][mt][0]), "r"(a[i][mt][1]), "r"(a[i][mt][2]), "r"(a[i][mt][3]), "r"(b[j][nt][0]),
+                    "r"(b[j][nt][1]));
     }
   }
-  double *dst = part + (long long)blockIdx.y * p.M * p.N;
+  double *dst_part = PART ? part + (long long)blockIdx.y * p.M * p.N : nullptr;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    long long m = m0 + ty * 4 + i;
-    if (m >= p.M) continue;
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      long long n = n0 + tx * 4 + j;
-      if (n < p.N) dst[m * p.N + n] = acc[i][j];
-    }
-  }
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int rl = wm * 32 + mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int cl = wn * 16 + nt * 8 + 2 * tg + (e & 1);
+        const long long m = m0 + rl, n = n0 + cl;
+        if (m >= p.M || n >= p.N) continue;
+        if (PART) {
+          dst_part[m * p.N + n] = (double)acc[mt][nt][e];
+        } else {
+          double *dst = p.C + crow_s[rl] + ccol_s[cl];
+          double val = p.alpha * (double)acc[mt][nt][e];
+          if (p.accumulate)
+            *dst += val;
+          else
+            *dst = val;
+        }
+      }
 }
 
-// Small outputs (M*N <= 256): one thread per output, blocks split K; every
-// useful multiply-add is done once. Partials go to part[blockIdx.x][M*N].
+// Small outputs (M*N <= 256): blocks split K; inside a block the K chunk is
+// staged 256 offsets at a time, warp w owns outputs w, w + 8, ... (at most
+// 32), its lanes stride over K and a shuffle reduction closes each output.
+// Partials go to part[blockIdx.x][M*N]; every useful multiply-add is done once.
 __global__ void __launch_bounds__(256) k_gemm_small(const GemmParams p, double *part) {
-  __shared__ long long acol_s[256], brow_s[256];
-  const int t = threadIdx.x;
+  __shared__ long long acol_s[256], brow_s[256], ar_s[256], bc_s[256];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const long long O = p.M * p.N;
-  long long ar = 0, bc = 0;
   if (t < O) {
-    ar = map_off(p.arow, t / p.N);
-    bc = map_off(p.bcol, t % p.N);
+    ar_s[t] = map_off(p.arow, t / p.N);
+    bc_s[t] = map_off(p.bcol, t % p.N);
   }
   const long long kb = (long long)blockIdx.x * p.kchunk;
   const long long ke = min(p.K, kb + p.kchunk);
-  double acc = 0.0;
+  double acc[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = 0.0;
   for (long long k0 = kb; k0 < ke; k0 += 256) {
     __syncthreads();
     long long k = k0 + t;
@@ -224,10 +303,26 @@ __global__ void __launch_bounds__(256) k_gemm_small(const GemmParams p, double *
     brow_s[t] = k < ke ? map_off(p.brow, k) : 0;
     __syncthreads();
     const int nk = (int)min((long long)256, ke - k0);
-    if (t < O)
-      for (int kk = 0; kk < nk; ++kk) acc = fma(p.A[ar + acol_s[kk]], p.B[brow_s[kk] + bc], acc);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int o = warp + 8 * j;
+      if (o < O) {
+        const long long ab = ar_s[o], bb = bc_s[o];
+        double s = acc[j];
+        for (int kk = lane; kk < nk; kk += 32) s = fma(p.A[ab + acol_s[kk]], p.B[brow_s[kk] + bb], s);
+        acc[j] = s;
+      }
+    }
   }
-  if (t < O) part[(long long)blockIdx.x * O + t] = acc;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int o = warp + 8 * j;
+    if (o < O) {  // uniform across the warp
+      double v = acc[j];
+      for (int w = 16; w > 0; w >>= 1) v += __shfl_down_sync(0xffffffffu, v, w);
+      if (lane == 0) part[(long long)blockIdx.x * O + o] = v;
+    }
+  }
 }
 
 // C[crow(m) + ccol(n)] (+)= alpha * sum_z part[z][m * N + n], z in order
@@ -664,9 +759,16 @@ __global__ void k_cc_den(const double *fd, int o, int rank, const int *htab, lon
 
 inline unsigned blocks_for(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 
+// The permutation tables live in constant memory, one copy per device: fill
+// each device's copy once (thread-safe; contexts may run on host threads).
 void ensure_perm_tables() {
-  static bool done = false;
-  if (done) return;
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  FNOCC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64) throw std::runtime_error("device index out of range");
+  if (done[dev]) return;
   signed char perm[5][24][4] = {};
   signed char sgn[5][24] = {};
   int cnt[5] = {};
@@ -687,7 +789,7 @@ void ensure_perm_tables() {
   FNOCC_CUDA(cudaMemcpyToSymbol(c_perm, perm, sizeof(perm)));
   FNOCC_CUDA(cudaMemcpyToSymbol(c_psign, sgn, sizeof(sgn)));
   FNOCC_CUDA(cudaMemcpyToSymbol(c_pcount, cnt, sizeof(cnt)));
-  done = true;
+  done[dev] = true;
 }
 
 inline void post(const Launch &L) {
@@ -697,11 +799,11 @@ inline void post(const Launch &L) {
 
 }  // namespace
 
-void gather_gemm(const Launch &L, long long M, long long N, long long K, double alpha, const double *A,
+int gather_gemm(const Launch &L, long long M, long long N, long long K, double alpha, const double *A,
                  const DMap &arow, const DMap &acol, const double *B, const DMap &brow, const DMap &bcol, double *C,
                  const DMap &crow, const DMap &ccol, bool accumulate, long long asize, long long bsize,
-                 long long csize) {
-  if (M <= 0 || N <= 0) return;
+                 long long csize, int shape_req) {
+  if (M <= 0 || N <= 0) return -1;
   if (arow.maxoff + acol.maxoff >= asize || brow.maxoff + bcol.maxoff >= bsize || crow.maxoff + ccol.maxoff >= csize ||
       arow.maxoff < 0 || acol.maxoff < 0 || brow.maxoff < 0 || bcol.maxoff < 0 || crow.maxoff < 0 || ccol.maxoff < 0)
     throw std::runtime_error("gather_gemm: index map exceeds operand bounds");
@@ -719,9 +821,46 @@ void gather_gemm(const Launch &L, long long M, long long N, long long K, double 
   p.bcol = bcol;
   p.crow = crow;
   p.ccol = ccol;
-  p.tiles_n = (N + BN - 1) / BN;
-  long long tiles = ((M + BM - 1) / BM) * p.tiles_n;
+  const bool mixed = L.precision == 1 && M >= 32 && N >= 32 && p.K >= 32;
+  // tile shape with the least padding (ties: the square 64 x 64 tile)
+  static const int shapes[kTileShapes][2] = {{4, 4}, {8, 2}, {2, 8}, {8, 1}, {1, 8}};
+  int shape = 0;
+  double best_pad = -1;
+  for (int sidx = 0; sidx < kTileShapes; ++sidx) {
+    long long bm = 16 * shapes[sidx][0], bn = 16 * shapes[sidx][1];
+    double pad = double((M + bm - 1) / bm * bm) * double((N + bn - 1) / bn * bn);
+    if (best_pad < 0 || pad < best_pad * 0.999) {
+      best_pad = pad;
+      shape = sidx;
+    }
+  }
+  if (shape_req >= 0 && shape_req < kTileShapes) shape = shape_req;
+  const long long tbm = mixed ? 64 : 16 * shapes[shape][0], tbn = mixed ? 64 : 16 * shapes[shape][1];
+  p.tiles_n = (N + tbn - 1) / tbn;
+  long long tiles = ((M + tbm - 1) / tbm) * p.tiles_n;
   p.accumulate = accumulate ? 1 : 0;
+  auto launch_tiled = [&](dim3 grid, bool part_mode, double *partp) {
+    if (mixed) {
+      if (part_mode)
+        k_gather_gemm_bf16x3<true><<<grid, NT, 0, L.stream>>>(p, partp);
+      else
+        k_gather_gemm_bf16x3<false><<<grid, NT, 0, L.stream>>>(p, partp);
+      return;
+    }
+#define FNOCC_TILED(a, b)                                                                       \
+  if (part_mode)                                                                               \
+    k_gather_gemm<a, b, true><<<grid, NT, 0, L.stream>>>(p, partp);                            \
+  else                                                                                         \
+    k_gather_gemm<a, b, false><<<grid, NT, 0, L.stream>>>(p, partp);
+    switch (shape) {
+      case 0: FNOCC_TILED(4, 4) break;
+      case 1: FNOCC_TILED(8, 2) break;
+      case 2: FNOCC_TILED(2, 8) break;
+      case 3: FNOCC_TILED(8, 1) break;
+      default: FNOCC_TILED(1, 8) break;
+    }
+#undef FNOCC_TILED
+  };
   GemmProfile *pr = (L.prof && L.prof->enabled) ? L.prof : nullptr;
   int e0 = -1;
   auto begin = [&]() {
@@ -752,7 +891,7 @@ void gather_gemm(const Launch &L, long long M, long long N, long long K, double 
     k_gemv_rows<<<blocks_for(M, 256), 256, 0, L.stream>>>(p);
     post(L);
     end(3);
-    return;
+    return -1;
   }
   // tiny outputs: one thread per output, K split over blocks, ordered reduction
   if (O <= 256) {
@@ -768,7 +907,7 @@ void gather_gemm(const Launch &L, long long M, long long N, long long K, double 
     k_reduce_partials<<<blocks_for(O, 256), 256, 0, L.stream>>>(p, L.partials->d(), (int)nblk);
     post(L);
     end(2);
-    return;
+    return -1;
   }
   long long ksplit = 1;
   if (tiles < want && p.K >= 4 * BK && L.partials) {
@@ -786,18 +925,19 @@ void gather_gemm(const Launch &L, long long M, long long N, long long K, double 
     L.partials->reserve(sizeof(double) * (size_t)(ksplit * O));
     dim3 g2((unsigned)tiles, (unsigned)ksplit);
     begin();
-    k_gather_gemm_part<<<g2, NT, 0, L.stream>>>(p, L.partials->d());
+    launch_tiled(g2, true, L.partials->d());
     post(L);
     k_reduce_partials<<<blocks_for(O, 256), 256, 0, L.stream>>>(p, L.partials->d(), (int)ksplit);
     post(L);
     end(1);
-    return;
+    return mixed ? -1 : shape;
   }
   dim3 grid((unsigned)tiles, 1);
   begin();
-  k_gather_gemm<<<grid, NT, 0, L.stream>>>(p);
+  launch_tiled(grid, false, nullptr);
   post(L);
   end(0);
+  return mixed ? -1 : shape;
 }
 
 void GemmProfile::fold() {
@@ -930,10 +1070,17 @@ void t1_transform_mats(const Launch &L, const double *t1, int o, int v, double *
 void jacobi_eig(const Launch &L, double *A, int n, double *evals, double *V, int *info_dev) {
   if (n > 128) throw std::runtime_error("jacobi_eig: n > 128");
   size_t smem = sizeof(double) * (size_t)n * n;
-  static bool attr = false;
-  if (!attr) {
-    FNOCC_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8));
-    attr = true;
+  {
+    static std::mutex mu;
+    static bool attr[64] = {false};
+    int dev = 0;
+    FNOCC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) throw std::runtime_error("device index out of range");
+    if (!attr[dev]) {
+      FNOCC_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8));
+      attr[dev] = true;
+    }
   }
   k_jacobi_eig<<<1, 512, smem, L.stream>>>(A, n, evals, V, info_dev);
   post(L);

@@ -1,0 +1,65 @@
+"""Batched independent solves (several contexts and streams on one GPU)
+against the same systems solved one by one: identical energies.
+
+Each system runs the whole path on its own context; the kernels are
+deterministic (no atomics), so concurrency must not change a single result
+beyond the convergence tolerance of the solvers."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2509_14157_gb300 as p
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p.load_library()
+    return p
+
+
+def small_systems():
+    out = []
+    # (electrons, orbitals, seed, nkeep): seeds whose RHF converges
+    for ne, n, seed, nkeep in [(4, 8, 2, 3), (6, 10, 0, 0), (4, 9, 1, 4), (6, 11, 3, 5), (8, 12, 2, 0)]:
+        h, eri = synth.hamiltonian(ne, n, seed=seed)
+        out.append(dict(h=h, eri=eri, nocc=ne // 2, threshold=1e-4, nkeep=nkeep))
+    return out
+
+
+def test_batch_equals_solo(pkg):
+    systems = small_systems()
+    variants = ["ip", "ea"]
+    om, info = pkg.batch_solve(systems, variants, 2, nworkers=3)
+    assert om.shape == (len(systems), 2, 2)
+    assert sum(i["status"] == 0 for i in info) >= 4, info
+    for s, sy in enumerate(systems):
+        ctx = pkg.Context(0)
+        try:
+            fi = ctx.fno_truncate(sy["h"], sy["eri"], sy["nocc"], sy["threshold"], nkeep=sy["nkeep"])
+        except pkg.FnoccError as err:  # the same failure as in the batch
+            assert err.status == info[s]["status"], (s, err, info[s])
+            ctx.close()
+            continue
+        assert info[s]["status"] == 0, (s, info[s])
+        assert fi["nkept"] == info[s]["nkept"]
+        if sy["nkeep"]:
+            assert fi["nkept"] == sy["nkeep"]
+        cc = ctx.ccsdt_solve()
+        assert abs(cc["e_tot"] - info[s]["e_ccsdt"]) < 1e-9
+        for k, var in enumerate(variants):
+            r = ctx.eom_solve(var, 2)
+            assert np.max(np.abs(r["omegas"] - om[s, k])) < 1e-9, (s, var)
+        ctx.close()
+
+
+def test_batch_rejects_bad_input(pkg):
+    h, eri = synth.hamiltonian(4, 8, seed=0)
+    with pytest.raises(pkg.FnoccError):
+        pkg.batch_solve([dict(h=h, eri=eri, nocc=8, threshold=1e-4)], ["ip"], 1)
+    with pytest.raises(pkg.FnoccError):
+        pkg.batch_solve([dict(h=h, eri=eri, nocc=2, threshold=1e-4)], [7], 1)
