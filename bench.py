@@ -40,6 +40,15 @@ VARIANTS = ("ip", "ea", "dip", "dea")
 METRIC = "s per converged EOM-CCSDT solve"
 # FP64 FMA issue on this part: 2 FMA per clock per SM (measured), 152 SMs, 2070 MHz max
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def measured_bf16_peak():
+    """Sustained dense BF16 tensor peak measured on this machine (TFLOP/s)."""
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"]), "measured (sustained cuBLAS bf16)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback (sustained bf16)"
 # Iteration counts and algorithmic flops per evaluation of one converged step
 # of this workload, as the library measured them on a GB300; the reference
 # arm uses them to turn its timed oracle sample into seconds per solve.
@@ -112,13 +121,13 @@ class ClockSampler:
 def read_traffic():
     """Per-launch DRAM bytes of the contraction kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    src = os.path.join(HERE, "paper_2509_14157_gb300", "csrc", "kernels.cu")
+    src = os.path.join(HERE, "paper_2509_14157_gb300", "csrc", "gemm_grouped.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    path = os.path.join(HERE, "profiles", "k_gather_gemm_fno_eom_c2.md")
+    path = os.path.join(HERE, "profiles", "k_ggemm_fno_eom_c2.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m_sha = re.search(r"kernels\.cu sha256:\s*([0-9a-f]{64})", text)
+    m_sha = re.search(r"gemm_grouped\.cu sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram bytes per launch \(bench workload\):\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
@@ -247,13 +256,18 @@ def main():
 
     counts = {"cc_iters": 0, "sigma": {}, "detail": {}, "flops_per_sigma": {}}
 
-    def step(device_inputs):
+    # mixed: BF16x3 products throughout the Davidson solves, converged to the
+    # 1e-6 Eh accuracy target (no FP64 refinement sweep); CCSDT refines in FP64
+    eom_kw = (dict(precision="mixed", switch_tol=0.0, tol_res=1e-6, tol_e=1e-8)
+              if args.precision == "mixed" else dict(precision="fp64"))
+
+    def step(device_inputs, prec=args.precision, kw=eom_kw):
         if device_inputs:
             ctx.fno_truncate_dev(h_dev.data_ptr(), eri_dev.data_ptr(), NORB, nocc, args.threshold)
         else:
             ctx.fno_truncate(h, eri, nocc, args.threshold)
         f0 = ctx.flops
-        res = ctx.ccsdt_solve(precision=args.precision)
+        res = ctx.ccsdt_solve(precision=prec)
         if not res["converged"]:
             raise RuntimeError("CCSDT did not converge")
         counts["cc_iters"] = res["iters"]
@@ -261,7 +275,7 @@ def main():
         out = {}
         for var in VARIANTS:
             f0 = ctx.flops
-            r = ctx.eom_solve(var, NROOTS, precision=args.precision)
+            r = ctx.eom_solve(var, NROOTS, **kw)
             counts["flops_per_sigma"][var] = (ctx.flops - f0) / max(1, r["sigma_calls"])
             if not r["converged"]:
                 raise RuntimeError("%s-EOM did not converge" % var)
@@ -322,10 +336,36 @@ def main():
         t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
+    accuracy = None
+    if args.precision == "mixed":
+        # every root against the same solve in FP64 (outside the timed region)
+        _, mixed_e = step(True)
+        _, ref_e = step(True, "fp64", dict(precision="fp64"))
+        accuracy = {"target_eh": 1e-6, "reference": "FP64 path, same inputs",
+                    "max_abs_err_eh": {v: float(np.max(np.abs(np.asarray(mixed_e[v]) - np.asarray(ref_e[v]))))
+                                       for v in VARIANTS},
+                    "per_root_err_eh": {v: [float(x) for x in np.asarray(mixed_e[v]) - np.asarray(ref_e[v])]
+                                        for v in VARIANTS}}
     solves = len(VARIANTS) * args.steps * world
     value = total / solves
     achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
     traffic = read_traffic()
+    if dominant.startswith("k_ggemm_bf16x3"):
+        # six BF16 slice products per FP64-equivalent multiply-add
+        peak, basis = measured_bf16_peak()
+        roof = {"bound": "tensor", "kernel": dominant + " (BF16 mma.sync, 6 slice products)",
+                "achieved": 6 * achieved if achieved else None, "peak": peak, "unit": "TFLOP/s",
+                "frac": 6 * achieved / peak if achieved else None, "traffic": None, "peak_basis": basis}
+    else:
+        roof = {"bound": "alu", "kernel": dominant + " (FP64 FMA)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": traffic if dominant == "k_ggemm" else None,
+                "peak_basis": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz"}
+    roof.update({"launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / total if total else None,
+                 "paths": {k: {"ms": round(x["ms"], 3),
+                               "tflops": (x["flops"] / x["ms"] / 1e9) if x["ms"] else None,
+                               "launches": x["launches"]} for k, x in paths.items()}})
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": False,
@@ -333,18 +373,12 @@ def main():
         "dtype": "f64" if args.precision == "fp64" else "bf16x3->f32, f64 refinement",
         "data": "synthetic", "config": dict(config(args.threshold, seed), precision=args.precision),
         "tflops": flops * world / total / 1e12 if total > 0 else None,
-        "roofline": {"bound": "alu", "kernel": dominant + " (FP64 FMA)", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                     "traffic": traffic if dominant == "k_gather_gemm" else None,
-                     "launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / total if total else None,
-                     "peak_basis": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz",
-                     "paths": {k: {"ms": round(x["ms"], 3), "tflops": (x["flops"] / x["ms"] / 1e9) if x["ms"] else None,
-                                   "launches": x["launches"]} for k, x in paths.items()}},
+        "roofline": roof,
         "e2e": {"value": e2e_total / solves, "unit": "s",
                 "h2d_bytes_per_step": int(h.nbytes + eri.nbytes),
                 "d2h_bytes_per_step": int(8 * (len(VARIANTS) * NROOTS * 2 + (NORB - nocc)))},
         "gpu_launches": launches, "clocks": clocks,
+        **({"accuracy": accuracy} if accuracy else {}),
         "solver": {"ccsdt_iters": counts["cc_iters"], "sigma_calls": counts["sigma"], "eom": counts["detail"],
                    "flops_per_residual": counts["flops_per_residual"], "flops_per_sigma": counts["flops_per_sigma"]},
     }

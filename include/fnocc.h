@@ -178,9 +178,14 @@ fnocc_status ccsdt_residual_dev(fnocc_ctx *ctx, const double *t1, const double *
 /* EOM-CCSDT (Eq. 1-4) ----------------------------------------------------------
  * Lowest nroots roots (by real part) of H-bar in the variant's operator space
  * and target spin sector (IP, EA: 2*dM_s = +1; DIP, DEA: 0), by
- * non-symmetric Davidson. Needs a preceding ccsdt_solve (or
- * fnocc_set_amplitudes). energies: total energies E_CC + omega (ascending);
- * omegas may be NULL. */
+ * non-symmetric Davidson. Roots are counted among eigenstates with weight
+ * >= 1e-6 in the principal block (1h, 1p, 2h or 2p): the sector also holds
+ * states of spin multiplicities the principal block cannot form (quartet
+ * 2h1p of IP, quintet 3h1p of DIP, ...), which have no principal weight and
+ * which a Davidson started on principal determinants reaches only through
+ * rounding; where fewer principal states than nroots exist, the lowest
+ * others fill up. Needs a preceding ccsdt_solve (or fnocc_set_amplitudes).
+ * energies: total energies E_CC + omega (ascending); omegas may be NULL. */
 fnocc_status eom_ccsdt_solve(fnocc_ctx *ctx, int variant, int nroots, int guess,
                              const eom_options *opt, double *energies, double *omegas,
                              eom_info *out);
@@ -314,12 +319,14 @@ double fnocc_flop_count(const fnocc_ctx *ctx);
 
 /* Contraction-kernel timing: when enabled, every contraction launch is
  * bracketed by CUDA events on the context stream. Contractions run on one of
- * four kernel paths: 0 the tiled gather-GEMM (k_gather_gemm), 1 its split-K
- * form with an ordered reduction, 2 the small-output kernel (<= 256 outputs)
- * with its reduction, 3 the row-parallel GEMV. fnocc_profile_read returns,
- * for one path (or all with path = -1), the summed device time (ms), the
- * summed algorithmic flops (2*M*N*K) and the number of launches, then resets
- * those counters. */
+ * six kernel paths: 0 the grouped FP64 gather-GEMM (k_ggemm: all spin blocks
+ * of a step in one launch), 1 the same with a split reduction and its
+ * ordered sum (k_greduce), 2 the small-output kernel (<= 256 outputs) with
+ * its reduction, 3 the row-parallel GEMV, 4 and 5 the grouped BF16
+ * three-slice tensor-core kernel (k_ggemm_bf16x3) without / with a split
+ * reduction. fnocc_profile_read returns, for one path (or all with path =
+ * -1), the summed device time (ms), the summed algorithmic flops (2*M*N*K)
+ * and the number of launches, then resets those counters. */
 fnocc_status fnocc_profile(fnocc_ctx *ctx, int enable);
 fnocc_status fnocc_profile_read(fnocc_ctx *ctx, int path, double *kernel_ms, double *kernel_flops,
                                 uint64_t *launches);

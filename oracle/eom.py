@@ -106,11 +106,18 @@ def _orthonormalise(vec, basis, tol=1e-10):
 
 
 def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
-             maxiter=200, nguess=None, guess_mask=None):
+             maxiter=200, nguess=None, guess_mask=None, principal=None, min_weight=1e-6):
     """Lowest-Re roots of a non-symmetric operator restricted to `mask`.
     Guess unit vectors sit on the lowest `diag` entries inside guess_mask.
     When the subspace would exceed max_sub it is restarted from the 2*nroots
-    lowest Ritz vectors, whose products follow as the same combinations."""
+    lowest Ritz vectors, whose products follow as the same combinations.
+
+    principal: length of the leading (principal, 1h/1p/2h/2p) block. Roots
+    are counted only among Ritz vectors whose weight there is at least
+    min_weight: states of other spin multiplicities (e.g. the quintet 3h1p
+    states of DIP) have none, and a Davidson started on principal
+    determinants reaches them only through rounding. Where the sector holds
+    fewer principal states than nroots, the lowest others fill up."""
     n = len(diag)
     allowed = np.where(mask)[0]
     if nguess is None:
@@ -153,6 +160,16 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
         gmat = vmat @ smat.T
         w_all, y_all = np.linalg.eig(gmat)
         srt = np.argsort(w_all.real, kind="stable")
+        if principal is not None:
+            good, rest_idx = [], []
+            for j in srt:
+                yv = np.real(y_all[:, j])
+                xv = vmat.T @ (yv / np.linalg.norm(yv))
+                (good if xv[:principal] @ xv[:principal] >= min_weight else rest_idx).append(j)
+            # fewer principal states than roots: the lowest others fill up
+            chosen = good[:nroots] + rest_idx[:max(0, nroots - len(good))]
+            chosen.sort(key=lambda j: w_all[j].real)
+            srt = np.array(chosen + [j for j in good[nroots:]])
         w = w_all[srt][:nroots]
         yr = np.real(y_all[:, srt])
         theta = w.real
@@ -178,7 +195,7 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
             den = np.where(np.abs(den) < 1e-8, 1e-8, den)
             new.append((res[r] / den) * mask)
         if len(basis) + len(new) > max_sub:
-            nkeep = min(len(basis), 2 * nroots)
+            nkeep = min(len(srt), 2 * nroots)
             keep = []
             for q in range(nkeep):
                 yv = yr[:, q] / np.linalg.norm(yr[:, q])
@@ -213,7 +230,8 @@ def eom_ccsdt(variant, f, g, o, v, t1, t2, t3, nroots, tol_res=1e-8, tol_e=1e-10
     def apply(x):
         return sigma_packed(variant, f, g, o, v, t1, t2, t3, x)
 
-    return davidson(apply, diag, mask, nroots, tol_res, tol_e, max_sub, maxiter, nguess, gmask)
+    return davidson(apply, diag, mask, nroots, tol_res, tol_e, max_sub, maxiter, nguess, gmask,
+                    principal=first)
 
 
 def sigma_matrix(variant, f, g, o, v, t1, t2, t3):

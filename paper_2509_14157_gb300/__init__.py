@@ -276,8 +276,8 @@ class Context:
     def profile(self, enable=True):
         self._check(self.lib.fnocc_profile(self._h, 1 if enable else 0))
 
-    PROFILE_PATHS = {0: "k_gather_gemm", 1: "k_gather_gemm_part+k_reduce_partials",
-                     2: "k_gemm_small+k_reduce_partials", 3: "k_gemv_rows"}
+    PROFILE_PATHS = {0: "k_ggemm", 1: "k_ggemm_split+k_greduce", 2: "k_gemm_small+k_reduce_partials",
+                     3: "k_gemv_rows", 4: "k_ggemm_bf16x3", 5: "k_ggemm_bf16x3_split+k_greduce"}
 
     def profile_read(self, path=-1):
         """(device ms, algorithmic flops, launches) of one contraction kernel path

@@ -156,12 +156,16 @@ struct fnocc_ctx {
   double e_corr = 0;
 
   std::unique_ptr<ExecEquation> cc_eq[4];
-  DevBuf Y[4], scratch, red, small;
+  DevBuf Y[4], scratch, red, small, coef;
 
   // EOM
   std::unique_ptr<ExecEquation> eom_eq[4][3][3];
   DevBuf rd[3], sy[3];
   uint64_t hbar_version = 0;
+  // the dressed operators and dense T2/T3 hold the stored amplitudes' H-bar
+  // (cleared by every residual evaluation and by new amplitudes)
+  bool hbar_valid = false;
+  int cache_precision = 0;  // arithmetic of the cached R-independent intermediates
   uint64_t eq_seen[4][3][3] = {};  // H-bar version whose cached flops were counted
   int last_variant = -1, last_nroots = 0;
   size_t last_dim = 0;
@@ -223,6 +227,10 @@ const int kSectorMs2[4] = {1, 1, 0, 0};
 // one cached intermediate may hold at most 2^28 doubles (2 GiB).
 const double kSigmaAmortize = 100.0;
 const double kCacheCapDoubles = double(1LL << 28);
+// Davidson roots need at least this weight in the principal (1h / 1p / 2h / 2p)
+// block: states without it belong to spin multiplicities the principal
+// determinants do not reach (see eom_ccsdt_solve)
+const double kMinPrincipalWeight = 1e-6;
 
 // ---- Hamiltonian installation ---------------------------------------------------
 
@@ -254,6 +262,7 @@ void install_hamiltonian(fnocc_ctx *c, int nocc, int nact_spatial) {
   c->nt[3] = (size_t)binom_ll(c->o, 3) * binom_ll(c->v, 3);
   c->have_ham = true;
   c->have_amps = false;
+  c->hbar_valid = false;
   c->last_variant = -1;
 }
 
@@ -302,6 +311,7 @@ void ensure_cc_plans(fnocc_ctx *c) {
 
 // residual of packed amplitudes tp (device) into rp (device); returns E_corr
 double cc_residual_dev(fnocc_ctx *c, const double *tp, double *rp) {
+  c->hbar_valid = false;  // the residual overwrites the dressed operators
   Launch L = c->L();
   ensure_cc_plans(c);
   const int o = c->o, v = c->v;
@@ -372,6 +382,7 @@ void ensure_eom_plans(fnocc_ctx *c, int var) {
 // prepares dressed operators and dense T2/T3 from the stored amplitudes
 void prepare_hbar(fnocc_ctx *c) {
   if (!c->have_amps) throw StatusError(FNOCC_E_STATE, "no ground-state amplitudes (call ccsdt_solve or fnocc_set_amplitudes)");
+  if (c->hbar_valid) return;
   Launch L = c->L();
   const int o = c->o, v = c->v;
   const double *tp = c->tpk.d();
@@ -383,11 +394,16 @@ void prepare_hbar(fnocc_ctx *c) {
   unpack_dense(L, tp + c->nt[1] + c->nt[2], 3, 3, o, v, c->otab[3].dev.as<int>(), c->otab[3].count,
                c->vtab[3].dev.as<int>(), c->vtab[3].count, c->t3d.d());
   ++c->hbar_version;
+  c->hbar_valid = true;
 }
 
 uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic) { return c->eq_seen[var][oc][ic]; }
 
 void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s) {
+  if (c->precision != c->cache_precision) {  // cached intermediates follow the arithmetic in use
+    ++c->hbar_version;
+    c->cache_precision = c->precision;
+  }
   Launch L = c->L();
   const int o = c->o, v = c->v;
   ensure_eom_plans(c, var);
@@ -459,21 +475,11 @@ void combine_rows(fnocc_ctx *c, long long n, const double *X, int k, const std::
     if (!accumulate) FNOCC_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, c->stream));
     return;
   }
-  c->small.reserve(sizeof(double) * std::max<size_t>(64, coef.size()));
-  FNOCC_CUDA(cudaMemcpyAsync(c->small.p, coef.data(), sizeof(double) * k, cudaMemcpyHostToDevice, c->stream));
-  MapSet ms;
-  DMap arow, acol, brow, bcol, crow, ccol;
-  ms.add(&arow, {{n, 1}});
-  ms.add(&acol, {{k, n}});
-  ms.add(&brow, {{k, 1}});
-  ms.add(&bcol, {{1, 0}});
-  ms.add(&crow, {{n, 1}});
-  ms.add(&ccol, {{1, 0}});
-  ms.upload();
-  if (!accumulate) FNOCC_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, c->stream));
-  gather_gemm(c->L(), n, 1, k, 1.0, X, arow, acol, c->small.d(), brow, bcol, y, crow, ccol, true, n * (long long)k,
-              (long long)k, n);
-  sync(c);  // MapSet and coefficients must outlive the launch
+  // coefficients go through their own buffer: stream order keeps them until
+  // the launch has read them
+  c->coef.reserve(sizeof(double) * std::max<size_t>(64, coef.size()));
+  FNOCC_CUDA(cudaMemcpyAsync(c->coef.p, coef.data(), sizeof(double) * k, cudaMemcpyHostToDevice, c->stream));
+  lincomb(c->L(), n, X, n, k, c->coef.d(), y, accumulate);
 }
 
 // ---- FNO setup --------------------------------------------------------------------
@@ -1293,6 +1299,8 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
     const unsigned char *mask = mk.as<unsigned char>();
     int kb = 0, sigma_calls = 0;
     std::vector<double> G;  // kb x kb, row-major, G[i][j] = V_i . S_j
+    std::vector<double> G1;  // kb x kb, principal-block overlaps V_i[0:sz0] . V_j[0:sz0]
+    const long long sz0 = (long long)sz[0];
     auto vrow = [&](int i) { return Vb.d() + (size_t)i * dim; };
     auto srow = [&](int i) { return Sb.d() + (size_t)i * dim; };
     // Appends src, orthonormalised against the basis (Gram-Schmidt twice), and
@@ -1341,6 +1349,13 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
         for (int j = 0; j < kb; ++j) Gn[kb * k1 + j] = row[j];
       }
       G.swap(Gn);
+      std::vector<double> G1n((size_t)k1 * k1, 0.0);
+      for (int i = 0; i < kb; ++i)
+        for (int j = 0; j < kb; ++j) G1n[i * k1 + j] = G1[i * kb + j];
+      multi_dot(L, sz0, vrow(kb), Vb.d(), dim, k1, c->small.d(), c->red);  // principal overlaps
+      auto pc = to_host(c, c->small.d(), k1);
+      for (int i = 0; i < k1; ++i) G1n[i * k1 + kb] = G1n[kb * k1 + i] = pc[i];
+      G1.swap(G1n);
       kb = k1;
       return true;
     };
@@ -1360,6 +1375,27 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
       std::vector<int> idx(kb);
       std::iota(idx.begin(), idx.end(), 0);
       std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a].real() < w[b].real(); });
+      {
+        // roots are counted among Ritz vectors with principal-block weight:
+        // states of other spin multiplicities (pure satellites, e.g. the
+        // quintet 3h1p states of DIP) have none and appear only by rounding
+        // (fewer principal states than roots: the lowest others fill up)
+        std::vector<int> good, rest;
+        for (int j : idx) {
+          double yy = 0, wt = 0;
+          for (int a = 0; a < kb; ++a) {
+            const double ya = Y[(size_t)a * kb + j].real();
+            yy += ya * ya;
+            for (int b = 0; b < kb; ++b) wt += ya * G1[(size_t)a * kb + b] * Y[(size_t)b * kb + j].real();
+          }
+          (yy > 0 && wt / yy >= kMinPrincipalWeight ? good : rest).push_back(j);
+        }
+        std::vector<int> chosen(good.begin(), good.begin() + std::min<size_t>(good.size(), nr));
+        for (size_t q = 0; (int)chosen.size() < nr && q < rest.size(); ++q) chosen.push_back(rest[q]);
+        std::stable_sort(chosen.begin(), chosen.end(), [&](int a, int b) { return w[a].real() < w[b].real(); });
+        for (size_t q = nr; q < good.size(); ++q) chosen.push_back(good[q]);
+        idx = chosen;
+      }
       ncomplex = 0;
       std::vector<std::vector<double>> ys(nr);
       for (int r = 0; r < nr; ++r) {
@@ -1398,6 +1434,7 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
           FNOCC_CUDA(cudaMemcpyAsync(keep.p, xr.p, sizeof(double) * dim * nr, cudaMemcpyDeviceToDevice, c->stream));
           kb = 0;
           G.clear();
+          G1.clear();
           for (int r = 0; r < nr; ++r) add_vector(keep.d() + (size_t)r * dim);
           have_old = false;
           continue;
@@ -1422,7 +1459,7 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
       if (kb + nnew > max_sub) {
         // thick restart: keep the lowest nkeep Ritz vectors with their
         // products, formed as the same linear combinations (no new products)
-        const int nkeep = std::min(kb, 2 * nr);
+        const int nkeep = std::min((int)idx.size(), 2 * nr);
         DevBuf kx, ks;
         kx.reserve(sizeof(double) * dim * nkeep);
         ks.reserve(sizeof(double) * dim * nkeep);
@@ -1440,6 +1477,7 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
         }
         kb = 0;
         G.clear();
+        G1.clear();
         for (int q = 0; q < nkeep; ++q) add_vector(kx.d() + (size_t)q * dim, ks.d() + (size_t)q * dim);
       }
       for (int r = 0; r < nr; ++r) {

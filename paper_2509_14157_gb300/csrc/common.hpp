@@ -63,17 +63,18 @@ struct DMap {
 };
 
 // Optional event timing of contraction launches (owned by a context), per
-// kernel path: 0 tiled GEMM, 1 split-K tiled GEMM + ordered reduction,
-// 2 small-output kernel + reduction, 3 GEMV.
-constexpr int kGemmPaths = 4;
+// kernel path: 0 grouped FP64 GEMM, 1 the same with split reduction + ordered
+// sum, 2 small-output kernel + reduction, 3 GEMV, 4 / 5 grouped BF16x3 GEMM
+// without / with split reduction.
+constexpr int kGemmPaths = 6;
 struct GemmProfile {
   bool enabled = false;
   std::vector<cudaEvent_t> pool;           // events, reused
   std::vector<std::pair<int, int>> pairs;  // (start, stop) indices into pool
   std::vector<double> flops;               // per recorded launch
   std::vector<int> path;                   // per recorded launch
-  double ms[kGemmPaths] = {0, 0, 0, 0}, flop_sum[kGemmPaths] = {0, 0, 0, 0};
-  uint64_t launches[kGemmPaths] = {0, 0, 0, 0};
+  double ms[kGemmPaths] = {0}, flop_sum[kGemmPaths] = {0};
+  uint64_t launches[kGemmPaths] = {0};
   void fold();                             // accumulate completed pairs (synchronises)
 };
 
@@ -84,6 +85,42 @@ struct Launch {
   DevBuf *partials = nullptr;  // split-K partial sums (deterministic reduction)
   int precision = 0;           // 0 FP64; 1 BF16 three-slice split on tensor cores (tiled path)
 };
+
+// One sub-GEMM of a grouped launch: C[crow[m] + ccol[n]] += alpha *
+// sum_k A[arow[m] + acol[k]] * B[brow[k] + bcol[n]] with flat device offset
+// tables (one entry per index). The launch fields (tiles, split, CTA and
+// partial offsets) belong to one tile shape.
+struct GTask {
+  long long M = 0, N = 0, K = 0;
+  const long long *arow = nullptr, *acol = nullptr, *brow = nullptr, *bcol = nullptr, *crow = nullptr,
+                  *ccol = nullptr;
+  long long tiles_n = 0, tiles = 0;  // tiles of the shape, row-major over (m, n) tiles
+  long long kchunk = 0;              // reduction length per CTA (multiple of the shape's K tile)
+  int ksplit = 1;                    // > 1: partial products to part + part_off, reduced in order
+  long long cta_begin = 0;           // first CTA of this task in the grid
+  long long part_off = 0;            // doubles, [ksplit][M][N]
+  long long red_begin = 0;           // first output of this task in the reduction launch
+};
+
+// A grouped launch: tasks ordered by cta_begin (device array) plus the list
+// of tasks with a split reduction.
+constexpr int kGShapes = 10;           // FP64 tile shapes
+constexpr int kGShapeBf16 = kGShapes;  // BF16 three-slice split 64 x 64 tile (mixed precision)
+struct GroupedLaunch {
+  const GTask *tasks = nullptr;
+  int ntasks = 0;
+  long long ncta = 0;
+  const int *split_ids = nullptr;
+  int nsplit = 0;
+  long long nred = 0, part_need = 0;
+  int shape = 0;
+  double flops = 0;      // algorithmic flops of the launch (profiling)
+  double padded = 0;     // multiply-adds including tile padding x 2
+};
+// rows, columns and K tile of a shape (kGShapeBf16 included)
+void grouped_shape(int shape, int *tbm, int *tbn, int *tbk);
+// runs the launch (and the ordered reduction of split tasks) on L.stream
+void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const double *A, const double *B, double *C);
 
 // C[crow(m) + ccol(n)] (+)= alpha * sum_k A[arow(m)+acol(k)] * B[brow(k)+bcol(n)]
 // asize, bsize, csize: element counts of the buffers; every launch checks on
@@ -124,6 +161,9 @@ void multi_dot(const Launch &L, long long n, const double *x, const double *Y, l
                int nvec, double *dots_dev, DevBuf &scratch);
 // max |x| and sum x^2 into out2[0], out2[1] (NaN reported as an infinite max)
 void absmax_sumsq(const Launch &L, long long n, const double *x, double *out2_dev, DevBuf &scratch);
+// y (+)= sum_j coef[j] * X[j * ld : j * ld + n], coef_dev: k device doubles
+void lincomb(const Launch &L, long long n, const double *X, long long ld, int k, const double *coef_dev, double *y,
+             bool accumulate);
 // spin-orbital antisymmetrised integrals from spatial (pq|rs) over n spatial orbitals
 void spin_orbital_eri(const Launch &L, const double *eri_sp, int n, double *g);
 void spin_orbital_h(const Launch &L, const double *h_sp, int n, double *hso);

@@ -182,6 +182,31 @@ struct TableBuilder {
   std::vector<long long> host;
   struct Pending { DMap *map; std::vector<long long> offs; };
   std::vector<Pending> pend;
+  std::map<const DMap *, std::vector<long long>> hoffs;  // host offset of each group's table
+
+  // flat offsets of the rows of `map` restricted to segments (start, length)
+  // per group (group ng-1 fastest, as map_off decomposes), appended to out;
+  // returns the largest entry
+  long long flatten(const DMap &map, const std::vector<std::pair<long long, long long>> &segs,
+                    std::vector<long long> &out) const {
+    const auto &offs = hoffs.at(&map);
+    const int ng = map.ng;
+    long long total = 1;
+    for (int g = 0; g < ng; ++g) total *= segs[g].second;
+    long long mx = 0;
+    std::vector<long long> idx(ng, 0);
+    for (long long r = 0; r < total; ++r) {
+      long long off = 0;
+      for (int g = 0; g < ng; ++g) off += host[offs[g] + segs[g].first + idx[g]];
+      out.push_back(off);
+      mx = std::max(mx, off);
+      for (int g = ng - 1; g >= 0; --g) {
+        if (++idx[g] < segs[g].second) break;
+        idx[g] = 0;
+      }
+    }
+    return mx;
+  }
 
   // appends the tables of `groups` over storage `s` and records a map to fix up
   long long add(DMap *map, const std::vector<DimGroup> &groups, const Storage &s, int o, int v) {
@@ -240,6 +265,7 @@ struct TableBuilder {
       map->maxoff += mx;
       total *= cnt;
     }
+    hoffs[map] = p.offs;
     pend.push_back(p);
     return total;
   }
@@ -265,6 +291,7 @@ struct TableBuilder {
       map->maxoff += (d.size - 1) * d.stride;
       total *= d.size;
     }
+    hoffs[map] = p.offs;
     pend.push_back(p);
     return total;
   }
@@ -321,10 +348,72 @@ int group_sign(const DimGroup &g, const SpinInfo &si) {
 
 }  // namespace
 
+namespace {
+using Segs = std::vector<std::pair<long long, long long>>;
+Segs full_segs(const DMap &m) {
+  Segs v;
+  for (int g = 0; g < m.ng; ++g) v.push_back({0, m.n[g]});
+  return v;
+}
+long long seg_count(const Segs &sg) {
+  long long t = 1;
+  for (auto &x : sg) t *= x.second;
+  return t;
+}
+
+// Tasks of a binary step: spin-allowed blocks with equal (row, column)
+// segments merge into one task whose reduction runs over all their K
+// segments in turn. Flat tables go to flat_host (row and column tables shared
+// between tasks).
+void build_tasks(const TableBuilder &tb, ExecStep &e, std::vector<long long> &flat_host) {
+  std::map<std::pair<Segs, Segs>, std::vector<Segs>> by_mn;
+  if (e.blocked) {
+    for (const SubGemm &b : e.blocks)
+      if (b.M > 0 && b.N > 0 && b.K > 0) by_mn[{b.mseg, b.nseg}].push_back(b.kseg);
+  } else {
+    by_mn[{full_segs(e.arow), full_segs(e.bcol)}].push_back(full_segs(e.acol));
+  }
+  std::map<std::pair<const DMap *, Segs>, std::pair<long long, long long>> memo;  // -> (offset, max)
+  auto flat = [&](const DMap &m, const Segs &sg) {
+    auto key = std::make_pair(&m, sg);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    long long off = (long long)flat_host.size();
+    long long mx = tb.flatten(m, sg, flat_host);
+    return memo[key] = {off, mx};
+  };
+  e.grouped = true;
+  for (auto &kv : by_mn) {
+    ExecStep::TaskRef tr;
+    auto ar = flat(e.arow, kv.first.first), cr = flat(e.crow, kv.first.first);
+    auto bc = flat(e.bcol, kv.first.second), cc = flat(e.ccol, kv.first.second);
+    tr.acol = (long long)flat_host.size();
+    long long amx = 0, bmx = 0;
+    for (auto &ks : kv.second) amx = std::max(amx, tb.flatten(e.acol, ks, flat_host));
+    tr.brow = (long long)flat_host.size();
+    for (auto &ks : kv.second) bmx = std::max(bmx, tb.flatten(e.brow, ks, flat_host));
+    tr.K = tr.brow - tr.acol;
+    tr.M = seg_count(kv.first.first);
+    tr.N = seg_count(kv.first.second);
+    if (tr.M == 0 || tr.N == 0 || tr.K == 0) continue;  // contributes nothing
+    tr.arow = ar.first;
+    tr.crow = cr.first;
+    tr.bcol = bc.first;
+    tr.ccol = cc.first;
+    e.gmax_a = std::max(e.gmax_a, ar.second + amx);
+    e.gmax_b = std::max(e.gmax_b, bmx + bc.second);
+    e.gmax_c = std::max(e.gmax_c, cr.second + cc.second);
+    e.tasks.push_back(tr);
+  }
+}
+
+}  // namespace
+
 ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize,
                            double cache_cap, int r_charge)
     : nh_(eq.nh), np_(eq.np), o_(o), v_(v) {
   TableBuilder tb;
+  std::vector<long long> flat_host;
   Storage outs = output_storage(nh_, np_, o, v);
   std::vector<TermPlan> raw;
   for (const Term &t : eq.terms) raw.push_back(plan_term(t, nh_, np_, o, v, amortize, cache_cap));
@@ -500,11 +589,111 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
         done_flops = blocked_flops;
       }
       (s.constant ? cached_flops_ : flops_) += done_flops;
+      if (binary && double(e.M) * double(e.N) > 256.0) build_tasks(tb, e, flat_host);
     }
     terms_.push_back(std::move(et));
   }
   (void)rdims;
   tb.upload(tables_);
+  build_launches(flat_host);
+}
+
+// Uploads the flat tables, then builds for every grouped step and tile shape
+// its GTask array: tiles, a split of the reduction when the step has fewer
+// tiles than two per SM, CTA, partial and reduction offsets.
+void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
+  if (flat_host.empty()) return;
+  flat_.reserve(sizeof(long long) * flat_host.size());
+  FNOCC_CUDA(cudaMemcpy(flat_.p, flat_host.data(), sizeof(long long) * flat_host.size(), cudaMemcpyHostToDevice));
+  const long long *fb = flat_.as<long long>();
+  constexpr long long kWantCta = 2 * 152;
+  constexpr long long kPartCap = 1LL << 27;  // doubles of split partials per launch
+  std::vector<GTask> gt;
+  std::vector<int> sid;
+  struct Fix { GroupedLaunch *gl; size_t t0, s0; };
+  std::vector<Fix> fix;
+  for (ExecTerm &t : terms_)
+    for (ExecStep &e : t.steps) {
+      if (!e.grouped) continue;
+      double est[kGShapes + 1];
+      for (int shape = 0; shape <= kGShapes; ++shape) {
+        int tbm, tbn, tbk;
+        grouped_shape(shape, &tbm, &tbn, &tbk);
+        long long T = 0;
+        for (auto &tr : e.tasks) T += ((tr.M + tbm - 1) / tbm) * ((tr.N + tbn - 1) / tbn);
+        const long long want = T < kWantCta ? (kWantCta + T - 1) / T : 1;
+        GroupedLaunch &gl = e.gl[shape];
+        gl.shape = shape;
+        gl.ntasks = (int)e.tasks.size();
+        fix.push_back({&gl, gt.size(), sid.size()});
+        long long cta = 0, part = 0, red = 0;
+        double padded = 0, flops = 0;
+        for (size_t i = 0; i < e.tasks.size(); ++i) {
+          const auto &tr = e.tasks[i];
+          GTask g;
+          g.M = tr.M;
+          g.N = tr.N;
+          g.K = tr.K;
+          g.arow = fb + tr.arow;
+          g.acol = fb + tr.acol;
+          g.brow = fb + tr.brow;
+          g.bcol = fb + tr.bcol;
+          g.crow = fb + tr.crow;
+          g.ccol = fb + tr.ccol;
+          const long long tm = (tr.M + tbm - 1) / tbm;
+          g.tiles_n = (tr.N + tbn - 1) / tbn;
+          g.tiles = tm * g.tiles_n;
+          long long ks = std::min<long long>(want, std::max<long long>(1, tr.K / (4 * tbk)));
+          if (ks > 1 && part + ks * tr.M * tr.N > kPartCap) ks = 1;
+          long long kchunk = (tr.K + ks - 1) / ks;
+          kchunk = (kchunk + tbk - 1) / tbk * tbk;
+          ks = (tr.K + kchunk - 1) / kchunk;
+          g.ksplit = (int)ks;
+          g.kchunk = kchunk;
+          g.cta_begin = cta;
+          cta += g.tiles * ks;
+          if (ks > 1) {
+            g.part_off = part;
+            part += ks * tr.M * tr.N;
+            g.red_begin = red;
+            red += tr.M * tr.N;
+            sid.push_back((int)i);
+          }
+          padded += 2.0 * double(tm * tbm) * double(g.tiles_n * tbn) * double((tr.K + tbk - 1) / tbk * tbk);
+          flops += 2.0 * double(tr.M) * double(tr.N) * double(tr.K);
+          gt.push_back(g);
+        }
+        if (cta > 0x7fffffffLL) throw std::runtime_error("engine: grouped grid too large");
+        gl.ncta = cta;
+        gl.nsplit = (int)(sid.size() - fix.back().s0);
+        gl.nred = red;
+        gl.part_need = part;
+        gl.padded = padded;
+        gl.flops = flops;
+        est[shape] = padded / double(std::max<long long>(1, std::min<long long>(cta, 152)));
+      }
+      int best = 0;
+      for (int shape = 1; shape < kGShapes; ++shape)
+        if (est[shape] < est[best]) best = shape;
+      e.default_shape = best;
+      std::vector<int> order;
+      for (int shape = 0; shape < kGShapes; ++shape)
+        if (est[shape] <= 1.25 * est[best]) order.push_back(shape);
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return est[a] < est[b]; });
+      if (order.size() > 4) order.resize(4);
+      e.cand = order;
+    }
+  const size_t tbytes = sizeof(GTask) * gt.size(), ibytes = sizeof(int) * sid.size();
+  const size_t ioff = (tbytes + 255) / 256 * 256;
+  gtasks_.reserve(ioff + std::max<size_t>(ibytes, 8));
+  FNOCC_CUDA(cudaMemcpy(gtasks_.p, gt.data(), tbytes, cudaMemcpyHostToDevice));
+  if (ibytes) FNOCC_CUDA(cudaMemcpy((char *)gtasks_.p + ioff, sid.data(), ibytes, cudaMemcpyHostToDevice));
+  const GTask *tb = reinterpret_cast<const GTask *>(gtasks_.p);
+  const int *ib = reinterpret_cast<const int *>((char *)gtasks_.p + ioff);
+  for (auto &f : fix) {
+    f.gl->tasks = tb + f.t0;
+    f.gl->split_ids = ib + f.s0;
+  }
 }
 
 bool ExecEquation::autotune = true;
@@ -567,73 +756,69 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         }
         return m;
       };
-      if (s.blocked) {
+      if (s.blocked && s.b_kind < 0) {  // unary step: spin-allowed blocks only
         for (const SubGemm &b : s.blocks) {
-          if (b.M == 0 || b.N == 0 || b.K == 0) continue;
+          if (b.M == 0) continue;
           DMap arow = sub_map(s.arow, b.mseg), crow = sub_map(s.crow, b.mseg);
-          if (s.b_kind < 0) {
-            gather_axpy(L, b.M, s.alpha, A, arow, C, crow, size(s.a_kind, s.a_inter), csize);
-            continue;
-          }
-          const double *B = ptr(s.b_kind, s.b_inter);
-          DMap acol = sub_map(s.acol, b.kseg), brow = sub_map(s.brow, b.kseg);
-          DMap bcol = sub_map(s.bcol, b.nseg), ccol = sub_map(s.ccol, b.nseg);
-          gather_gemm(L, b.M, b.N, b.K, s.alpha, A, arow, acol, B, brow, bcol, C, crow, ccol, true,
-                      size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize);
+          gather_axpy(L, b.M, s.alpha, A, arow, C, crow, size(s.a_kind, s.a_inter), csize);
         }
         continue;
       }
       if (s.b_kind < 0) {
         gather_axpy(L, s.M, s.alpha, A, s.arow, C, s.crow, size(s.a_kind, s.a_inter), csize);
-      } else {
-        const double *B = ptr(s.b_kind, s.b_inter);
-        if (!B) throw std::runtime_error("engine: missing operand");
-        ExecStep &ms = const_cast<ExecStep &>(s);
-        const bool tune = autotune && L.precision == 0 && ms.tuned_shape < 0 &&
-                          2.0 * double(s.M) * double(s.N) * double(s.K) >= 2e8;
-        if (!tune) {
-          const int shape = (ms.tuned_shape >= 0 && ms.tuned_shape < kTileShapes) ? ms.tuned_shape : -1;
-          gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol, true,
-                      size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize, shape);
-          continue;
-        }
-        if (ms.pending < 0) {  // first use: an event pair of its own
-          ms.pending = tune_count_++;
-          while ((int)tune_events_.size() < 2 * tune_count_) {
-            cudaEvent_t ev;
-            FNOCC_CUDA(cudaEventCreate(&ev));
-            tune_events_.push_back(ev);
-          }
-        }
-        cudaEvent_t e0 = tune_events_[2 * ms.pending], e1 = tune_events_[2 * ms.pending + 1];
-        for (int k = 0; k < kTileShapes; ++k)
-          if (ms.trial_ms[k] < 0) {  // the trial of the previous run
-            FNOCC_CUDA(cudaEventSynchronize(e1));
-            float t = 0;
-            FNOCC_CUDA(cudaEventElapsedTime(&t, e0, e1));
-            ms.trial_ms[k] = std::max(t, 1e-6f);
-          }
-        int next = -1;
-        for (int k = 0; k < kTileShapes && next < 0; ++k)
-          if (ms.trial_ms[k] == 0) next = k;
-        if (next < 0) {
-          int best = 0;
-          for (int k = 1; k < kTileShapes; ++k)
-            if (ms.trial_ms[k] < ms.trial_ms[best]) best = k;
-          ms.tuned_shape = best;
-          gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol, true,
-                      size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize, best);
-          continue;
-        }
-        FNOCC_CUDA(cudaEventRecord(e0, L.stream));
-        int used = gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol,
-                               true, size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize, next);
-        FNOCC_CUDA(cudaEventRecord(e1, L.stream));
-        if (used < 0)
-          ms.tuned_shape = kTileShapes;  // not a tiled launch: nothing to tune
-        else
-          ms.trial_ms[next] = -1.f;       // in flight; read on the next run
+        continue;
       }
+      const double *B = ptr(s.b_kind, s.b_inter);
+      if (!B) throw std::runtime_error("engine: missing operand");
+      if (!s.grouped) {  // output of at most 256 elements: the small-output kernel
+        gather_gemm(L, s.M, s.N, s.K, s.alpha, A, s.arow, s.acol, B, s.brow, s.bcol, C, s.crow, s.ccol, true,
+                    size(s.a_kind, s.a_inter), size(s.b_kind, s.b_inter), csize);
+        continue;
+      }
+      if (s.gmax_a >= size(s.a_kind, s.a_inter) || s.gmax_b >= size(s.b_kind, s.b_inter) || s.gmax_c >= csize)
+        throw std::runtime_error("engine: grouped index tables exceed operand bounds");
+      ExecStep &ms = const_cast<ExecStep &>(s);
+      if (L.precision == 1 && s.gl[0].flops >= 1e5) {
+        grouped_gemm(L, s.gl[kGShapeBf16], s.alpha, A, B, C);
+        continue;
+      }
+      const bool tune = autotune && L.precision == 0 && ms.tuned_shape < 0 && ms.cand.size() > 1 &&
+                        s.gl[s.default_shape].padded >= 1e8;
+      if (!tune) {
+        grouped_gemm(L, s.gl[ms.tuned_shape >= 0 ? ms.tuned_shape : s.default_shape], s.alpha, A, B, C);
+        continue;
+      }
+      if (ms.pending < 0) {  // first use: an event pair of its own
+        ms.pending = tune_count_++;
+        while ((int)tune_events_.size() < 2 * tune_count_) {
+          cudaEvent_t ev;
+          FNOCC_CUDA(cudaEventCreate(&ev));
+          tune_events_.push_back(ev);
+        }
+      }
+      cudaEvent_t e0 = tune_events_[2 * ms.pending], e1 = tune_events_[2 * ms.pending + 1];
+      for (int k : ms.cand)
+        if (ms.trial_ms[k] < 0) {  // the trial of the previous run
+          FNOCC_CUDA(cudaEventSynchronize(e1));
+          float tms = 0;
+          FNOCC_CUDA(cudaEventElapsedTime(&tms, e0, e1));
+          ms.trial_ms[k] = std::max(tms, 1e-6f);
+        }
+      int next = -1;
+      for (int k : ms.cand)
+        if (next < 0 && ms.trial_ms[k] == 0) next = k;
+      if (next < 0) {
+        int best = ms.cand[0];
+        for (int k : ms.cand)
+          if (ms.trial_ms[k] < ms.trial_ms[best]) best = k;
+        ms.tuned_shape = best;
+        grouped_gemm(L, s.gl[best], s.alpha, A, B, C);
+        continue;
+      }
+      FNOCC_CUDA(cudaEventRecord(e0, L.stream));
+      grouped_gemm(L, s.gl[next], s.alpha, A, B, C);
+      FNOCC_CUDA(cudaEventRecord(e1, L.stream));
+      ms.trial_ms[next] = -1.f;  // in flight; read on the next run
     }
   }
   if (refresh) cache_version_ = version;

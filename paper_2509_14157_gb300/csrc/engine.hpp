@@ -37,11 +37,24 @@ struct ExecStep {
   long long M, N, K;
   double alpha;
   DMap arow, acol, brow, bcol, crow, ccol;
-  // tile-shape autotuning of large FP64 steps: every shape is timed once,
+  // grouped launch (every binary step whose output has more than 256
+  // elements): one task per spin-allowed (row block, column block) pair with
+  // its reduction blocks concatenated, flat offset tables, and one launch
+  // descriptor per tile shape
+  bool grouped = false;
+  struct TaskRef {
+    long long M, N, K, arow, acol, brow, bcol, crow, ccol;  // offsets into the flat table buffer
+  };
+  std::vector<TaskRef> tasks;
+  GroupedLaunch gl[kGShapes + 1];
+  long long gmax_a = 0, gmax_b = 0, gmax_c = 0;  // largest row + column offset per operand
+  int default_shape = 0;                          // least padded work per busy SM
+  std::vector<int> cand;                          // FP64 shapes worth timing, best estimate first
+  // tile-shape autotuning of large FP64 steps: every candidate is timed once,
   // then the fastest is kept
-  int tuned_shape = -1;  // -1 untuned, kTileShapes: not a tiled launch
-  float trial_ms[kTileShapes] = {0, 0, 0, 0, 0};  // 0 untimed, < 0 in flight
-  int pending = -1;      // index of this step's event pair, -1 none yet
+  int tuned_shape = -1;
+  float trial_ms[kGShapes] = {0};  // 0 untimed, < 0 in flight
+  int pending = -1;                // index of this step's event pair, -1 none yet
 };
 
 struct ExecTerm {
@@ -75,9 +88,12 @@ class ExecEquation {
   size_t nterms() const { return terms_.size(); }
 
  private:
+  void build_launches(const std::vector<long long> &flat_host);
   int nh_, np_, o_, v_;
   std::vector<ExecTerm> terms_;
   DevBuf tables_;
+  DevBuf flat_;    // flat offset tables of the grouped steps
+  DevBuf gtasks_;  // GTask arrays and split-task lists of every step and shape
   DevBuf cache_;
   std::vector<cudaEvent_t> tune_events_;  // two per tuned step
   int tune_count_ = 0;

@@ -1,0 +1,378 @@
+// Grouped gather-GEMM: every spin-allowed sub-GEMM of one contraction step in
+// one launch.
+//
+// A step of a projected equation (a term of Eq. 6 for the CCSDT residual, or
+// of sigma = <mu|(H-bar R)_c|0> for the EOM variants) is one contraction
+// C[m, n] += alpha * sum_k A[m, k] * B[k, n] whose row, column and reduction
+// indices are index tuples of the operands. Spin symmetry splits it into
+// independent sub-GEMMs (tasks). Each task carries flat offset tables, one
+// 64-bit element offset per row, column and reduction index, so the kernels
+// read operands in place through a single table lookup per index.
+//
+// The CTAs of all tasks form one grid: CTA c finds its task by binary search
+// over the tasks' first-CTA offsets, then its tile and reduction slice. A task
+// with few tiles splits its reduction; those partial products go to a buffer
+// and a second launch adds them in a fixed order (deterministic results).
+//
+// On this part FP64 FMA issue is about two per clock per SM, so an FP64 tile
+// is FMA-bound whatever its shape: shapes are chosen for the least padding
+// (padded multiply-adds cost full time) and for enough CTAs to occupy all SMs.
+// The mixed-precision kernel runs the same tasks on the tensor cores as BF16
+// three-slice split products with FP32 accumulation.
+#include "common.hpp"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+namespace fnocc {
+
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ int find_task(const GTask *tasks, int ntasks, long long cta) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].cta_begin <= cta)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// FP64 tile kernel: threads as TY x TX (TX = 256 / TY), each a TM x TN
+// micro-tile; the block covers (TY*TM) x (TX*TN) outputs; K staged 16 at a
+// time through shared memory.
+template <int TY, int TM, int TN>
+__global__ void __launch_bounds__(NT) k_ggemm(const GTask *__restrict__ tasks, int ntasks, double alpha,
+                                              const double *__restrict__ A, const double *__restrict__ B,
+                                              double *__restrict__ C, double *__restrict__ part) {
+  constexpr int TX = NT / TY, TBM = TY * TM, TBN = TX * TN, BKG = 16;
+  __shared__ double As[BKG][TBM];
+  __shared__ double Bs[BKG][TBN];
+  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[BKG], brow_s[BKG];
+  __shared__ GTask t;
+  const int tid = threadIdx.x;
+  const long long cta = blockIdx.x;
+  if (tid == 0) t = tasks[find_task(tasks, ntasks, cta)];
+  __syncthreads();
+  const long long local = cta - t.cta_begin;
+  const long long z = local / t.tiles, tile = local - z * t.tiles;
+  const long long m0 = (tile / t.tiles_n) * TBM, n0 = (tile % t.tiles_n) * TBN;
+  const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
+  const bool split = t.ksplit > 1;
+  for (int i = tid; i < TBM; i += NT) {
+    const long long m = m0 + i;
+    arow_s[i] = m < t.M ? t.arow[m] : 0;
+    crow_s[i] = (!split && m < t.M) ? t.crow[m] : 0;
+  }
+  for (int i = tid; i < TBN; i += NT) {
+    const long long n = n0 + i;
+    bcol_s[i] = n < t.N ? t.bcol[n] : 0;
+    ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
+  }
+  const int tx = tid % TX, ty = tid / TX;
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  for (long long k0 = kb; k0 < ke; k0 += BKG) {
+    __syncthreads();
+    if (tid < BKG) {
+      const long long k = k0 + tid;
+      acol_s[tid] = k < ke ? t.acol[k] : 0;
+    } else if (tid < 2 * BKG) {
+      const long long k = k0 + tid - BKG;
+      brow_s[tid - BKG] = k < ke ? t.brow[k] : 0;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < TBM * BKG; idx += NT) {
+      const int kk = idx % BKG, row = idx / BKG;
+      const bool ok = (m0 + row < t.M) && (k0 + kk < ke);
+      As[kk][row] = ok ? __ldg(A + arow_s[row] + acol_s[kk]) : 0.0;
+    }
+    for (int idx = tid; idx < TBN * BKG; idx += NT) {
+      const int col = idx % TBN, kk = idx / TBN;
+      const bool ok = (n0 + col < t.N) && (k0 + kk < ke);
+      Bs[kk][col] = ok ? __ldg(B + brow_s[kk] + bcol_s[col]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BKG; ++kk) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  const long long MN = t.M * t.N;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const long long m = m0 + ty * TM + i;
+    if (m >= t.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const long long n = n0 + tx * TN + j;
+      if (n >= t.N) continue;
+      if (split)
+        part[t.part_off + z * MN + m * t.N + n] = acc[i][j];
+      else
+        C[crow_s[ty * TM + i] + ccol_s[tx * TN + j]] += alpha * acc[i][j];
+    }
+  }
+}
+
+// FP64 -> FP32 by truncation of the significand, in integer arithmetic (the
+// FP64 pipe is the scarce unit on this part). Magnitudes below the FP32
+// normal range become zero; the operands of the method are far above it.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
+  return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+
+// exact split of an FP32 value into three BF16 slices (8 significant bits each)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &s0, __nv_bfloat16 &s1, __nv_bfloat16 &s2) {
+  s0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(s0);
+  s1 = __float2bfloat16_rn(r1);
+  s2 = __float2bfloat16_rn(r1 - __bfloat162float(s1));
+}
+
+// BF16 three-slice split on the tensor cores (mma.sync m16n8k16, FP32
+// accumulation): the six slice products with i + j <= 2. Tile 64 x 64, K
+// tile 32, 8 warps as 2 x 4, each warp 32 x 16 outputs.
+__global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ tasks, int ntasks, double alpha,
+                                                     const double *__restrict__ A, const double *__restrict__ B,
+                                                     double *__restrict__ C, double *__restrict__ part) {
+  constexpr int TBM = 64, TBN = 64, TBK = 32, LDS = 40;  // padded row stride (bf16) avoids bank conflicts
+  __shared__ __align__(16) __nv_bfloat16 As[3][TBM][LDS];
+  __shared__ __align__(16) __nv_bfloat16 Bs[3][TBN][LDS];
+  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[TBK], brow_s[TBK];
+  __shared__ GTask t;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 2, wn = warp & 3;
+  const int g = lane >> 2, tg = lane & 3;
+  const long long cta = blockIdx.x;
+  if (tid == 0) t = tasks[find_task(tasks, ntasks, cta)];
+  __syncthreads();
+  const long long local = cta - t.cta_begin;
+  const long long z = local / t.tiles, tile = local - z * t.tiles;
+  const long long m0 = (tile / t.tiles_n) * TBM, n0 = (tile % t.tiles_n) * TBN;
+  const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
+  const bool split = t.ksplit > 1;
+  if (tid < TBM) {
+    const long long m = m0 + tid;
+    arow_s[tid] = m < t.M ? t.arow[m] : 0;
+    crow_s[tid] = (!split && m < t.M) ? t.crow[m] : 0;
+  } else if (tid < TBM + TBN) {
+    const long long n = n0 + tid - TBM;
+    bcol_s[tid - TBM] = n < t.N ? t.bcol[n] : 0;
+    ccol_s[tid - TBM] = (!split && n < t.N) ? t.ccol[n] : 0;
+  }
+  float acc[2][2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  for (long long k0 = kb; k0 < ke; k0 += TBK) {
+    __syncthreads();
+    if (tid < TBK) {
+      const long long k = k0 + tid;
+      acol_s[tid] = k < ke ? t.acol[k] : 0;
+    } else if (tid < 2 * TBK) {
+      const long long k = k0 + tid - TBK;
+      brow_s[tid - TBK] = k < ke ? t.brow[k] : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < (TBM * TBK) / NT; ++r) {
+      const int idx = tid + NT * r;
+      const int kk = idx % TBK, row = idx / TBK;
+      const bool ok = (m0 + row < t.M) && (k0 + kk < ke);
+      const float xf = ok ? f64_to_f32_trunc(__ldg(A + arow_s[row] + acol_s[kk])) : 0.f;
+      split3(xf, As[0][row][kk], As[1][row][kk], As[2][row][kk]);
+    }
+#pragma unroll
+    for (int r = 0; r < (TBN * TBK) / NT; ++r) {
+      const int idx = tid + NT * r;
+      const int col = idx % TBN, kk = idx / TBN;
+      const bool ok = (n0 + col < t.N) && (k0 + kk < ke);
+      const float xf = ok ? f64_to_f32_trunc(__ldg(B + brow_s[kk] + bcol_s[col])) : 0.f;
+      split3(xf, Bs[0][col][kk], Bs[1][col][kk], Bs[2][col][kk]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < TBK; ks += 16) {
+      unsigned a[3][2][4], b[3][2][2];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const int r0 = wm * 32 + mt * 16 + g;
+          const int c0 = ks + 2 * tg;
+          a[s][mt][0] = *reinterpret_cast<const unsigned *>(&As[s][r0][c0]);
+          a[s][mt][1] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0]);
+          a[s][mt][2] = *reinterpret_cast<const unsigned *>(&As[s][r0][c0 + 8]);
+          a[s][mt][3] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0 + 8]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int n = wn * 16 + nt * 8 + g;
+          b[s][nt][0] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg]);
+          b[s][nt][1] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg + 8]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3 - i; ++j)
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+              asm volatile(
+                  "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                  "{%0,%1,%2,%3};\n"
+                  : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
+                  : "r"(a[i][mt][0]), "r"(a[i][mt][1]), "r"(a[i][mt][2]), "r"(a[i][mt][3]), "r"(b[j][nt][0]),
+                    "r"(b[j][nt][1]));
+    }
+  }
+  const long long MN = t.M * t.N;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int rl = wm * 32 + mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int cl = wn * 16 + nt * 8 + 2 * tg + (e & 1);
+        const long long m = m0 + rl, n = n0 + cl;
+        if (m >= t.M || n >= t.N) continue;
+        if (split)
+          part[t.part_off + z * MN + m * t.N + n] = (double)acc[mt][nt][e];
+        else
+          C[crow_s[rl] + ccol_s[cl]] += alpha * (double)acc[mt][nt][e];
+      }
+}
+
+// C[crow(m) + ccol(n)] += alpha * sum_z part[task][z][m, n], z in order, for
+// the tasks whose reduction was split
+__global__ void k_greduce(const GTask *__restrict__ tasks, const int *__restrict__ split_ids, int nsplit,
+                          long long nred, double alpha, const double *__restrict__ part, double *__restrict__ C) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= nred) return;
+  int lo = 0, hi = nsplit - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tasks[split_ids[mid]].red_begin <= idx)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const GTask &t = tasks[split_ids[lo]];
+  const long long local = idx - t.red_begin;
+  const long long m = local / t.N, n = local - m * t.N;
+  const long long MN = t.M * t.N;
+  double s = 0.0;
+  for (int z = 0; z < t.ksplit; ++z) s += part[t.part_off + z * MN + local];
+  C[t.crow[m] + t.ccol[n]] += alpha * s;
+}
+
+// (TY, TM, TN) of the FP64 shapes
+constexpr int kShapeDims[kGShapes][3] = {{16, 4, 4}, {16, 8, 2}, {16, 2, 8}, {16, 8, 1}, {16, 1, 8},
+                                         {16, 2, 2}, {16, 1, 1}, {64, 2, 1}, {256, 1, 1}, {4, 1, 2}};
+
+inline unsigned blocks_for(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
+
+}  // namespace
+
+void grouped_shape(int shape, int *tbm, int *tbn, int *tbk) {
+  if (shape == kGShapeBf16) {
+    *tbm = 64;
+    *tbn = 64;
+    *tbk = 32;
+    return;
+  }
+  if (shape < 0 || shape >= kGShapes) throw std::runtime_error("grouped_shape: bad shape");
+  const int ty = kShapeDims[shape][0], tx = NT / ty;
+  *tbm = ty * kShapeDims[shape][1];
+  *tbn = tx * kShapeDims[shape][2];
+  *tbk = 16;
+}
+
+void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const double *A, const double *B, double *C) {
+  if (g.ntasks <= 0 || g.ncta <= 0) return;
+  if (g.ncta > 0x7fffffffLL) throw std::runtime_error("grouped_gemm: grid too large");
+  double *part = nullptr;
+  if (g.nsplit > 0) {
+    if (!L.partials) throw std::runtime_error("grouped_gemm: no partial-sum scratch");
+    L.partials->reserve(sizeof(double) * (size_t)g.part_need);
+    part = L.partials->d();
+  }
+  GemmProfile *pr = (L.prof && L.prof->enabled) ? L.prof : nullptr;
+  int e0 = -1;
+  if (pr) {
+    while (pr->pool.size() < 2 * pr->pairs.size() + 2) {
+      cudaEvent_t ev;
+      FNOCC_CUDA(cudaEventCreate(&ev));
+      pr->pool.push_back(ev);
+    }
+    e0 = (int)(2 * pr->pairs.size());
+    FNOCC_CUDA(cudaEventRecord(pr->pool[e0], L.stream));
+  }
+  const unsigned grid = (unsigned)g.ncta;
+#define FNOCC_G(i, ty, tm, tn) \
+  case i: k_ggemm<ty, tm, tn><<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part); break;
+  switch (g.shape) {
+    FNOCC_G(0, 16, 4, 4)
+    FNOCC_G(1, 16, 8, 2)
+    FNOCC_G(2, 16, 2, 8)
+    FNOCC_G(3, 16, 8, 1)
+    FNOCC_G(4, 16, 1, 8)
+    FNOCC_G(5, 16, 2, 2)
+    FNOCC_G(6, 16, 1, 1)
+    FNOCC_G(7, 64, 2, 1)
+    FNOCC_G(8, 256, 1, 1)
+    FNOCC_G(9, 4, 1, 2)
+    case kGShapeBf16:
+      k_ggemm_bf16x3<<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part);
+      break;
+    default:
+      throw std::runtime_error("grouped_gemm: bad shape");
+  }
+#undef FNOCC_G
+  FNOCC_CUDA(cudaGetLastError());
+  if (L.counter) ++*L.counter;
+  if (g.nsplit > 0) {
+    k_greduce<<<blocks_for(g.nred, 256), 256, 0, L.stream>>>(g.tasks, g.split_ids, g.nsplit, g.nred, alpha, part, C);
+    FNOCC_CUDA(cudaGetLastError());
+    if (L.counter) ++*L.counter;
+  }
+  if (pr) {
+    FNOCC_CUDA(cudaEventRecord(pr->pool[e0 + 1], L.stream));
+    pr->pairs.push_back({e0, e0 + 1});
+    pr->flops.push_back(g.flops);
+    pr->path.push_back((g.shape == kGShapeBf16 ? 4 : 0) + (g.nsplit > 0 ? 1 : 0));
+    if (pr->pairs.size() >= 4096) pr->fold();
+  }
+}
+
+}  // namespace fnocc

@@ -456,6 +456,22 @@ __global__ void k_precondition(long long n, const double *r, const double *d, do
   out[i] = mask[i] ? r[i] / den : 0.0;
 }
 
+// y[i] (+)= sum_j coef[j] * X[j * ld + i]: one streaming pass over the k
+// rows (each row read coalesced), coefficients staged in shared memory
+__global__ void k_lincomb(long long n, const double *__restrict__ X, long long ld, int k,
+                          const double *__restrict__ coef, double *__restrict__ y, int accumulate) {
+  extern __shared__ double cs[];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = coef[j];
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    double acc = accumulate ? y[i] : 0.0;
+    const double *xp = X + i;
+    for (int j = 0; j < k; ++j) acc = fma(cs[j], __ldg(xp + (long long)j * ld), acc);
+    y[i] = acc;
+  }
+}
+
 // partial dot products: grid (gx, nvec)
 __global__ void k_dot_partial(long long n, const double *x, const double *Y, long long ld, double *part) {
   __shared__ double red[256];
@@ -895,7 +911,9 @@ int gather_gemm(const Launch &L, long long M, long long N, long long K, double a
   }
   // tiny outputs: one thread per output, K split over blocks, ordered reduction
   if (O <= 256) {
-    long long nblk = std::min<long long>(std::max<long long>(1, p.K / 2048), 1024);
+    // FP64 issue is slow per SM: spread K over about two blocks per SM
+    // (chunks of at least 64) so that the whole GPU works on the few outputs
+    long long nblk = std::min<long long>(std::max<long long>(1, p.K / 64), 2 * 152);
     long long kchunk = (p.K + nblk - 1) / nblk;
     nblk = (p.K + kchunk - 1) / kchunk;
     p.kchunk = kchunk;
@@ -1027,6 +1045,14 @@ void multi_dot(const Launch &L, long long n, const double *x, const double *Y, l
   k_dot_partial<<<grid, 256, 0, L.stream>>>(n, x, Y, ld, part.d());
   post(L);
   k_dot_final<<<blocks_for(nvec, 128), 128, 0, L.stream>>>(gx, nvec, part.d(), dots_dev);
+  post(L);
+}
+
+void lincomb(const Launch &L, long long n, const double *X, long long ld, int k, const double *coef_dev, double *y,
+             bool accumulate) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<long long>(blocks_for(n, 256), 152 * 8);
+  k_lincomb<<<grid, 256, sizeof(double) * std::max(k, 1), L.stream>>>(n, X, ld, k, coef_dev, y, accumulate ? 1 : 0);
   post(L);
 }
 

@@ -99,10 +99,18 @@ def test_ccsdt_three_electrons_is_fci():
     assert abs(e_ref + res["e_corr"] - e_fci[0]) < 1e-9
 
 
-def _dense_roots(variant, act, res, k):
+def _dense_roots(variant, act, res, k, principal_only=False):
+    """Lowest k eigenvalues (total energies) of the dense sector matrix; with
+    principal_only, among eigenvectors with principal-block weight >= 1e-6."""
     f, g, o, v = act["f"], act["g"], act["o"], act["v"]
     m = eom.sigma_matrix(variant, f, g, o, v, res["t1"], res["t2"], res["t3"])
-    w = np.sort(np.linalg.eigvals(m).real)
+    w, vecs = np.linalg.eig(m)
+    if principal_only:
+        idx = np.where(eom.ms_mask(variant, o, v))[0]
+        npr = int(np.sum(idx < eom.sizes(variant, o, v)[0]))
+        weight = np.sum(np.abs(vecs[:npr]) ** 2, axis=0) / np.sum(np.abs(vecs) ** 2, axis=0)
+        w = w[weight >= 1e-6]
+    w = np.sort(w.real)
     return act["e_ref"] + res["e_corr"] + w[:k], m.shape[0]
 
 
@@ -148,11 +156,37 @@ def test_davidson_matches_dense_diagonalisation():
     f, g, o, v = act["f"], act["g"], act["o"], act["v"]
     res = cc.ccsdt(f, g, o, v)
     for variant in ("ip", "dea"):
-        dense, _ = _dense_roots(variant, act, res, 3)
+        dense, _ = _dense_roots(variant, act, res, 3, principal_only=True)
         out = eom.eom_ccsdt(variant, f, g, o, v, res["t1"], res["t2"], res["t3"], 3, tol_res=1e-9)
         assert out["converged"]
         got = act["e_ref"] + res["e_corr"] + out["omega"]
         assert np.max(np.abs(got - dense)) < 1e-9, (variant, got, dense)
+
+
+def test_davidson_returns_lowest_principal_states():
+    """Six electrons in five orbitals: the IP operator space holds quartet
+    2h1p states with no 1h weight below the third doublet root (and DIP
+    quintet 3h1p states likewise). The roots are the lowest eigenvalues of
+    the dense sector matrix among eigenvectors with principal-block weight
+    (at least 1e-6); the zero-weight states are excluded, not missed."""
+    h, eri = synth.hamiltonian(6, 5, seed=0)
+    act = fno.fno_truncate(h, eri, 3, 0.0)
+    f, g, o, v = act["f"], act["g"], act["o"], act["v"]
+    res = cc.ccsdt(f, g, o, v)
+    assert res["converged"]
+    variant = "ip"
+    m = eom.sigma_matrix(variant, f, g, o, v, res["t1"], res["t2"], res["t3"])
+    w, vecs = np.linalg.eig(m)
+    idx = np.where(eom.ms_mask(variant, o, v))[0]
+    npr = int(np.sum(idx < eom.sizes(variant, o, v)[0]))
+    weight = np.sum(np.abs(vecs[:npr]) ** 2, axis=0) / np.sum(np.abs(vecs) ** 2, axis=0)
+    order = np.argsort(w.real)
+    principal = [w[j].real for j in order if weight[j] >= 1e-6][:3]
+    # the pin means something: a zero-weight state lies below the third root
+    assert any(weight[j] < 1e-12 and w[j].real < principal[-1] for j in order)
+    out = eom.eom_ccsdt(variant, f, g, o, v, res["t1"], res["t2"], res["t3"], 3, tol_res=1e-9)
+    assert out["converged"]
+    assert np.max(np.abs(out["omega"] - np.array(principal))) < 1e-9, (out["omega"], principal)
 
 
 def test_mp2_energy_and_density_from_perturbation_theory():
@@ -246,13 +280,19 @@ def test_noninteracting_limit_is_koopmans(variant):
     eso = np.repeat(eps, 2)
     occ, vir = list(range(o)), list(range(o, 2 * n))
     spin = lambda p: 1 if p % 2 == 0 else -1
-    vals = []
-    for nh, np_ in wick.EOM_SPACES[variant]:
+    # eigenvectors are single determinants here: the roots are the lowest
+    # principal-block (1h / 1p / 2h / 2p) determinant energies of the sector
+    # (the others carry no principal weight), filled up by the lowest others
+    # where the sector has fewer than three principal determinants
+    vals = [[], []]
+    for k, (nh, np_) in enumerate(wick.EOM_SPACES[variant]):
         for hs in itertools.combinations(occ, nh):
             for ps in itertools.combinations(vir, np_):
                 if sum(spin(a) for a in ps) - sum(spin(i) for i in hs) == eom.SECTOR_MS2[variant]:
-                    vals.append(sum(eso[a] for a in ps) - sum(eso[i] for i in hs))
-    assert np.max(np.abs(np.sort(out["omega"]) - np.sort(vals)[:3])) < 1e-10
+                    vals[min(k, 1)].append(sum(eso[a] for a in ps) - sum(eso[i] for i in hs))
+    principal = sorted(vals[0])[:3]
+    expect = np.sort(principal + sorted(vals[1])[:3 - len(principal)])
+    assert np.max(np.abs(np.sort(out["omega"]) - expect)) < 1e-10
 
 
 def test_xfno_is_exact_on_linear_data():
