@@ -58,7 +58,10 @@ typedef enum {
 } fnocc_status;
 
 typedef enum { FNOCC_IP = 0, FNOCC_EA = 1, FNOCC_DIP = 2, FNOCC_DEA = 3 } fnocc_variant;
-typedef enum { FNOCC_GUESS_KOOPMANS = 0, FNOCC_GUESS_DIAGONAL = 1 } fnocc_guess;
+/* KOOPMANS: unit vectors on the lowest diagonal entries of the principal
+ * block; DIAGONAL: of the whole space; LEARNED: chosen and preconditioned by
+ * the context's guess network (fnocc_set_guess_model), DIAGONAL as fallback */
+typedef enum { FNOCC_GUESS_KOOPMANS = 0, FNOCC_GUESS_DIAGONAL = 1, FNOCC_GUESS_LEARNED = 2 } fnocc_guess;
 typedef enum { FNOCC_CRIT_ABS = 0, FNOCC_CRIT_OCCT = 1 } fnocc_criterion;
 /* Arithmetic of the contractions (the single- and double-precision
  * algorithms of Sec. 1). MIXED runs the large contractions as BF16
@@ -129,6 +132,7 @@ typedef struct {
   int complex_roots;      /* roots whose Ritz value had |Im| > 1e-8 */
   double res_max;         /* max residual norm over roots at exit */
   int sigma_calls_mixed;  /* products evaluated in MIXED precision */
+  int guess_used;         /* fnocc_guess that produced the roots (LEARNED falls back to DIAGONAL) */
 } eom_info;
 
 /* Context ---------------------------------------------------------------- */
@@ -278,6 +282,54 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
                                const int *variants, int nroots, const ccsdt_options *cc_opt,
                                const eom_options *eom_opt, int nworkers, double *omegas,
                                fnocc_system_result *results);
+
+/* Learned Davidson guess (not in the paper; the learned-guess extension) ----
+ * A per-amplitude MLP maps features of each element of the packed operator
+ * space to (0) a guess importance, log10 of the element's largest squared
+ * amplitude over the lowest roots, and (1) a correction to the diagonal
+ * preconditioner, H-bar_mumu - D_mu with D_mu the orbital-energy difference.
+ * Network nin = 8 features -> width -> width -> nout = 2, ReLU hidden layers,
+ * FP32 parameters (W1 [8 x width], b1, W2 [width x width], b2,
+ * W3 [width x 2], b3, row-major, input index first); trained by the
+ * library's FP32 kernels (MSE with per-sample per-output weights, Adam),
+ * evaluated in BF16 on the tensor cores inside eom_ccsdt_solve. All arrays
+ * here are host arrays, row-major [n x 8] / [n x 2]. Training calls on one
+ * network must not overlap; solves may share a network (its parameters are
+ * only read there). */
+typedef struct fnocc_mlp fnocc_mlp;
+fnocc_status fnocc_mlp_create(fnocc_mlp **mlp, int device, int nin, int width, int nout, unsigned long long seed);
+void fnocc_mlp_destroy(fnocc_mlp *mlp);
+const char *fnocc_mlp_last_error(const fnocc_mlp *mlp);
+size_t fnocc_mlp_param_count(const fnocc_mlp *mlp);
+fnocc_status fnocc_mlp_get_params(fnocc_mlp *mlp, float *params, size_t len);
+/* also resets the optimiser state */
+fnocc_status fnocc_mlp_set_params(fnocc_mlp *mlp, const float *params, size_t len);
+/* y = net(x); bf16 = 1: the BF16 tensor-core inference path, 0: FP32 */
+fnocc_status fnocc_mlp_forward(fnocc_mlp *mlp, const float *x, long long n, float *y, int bf16);
+/* loss = sum_i sum_o w[i,o] (net(x)[i,o] - t[i,o])^2 / n and its gradient
+ * (param_count floats, parameter layout) at the current parameters */
+fnocc_status fnocc_mlp_loss_grad(fnocc_mlp *mlp, const float *x, const float *t, const float *w, long long n,
+                                 double *loss, float *grad);
+/* minibatch Adam (beta 0.9 / 0.999, eps 1e-8), rows shuffled per epoch by a
+ * SplitMix64 generator seeded with `seed`; history[epoch] = mean loss (may
+ * be NULL). One epoch with batch >= n is exactly one Adam step on loss_grad. */
+fnocc_status fnocc_mlp_train(fnocc_mlp *mlp, const float *x, const float *t, const float *w, long long n,
+                             int epochs, int batch, float lr, unsigned long long seed, double *history);
+
+/* Features [dim x 8] of every element of the variant's packed operator space
+ * (components concatenated as in eom_sigma): orbital-energy difference D,
+ * two-body shift of the element's determinant (sum of <pq||pq> over hole
+ * pairs and particle pairs minus over hole-particle pairs), highest hole and
+ * lowest particle energy, mean particle energy, sum over particles of log10
+ * of the virtual's natural occupation (0 without FNO), component index,
+ * variant. Orbital energies are the diagonal of the active-space Fock
+ * operator, integrals the bare antisymmetrised ones. */
+fnocc_status fnocc_eom_features(fnocc_ctx *ctx, int variant, float *features);
+/* Exact diagonal H-bar_mumu of the sector's elements (others 0), one sigma
+ * product per element: training data on small systems. */
+fnocc_status fnocc_eom_diagonal(fnocc_ctx *ctx, int variant, double *diag);
+/* The network FNOCC_GUESS_LEARNED uses (not owned; NULL detaches). */
+fnocc_status fnocc_set_guess_model(fnocc_ctx *ctx, fnocc_mlp *mlp);
 
 /* XFNO (Sec. 2): least-squares line E(f) through (kept_fraction, energy)
  * points evaluated at f = 1 (the paper prints no formula; this is the

@@ -200,8 +200,12 @@ def fno_truncate(h, eri, nocc, threshold, criterion="abs", nkeep=0):
     c_vir = fix_phase(c[:, nocc:] @ uk @ w)
     c_act = np.concatenate([c[:, :nocc], c_vir], axis=1)
     act = active_hamiltonian(h, eri, c_act, nocc)
+    # natural occupation carried by each semicanonical virtual (diagonal of
+    # the kept NO density in the semicanonical basis): a feature of the
+    # learned Davidson guess, not a quantity of the paper's method
+    virt_occ = (w ** 2).T @ occ[:k] if k > 0 else np.zeros(0)
     act.update(e_rhf=e_rhf, e_mp2=e_mp2, occ=occ, nkept=k,
-               kept_fraction=kept_fraction, c_act=c_act, scf_iters=scf["iters"])
+               kept_fraction=kept_fraction, c_act=c_act, scf_iters=scf["iters"], virt_occ=virt_occ)
     return act
 
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libfnocc.so")
 
 IP, EA, DIP, DEA = 0, 1, 2, 3
 VARIANTS = {"ip": IP, "ea": EA, "dip": DIP, "dea": DEA}
-GUESS = {"koopmans": 0, "diagonal": 1}
+GUESS = {"koopmans": 0, "diagonal": 1, "learned": 2}
 CRITERIA = {"abs": 0, "occt": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "E_INVALID", -2: "E_NOMEM", -3: "E_CUDA",
@@ -62,7 +62,7 @@ class EomOptions(ctypes.Structure):
 class EomInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("sigma_calls", ctypes.c_int), ("seconds", ctypes.c_double),
                 ("seconds_per_iter", ctypes.c_double), ("complex_roots", ctypes.c_int),
-                ("res_max", ctypes.c_double), ("sigma_calls_mixed", ctypes.c_int)]
+                ("res_max", ctypes.c_double), ("sigma_calls_mixed", ctypes.c_int), ("guess_used", ctypes.c_int)]
 
 
 class System(ctypes.Structure):
@@ -78,6 +78,7 @@ class SystemResult(ctypes.Structure):
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _vp = ctypes.c_void_p
 _cp = ctypes.c_void_p
 
@@ -113,6 +114,20 @@ SIGNATURES = {
     "fnocc_plan_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
     "fnocc_profile": (ctypes.c_int, [_cp, ctypes.c_int]),
+    "fnocc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_cp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_ulonglong]),
+    "fnocc_mlp_destroy": (None, [_cp]),
+    "fnocc_mlp_last_error": (ctypes.c_char_p, [_cp]),
+    "fnocc_mlp_param_count": (ctypes.c_size_t, [_cp]),
+    "fnocc_mlp_get_params": (ctypes.c_int, [_cp, _fp, ctypes.c_size_t]),
+    "fnocc_mlp_set_params": (ctypes.c_int, [_cp, _fp, ctypes.c_size_t]),
+    "fnocc_mlp_forward": (ctypes.c_int, [_cp, _fp, ctypes.c_longlong, _fp, ctypes.c_int]),
+    "fnocc_mlp_loss_grad": (ctypes.c_int, [_cp, _fp, _fp, _fp, ctypes.c_longlong, _dp, _fp]),
+    "fnocc_mlp_train": (ctypes.c_int, [_cp, _fp, _fp, _fp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_float, ctypes.c_ulonglong, _dp]),
+    "fnocc_eom_features": (ctypes.c_int, [_cp, ctypes.c_int, _fp]),
+    "fnocc_eom_diagonal": (ctypes.c_int, [_cp, ctypes.c_int, _dp]),
+    "fnocc_set_guess_model": (ctypes.c_int, [_cp, _cp]),
     "fnocc_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(System), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                          ctypes.POINTER(CcsdtOptions), ctypes.POINTER(EomOptions), ctypes.c_int,
@@ -205,6 +220,82 @@ def plan_text(kind, variant=0, out_comp=0, in_comp=0, o=10, v=30, amortize=0.0):
     buf = ctypes.create_string_buffer(n + 1)
     lib.fnocc_plan_text(kind, var, out_comp, in_comp, o, v, amortize, buf, n + 1)
     return buf.value.decode()
+
+
+def _farr(x, cols=None):
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if cols is not None and (a.ndim != 2 or a.shape[1] != cols):
+        raise ValueError("expected an array of shape (n, %d)" % cols)
+    return a, a.ctypes.data_as(_fp)
+
+
+class Mlp:
+    """Per-amplitude guess network (8 features -> width -> width -> 2) whose
+    training and inference run in the library's kernels; see fnocc_mlp_*."""
+    NIN, NOUT = 8, 2
+
+    def __init__(self, device=0, width=256, seed=0):
+        self.lib = load_library()
+        self._h = _cp()
+        st = self.lib.fnocc_mlp_create(ctypes.byref(self._h), int(device), self.NIN, int(width), self.NOUT,
+                                       int(seed))
+        if st != 0:
+            raise FnoccError(st, "fnocc_mlp_create failed")
+        self.width = width
+
+    def close(self):
+        if self._h:
+            self.lib.fnocc_mlp_destroy(self._h)
+            self._h = _cp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            msg = self.lib.fnocc_mlp_last_error(self._h)
+            raise FnoccError(st, msg.decode() if msg else "")
+
+    @property
+    def nparam(self):
+        return int(self.lib.fnocc_mlp_param_count(self._h))
+
+    def get_params(self):
+        p = np.zeros(self.nparam, dtype=np.float32)
+        self._check(self.lib.fnocc_mlp_get_params(self._h, p.ctypes.data_as(_fp), p.size))
+        return p
+
+    def set_params(self, p):
+        p, pp = _farr(p)
+        self._check(self.lib.fnocc_mlp_set_params(self._h, pp, p.size))
+
+    def forward(self, x, bf16=False):
+        x, xp = _farr(x, self.NIN)
+        y = np.zeros((x.shape[0], self.NOUT), dtype=np.float32)
+        self._check(self.lib.fnocc_mlp_forward(self._h, xp, x.shape[0], y.ctypes.data_as(_fp), 1 if bf16 else 0))
+        return y
+
+    def loss_grad(self, x, t, w):
+        x, xp = _farr(x, self.NIN)
+        t, tp = _farr(t, self.NOUT)
+        w, wp = _farr(w, self.NOUT)
+        loss = ctypes.c_double()
+        g = np.zeros(self.nparam, dtype=np.float32)
+        self._check(self.lib.fnocc_mlp_loss_grad(self._h, xp, tp, wp, x.shape[0], ctypes.byref(loss),
+                                                 g.ctypes.data_as(_fp)))
+        return loss.value, g
+
+    def train(self, x, t, w, epochs=20, batch=4096, lr=1e-3, seed=0):
+        x, xp = _farr(x, self.NIN)
+        t, tp = _farr(t, self.NOUT)
+        w, wp = _farr(w, self.NOUT)
+        hist = np.zeros(max(epochs, 1))
+        self._check(self.lib.fnocc_mlp_train(self._h, xp, tp, wp, x.shape[0], int(epochs), int(batch),
+                                             float(lr), int(seed), hist.ctypes.data_as(_dp)))
+        return hist[:epochs]
 
 
 class Context:
@@ -357,7 +448,25 @@ class Context:
         return dict(energies=en, omegas=om, iters=info.iters, sigma_calls=info.sigma_calls,
                     seconds=info.seconds, seconds_per_iter=info.seconds_per_iter,
                     complex_roots=info.complex_roots, res_max=info.res_max, converged=(st == 0),
-                    sigma_calls_mixed=info.sigma_calls_mixed)
+                    sigma_calls_mixed=info.sigma_calls_mixed, guess_used=info.guess_used)
+
+    def eom_features(self, variant):
+        var = VARIANTS.get(variant, variant)
+        dim = sum(self.eom_sizes(var))
+        f = np.zeros((dim, Mlp.NIN), dtype=np.float32)
+        self._check(self.lib.fnocc_eom_features(self._h, var, f.ctypes.data_as(_fp)))
+        return f
+
+    def eom_diagonal(self, variant):
+        """Exact H-bar diagonal of the sector's elements (one product each)."""
+        var = VARIANTS.get(variant, variant)
+        d = np.zeros(sum(self.eom_sizes(var)))
+        self._check(self.lib.fnocc_eom_diagonal(self._h, var, d.ctypes.data_as(_dp)))
+        return d
+
+    def set_guess_model(self, mlp):
+        self._guess_model = mlp  # keep the network alive while attached
+        self._check(self.lib.fnocc_set_guess_model(self._h, mlp._h if mlp is not None else None))
 
     def get_block(self, which, root=0):
         """which: 't1','t2','t3' or ('r', k) for component k=1..3 of EOM root `root`."""

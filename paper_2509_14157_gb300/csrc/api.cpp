@@ -1,5 +1,6 @@
 // C ABI of libfnocc (include/fnocc.h): context, FNO setup, CCSDT and EOM-CCSDT.
 #include "../../include/fnocc.h"
+#include "mlp.hpp"
 
 #include <algorithm>
 #include <atomic>
@@ -157,6 +158,11 @@ struct fnocc_ctx {
 
   std::unique_ptr<ExecEquation> cc_eq[4];
   DevBuf Y[4], scratch, red, small, coef;
+  // learned guess: the network (not owned), its inference scratch, and the
+  // natural occupations of the active virtuals (spatial, semicanonical basis)
+  fnocc_mlp *guess_model = nullptr;
+  DevBuf mlp_scratch, vocc;
+  std::vector<double> virt_occ;
 
   // EOM
   std::unique_ptr<ExecEquation> eom_eq[4][3][3];
@@ -653,6 +659,7 @@ fnocc_status fnocc_set_mo_hamiltonian(fnocc_ctx *c, const double *h_mo, const do
     if (!h_mo || !eri_mo || n <= 0 || nocc <= 0 || nocc >= n || n > 64)
       throw StatusError(FNOCC_E_INVALID, "invalid Hamiltonian dimensions");
     FNOCC_CUDA(cudaSetDevice(c->device));
+    c->virt_occ.clear();
     size_t n4 = (size_t)n * n * n * n;
     to_dev(c, c->h_act, h_mo, (size_t)n * n);
     to_dev(c, c->eri_act, eri_mo, n4);
@@ -867,6 +874,7 @@ static fnocc_status fno_truncate_impl(fnocc_ctx *c, const double *h, const doubl
     const double frac = tot > 0 ? kept / tot : 1.0;
     // semicanonicalise: F_vv in the kept NO basis, diagonalised
     int nact = nocc + k;
+    std::vector<double> semi_occ;
     c->c_act.reserve(sizeof(double) * n * nact);
     if (k > 0) {
       DevBuf evir, fno_, w, uw, tmp;
@@ -885,6 +893,13 @@ static fnocc_status fno_truncate_impl(fnocc_ctx *c, const double *h, const doubl
       matmul(c, k, k, nvir, uk.d(), k, true, tmp.d(), k, false, fno_.d(), k, nvk, nvk, (long long)k * k);
       w.reserve(sizeof(double) * k * k);
       sym_eig(c, fno_.d(), k, w.d());
+      {
+        // occupation of each semicanonical virtual: sum_j W[j][a]^2 n_j
+        auto wh = to_host(c, w.d(), (size_t)k * k);
+        semi_occ.assign(k, 0.0);
+        for (int a = 0; a < k; ++a)
+          for (int j = 0; j < k; ++j) semi_occ[a] += wh[(size_t)j * k + a] * wh[(size_t)j * k + a] * occ[j];
+      }
       uw.reserve(sizeof(double) * nvir * k);
       matmul(c, nvir, k, k, uk.d(), k, false, w.d(), k, false, uw.d(), k, nvk, (long long)k * k, nvk);
       // C_vir_new = C[:, nocc:] * UW
@@ -910,6 +925,7 @@ static fnocc_status fno_truncate_impl(fnocc_ctx *c, const double *h, const doubl
     spin_orbital_h(L, c->h_act.d(), nact, c->hso.d());
     spin_orbital_eri(L, c->eri_act.d(), nact, c->gso.d());
     install_hamiltonian(c, nocc, nact);
+    c->virt_occ = semi_occ;
     sync(c);
     if (out) {
       out->e_rhf = e_rhf;
@@ -1217,13 +1233,36 @@ fnocc_status eom_sigma(fnocc_ctx *c, int variant, const double *r, double *s) {
   });
 }
 
-fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, const eom_options *opt,
-                             double *energies, double *omegas, eom_info *out) {
+// features [dim x kMlpFeatures] of the variant's operator space (device)
+void eom_features_dev(fnocc_ctx *c, int variant, float *out) {
+  const int o = c->o, v = c->v;
+  std::vector<float> vl(std::max(v, 1), 0.f);
+  if (!c->virt_occ.empty())
+    for (int a = 0; a < v; ++a) vl[a] = (float)std::log10(std::max(c->virt_occ[a / 2], 1e-12));
+  c->vocc.reserve(sizeof(float) * vl.size());
+  FNOCC_CUDA(cudaMemcpyAsync(c->vocc.p, vl.data(), sizeof(float) * vl.size(), cudaMemcpyHostToDevice, c->stream));
+  size_t sz[3];
+  eom_sizes(c, variant, sz);
+  size_t off = 0;
+  for (int k = 0; k < 3; ++k) {
+    const int nh = kEom[variant][k][0], np = kEom[variant][k][1];
+    eom_features(c->stream, nh, np, o, c->n, c->otab[nh].dev.as<int>(), c->otab[nh].count,
+                 c->vtab[np].dev.as<int>(), c->vtab[np].count, c->fdiag.d(), c->gso.d(), c->vocc.as<float>(), k,
+                 variant, out + off * kMlpFeatures);
+    off += sz[k];
+  }
+}
+
+fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, const eom_options *opt,
+                            double *energies, double *omegas, eom_info *out) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
     if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
     if (nroots <= 0 || !energies) throw StatusError(FNOCC_E_INVALID, "bad nroots or null energies");
-    if (guess != FNOCC_GUESS_KOOPMANS && guess != FNOCC_GUESS_DIAGONAL) throw StatusError(FNOCC_E_INVALID, "bad guess");
+    if (guess != FNOCC_GUESS_KOOPMANS && guess != FNOCC_GUESS_DIAGONAL && guess != FNOCC_GUESS_LEARNED)
+      throw StatusError(FNOCC_E_INVALID, "bad guess");
+    if (guess == FNOCC_GUESS_LEARNED && (!c->guess_model || !c->guess_model->net))
+      throw StatusError(FNOCC_E_STATE, "no guess network (fnocc_set_guess_model)");
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     Timer timer;
@@ -1260,6 +1299,23 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
               kSectorMs2[variant], mk.as<unsigned char>() + off);
       off += sz[k];
     }
+    std::vector<float> score;  // learned guess: predicted importance per element
+    if (guess == FNOCC_GUESS_LEARNED) {
+      const Mlp &net = *c->guess_model->net;
+      if (net.device() != c->device) throw StatusError(FNOCC_E_INVALID, "guess network lives on another device");
+      DevBuf feats, yout;
+      feats.reserve(sizeof(float) * dim * kMlpFeatures);
+      yout.reserve(sizeof(float) * dim * kMlpOutputs);
+      eom_features_dev(c, variant, feats.as<float>());
+      net.infer_bf16(feats.as<float>(), dim, yout.as<float>(), c->stream, c->mlp_scratch);
+      // preconditioner: D + predicted correction (bounded)
+      add_diag_correction(c->stream, dim, yout.as<float>(), kMlpOutputs, 1, 5.0, dg.d());
+      std::vector<float> yh((size_t)dim * kMlpOutputs);
+      FNOCC_CUDA(cudaMemcpyAsync(yh.data(), yout.p, sizeof(float) * yh.size(), cudaMemcpyDeviceToHost, c->stream));
+      sync(c);
+      score.resize(dim);
+      for (long long i = 0; i < dim; ++i) score[i] = yh[(size_t)i * kMlpOutputs];
+    }
     auto dgh = to_host(c, dg.d(), dim);
     std::vector<unsigned char> mkh(dim);
     FNOCC_CUDA(cudaMemcpy(mkh.data(), mk.p, dim, cudaMemcpyDeviceToHost));
@@ -1287,6 +1343,12 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
     }
     std::vector<long long> order(pref);
     order.insert(order.end(), rest.begin(), rest.end());
+    if (guess == FNOCC_GUESS_LEARNED) {  // highest predicted importance first
+      order = allowed;
+      std::partial_sort(order.begin(), order.begin() + ng, order.end(), [&](long long a, long long b) {
+        return score[a] > score[b] || (score[a] == score[b] && a < b);
+      });
+    }
     order.resize(ng);
     // subspace storage
     const int cap = max_sub + nr + 1;
@@ -1510,9 +1572,95 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
       for (double x : norms) mx = std::max(mx, x);
       out->res_max = mx;
       out->sigma_calls_mixed = sigma_calls_mixed;
+      out->guess_used = guess;
     }
     return conv ? FNOCC_OK : FNOCC_NOT_CONVERGED;
   });
+}
+
+fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, const eom_options *opt,
+                             double *energies, double *omegas, eom_info *out) {
+  fnocc_status st = eom_solve_once(c, variant, nroots, guess, opt, energies, omegas, out);
+  if (guess == FNOCC_GUESS_LEARNED && st == FNOCC_NOT_CONVERGED) {
+    // plain Davidson from the diagonal guess judges: roots never depend on the network
+    eom_info first{};
+    if (out) first = *out;
+    st = eom_solve_once(c, variant, nroots, FNOCC_GUESS_DIAGONAL, opt, energies, omegas, out);
+    if (out) {
+      out->sigma_calls += first.sigma_calls;
+      out->sigma_calls_mixed += first.sigma_calls_mixed;
+      out->seconds += first.seconds;
+      out->iters += first.iters;
+    }
+  }
+  return st;
+}
+
+fnocc_status fnocc_eom_features(fnocc_ctx *c, int variant, float *features) {
+  if (!c || !features) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    require_ham(c);
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    size_t sz[3];
+    eom_sizes(c, variant, sz);
+    const size_t dim = sz[0] + sz[1] + sz[2];
+    DevBuf f;
+    f.reserve(sizeof(float) * dim * kMlpFeatures);
+    eom_features_dev(c, variant, f.as<float>());
+    FNOCC_CUDA(cudaMemcpyAsync(features, f.p, sizeof(float) * dim * kMlpFeatures, cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status fnocc_eom_diagonal(fnocc_ctx *c, int variant, double *diag) {
+  if (!c || !diag) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    require_ham(c);
+    FNOCC_CUDA(cudaSetDevice(c->device));
+    prepare_hbar(c);
+    c->precision = FNOCC_FP64;
+    Launch L = c->L();
+    size_t sz[3];
+    eom_sizes(c, variant, sz);
+    const long long dim = (long long)(sz[0] + sz[1] + sz[2]);
+    DevBuf mk, x, s, dd;
+    mk.reserve(dim);
+    size_t off = 0;
+    for (int k = 0; k < 3; ++k) {
+      const int nh = kEom[variant][k][0], np = kEom[variant][k][1];
+      ms_mask(L, nh, np, c->otab[nh].dev.as<int>(), c->otab[nh].count, c->vtab[np].dev.as<int>(), c->vtab[np].count,
+              kSectorMs2[variant], mk.as<unsigned char>() + off);
+      off += sz[k];
+    }
+    std::vector<unsigned char> mkh(dim);
+    FNOCC_CUDA(cudaMemcpyAsync(mkh.data(), mk.p, dim, cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    x.reserve(sizeof(double) * dim);
+    s.reserve(sizeof(double) * dim);
+    dd.reserve(sizeof(double) * dim);
+    FNOCC_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double) * dim, c->stream));
+    FNOCC_CUDA(cudaMemsetAsync(dd.p, 0, sizeof(double) * dim, c->stream));
+    const double one = 1.0, zero = 0.0;
+    for (long long i = 0; i < dim; ++i) {
+      if (!mkh[i]) continue;
+      FNOCC_CUDA(cudaMemcpyAsync(x.d() + i, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      sigma_dev(c, variant, x.d(), s.d());
+      FNOCC_CUDA(cudaMemcpyAsync(dd.d() + i, s.d() + i, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      FNOCC_CUDA(cudaMemcpyAsync(x.d() + i, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
+    FNOCC_CUDA(cudaMemcpyAsync(diag, dd.p, sizeof(double) * dim, cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status fnocc_set_guess_model(fnocc_ctx *c, fnocc_mlp *mlp) {
+  if (!c) return FNOCC_E_INVALID;
+  c->guess_model = mlp;
+  return FNOCC_OK;
 }
 
 fnocc_status fnocc_multi_dot(fnocc_ctx *c, const double *x, const double *Y, size_t n, size_t ld, int nvec,

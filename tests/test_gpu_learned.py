@@ -1,0 +1,115 @@
+"""Learned Davidson guess on the GPU: the network's kernels against the
+oracle (oracle/mlp.py), its features and training targets against the
+oracle's definitions, and solves with the learned start against plain
+Davidson: the roots never depend on the network, and a trained network
+saves products."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import eom, fno, mlp, packing, wick
+
+pytestmark = pytest.mark.gpu
+
+WIDTH = 64
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2509_14157_gb300 as p
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p.load_library()
+    return p
+
+
+def case(n=300, seed=0):
+    rng = np.random.default_rng(seed)
+    nparam = mlp.NIN * WIDTH + WIDTH + WIDTH * WIDTH + WIDTH + WIDTH * mlp.NOUT + mlp.NOUT
+    params = (rng.normal(0, 0.3, nparam)).astype(np.float32)
+    x = rng.normal(0, 1.0, (n, mlp.NIN)).astype(np.float32)
+    t = rng.normal(0, 1.0, (n, mlp.NOUT)).astype(np.float32)
+    w = rng.uniform(0.2, 1.5, (n, mlp.NOUT)).astype(np.float32)
+    return params, x, t, w
+
+
+def test_forward_fp32_and_bf16_match_oracle(pkg):
+    params, x, _, _ = case()
+    net = pkg.Mlp(0, WIDTH, seed=1)
+    net.set_params(params)
+    ref, _ = mlp.forward(params.astype(np.float64), x.astype(np.float64), WIDTH)
+    scale = np.max(np.abs(ref))
+    y32 = net.forward(x)
+    assert np.max(np.abs(y32 - ref)) < 1e-5 * scale
+    y16 = net.forward(x, bf16=True)  # BF16 operands (8 significant bits), FP32 accumulation
+    assert np.max(np.abs(y16 - ref)) < 3e-2 * scale
+    net.close()
+
+
+def test_loss_and_gradient_match_oracle(pkg):
+    params, x, t, w = case(n=5000, seed=2)  # several row splits of the weight-gradient reduction
+    net = pkg.Mlp(0, WIDTH, seed=1)
+    net.set_params(params)
+    loss, g = net.loss_grad(x, t, w)
+    ref_loss, ref_g = mlp.loss_grad(params.astype(np.float64), x.astype(np.float64), t, w, WIDTH)
+    assert abs(loss - ref_loss) < 1e-5 * abs(ref_loss)
+    assert np.max(np.abs(g - ref_g)) < 1e-4 * np.max(np.abs(ref_g))
+    net.close()
+
+
+def test_one_training_step_is_one_adam_step(pkg):
+    params, x, t, w = case(n=700, seed=3)
+    net = pkg.Mlp(0, WIDTH, seed=1)
+    net.set_params(params)
+    hist = net.train(x, t, w, epochs=1, batch=4096, lr=1e-2)
+    p64 = params.astype(np.float64)
+    ref_loss, g = mlp.loss_grad(p64, x.astype(np.float64), t, w, WIDTH)
+    new, _, _ = mlp.adam_step(p64, g, np.zeros_like(p64), np.zeros_like(p64), 1, lr=1e-2)
+    got = net.get_params()
+    # the first Adam step moves every parameter by ~lr * sign(g); elements
+    # with |g| far below the FP32 rounding of g may take either sign
+    big = np.abs(g) > 1e-3 * np.max(np.abs(g))
+    assert np.max(np.abs(got[big] - new[big])) < 1e-5
+    assert np.max(np.abs(got - new)) <= 2e-2 + 1e-6
+    assert abs(hist[0] - ref_loss) < 1e-5 * abs(ref_loss)
+    net.close()
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+def test_features_match_oracle(pkg, variant):
+    h, eri = synth.hamiltonian(6, 10, seed=0)
+    act = fno.fno_truncate(h, eri, 3, 1e-4)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, 3, 1e-4)
+    got = ctx.eom_features(variant)
+    ref = mlp.eom_features(wick.EOM_SPACES[variant], ["ip", "ea", "dip", "dea"].index(variant),
+                           np.diag(act["f"]), act["g"], act["o"], act["v"], act["virt_occ"])
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got[:, :5] - ref[:, :5])) < 1e-5 * max(1.0, np.max(np.abs(ref[:, :5])))
+    assert np.max(np.abs(got[:, 5] - ref[:, 5])) < 1e-4
+    assert np.array_equal(got[:, 6:], ref[:, 6:])
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", ["ip", "dip"])
+def test_exact_diagonal_matches_oracle(pkg, variant):
+    """fnocc_eom_diagonal (one product per element) against the diagonal of
+    the oracle's explicit sector matrix, random amplitudes."""
+    from math import comb
+    nocc, n = 2, 5
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 29)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    t = [synth.random_packed(comb(o, r) * comb(v, r), 40 + r, 0.05) * synth.packed_ms_mask(r, r, o, v, 0)
+         for r in (1, 2, 3)]
+    ctx = pkg.Context(0)
+    ctx.set_mo_hamiltonian(h, eri, nocc)
+    ctx.set_amplitudes(*t)
+    got = ctx.eom_diagonal(variant)
+    td = [packing.unpack(t[r - 1], r, r, o, v) for r in (1, 2, 3)]
+    m = eom.sigma_matrix(variant, ham["f"], ham["g"], o, v, *td)
+    idx = np.where(eom.ms_mask(variant, o, v))[0]
+    assert np.max(np.abs(got[idx] - np.diag(m))) < 1e-10
+    assert np.all(got[np.setdiff1d(np.arange(got.size), idx)] == 0)
+    ctx.close()

@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import cc, detspace, eom, fno, packing, wick, xfno
+from oracle import cc, detspace, eom, fno, mlp, packing, wick, xfno
 
 
 def spin_masked(nh, np_, o, v, seed, scale, ms2=0):
@@ -313,3 +313,99 @@ def test_truncation_rules():
     # a degenerate pair straddling the cut is kept whole
     occ2 = np.array([1e-2, 2e-3, 2e-3, 1e-5])
     assert fno.choose_kept(occ2, (occ2[0] + occ2[1]) / occ2.sum(), criterion="occt") == 3
+
+
+# ---- learned-guess network (oracle/mlp.py) -----------------------------------------
+
+def _mlp_case(width=5, n=7, seed=3):
+    rng = np.random.default_rng(seed)
+    nparam = mlp.NIN * width + width + width * width + width + width * mlp.NOUT + mlp.NOUT
+    params = rng.normal(0, 0.5, nparam)
+    x = rng.normal(0, 1.0, (n, mlp.NIN))
+    t = rng.normal(0, 1.0, (n, mlp.NOUT))
+    w = rng.uniform(0.2, 1.5, (n, mlp.NOUT))
+    return params, x, t, w, width
+
+
+def test_mlp_gradient_matches_finite_differences():
+    params, x, t, w, width = _mlp_case()
+    _, g = mlp.loss_grad(params, x, t, w, width)
+    h = 1e-6
+    fd = np.zeros_like(params)
+    for i in range(params.size):
+        e = np.zeros_like(params)
+        e[i] = h
+        fd[i] = (mlp.loss_grad(params + e, x, t, w, width)[0] - mlp.loss_grad(params - e, x, t, w, width)[0]) / (2 * h)
+    assert np.max(np.abs(g - fd)) < 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_mlp_zero_weights_closed_form():
+    params, x, t, w, width = _mlp_case()
+    layers = mlp.unpack(params, width)
+    b3 = np.array([0.3, -1.2])
+    zero = mlp.pack([np.zeros_like(layers[0]), layers[1], np.zeros_like(layers[2]), layers[3],
+                     np.zeros_like(layers[4]), b3])
+    y, _ = mlp.forward(zero, x, width)
+    assert np.allclose(y, b3)  # no path from the input: the output bias alone
+    loss, g = mlp.loss_grad(zero, x, t, w, width)
+    assert abs(loss - np.sum(w * (b3 - t) ** 2) / len(x)) < 1e-14
+    gl = mlp.unpack(g, width)
+    assert np.allclose(gl[5], np.sum(2 * w * (b3 - t), axis=0) / len(x))
+    assert np.all(gl[0] == 0) and np.all(gl[2] == 0)  # zero weights above pass nothing back
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    new, m, v = mlp.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    # bias-corrected first moments equal g and g^2: the step is lr * g / (|g| + eps)
+    assert np.allclose(new, p - 0.01 * g / (np.abs(g) + 1e-8))
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_eom_features_definition():
+    # 2 occupied / 4 virtual spin orbitals, IP spaces (1h, 2h1p, 3h2p), one
+    # two-electron integral <0 3||0 3> = 0.25 (hole 0, particle 1)
+    o, v = 2, 4
+    fdiag = np.array([-1.0, -0.8, 0.5, 0.7, 1.1, 1.3])
+    g = np.zeros((6,) * 4)
+    for p, q in [(0, 3), (3, 0)]:
+        g[p, q, p, q] = 0.25
+        g[p, q, q, p] = -0.25
+    occ = np.array([1e-2, 1e-4])
+    feats = mlp.eom_features(wick.EOM_SPACES["ip"], 0, fdiag, g, o, v, occ)
+    assert feats.shape == (2 + 1 * 4 + 0, 8)  # C(2,3) = 0: no 3h2p element
+    assert np.allclose(feats[0], [1.0, 0.0, -1.0, 0.0, 0.0, 0.0, 0, 0])
+    # holes 0,1 and particle 1 (orbital 3): the hole 0 - particle pair lowers
+    # the determinant's energy by <03||03>
+    assert np.allclose(feats[2 + 1], [0.7 + 1.8, -0.25, -0.8, 0.7, 0.7, -2.0, 1, 0])
+    # holes 0,1 and particle 2 (orbital 4, virtual spatial 1): no integral
+    assert np.allclose(feats[2 + 2], [1.1 + 1.8, 0.0, -0.8, 1.1, 1.1, -4.0, 1, 0])
+
+
+def test_en_shift_is_determinant_energy_difference():
+    """D plus the two-body shift is the energy of the element's determinant
+    relative to the reference (Slater rules), for every element of a small
+    DIP space."""
+    h, eri = synth.random_symmetric_mo_hamiltonian(4, 17)
+    ham = fno.mo_hamiltonian(h, eri, 2)
+    o, v = ham["o"], ham["v"]
+    hso, g = ham["hso"], ham["g"]
+    feats = mlp.eom_features(wick.EOM_SPACES["dip"], 2, np.diag(ham["f"]), g, o, v)
+
+    def det_energy(occupied):
+        e = sum(hso[p, p] for p in occupied)
+        for x in range(len(occupied)):
+            for y in range(x + 1, len(occupied)):
+                e += g[occupied[x], occupied[y], occupied[x], occupied[y]]
+        return e
+
+    e0 = det_energy(list(range(o)))
+    row = 0
+    for nh, np_ in wick.EOM_SPACES["dip"]:
+        for hs in itertools.combinations(range(o), nh):
+            for ps in itertools.combinations(range(v), np_):
+                occupied = [p for p in range(o) if p not in hs] + [o + a for a in ps]
+                assert abs(feats[row, 0] + feats[row, 1] - (det_energy(occupied) - e0)) < 1e-12
+                row += 1
+    assert row == feats.shape[0]
