@@ -113,3 +113,30 @@ def test_exact_diagonal_matches_oracle(pkg, variant):
     assert np.max(np.abs(got[idx] - np.diag(m))) < 1e-10
     assert np.all(got[np.setdiff1d(np.arange(got.size), idx)] == 0)
     ctx.close()
+
+
+def test_trained_network_saves_products_and_keeps_roots(pkg):
+    """Train on small seeded systems, solve a larger held-out one: the
+    learned start reaches the same roots (plain Davidson criteria) with
+    fewer sigma products than the diagonal start."""
+    from paper_2509_14157_gb300 import learned
+    systems = learned.seeded_training_systems(count=12)
+    X, T, W, _ = learned.training_set(systems, ["dip", "dea"], 3)
+    net, hist = learned.train_guess_model(X, T, W, epochs=30, batch=2048)
+    assert hist[-1] < 0.5 * hist[0]
+    h, eri = synth.hamiltonian(8, 20, seed=1)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, 4, 1e-4)
+    assert ctx.ccsdt_solve()["converged"]
+    ctx.set_guess_model(net)
+    plain = with_net = 0
+    for var in ("dip", "dea"):
+        a = ctx.eom_solve(var, 4, guess="diagonal")
+        b = ctx.eom_solve(var, 4, guess="learned")
+        assert a["converged"] and b["converged"] and b["guess_used"] == 2
+        assert np.max(np.abs(a["omegas"] - b["omegas"])) < 1e-9
+        plain += a["sigma_calls"]
+        with_net += b["sigma_calls"]
+    assert with_net < plain, (with_net, plain)
+    ctx.close()
+    net.close()
