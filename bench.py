@@ -197,7 +197,10 @@ def run_reference(args):
 
 
 def run_sigma_only(args):
-    """FNO setup, random amplitudes, then one sigma product of one variant."""
+    """Profiling case: FNO setup, random amplitudes, two warm sigma products of
+    one variant (the second with the R-independent intermediates cached, as
+    inside a Davidson solve), then one more inside the NVTX range "sig"."""
+    import torch
     import paper_2509_14157_gb300 as pkg
     import synth
     h, eri = synth.hamiltonian(NE, NORB, seed=0)
@@ -206,11 +209,20 @@ def run_sigma_only(args):
     rng = np.random.default_rng(0)
     ctx.set_amplitudes(*[rng.normal(0, 0.01, s) for s in ctx.amp_sizes()])
     ctx.set_precision(args.precision)
-    x = rng.normal(0, 0.1, sum(ctx.eom_sizes(args.sigma_only)))
+    dim = sum(ctx.eom_sizes(args.sigma_only))
+    x = torch.from_numpy(rng.normal(0, 0.1, dim)).cuda()
+    s = torch.empty_like(x)
+    for _ in range(2):
+        ctx.eom_sigma_dev(args.sigma_only, x.data_ptr(), s.data_ptr())
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("sig")
     t0 = time.perf_counter()
-    ctx.eom_sigma(args.sigma_only, x)
-    print(json.dumps({"sigma_only": args.sigma_only, "precision": args.precision,
-                      "seconds": time.perf_counter() - t0, "flops": ctx.flops}), flush=True)
+    ctx.eom_sigma_dev(args.sigma_only, x.data_ptr(), s.data_ptr())
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"sigma_only": args.sigma_only, "precision": args.precision, "seconds": dt,
+                      "flops": ctx.flops}), flush=True)
     ctx.close()
 
 
