@@ -171,6 +171,7 @@ struct fnocc_ctx {
   // the dressed operators and dense T2/T3 hold the stored amplitudes' H-bar
   // (cleared by every residual evaluation and by new amplitudes)
   bool hbar_valid = false;
+  int plan_o = -1, plan_v = -1;  // shape the contraction plans were built for
   int cache_precision = 0;  // arithmetic of the cached R-independent intermediates
   uint64_t eq_seen[4][3][3] = {};  // H-bar version whose cached flops were counted
   int last_variant = -1, last_nroots = 0;
@@ -254,15 +255,22 @@ void install_hamiltonian(fnocc_ctx *c, int nocc, int nact_spatial) {
   c->fdiag.reserve(sizeof(double) * c->n);
   diag_of(L, c->fso.d(), c->n, c->fdiag.d());
   c->fdiag_host = to_host(c, c->fdiag.d(), c->n);
-  for (int k = 0; k <= 4; ++k) {
-    c->otab[k].build(c->o, k);
-    c->vtab[k].build(c->v, k);
+  // contraction plans depend on (o, v) only: kept across Hamiltonians of the
+  // same shape (their cached intermediates follow the H-bar version)
+  if (c->o != c->plan_o || c->v != c->plan_v) {
+    for (int k = 0; k <= 4; ++k) {
+      c->otab[k].build(c->o, k);
+      c->vtab[k].build(c->v, k);
+    }
+    c->dress_plan.build(c->n, c->n);
+    for (int r = 0; r < 4; ++r) c->cc_eq[r].reset();
+    for (auto &a : c->eom_eq)
+      for (auto &b : a)
+        for (auto &e : b) e.reset();
+    c->plan_o = c->o;
+    c->plan_v = c->v;
   }
-  c->dress_plan.build(c->n, c->n);
-  for (int r = 0; r < 4; ++r) c->cc_eq[r].reset();
-  for (auto &a : c->eom_eq)
-    for (auto &b : a)
-      for (auto &e : b) e.reset();
+  ++c->hbar_version;
   c->nt[1] = (size_t)binom_ll(c->o, 1) * binom_ll(c->v, 1);
   c->nt[2] = (size_t)binom_ll(c->o, 2) * binom_ll(c->v, 2);
   c->nt[3] = (size_t)binom_ll(c->o, 3) * binom_ll(c->v, 3);
@@ -316,6 +324,16 @@ void ensure_cc_plans(fnocc_ctx *c) {
 }
 
 // residual of packed amplitudes tp (device) into rp (device); returns E_corr
+// dense antisymmetric [o^nh v^np] work tensor from packed elements
+void unpack(fnocc_ctx *c, const Launch &L, const double *packed, int nh, int np, double *dense) {
+  if (np >= 1)
+    unpack_dense_rows(L, packed, nh, np, c->o, c->v, c->otab[nh].rank(), c->vtab[np].rank(), c->vtab[np].count,
+                      dense);
+  else
+    unpack_dense(L, packed, nh, np, c->o, c->v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
+                 c->vtab[np].dev.as<int>(), c->vtab[np].count, dense);
+}
+
 double cc_residual_dev(fnocc_ctx *c, const double *tp, double *rp) {
   c->hbar_valid = false;  // the residual overwrites the dressed operators
   Launch L = c->L();
@@ -325,10 +343,8 @@ double cc_residual_dev(fnocc_ctx *c, const double *tp, double *rp) {
   dress(c, t1);
   c->t2d.reserve(sizeof(double) * ipow(o, 2) * ipow(v, 2));
   c->t3d.reserve(sizeof(double) * std::max<long long>(1, ipow(o, 3) * ipow(v, 3)));
-  unpack_dense(L, t2, 2, 2, o, v, c->otab[2].dev.as<int>(), c->otab[2].count, c->vtab[2].dev.as<int>(),
-               c->vtab[2].count, c->t2d.d());
-  unpack_dense(L, t3, 3, 3, o, v, c->otab[3].dev.as<int>(), c->otab[3].count, c->vtab[3].dev.as<int>(),
-               c->vtab[3].count, c->t3d.d());
+  unpack(c, L, t2, 2, 2, c->t2d.d());
+  unpack(c, L, t3, 3, 3, c->t3d.d());
   Operands ops;
   ops.f = c->fdr.d();
   ops.v = c->gd.d();
@@ -395,10 +411,8 @@ void prepare_hbar(fnocc_ctx *c) {
   dress(c, tp);
   c->t2d.reserve(sizeof(double) * ipow(o, 2) * ipow(v, 2));
   c->t3d.reserve(sizeof(double) * std::max<long long>(1, ipow(o, 3) * ipow(v, 3)));
-  unpack_dense(L, tp + c->nt[1], 2, 2, o, v, c->otab[2].dev.as<int>(), c->otab[2].count, c->vtab[2].dev.as<int>(),
-               c->vtab[2].count, c->t2d.d());
-  unpack_dense(L, tp + c->nt[1] + c->nt[2], 3, 3, o, v, c->otab[3].dev.as<int>(), c->otab[3].count,
-               c->vtab[3].dev.as<int>(), c->vtab[3].count, c->t3d.d());
+  unpack(c, L, tp + c->nt[1], 2, 2, c->t2d.d());
+  unpack(c, L, tp + c->nt[1] + c->nt[2], 3, 3, c->t3d.d());
   ++c->hbar_version;
   c->hbar_valid = true;
 }
@@ -430,8 +444,7 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s) {
     int nh = kEom[var][k][0], np = kEom[var][k][1];
     long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
     c->rd[k].reserve(sizeof(double) * dn);
-    unpack_dense(L, x + off, nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count, c->vtab[np].dev.as<int>(),
-                 c->vtab[np].count, c->rd[k].d());
+    unpack(c, L, x + off, nh, np, c->rd[k].d());
     ops.r[k] = c->rd[k].d();
     ops.r_size[k] = dn;
     off += sz[k];

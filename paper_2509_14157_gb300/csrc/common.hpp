@@ -146,6 +146,10 @@ void antisym_pack(const Launch &L, const double *Y, int nh, int np, int o, int v
                   const int *htab, long long nhtup, const int *ptab, long long nptup, double *out,
                   double scale, bool accumulate);
 // Dense antisymmetric tensor from packed elements (dense zeroed here).
+// same result as unpack_dense as one coalesced gather (np >= 1); hrank /
+// prank: rank prefix tables of the hole / particle tuple lists
+void unpack_dense_rows(const Launch &L, const double *packed, int nh, int np, int o, int v, const long long *hrank,
+                       const long long *prank, long long nptup, double *dense);
 void unpack_dense(const Launch &L, const double *packed, int nh, int np, int o, int v,
                   const int *htab, long long nhtup, const int *ptab, long long nptup,
                   double *dense);

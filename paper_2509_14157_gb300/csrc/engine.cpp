@@ -37,6 +37,11 @@ void TupleTable::build(int n_, int k_) {
   if (host.empty()) host.push_back(0);
   dev.reserve(host.size() * sizeof(int));
   FNOCC_CUDA(cudaMemcpy(dev.p, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<long long> rk((size_t)std::max(k, 1) * (n + 1), 0);
+  for (int i = 0; i < k; ++i)
+    for (int x = 1; x <= n; ++x) rk[(size_t)i * (n + 1) + x] = rk[(size_t)i * (n + 1) + x - 1] + binom_ll(n - x, k - 1 - i);
+  rankdev.reserve(rk.size() * sizeof(long long));
+  FNOCC_CUDA(cudaMemcpy(rankdev.p, rk.data(), rk.size() * sizeof(long long), cudaMemcpyHostToDevice));
 }
 
 namespace {

@@ -107,6 +107,10 @@ struct TupleTable {
   int n = 0, k = 0;
   long long count = 0;
   DevBuf dev;
+  // lexicographic rank of a sorted tuple c: sum_i S_i(c_i) - S_i(c_{i-1} + 1)
+  // with S_i(x) = sum_{j < x} C(n-1-j, k-1-i) stored at rank[i * (n+1) + x]
+  DevBuf rankdev;
+  const long long *rank() const { return rankdev.as<long long>(); }
   void build(int n, int k);
 };
 
