@@ -105,7 +105,9 @@ struct GTask {
 // A grouped launch: tasks ordered by cta_begin (device array) plus the list
 // of tasks with a split reduction.
 constexpr int kGShapes = 10;           // FP64 tile shapes
-constexpr int kGShapeBf16 = kGShapes;  // BF16 three-slice split 64 x 64 tile (mixed precision)
+constexpr int kGShapeBf16 = kGShapes;  // first BF16 three-slice split shape (mixed precision)
+constexpr int kGShapesBf16 = 6;        // BF16x3 tiles 64x64, 32x32, 128x16, 16x128, 64x16, 16x64
+constexpr int kGShapesAll = kGShapes + kGShapesBf16;
 struct GroupedLaunch {
   const GTask *tasks = nullptr;
   int ntasks = 0;
@@ -117,7 +119,7 @@ struct GroupedLaunch {
   double flops = 0;      // algorithmic flops of the launch (profiling)
   double padded = 0;     // multiply-adds including tile padding x 2
 };
-// rows, columns and K tile of a shape (kGShapeBf16 included)
+// rows, columns and K tile of a shape (FP64 and BF16x3 shapes)
 void grouped_shape(int shape, int *tbm, int *tbn, int *tbk);
 // runs the launch (and the ordered reduction of split tasks) on L.stream
 void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const double *A, const double *B, double *C);

@@ -620,8 +620,8 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
   for (ExecTerm &t : terms_)
     for (ExecStep &e : t.steps) {
       if (!e.grouped) continue;
-      double est[kGShapes + 1];
-      for (int shape = 0; shape <= kGShapes; ++shape) {
+      double est[kGShapesAll];
+      for (int shape = 0; shape < kGShapesAll; ++shape) {
         int tbm, tbn, tbk;
         grouped_shape(shape, &tbm, &tbn, &tbk);
         long long T = 0;
@@ -675,8 +675,21 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
         gl.part_need = part;
         gl.padded = padded;
         gl.flops = flops;
-        est[shape] = padded / double(std::max<long long>(1, std::min<long long>(cta, 152)));
+        if (shape < kGShapeBf16) {
+          est[shape] = padded / double(std::max<long long>(1, std::min<long long>(cta, 152)));
+        } else {
+          // tensor-core tiles: the cost is staging (gather, convert, split) of
+          // the (tbm + tbn) x tbk operand panels of every K tile, two CTAs per SM
+          double staged = 0;
+          for (size_t i = gt.size() - e.tasks.size(); i < gt.size(); ++i)
+            staged += double(gt[i].tiles) * double((gt[i].K + tbk - 1) / tbk) * double((tbm + tbn) * tbk);
+          est[shape] = staged / double(std::max<long long>(1, std::min<long long>(cta, 2 * 152)));
+        }
       }
+      int bbest = kGShapeBf16;
+      for (int shape = kGShapeBf16 + 1; shape < kGShapesAll; ++shape)
+        if (est[shape] < est[bbest]) bbest = shape;
+      e.bf16_shape = bbest;
       int best = 0;
       for (int shape = 1; shape < kGShapes; ++shape)
         if (est[shape] < est[best]) best = shape;
@@ -784,7 +797,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         throw std::runtime_error("engine: grouped index tables exceed operand bounds");
       ExecStep &ms = const_cast<ExecStep &>(s);
       if (L.precision == 1 && s.gl[0].flops >= 1e5) {
-        grouped_gemm(L, s.gl[kGShapeBf16], s.alpha, A, B, C);
+        grouped_gemm(L, s.gl[s.bf16_shape], s.alpha, A, B, C);
         continue;
       }
       const bool tune = autotune && L.precision == 0 && ms.tuned_shape < 0 && ms.cand.size() > 1 &&

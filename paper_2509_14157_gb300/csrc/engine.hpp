@@ -46,9 +46,10 @@ struct ExecStep {
     long long M, N, K, arow, acol, brow, bcol, crow, ccol;  // offsets into the flat table buffer
   };
   std::vector<TaskRef> tasks;
-  GroupedLaunch gl[kGShapes + 1];
+  GroupedLaunch gl[kGShapesAll];
   long long gmax_a = 0, gmax_b = 0, gmax_c = 0;  // largest row + column offset per operand
   int default_shape = 0;                          // least padded work per busy SM
+  int bf16_shape = kGShapeBf16;                   // mixed precision: least staged work per busy SM
   std::vector<int> cand;                          // FP64 shapes worth timing, best estimate first
   // tile-shape autotuning of large FP64 steps: every candidate is timed once,
   // then the fastest is kept

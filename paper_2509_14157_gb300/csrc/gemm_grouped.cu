@@ -153,19 +153,22 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &s0, __nv_bfloat16
 }
 
 // BF16 three-slice split on the tensor cores (mma.sync m16n8k16, FP32
-// accumulation): the six slice products with i + j <= 2. Tile 64 x 64, K
-// tile 32, 8 warps as 2 x 4, each warp 32 x 16 outputs.
+// accumulation): the six slice products with i + j <= 2. 8 warps as WM x WN,
+// each warp MT x NT2 mma tiles (16 x 8), so the block tile is
+// (WM*MT*16) x (WN*NT2*8); K tile 32.
+template <int WM, int WN, int MT, int NT2>
 __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ tasks, int ntasks, double alpha,
                                                      const double *__restrict__ A, const double *__restrict__ B,
                                                      double *__restrict__ C, double *__restrict__ part) {
-  constexpr int TBM = 64, TBN = 64, TBK = 32, LDS = 40;  // padded row stride (bf16) avoids bank conflicts
+  constexpr int TBM = WM * MT * 16, TBN = WN * NT2 * 8, TBK = 32, LDS = 40;  // padded row stride (bf16)
+  static_assert(WM * WN == 8, "8 warps");
   __shared__ __align__(16) __nv_bfloat16 As[3][TBM][LDS];
   __shared__ __align__(16) __nv_bfloat16 Bs[3][TBN][LDS];
   __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[TBK], brow_s[TBK];
   __shared__ GTask t;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int wm = warp >> 2, wn = warp & 3;
+  const int wm = warp / WN, wn = warp % WN;
   const int g = lane >> 2, tg = lane & 3;
   const long long cta = blockIdx.x;
   if (tid == 0) t = tasks[find_task(tasks, ntasks, cta)];
@@ -175,20 +178,21 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
   const long long m0 = (tile / t.tiles_n) * TBM, n0 = (tile % t.tiles_n) * TBN;
   const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
   const bool split = t.ksplit > 1;
-  if (tid < TBM) {
-    const long long m = m0 + tid;
-    arow_s[tid] = m < t.M ? t.arow[m] : 0;
-    crow_s[tid] = (!split && m < t.M) ? t.crow[m] : 0;
-  } else if (tid < TBM + TBN) {
-    const long long n = n0 + tid - TBM;
-    bcol_s[tid - TBM] = n < t.N ? t.bcol[n] : 0;
-    ccol_s[tid - TBM] = (!split && n < t.N) ? t.ccol[n] : 0;
+  for (int i = tid; i < TBM; i += NT) {
+    const long long m = m0 + i;
+    arow_s[i] = m < t.M ? t.arow[m] : 0;
+    crow_s[i] = (!split && m < t.M) ? t.crow[m] : 0;
   }
-  float acc[2][2][4];
+  for (int i = tid; i < TBN; i += NT) {
+    const long long n = n0 + i;
+    bcol_s[i] = n < t.N ? t.bcol[n] : 0;
+    ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
+  }
+  float acc[MT][NT2][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < NT2; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
   for (long long k0 = kb; k0 < ke; k0 += TBK) {
@@ -201,17 +205,13 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
       brow_s[tid - TBK] = k < ke ? t.brow[k] : 0;
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < (TBM * TBK) / NT; ++r) {
-      const int idx = tid + NT * r;
+    for (int idx = tid; idx < TBM * TBK; idx += NT) {
       const int kk = idx % TBK, row = idx / TBK;
       const bool ok = (m0 + row < t.M) && (k0 + kk < ke);
       const float xf = ok ? f64_to_f32_trunc(__ldg(A + arow_s[row] + acol_s[kk])) : 0.f;
       split3(xf, As[0][row][kk], As[1][row][kk], As[2][row][kk]);
     }
-#pragma unroll
-    for (int r = 0; r < (TBN * TBK) / NT; ++r) {
-      const int idx = tid + NT * r;
+    for (int idx = tid; idx < TBN * TBK; idx += NT) {
       const int col = idx % TBN, kk = idx / TBN;
       const bool ok = (n0 + col < t.N) && (k0 + kk < ke);
       const float xf = ok ? f64_to_f32_trunc(__ldg(B + brow_s[kk] + bcol_s[col])) : 0.f;
@@ -220,12 +220,12 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
     __syncthreads();
 #pragma unroll
     for (int ks = 0; ks < TBK; ks += 16) {
-      unsigned a[3][2][4], b[3][2][2];
+      unsigned a[3][MT][4], b[3][NT2][2];
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          const int r0 = wm * 32 + mt * 16 + g;
+        for (int mt = 0; mt < MT; ++mt) {
+          const int r0 = wm * MT * 16 + mt * 16 + g;
           const int c0 = ks + 2 * tg;
           a[s][mt][0] = *reinterpret_cast<const unsigned *>(&As[s][r0][c0]);
           a[s][mt][1] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0]);
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
           a[s][mt][3] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0 + 8]);
         }
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-          const int n = wn * 16 + nt * 8 + g;
+        for (int nt = 0; nt < NT2; ++nt) {
+          const int n = wn * NT2 * 8 + nt * 8 + g;
           b[s][nt][0] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg]);
           b[s][nt][1] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg + 8]);
         }
@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
 #pragma unroll
         for (int j = 0; j < 3 - i; ++j)
 #pragma unroll
-          for (int mt = 0; mt < 2; ++mt)
+          for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
+            for (int nt = 0; nt < NT2; ++nt)
               asm volatile(
                   "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                   "{%0,%1,%2,%3};\n"
@@ -257,13 +257,13 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
   }
   const long long MN = t.M * t.N;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+    for (int nt = 0; nt < NT2; ++nt)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int rl = wm * 32 + mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int cl = wn * 16 + nt * 8 + 2 * tg + (e & 1);
+        const int rl = wm * MT * 16 + mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int cl = wn * NT2 * 8 + nt * 8 + 2 * tg + (e & 1);
         const long long m = m0 + rl, n = n0 + cl;
         if (m >= t.M || n >= t.N) continue;
         if (split)
@@ -299,15 +299,19 @@ __global__ void k_greduce(const GTask *__restrict__ tasks, const int *__restrict
 // (TY, TM, TN) of the FP64 shapes
 constexpr int kShapeDims[kGShapes][3] = {{16, 4, 4}, {16, 8, 2}, {16, 2, 8}, {16, 8, 1}, {16, 1, 8},
                                          {16, 2, 2}, {16, 1, 1}, {64, 2, 1}, {256, 1, 1}, {4, 1, 2}};
+// (WM, WN, MT, NT2) of the BF16x3 shapes: 64x64, 32x32, 128x16, 16x128, 64x16, 16x64
+constexpr int kBf16Dims[kGShapesBf16][4] = {{2, 4, 2, 2}, {2, 4, 1, 1}, {8, 1, 1, 2},
+                                            {1, 8, 1, 2}, {4, 2, 1, 1}, {1, 8, 1, 1}};
 
 inline unsigned blocks_for(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 
 }  // namespace
 
 void grouped_shape(int shape, int *tbm, int *tbn, int *tbk) {
-  if (shape == kGShapeBf16) {
-    *tbm = 64;
-    *tbn = 64;
+  if (shape >= kGShapeBf16 && shape < kGShapesAll) {
+    const int *d = kBf16Dims[shape - kGShapeBf16];
+    *tbm = d[0] * d[2] * 16;
+    *tbn = d[1] * d[3] * 8;
     *tbk = 32;
     return;
   }
@@ -352,9 +356,16 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_G(7, 64, 2, 1)
     FNOCC_G(8, 256, 1, 1)
     FNOCC_G(9, 4, 1, 2)
-    case kGShapeBf16:
-      k_ggemm_bf16x3<<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part);
-      break;
+#define FNOCC_B(i, wm, wn, mt, nt) \
+  case kGShapeBf16 + i:           \
+    k_ggemm_bf16x3<wm, wn, mt, nt><<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part); break;
+    FNOCC_B(0, 2, 4, 2, 2)
+    FNOCC_B(1, 2, 4, 1, 1)
+    FNOCC_B(2, 8, 1, 1, 2)
+    FNOCC_B(3, 1, 8, 1, 2)
+    FNOCC_B(4, 4, 2, 1, 1)
+    FNOCC_B(5, 1, 8, 1, 1)
+#undef FNOCC_B
     default:
       throw std::runtime_error("grouped_gemm: bad shape");
   }
@@ -370,7 +381,7 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0 + 1], L.stream));
     pr->pairs.push_back({e0, e0 + 1});
     pr->flops.push_back(g.flops);
-    pr->path.push_back((g.shape == kGShapeBf16 ? 4 : 0) + (g.nsplit > 0 ? 1 : 0));
+    pr->path.push_back((g.shape >= kGShapeBf16 ? 4 : 0) + (g.nsplit > 0 ? 1 : 0));
     if (pr->pairs.size() >= 4096) pr->fold();
   }
 }
