@@ -259,7 +259,8 @@ def run_batch(args):
     print(json.dumps({"metric": METRIC + " (batched independent systems)", "value": t_bat / max(solves, 1),
                       "unit": "s", "higher_is_better": False, "sequential_value": t_seq / max(solves, 1),
                       "speedup": t_seq / t_bat if t_bat > 0 else None, "systems": len(systems),
-                      "converged_systems": len(ok), "workers": 4, "max_root_diff_eh": diff,
+                      "converged_systems": len(ok), "statuses": [i["status"] for i in info4],
+                      "workers": 4, "max_root_diff_eh": diff,
                       "config": {"workload": "16 seeded systems, 6/8/10 electrons, 8-14 kept natural virtuals "
                                              "(nkeep), IP and EA x 4 roots", "precision": "fp64"},
                       "data": "synthetic"}), flush=True)

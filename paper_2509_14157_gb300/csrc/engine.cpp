@@ -648,7 +648,10 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
           const long long tm = (tr.M + tbm - 1) / tbm;
           g.tiles_n = (tr.N + tbn - 1) / tbn;
           g.tiles = tm * g.tiles_n;
-          long long ks = std::min<long long>(want, std::max<long long>(1, tr.K / (4 * tbk)));
+          // reduction chunks of at least 4 K tiles (FP64) or 2 (tensor-core
+          // tiles, whose K tile is cheap next to the launch's CTA count)
+          const long long min_tiles = shape < kGShapeBf16 ? 4 : 2;
+          long long ks = std::min<long long>(want, std::max<long long>(1, tr.K / (min_tiles * tbk)));
           if (ks > 1 && part + ks * tr.M * tr.N > kPartCap) ks = 1;
           long long kchunk = (tr.K + ks - 1) / ks;
           kchunk = (kchunk + tbk - 1) / tbk * tbk;

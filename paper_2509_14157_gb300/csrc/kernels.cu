@@ -442,63 +442,53 @@ __device__ __forceinline__ void sort_small(int *t, int n, int &sgn, bool &dup) {
 
 // Dense antisymmetric tensor [o^nh v^np] from its packed unique elements, as
 // a coalesced gather (every dense element written once, no prior clear):
-// a warp owns one row (all indices but the last particle), its lanes the
-// last particle index. dense = sign(sorting permutation) * packed[rank], 0
-// on repeated indices. hr / pr: rank prefix tables of the hole / particle
-// tuple lists (TupleTable::rank). Needs np >= 1.
-__global__ void __launch_bounds__(256) k_unpack_rows(const double *__restrict__ packed, int nh, int np, int o, int v,
-                                                     const long long *__restrict__ hr,
-                                                     const long long *__restrict__ pr, long long nptup,
-                                                     long long nrows, double *__restrict__ dense) {
-  constexpr int ROWS = 64;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long r0 = (long long)blockIdx.x * ROWS;
-  const long long r1 = min(nrows, r0 + ROWS);
-  for (long long row = r0 + warp; row < r1; row += 8) {
-    long long rem = row;
-    int pp[4], hh[4];
-    for (int k = np - 2; k >= 0; --k) {
-      pp[k] = (int)(rem % v);
-      rem /= v;
-    }
-    for (int k = nh - 1; k >= 0; --k) {
-      hh[k] = (int)(rem % o);
-      rem /= o;
-    }
-    int sgn = 1;
-    bool dup = false;
-    sort_small(hh, nh, sgn, dup);
-    sort_small(pp, np - 1, sgn, dup);
-    long long hrank = 0;
-    for (int i = 0; i < nh; ++i) hrank += hr[i * (o + 1) + hh[i]] - hr[i * (o + 1) + (i ? hh[i - 1] + 1 : 0)];
-    double *drow = dense + row * v;
-    for (int a = lane; a < v; a += 32) {
-      double val = 0.0;
-      if (!dup) {
-        int q[4], s = sgn, m = 0;
-        bool d2 = false;
-        for (int k = 0; k < np - 1; ++k) {
-          if (pp[k] == a) d2 = true;
-          if (pp[k] > a) s = -s;
-        }
-        // merge a into the sorted prefix
-        bool placed = false;
-        for (int k = 0; k < np - 1; ++k) {
-          if (!placed && a < pp[k]) {
-            q[m++] = a;
-            placed = true;
-          }
-          q[m++] = pp[k];
-        }
-        if (!placed) q[m++] = a;
-        if (!d2) {
-          long long prank = 0;
-          for (int i = 0; i < np; ++i) prank += pr[i * (v + 1) + q[i]] - pr[i * (v + 1) + (i ? q[i - 1] + 1 : 0)];
-          val = s * __ldg(packed + hrank * nptup + prank);
-        }
+// block b owns the outer indices (holes and all but the last ni particles),
+// its threads stride over the inner ni particle indices, which are the
+// fastest-varying part of the dense layout. dense = sign(sorting
+// permutation) * packed[rank], 0 on repeated indices. hr / pr: rank prefix
+// tables of the hole / particle tuple lists (TupleTable::rank).
+__global__ void __launch_bounds__(256) k_unpack_blocks(const double *__restrict__ packed, int nh, int np, int ni,
+                                                       int o, int v, const long long *__restrict__ hr,
+                                                       const long long *__restrict__ pr, long long nptup,
+                                                       long long inner, double *__restrict__ dense) {
+  const long long outer = blockIdx.x;
+  long long rem = outer;
+  const int no = np - ni;  // outer particles
+  int po[4], hh[4];
+  for (int k = no - 1; k >= 0; --k) {
+    po[k] = (int)(rem % v);
+    rem /= v;
+  }
+  for (int k = nh - 1; k >= 0; --k) {
+    hh[k] = (int)(rem % o);
+    rem /= o;
+  }
+  int sgn0 = 1;
+  bool dup0 = false;
+  sort_small(hh, nh, sgn0, dup0);
+  long long hrank = 0;
+  for (int i = 0; i < nh; ++i) hrank += hr[i * (o + 1) + hh[i]] - hr[i * (o + 1) + (i ? hh[i - 1] + 1 : 0)];
+  double *dst = dense + outer * inner;
+  for (long long j = threadIdx.x; j < inner; j += blockDim.x) {
+    double val = 0.0;
+    if (!dup0) {
+      int q[4];
+      for (int k = 0; k < no; ++k) q[k] = po[k];
+      unsigned r = (unsigned)j;
+      for (int k = np - 1; k >= no; --k) {
+        q[k] = (int)(r % (unsigned)v);
+        r /= (unsigned)v;
       }
-      drow[a] = val;
+      int sgn = sgn0;
+      bool dup = false;
+      sort_small(q, np, sgn, dup);
+      if (!dup) {
+        long long prank = 0;
+        for (int i = 0; i < np; ++i) prank += pr[i * (v + 1) + q[i]] - pr[i * (v + 1) + (i ? q[i - 1] + 1 : 0)];
+        val = sgn * __ldg(packed + hrank * nptup + prank);
+      }
     }
+    dst[j] = val;
   }
 }
 
@@ -1070,13 +1060,14 @@ void antisym_pack(const Launch &L, const double *Y, int nh, int np, int o, int v
 void unpack_dense_rows(const Launch &L, const double *packed, int nh, int np, int o, int v, const long long *hrank,
                        const long long *prank, long long nptup, double *dense) {
   if (np < 1 || nh > 4 || np > 4) throw std::runtime_error("unpack_dense_rows: unsupported tuple sizes");
-  long long nrows = 1;
-  for (int k = 0; k < nh; ++k) nrows *= o;
-  for (int k = 0; k < np - 1; ++k) nrows *= v;
-  if (nrows <= 0 || v <= 0) return;
-  const long long nblk = (nrows + 63) / 64;
-  if (nblk > 0x7fffffffLL) throw std::runtime_error("unpack_dense_rows: grid too large");
-  k_unpack_rows<<<(unsigned)nblk, 256, 0, L.stream>>>(packed, nh, np, o, v, hrank, prank, nptup, nrows, dense);
+  const int ni = std::min(np, 3);  // inner particles: at most v^3 elements per block
+  long long outer = 1, inner = 1;
+  for (int k = 0; k < nh; ++k) outer *= o;
+  for (int k = 0; k < np - ni; ++k) outer *= v;
+  for (int k = 0; k < ni; ++k) inner *= v;
+  if (outer <= 0 || inner <= 0) return;
+  if (outer > 0x7fffffffLL || inner > 0xffffffffLL) throw std::runtime_error("unpack_dense_rows: too large");
+  k_unpack_blocks<<<(unsigned)outer, 256, 0, L.stream>>>(packed, nh, np, ni, o, v, hrank, prank, nptup, inner, dense);
   post(L);
 }
 
