@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace fnocc {
 
@@ -155,16 +156,30 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &s0, __nv_bfloat16
 // BF16 three-slice split on the tensor cores (mma.sync m16n8k16, FP32
 // accumulation): the six slice products with i + j <= 2. 8 warps as WM x WN,
 // each warp MT x NT2 mma tiles (16 x 8), so the block tile is
-// (WM*MT*16) x (WN*NT2*8); K tile 32.
+// (WM*MT*16) x (WN*NT2*8); K tile 32. Software pipeline: the operand
+// gathers of K tile t+1 are in flight (registers) while the tensor cores
+// work on tile t, whose slices sit in one of two shared-memory buffers; one
+// barrier per K tile.
+template <int WM, int WN, int MT, int NT2>
+struct Bf16Tile {
+  static constexpr int TBM = WM * MT * 16, TBN = WN * NT2 * 8, TBK = 32, LDS = 40;  // padded row stride
+  static constexpr int EA = TBM * TBK / NT, EB = TBN * TBK / NT;  // gathered elements per thread and tile
+  static constexpr size_t kSmem = sizeof(__nv_bfloat16) * 2 * 3 * (TBM + TBN) * LDS;
+  static_assert(WM * WN == 8, "8 warps");
+  static_assert(EA * NT == TBM * TBK && EB * NT == TBN * TBK, "whole tiles per thread");
+};
+
 template <int WM, int WN, int MT, int NT2>
 __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ tasks, int ntasks, double alpha,
                                                      const double *__restrict__ A, const double *__restrict__ B,
                                                      double *__restrict__ C, double *__restrict__ part) {
-  constexpr int TBM = WM * MT * 16, TBN = WN * NT2 * 8, TBK = 32, LDS = 40;  // padded row stride (bf16)
-  static_assert(WM * WN == 8, "8 warps");
-  __shared__ __align__(16) __nv_bfloat16 As[3][TBM][LDS];
-  __shared__ __align__(16) __nv_bfloat16 Bs[3][TBN][LDS];
-  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[TBK], brow_s[TBK];
+  using T = Bf16Tile<WM, WN, MT, NT2>;
+  constexpr int TBM = T::TBM, TBN = T::TBN, TBK = T::TBK, LDS = T::LDS, EA = T::EA, EB = T::EB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // As[buf][slice][row][k], Bs[buf][slice][col][k]
+  __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+  __nv_bfloat16 *Bs = As + 2 * 3 * TBM * LDS;
+  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN];
   __shared__ GTask t;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -188,6 +203,25 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
     bcol_s[i] = n < t.N ? t.bcol[n] : 0;
     ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
   }
+  __syncthreads();
+  double ra[EA], rb[EB];
+  // gathers of the K tile at k0 into registers (0 outside the task)
+  auto load = [&](long long k0) {
+#pragma unroll
+    for (int r = 0; r < EA; ++r) {
+      const int idx = tid + NT * r;
+      const int kk = idx % TBK, row = idx / TBK;
+      const long long k = k0 + kk;
+      ra[r] = (m0 + row < t.M && k < ke) ? __ldg(A + arow_s[row] + __ldg(t.acol + k)) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < EB; ++r) {
+      const int idx = tid + NT * r;
+      const int col = idx % TBN, kk = idx / TBN;
+      const long long k = k0 + kk;
+      rb[r] = (n0 + col < t.N && k < ke) ? __ldg(B + __ldg(t.brow + k) + bcol_s[col]) : 0.0;
+    }
+  };
   float acc[MT][NT2][4];
 #pragma unroll
   for (int i = 0; i < MT; ++i)
@@ -195,48 +229,45 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
     for (int j = 0; j < NT2; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  for (long long k0 = kb; k0 < ke; k0 += TBK) {
-    __syncthreads();
-    if (tid < TBK) {
-      const long long k = k0 + tid;
-      acol_s[tid] = k < ke ? t.acol[k] : 0;
-    } else if (tid < 2 * TBK) {
-      const long long k = k0 + tid - TBK;
-      brow_s[tid - TBK] = k < ke ? t.brow[k] : 0;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < TBM * TBK; idx += NT) {
+  if (kb < ke) load(kb);
+  int buf = 0;
+  for (long long k0 = kb; k0 < ke; k0 += TBK, buf ^= 1) {
+    __nv_bfloat16 *as = As + buf * 3 * TBM * LDS, *bs = Bs + buf * 3 * TBN * LDS;
+#pragma unroll
+    for (int r = 0; r < EA; ++r) {
+      const int idx = tid + NT * r;
       const int kk = idx % TBK, row = idx / TBK;
-      const bool ok = (m0 + row < t.M) && (k0 + kk < ke);
-      const float xf = ok ? f64_to_f32_trunc(__ldg(A + arow_s[row] + acol_s[kk])) : 0.f;
-      split3(xf, As[0][row][kk], As[1][row][kk], As[2][row][kk]);
+      split3(f64_to_f32_trunc(ra[r]), as[row * LDS + kk], as[(TBM + row) * LDS + kk],
+             as[(2 * TBM + row) * LDS + kk]);
     }
-    for (int idx = tid; idx < TBN * TBK; idx += NT) {
+#pragma unroll
+    for (int r = 0; r < EB; ++r) {
+      const int idx = tid + NT * r;
       const int col = idx % TBN, kk = idx / TBN;
-      const bool ok = (n0 + col < t.N) && (k0 + kk < ke);
-      const float xf = ok ? f64_to_f32_trunc(__ldg(B + brow_s[kk] + bcol_s[col])) : 0.f;
-      split3(xf, Bs[0][col][kk], Bs[1][col][kk], Bs[2][col][kk]);
+      split3(f64_to_f32_trunc(rb[r]), bs[col * LDS + kk], bs[(TBN + col) * LDS + kk],
+             bs[(2 * TBN + col) * LDS + kk]);
     }
     __syncthreads();
+    if (k0 + TBK < ke) load(k0 + TBK);  // next tile's gathers overlap this tile's products
 #pragma unroll
     for (int ks = 0; ks < TBK; ks += 16) {
       unsigned a[3][MT][4], b[3][NT2][2];
 #pragma unroll
-      for (int s = 0; s < 3; ++s) {
+      for (int sl = 0; sl < 3; ++sl) {
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt) {
-          const int r0 = wm * MT * 16 + mt * 16 + g;
+          const int r0 = sl * TBM + wm * MT * 16 + mt * 16 + g;
           const int c0 = ks + 2 * tg;
-          a[s][mt][0] = *reinterpret_cast<const unsigned *>(&As[s][r0][c0]);
-          a[s][mt][1] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0]);
-          a[s][mt][2] = *reinterpret_cast<const unsigned *>(&As[s][r0][c0 + 8]);
-          a[s][mt][3] = *reinterpret_cast<const unsigned *>(&As[s][r0 + 8][c0 + 8]);
+          a[sl][mt][0] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0]);
+          a[sl][mt][1] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0]);
+          a[sl][mt][2] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0 + 8]);
+          a[sl][mt][3] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0 + 8]);
         }
 #pragma unroll
         for (int nt = 0; nt < NT2; ++nt) {
-          const int n = wn * NT2 * 8 + nt * 8 + g;
-          b[s][nt][0] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg]);
-          b[s][nt][1] = *reinterpret_cast<const unsigned *>(&Bs[s][n][ks + 2 * tg + 8]);
+          const int n = sl * TBN + wn * NT2 * 8 + nt * 8 + g;
+          b[sl][nt][0] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg]);
+          b[sl][nt][1] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg + 8]);
         }
       }
 #pragma unroll
@@ -271,6 +302,27 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
         else
           C[crow_s[rl] + ccol_s[cl]] += alpha * (double)acc[mt][nt][e];
       }
+}
+
+// dynamic shared memory above the 48 KiB default, opted in once per device
+template <int WM, int WN, int MT, int NT2>
+void launch_bf16(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha, const double *A,
+                 const double *B, double *C, double *part) {
+  constexpr size_t smem = Bf16Tile<WM, WN, MT, NT2>::kSmem;
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  FNOCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw std::runtime_error("grouped_gemm: device index out of range");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+      FNOCC_CUDA(cudaFuncSetAttribute(k_ggemm_bf16x3<WM, WN, MT, NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+      done[dev] = true;
+    }
+  }
+  k_ggemm_bf16x3<WM, WN, MT, NT2><<<grid, NT, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
 }
 
 // C[crow(m) + ccol(n)] += alpha * sum_z part[task][z][m, n], z in order, for
@@ -358,7 +410,7 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_G(9, 4, 1, 2)
 #define FNOCC_B(i, wm, wn, mt, nt) \
   case kGShapeBf16 + i:           \
-    k_ggemm_bf16x3<wm, wn, mt, nt><<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part); break;
+    launch_bf16<wm, wn, mt, nt>(grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part); break;
     FNOCC_B(0, 2, 4, 2, 2)
     FNOCC_B(1, 2, 4, 1, 1)
     FNOCC_B(2, 8, 1, 1, 2)
