@@ -58,9 +58,14 @@ typedef enum {
 } fnocc_status;
 
 typedef enum { FNOCC_IP = 0, FNOCC_EA = 1, FNOCC_DIP = 2, FNOCC_DEA = 3 } fnocc_variant;
-/* KOOPMANS: unit vectors on the lowest diagonal entries of the principal
- * block; DIAGONAL: of the whole space; LEARNED: chosen and preconditioned by
- * the context's guess network (fnocc_set_guess_model), DIAGONAL as fallback */
+/* KOOPMANS (recommended): unit vectors on the lowest diagonal entries of the
+ * principal block; DIAGONAL: of the whole space (its non-principal unit
+ * vectors also carry spin multiplicities the principal block cannot form);
+ * LEARNED: principal unit vectors chosen by the context's guess network
+ * (fnocc_set_guess_model), which also corrects the preconditioner; KOOPMANS
+ * as fallback. Where the chosen block holds fewer elements than guesses are
+ * needed, products of the basis (Krylov vectors) fill up, then the
+ * lowest-diagonal remaining elements. */
 typedef enum { FNOCC_GUESS_KOOPMANS = 0, FNOCC_GUESS_DIAGONAL = 1, FNOCC_GUESS_LEARNED = 2 } fnocc_guess;
 typedef enum { FNOCC_CRIT_ABS = 0, FNOCC_CRIT_OCCT = 1 } fnocc_criterion;
 /* Arithmetic of the contractions (the single- and double-precision
@@ -318,8 +323,9 @@ fnocc_status fnocc_mlp_train(fnocc_mlp *mlp, const float *x, const float *t, con
 
 /* Features [dim x 8] of every element of the variant's packed operator space
  * (components concatenated as in eom_sigma): orbital-energy difference D,
- * two-body shift of the element's determinant (sum of <pq||pq> over hole
- * pairs and particle pairs minus over hole-particle pairs), highest hole and
+ * spin-averaged two-body shift of the element's determinant (sum over hole
+ * pairs and particle pairs minus over hole-particle pairs of J_PP for one
+ * spatial orbital, J_PQ - K_PQ / 2 otherwise), highest hole and
  * lowest particle energy, mean particle energy, sum over particles of log10
  * of the virtual's natural occupation (0 without FNO), component index,
  * variant. Orbital energies are the diagonal of the active-space Fock

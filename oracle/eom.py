@@ -129,8 +129,8 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
     max_sub = max(max_sub, max(nguess, 2 * nroots) + nroots)
     pref = allowed if guess_mask is None else np.where(mask & guess_mask)[0]
     rest = np.setdiff1d(allowed, pref)
-    order = np.concatenate([pref[np.argsort(diag[pref], kind="stable")],
-                            rest[np.argsort(diag[rest], kind="stable")]])[:nguess]
+    order = pref[np.argsort(diag[pref], kind="stable")][:nguess]
+    rest = rest[np.argsort(diag[rest], kind="stable")]
     basis, sig = [], []
 
     def add(vec, svec=None):
@@ -149,10 +149,23 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
         basis.append(vec / nrm)
         sig.append(svec / nrm if svec is not None else apply(vec / nrm) * mask)
 
-    for k in order:
+    def unit(k):
         e = np.zeros(n)
         e[k] = 1.0
-        add(e)
+        return e
+
+    for k in order:
+        add(unit(k))
+    # fewer guess elements than nguess: Krylov vectors (products of the
+    # basis), then the lowest-diagonal remaining elements
+    src = 0
+    while len(basis) < nguess and src < len(basis):
+        add(sig[src])
+        src += 1
+    for k in rest:
+        if len(basis) >= nguess:
+            break
+        add(unit(k))
     theta_old = None
     for it in range(1, maxiter + 1):
         vmat = np.array(basis)
@@ -210,12 +223,13 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
 
 
 def eom_ccsdt(variant, f, g, o, v, t1, t2, t3, nroots, tol_res=1e-8, tol_e=1e-10,
-              max_sub=None, maxiter=200, nguess=None, guess="diagonal"):
+              max_sub=None, maxiter=200, nguess=None, guess="koopmans"):
     """Lowest nroots EOM-CCSDT excitation energies omega in the target sector.
 
     guess 'koopmans': unit vectors on the lowest diagonal elements of the
     first component (1h, 1p, 2h or 2p); 'diagonal': on the lowest diagonal
-    elements of the whole operator space."""
+    elements of the whole operator space. Fewer elements than guesses: Krylov
+    vectors, then the lowest-diagonal remaining elements (see davidson)."""
     mask = ms_mask(variant, o, v)
     diag = diagonal(variant, f, o, v)
     first = sizes(variant, o, v)[0]

@@ -87,11 +87,13 @@ def adam_step(params, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 def eom_features(spaces, variant_id, fdiag, g, o, v, virt_occ=None):
     """Features of every packed element, components in order, tuples in
     lexicographic order (holes, then particles): orbital-energy difference D;
-    two-body (Epstein-Nesbet) shift of the element's determinant, the sum of
-    <pq||pq> over hole pairs and particle pairs minus over hole-particle
-    pairs; highest hole and lowest particle energy; mean particle energy; sum
-    of log10 natural occupations of the particles' virtuals (0 without them);
-    component index; variant. g: antisymmetrised <pq||rs>, occupied first."""
+    spin-averaged two-body (Epstein-Nesbet) shift of the element's
+    determinant: over hole pairs and particle pairs +w, over hole-particle
+    pairs -w, w = <pq||pq> averaged over the spin of q (J_PP within one
+    spatial orbital, J_PQ - K_PQ/2 otherwise); highest hole and lowest
+    particle energy; mean particle energy; sum of log10 natural occupations
+    of the particles' virtuals (0 without them); component index; variant.
+    g: antisymmetrised <pq||rs> (alpha even), occupied first."""
     rows = []
     for comp, (nh, np_) in enumerate(spaces):
         for hs in itertools.combinations(range(o), nh):
@@ -102,8 +104,12 @@ def eom_features(spaces, variant_id, fdiag, g, o, v, virt_occ=None):
                 en = 0.0
                 for x in range(len(orbs)):
                     for y in range(x + 1, len(orbs)):
+                        p, q = orbs[x], orbs[y]
+                        w = g[p, q, p, q]
+                        if p // 2 != q // 2:
+                            w = 0.5 * (w + g[p, q ^ 1, p, q ^ 1])
                         same = (x < nh) == (y < nh)
-                        en += (1 if same else -1) * g[orbs[x], orbs[y], orbs[x], orbs[y]]
+                        en += (1 if same else -1) * w
                 occ = 0.0
                 if virt_occ is not None:
                     occ = sum(np.log10(max(virt_occ[a // 2], 1e-12)) for a in ps)

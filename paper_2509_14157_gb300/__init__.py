@@ -434,7 +434,7 @@ class Context:
     def eom_sigma_dev(self, variant, r_ptr, s_ptr):
         self._check(self.lib.eom_sigma_dev(self._h, VARIANTS.get(variant, variant), r_ptr, s_ptr))
 
-    def eom_solve(self, variant, nroots, guess="diagonal", tol_res=1e-8, tol_e=1e-10, max_sub=0,
+    def eom_solve(self, variant, nroots, guess="koopmans", tol_res=1e-8, tol_e=1e-10, max_sub=0,
                   maxiter=200, nguess=0, precision="fp64", switch_tol=1e-5):
         var = VARIANTS.get(variant, variant)
         self._last_sizes = self.eom_sizes(var)

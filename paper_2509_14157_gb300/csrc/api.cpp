@@ -1354,15 +1354,15 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
         if (!inpref[i]) rest.push_back(i);
       std::stable_sort(rest.begin(), rest.end(), by_diag);
     }
+    // unit guesses: KOOPMANS and LEARNED on the principal block only (its
+    // determinants reach only the spin multiplicities whose states are
+    // counted as roots), DIAGONAL on the whole space
     std::vector<long long> order(pref);
-    order.insert(order.end(), rest.begin(), rest.end());
-    if (guess == FNOCC_GUESS_LEARNED) {  // highest predicted importance first
-      order = allowed;
-      std::partial_sort(order.begin(), order.begin() + ng, order.end(), [&](long long a, long long b) {
+    if (guess == FNOCC_GUESS_LEARNED)  // highest predicted importance first
+      std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) {
         return score[a] > score[b] || (score[a] == score[b] && a < b);
       });
-    }
-    order.resize(ng);
+    if ((long long)order.size() > ng) order.resize(ng);
     // subspace storage
     const int cap = max_sub + nr + 1;
     DevBuf Vb, Sb, xr, rr, tmp;
@@ -1434,13 +1434,19 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       kb = k1;
       return true;
     };
-    for (long long idx : order) {
+    auto add_unit = [&](long long idx) {
       FNOCC_CUDA(cudaMemsetAsync(tmp.p, 0, sizeof(double) * dim, c->stream));
       double one = 1.0;
       FNOCC_CUDA(cudaMemcpyAsync(tmp.d() + idx, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
       sync(c);
-      add_vector(tmp.d());
-    }
+      return add_vector(tmp.d());
+    };
+    for (long long idx : order) add_unit(idx);
+    // fewer unit guesses than ng: Krylov vectors (products of the basis stay
+    // in the multiplicities reached so far), then the lowest-diagonal
+    // remaining elements
+    for (int src = 0; kb < ng && src < kb; ++src) add_vector(srow(src));
+    for (size_t q = 0; kb < ng && q < rest.size(); ++q) add_unit(rest[q]);
     std::vector<double> theta(nr, 0.0), theta_old(nr, 0.0), norms(nr, 0.0);
     bool have_old = false, conv = false;
     int it, ncomplex = 0;
@@ -1595,10 +1601,10 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
                              double *energies, double *omegas, eom_info *out) {
   fnocc_status st = eom_solve_once(c, variant, nroots, guess, opt, energies, omegas, out);
   if (guess == FNOCC_GUESS_LEARNED && st == FNOCC_NOT_CONVERGED) {
-    // plain Davidson from the diagonal guess judges: roots never depend on the network
+    // plain Davidson from the Koopmans guess judges: roots never depend on the network
     eom_info first{};
     if (out) first = *out;
-    st = eom_solve_once(c, variant, nroots, FNOCC_GUESS_DIAGONAL, opt, energies, omegas, out);
+    st = eom_solve_once(c, variant, nroots, FNOCC_GUESS_KOOPMANS, opt, energies, omegas, out);
     if (out) {
       out->sigma_calls += first.sigma_calls;
       out->sigma_calls_mixed += first.sigma_calls_mixed;
@@ -1753,7 +1759,7 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
           for (int k = 0; k < nvariants; ++k) {
             eom_info ei{};
             std::vector<double> en(nroots);
-            fnocc_status es = eom_ccsdt_solve(c, variants[k], nroots, FNOCC_GUESS_DIAGONAL, eom_opt, en.data(),
+            fnocc_status es = eom_ccsdt_solve(c, variants[k], nroots, FNOCC_GUESS_KOOPMANS, eom_opt, en.data(),
                                               omegas + ((size_t)s * nvariants + k) * nroots, &ei);
             sig += ei.sigma_calls;
             if (es < 0 || (es != FNOCC_OK && worst >= 0)) worst = es;

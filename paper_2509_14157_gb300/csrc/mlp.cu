@@ -264,13 +264,17 @@ uint64_t splitmix64(uint64_t &x) {
   return z ^ (z >> 31);
 }
 
-// x0 orbital-energy difference D = sum_p f_pp - sum_h f_hh; x1 two-body
-// shift of the element's determinant (Epstein-Nesbet): sum over hole pairs
-// <hh'||hh'> + over particle pairs <pp'||pp'> - over hole-particle pairs
-// <hp||hp>; x2 highest hole energy; x3 lowest particle energy; x4 mean
-// particle energy; x5 sum over particles of log10 of their virtual's natural
-// occupation; x6 component (0, 1, 2); x7 variant (0..3). g: antisymmetrised
-// <pq||rs> of the n active spin orbitals, occupied first.
+// x0 orbital-energy difference D = sum_p f_pp - sum_h f_hh; x1 spin-averaged
+// two-body shift of the element's determinant (Epstein-Nesbet): over hole
+// pairs and particle pairs +w_pq, over hole-particle pairs -w_pq, with w_pq =
+// J_PP for two spin orbitals of one spatial orbital P and J_PQ - K_PQ / 2
+// otherwise (the pair's <pq||pq> averaged over the spin of q); x2 highest
+// hole energy; x3 lowest particle energy; x4 mean particle energy; x5 sum over
+// particles of log10 of their virtual's natural occupation; x6 component
+// (0, 1, 2); x7 variant (0..3). Every feature depends on spatial orbitals
+// only, so a preconditioner built from them treats all spin couplings of a
+// spatial configuration alike. g: antisymmetrised <pq||rs> of the n active
+// spin orbitals (alpha even), occupied first.
 __global__ void k_eom_features(int nh, int np, int o, int n, const int *htab, long long nhtup, const int *ptab,
                                long long nptup, const double *fdiag, const double *g, const float *vocc_log,
                                int comp, int variant, float *out) {
@@ -296,7 +300,8 @@ __global__ void k_eom_features(int nh, int np, int o, int n, const int *htab, lo
   for (int a = 0; a < nh + np; ++a)
     for (int b = a + 1; b < nh + np; ++b) {
       const long long p = idx[a], q = idx[b];
-      const double gv = g[((p * nn + q) * nn + p) * nn + q];
+      double gv = g[((p * nn + q) * nn + p) * nn + q];
+      if ((p >> 1) != (q >> 1)) gv = 0.5 * (gv + g[((p * nn + (q ^ 1)) * nn + p) * nn + (q ^ 1)]);
       en += ((a < nh) == (b < nh)) ? gv : -gv;
     }
   float *x = out + r * kMlpFeatures;

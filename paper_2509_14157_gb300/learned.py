@@ -24,7 +24,7 @@ from . import Context, FnoccError, Mlp, VARIANTS
 def system_samples(ctx, variant, nroots):
     """(features, targets, weights) of one system whose ground state is
     solved in ctx; runs a plain Davidson solve and the exact diagonal."""
-    res = ctx.eom_solve(variant, nroots, guess="diagonal")
+    res = ctx.eom_solve(variant, nroots, guess="koopmans")
     if not res["converged"]:
         return None
     feats = ctx.eom_features(variant)

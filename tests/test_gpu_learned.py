@@ -118,7 +118,7 @@ def test_exact_diagonal_matches_oracle(pkg, variant):
 def test_trained_network_saves_products_and_keeps_roots(pkg):
     """Train on small seeded systems, solve a larger held-out one: the
     learned start reaches the same roots (plain Davidson criteria) with
-    fewer sigma products than the diagonal start."""
+    fewer sigma products than the Koopmans start."""
     from paper_2509_14157_gb300 import learned
     systems = learned.seeded_training_systems(count=12)
     X, T, W, _ = learned.training_set(systems, ["dip", "dea"], 3)
@@ -131,7 +131,7 @@ def test_trained_network_saves_products_and_keeps_roots(pkg):
     ctx.set_guess_model(net)
     plain = with_net = 0
     for var in ("dip", "dea"):
-        a = ctx.eom_solve(var, 4, guess="diagonal")
+        a = ctx.eom_solve(var, 4, guess="koopmans")
         b = ctx.eom_solve(var, 4, guess="learned")
         assert a["converged"] and b["converged"] and b["guess_used"] == 2
         assert np.max(np.abs(a["omegas"] - b["omegas"])) < 1e-9

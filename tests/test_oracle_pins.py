@@ -364,48 +364,57 @@ def test_adam_first_step_is_signed_learning_rate():
 
 
 def test_eom_features_definition():
-    # 2 occupied / 4 virtual spin orbitals, IP spaces (1h, 2h1p, 3h2p), one
-    # two-electron integral <0 3||0 3> = 0.25 (hole 0, particle 1)
+    # 2 occupied / 4 virtual spin orbitals (alpha even), IP spaces (1h, 2h1p,
+    # 3h2p); integrals <0 3||0 3> = 0.25 (alpha hole 0, beta particle 1) and
+    # <0 2||0 2> = 0.1 (same spin, other spatial orbital pair entry)
     o, v = 2, 4
     fdiag = np.array([-1.0, -0.8, 0.5, 0.7, 1.1, 1.3])
     g = np.zeros((6,) * 4)
-    for p, q in [(0, 3), (3, 0)]:
-        g[p, q, p, q] = 0.25
-        g[p, q, q, p] = -0.25
+    for p, q, val in [(0, 3, 0.25), (0, 2, 0.1)]:
+        for a, b in [(p, q), (q, p)]:
+            g[a, b, a, b] = val
+            g[a, b, b, a] = -val
     occ = np.array([1e-2, 1e-4])
     feats = mlp.eom_features(wick.EOM_SPACES["ip"], 0, fdiag, g, o, v, occ)
     assert feats.shape == (2 + 1 * 4 + 0, 8)  # C(2,3) = 0: no 3h2p element
     assert np.allclose(feats[0], [1.0, 0.0, -1.0, 0.0, 0.0, 0.0, 0, 0])
     # holes 0,1 and particle 1 (orbital 3): the hole 0 - particle pair lowers
-    # the determinant's energy by <03||03>
-    assert np.allclose(feats[2 + 1], [0.7 + 1.8, -0.25, -0.8, 0.7, 0.7, -2.0, 1, 0])
+    # the energy by the spin average of <03||03> and <02||02>
+    assert np.allclose(feats[2 + 1], [0.7 + 1.8, -0.5 * (0.25 + 0.1), -0.8, 0.7, 0.7, -2.0, 1, 0])
+    # particle 0 (orbital 2, same spatial orbital as 3): the same average
+    assert np.allclose(feats[2 + 0], [0.5 + 1.8, -0.5 * (0.1 + 0.25), -0.8, 0.5, 0.5, -2.0, 1, 0])
     # holes 0,1 and particle 2 (orbital 4, virtual spatial 1): no integral
     assert np.allclose(feats[2 + 2], [1.1 + 1.8, 0.0, -0.8, 1.1, 1.1, -4.0, 1, 0])
 
 
-def test_en_shift_is_determinant_energy_difference():
-    """D plus the two-body shift is the energy of the element's determinant
-    relative to the reference (Slater rules), for every element of a small
-    DIP space."""
+def test_en_shift_from_spatial_coulomb_and_exchange():
+    """The spin-averaged two-body shift against J and K built directly from
+    the spatial chemists' integrals (an independent route): for every element
+    of a small DIP space, sum over pairs of +-(J_PP or J_PQ - K_PQ/2); and all
+    features are equal for an element and its spin-flipped partner."""
     h, eri = synth.random_symmetric_mo_hamiltonian(4, 17)
     ham = fno.mo_hamiltonian(h, eri, 2)
     o, v = ham["o"], ham["v"]
-    hso, g = ham["hso"], ham["g"]
-    feats = mlp.eom_features(wick.EOM_SPACES["dip"], 2, np.diag(ham["f"]), g, o, v)
-
-    def det_energy(occupied):
-        e = sum(hso[p, p] for p in occupied)
-        for x in range(len(occupied)):
-            for y in range(x + 1, len(occupied)):
-                e += g[occupied[x], occupied[y], occupied[x], occupied[y]]
-        return e
-
-    e0 = det_energy(list(range(o)))
+    feats = mlp.eom_features(wick.EOM_SPACES["dip"], 2, np.diag(ham["f"]), ham["g"], o, v)
+    jmat = np.einsum("ppqq->pq", eri)
+    kmat = np.einsum("pqqp->pq", eri)
+    rows = {}
     row = 0
-    for nh, np_ in wick.EOM_SPACES["dip"]:
+    for comp, (nh, np_) in enumerate(wick.EOM_SPACES["dip"]):
         for hs in itertools.combinations(range(o), nh):
             for ps in itertools.combinations(range(v), np_):
-                occupied = [p for p in range(o) if p not in hs] + [o + a for a in ps]
-                assert abs(feats[row, 0] + feats[row, 1] - (det_energy(occupied) - e0)) < 1e-12
+                orbs = list(hs) + [o + a for a in ps]
+                en = 0.0
+                for x in range(len(orbs)):
+                    for y in range(x + 1, len(orbs)):
+                        sp, sq = orbs[x] // 2, orbs[y] // 2
+                        w = jmat[sp, sp] if sp == sq else jmat[sp, sq] - 0.5 * kmat[sp, sq]
+                        en += w if (x < nh) == (y < nh) else -w
+                assert abs(feats[row, 1] - en) < 1e-12
+                rows[(comp, hs, ps)] = row
                 row += 1
     assert row == feats.shape[0]
+    for (comp, hs, ps), r in rows.items():
+        fh = tuple(sorted(i ^ 1 for i in hs))
+        fp = tuple(sorted(a ^ 1 for a in ps))
+        assert np.allclose(feats[r], feats[rows[(comp, fh, fp)]])
