@@ -326,7 +326,7 @@ void ensure_cc_plans(fnocc_ctx *c) {
 // residual of packed amplitudes tp (device) into rp (device); returns E_corr
 // dense antisymmetric [o^nh v^np] work tensor from packed elements
 void unpack(fnocc_ctx *c, const Launch &L, const double *packed, int nh, int np, double *dense) {
-  if (np >= 1)
+  if (np >= 1 && c->v <= 160)
     unpack_dense_rows(L, packed, nh, np, c->o, c->v, c->otab[nh].rank(), c->vtab[np].rank(), c->vtab[np].count,
                       dense);
   else

@@ -440,53 +440,78 @@ __device__ __forceinline__ void sort_small(int *t, int n, int &sgn, bool &dup) {
     }
 }
 
-// Dense antisymmetric tensor [o^nh v^np] from its packed unique elements, as
+// Dense antisymmetric tensor [o^NH v^NP] from its packed unique elements, as
 // a coalesced gather (every dense element written once, no prior clear):
-// block b owns the outer indices (holes and all but the last ni particles),
-// its threads stride over the inner ni particle indices, which are the
+// block b owns the outer indices (holes and all but the last NI particles),
+// its threads stride over the inner NI particle indices, which are the
 // fastest-varying part of the dense layout. dense = sign(sorting
 // permutation) * packed[rank], 0 on repeated indices. hr / pr: rank prefix
-// tables of the hole / particle tuple lists (TupleTable::rank).
-__global__ void __launch_bounds__(256) k_unpack_blocks(const double *__restrict__ packed, int nh, int np, int ni,
-                                                       int o, int v, const long long *__restrict__ hr,
+// tables of the hole / particle tuple lists (TupleTable::rank), staged in
+// shared memory (v <= 160).
+template <int NH, int NP>
+__global__ void __launch_bounds__(256) k_unpack_blocks(const double *__restrict__ packed, int o, int v,
+                                                       const long long *__restrict__ hr,
                                                        const long long *__restrict__ pr, long long nptup,
                                                        long long inner, double *__restrict__ dense) {
+  constexpr int NI = NP < 3 ? NP : 3, NO = NP - NI;
+  __shared__ long long prs[NP * 161];
+  for (int i = threadIdx.x; i < NP * (v + 1); i += blockDim.x) prs[i] = pr[i];
   const long long outer = blockIdx.x;
   long long rem = outer;
-  const int no = np - ni;  // outer particles
-  int po[4], hh[4];
-  for (int k = no - 1; k >= 0; --k) {
+  int po[NO > 0 ? NO : 1], hh[NH > 0 ? NH : 1];
+#pragma unroll
+  for (int k = NO - 1; k >= 0; --k) {
     po[k] = (int)(rem % v);
     rem /= v;
   }
-  for (int k = nh - 1; k >= 0; --k) {
+#pragma unroll
+  for (int k = NH - 1; k >= 0; --k) {
     hh[k] = (int)(rem % o);
     rem /= o;
   }
   int sgn0 = 1;
   bool dup0 = false;
-  sort_small(hh, nh, sgn0, dup0);
+  sort_small(hh, NH, sgn0, dup0);
   long long hrank = 0;
-  for (int i = 0; i < nh; ++i) hrank += hr[i * (o + 1) + hh[i]] - hr[i * (o + 1) + (i ? hh[i - 1] + 1 : 0)];
+#pragma unroll
+  for (int i = 0; i < NH; ++i) hrank += hr[i * (o + 1) + hh[i]] - hr[i * (o + 1) + (i ? hh[i - 1] + 1 : 0)];
+  __syncthreads();
+  if (dup0) {
+    for (long long j = threadIdx.x; j < inner; j += blockDim.x) dense[outer * inner + j] = 0.0;
+    return;
+  }
+  const double *pk = packed + hrank * nptup;
   double *dst = dense + outer * inner;
+  const unsigned uv = (unsigned)v;
   for (long long j = threadIdx.x; j < inner; j += blockDim.x) {
+    int q[NP];
+#pragma unroll
+    for (int k = 0; k < NO; ++k) q[k] = po[k];
+    unsigned r = (unsigned)j;
+#pragma unroll
+    for (int k = NP - 1; k >= NO; --k) {
+      q[k] = (int)(r % uv);
+      r /= uv;
+    }
+    int sgn = sgn0;
+    bool dup = false;
+#pragma unroll
+    for (int i = 1; i < NP; ++i)
+#pragma unroll
+      for (int k = i; k > 0; --k)
+        if (q[k - 1] >= q[k]) {
+          if (q[k - 1] == q[k]) dup = true;
+          const int x = q[k - 1];
+          q[k - 1] = q[k];
+          q[k] = x;
+          sgn = -sgn;
+        }
     double val = 0.0;
-    if (!dup0) {
-      int q[4];
-      for (int k = 0; k < no; ++k) q[k] = po[k];
-      unsigned r = (unsigned)j;
-      for (int k = np - 1; k >= no; --k) {
-        q[k] = (int)(r % (unsigned)v);
-        r /= (unsigned)v;
-      }
-      int sgn = sgn0;
-      bool dup = false;
-      sort_small(q, np, sgn, dup);
-      if (!dup) {
-        long long prank = 0;
-        for (int i = 0; i < np; ++i) prank += pr[i * (v + 1) + q[i]] - pr[i * (v + 1) + (i ? q[i - 1] + 1 : 0)];
-        val = sgn * __ldg(packed + hrank * nptup + prank);
-      }
+    if (!dup) {
+      long long prank = 0;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) prank += prs[i * (v + 1) + q[i]] - prs[i * (v + 1) + (i ? q[i - 1] + 1 : 0)];
+      val = sgn * __ldg(pk + prank);
     }
     dst[j] = val;
   }
@@ -1059,7 +1084,7 @@ void antisym_pack(const Launch &L, const double *Y, int nh, int np, int o, int v
 
 void unpack_dense_rows(const Launch &L, const double *packed, int nh, int np, int o, int v, const long long *hrank,
                        const long long *prank, long long nptup, double *dense) {
-  if (np < 1 || nh > 4 || np > 4) throw std::runtime_error("unpack_dense_rows: unsupported tuple sizes");
+  if (np < 1 || nh > 4 || np > 4 || v > 160) throw std::runtime_error("unpack_dense_rows: unsupported sizes");
   const int ni = std::min(np, 3);  // inner particles: at most v^3 elements per block
   long long outer = 1, inner = 1;
   for (int k = 0; k < nh; ++k) outer *= o;
@@ -1067,8 +1092,17 @@ void unpack_dense_rows(const Launch &L, const double *packed, int nh, int np, in
   for (int k = 0; k < ni; ++k) inner *= v;
   if (outer <= 0 || inner <= 0) return;
   if (outer > 0x7fffffffLL || inner > 0xffffffffLL) throw std::runtime_error("unpack_dense_rows: too large");
-  k_unpack_blocks<<<(unsigned)outer, 256, 0, L.stream>>>(packed, nh, np, ni, o, v, hrank, prank, nptup, inner, dense);
-  post(L);
+  const unsigned grid = (unsigned)outer;
+#define FNOCC_U(a, b)                                                                                      \
+  if (nh == a && np == b) {                                                                                \
+    k_unpack_blocks<a, b><<<grid, 256, 0, L.stream>>>(packed, o, v, hrank, prank, nptup, inner, dense); \
+    post(L);                                                                                               \
+    return;                                                                                                \
+  }
+  FNOCC_U(0, 1) FNOCC_U(0, 2) FNOCC_U(1, 1) FNOCC_U(1, 2) FNOCC_U(1, 3) FNOCC_U(2, 1) FNOCC_U(2, 2)
+  FNOCC_U(2, 3) FNOCC_U(2, 4) FNOCC_U(3, 1) FNOCC_U(3, 2) FNOCC_U(3, 3) FNOCC_U(4, 1) FNOCC_U(4, 2)
+#undef FNOCC_U
+  throw std::runtime_error("unpack_dense_rows: no kernel for this component");
 }
 
 void unpack_dense(const Launch &L, const double *packed, int nh, int np, int o, int v, const int *htab,
