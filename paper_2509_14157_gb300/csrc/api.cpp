@@ -130,11 +130,11 @@ struct fnocc_ctx {
   std::string err;
   uint64_t launches = 0;
   GemmProfile prof;
-  DevBuf partials, panels;  // split-K partial sums; packed BF16 operand panels
+  DevBuf partials;
   double flops_total = 0;
   int precision = 0;          // fnocc_precision of the contractions currently issued
   int default_precision = 0;  // for standalone residual / sigma calls
-  Launch L() { return Launch{stream, &launches, &prof, &partials, precision, &panels}; }
+  Launch L() { return Launch{stream, &launches, &prof, &partials, precision}; }
 
   // active Hamiltonian (spin orbitals, bare)
   bool have_ham = false;

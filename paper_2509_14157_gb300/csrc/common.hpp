@@ -84,7 +84,6 @@ struct Launch {
   GemmProfile *prof = nullptr;
   DevBuf *partials = nullptr;  // split-K partial sums (deterministic reduction)
   int precision = 0;           // 0 FP64; 1 BF16 three-slice split on tensor cores (tiled path)
-  DevBuf *panels = nullptr;    // packed BF16 operand panels of the tensor-core path
 };
 
 // One sub-GEMM of a grouped launch: C[crow[m] + ccol[n]] += alpha *
@@ -101,11 +100,6 @@ struct GTask {
   long long cta_begin = 0;           // first CTA of this task in the grid
   long long part_off = 0;            // doubles, [ksplit][M][N]
   long long red_begin = 0;           // first output of this task in the reduction launch
-  // tensor-core shapes with packed panels: the task's operands converted once
-  // to BF16 slices, A as [3][mp][kp] at apan, B as [3][np][kp] at bpan (BF16
-  // elements of the panel arena); ape / bpe: first element of the task in
-  // the packing launches
-  long long mp = 0, np = 0, kp = 0, apan = 0, bpan = 0, ape = 0, bpe = 0;
 };
 
 // A grouped launch: tasks ordered by cta_begin (device array) plus the list
@@ -124,8 +118,6 @@ struct GroupedLaunch {
   int shape = 0;
   double flops = 0;      // algorithmic flops of the launch (profiling)
   double padded = 0;     // multiply-adds including tile padding x 2
-  bool packed = false;   // tensor-core shape run on packed BF16 panels
-  long long npa = 0, npb = 0;  // packed A / B elements per slice (sum of mp*kp, np*kp)
 };
 // rows, columns and K tile of a shape (FP64 and BF16x3 shapes)
 void grouped_shape(int shape, int *tbm, int *tbn, int *tbk);

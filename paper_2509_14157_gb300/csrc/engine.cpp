@@ -631,7 +631,7 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
         gl.shape = shape;
         gl.ntasks = (int)e.tasks.size();
         fix.push_back({&gl, gt.size(), sid.size()});
-        long long cta = 0, part = 0, red = 0, npa = 0, npb = 0;
+        long long cta = 0, part = 0, red = 0;
         double padded = 0, flops = 0;
         for (size_t i = 0; i < e.tasks.size(); ++i) {
           const auto &tr = e.tasks[i];
@@ -667,34 +667,11 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
             red += tr.M * tr.N;
             sid.push_back((int)i);
           }
-          if (shape >= kGShapeBf16) {  // packed-panel layout of the task
-            g.mp = tm * tbm;
-            g.np = g.tiles_n * tbn;
-            g.kp = (tr.K + tbk - 1) / tbk * tbk;
-            g.ape = npa;
-            g.bpe = npb;
-            npa += g.mp * g.kp;
-            npb += g.np * g.kp;
-          }
           padded += 2.0 * double(tm * tbm) * double(g.tiles_n * tbn) * double((tr.K + tbk - 1) / tbk * tbk);
           flops += 2.0 * double(tr.M) * double(tr.N) * double(tr.K);
           gt.push_back(g);
         }
         if (cta > 0x7fffffffLL) throw std::runtime_error("engine: grouped grid too large");
-        if (shape >= kGShapeBf16) {
-          // arena: all A panels ([3][mp][kp] each), then all B panels
-          for (size_t i = gt.size() - e.tasks.size(); i < gt.size(); ++i) {
-            gt[i].apan = 3 * gt[i].ape;
-            gt[i].bpan = 3 * npa + 3 * gt[i].bpe;
-          }
-          gl.npa = npa;
-          gl.npb = npb;
-          // panels pay off once an operand element serves several tiles;
-          // the arena stays below 1 GiB
-          long long tiles = 0;
-          for (size_t i = gt.size() - e.tasks.size(); i < gt.size(); ++i) tiles += gt[i].tiles;
-          gl.packed = tiles >= 4 && 2.0 * 3.0 * double(npa + npb) <= double(1LL << 30);
-        }
         gl.ncta = cta;
         gl.nsplit = (int)(sid.size() - fix.back().s0);
         gl.nred = red;

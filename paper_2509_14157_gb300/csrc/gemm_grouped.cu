@@ -325,195 +325,6 @@ void launch_bf16(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, 
   k_ggemm_bf16x3<WM, WN, MT, NT2><<<grid, NT, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
 }
 
-// ---- packed-panel form of the tensor-core path ----------------------------
-// Each task's operands are gathered, truncated and split into BF16 slices
-// once (A as [3][mp][kp], B as [3][np][kp], zero-padded to whole tiles), so
-// that the tile kernel streams contiguous panels (16-byte cp.async) instead of
-// re-gathering and re-splitting an operand element for every tile row or
-// column that uses it.
-
-__device__ __forceinline__ int find_task_by(const GTask *tasks, int ntasks, long long e, bool b_side) {
-  int lo = 0, hi = ntasks - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if ((b_side ? tasks[mid].bpe : tasks[mid].ape) <= e)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-__global__ void k_pack_a(const GTask *__restrict__ tasks, int ntasks, long long npa, const double *__restrict__ A,
-                         __nv_bfloat16 *__restrict__ pan) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= npa) return;
-  const GTask &t = tasks[find_task_by(tasks, ntasks, e, false)];
-  const long long local = e - t.ape, m = local / t.kp, k = local - m * t.kp;
-  const double x = (m < t.M && k < t.K) ? __ldg(A + t.arow[m] + t.acol[k]) : 0.0;
-  const long long plane = t.mp * t.kp, off = t.apan + m * t.kp + k;
-  split3(f64_to_f32_trunc(x), pan[off], pan[off + plane], pan[off + 2 * plane]);
-}
-
-__global__ void k_pack_b(const GTask *__restrict__ tasks, int ntasks, long long npb, const double *__restrict__ B,
-                         __nv_bfloat16 *__restrict__ pan) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= npb) return;
-  const GTask &t = tasks[find_task_by(tasks, ntasks, e, true)];
-  const long long local = e - t.bpe, n = local / t.kp, k = local - n * t.kp;
-  const double x = (n < t.N && k < t.K) ? __ldg(B + t.brow[k] + t.bcol[n]) : 0.0;
-  const long long plane = t.np * t.kp, off = t.bpan + n * t.kp + k;
-  split3(f64_to_f32_trunc(x), pan[off], pan[off + plane], pan[off + 2 * plane]);
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-// tile kernel on packed panels: same tiles, warps and products as
-// k_ggemm_bf16x3; each K tile of 32 is 4 x 16-byte chunks per panel row and
-// slice, copied asynchronously into one of two shared-memory buffers while
-// the other is in use
-template <int WM, int WN, int MT, int NT2>
-__global__ void __launch_bounds__(NT) k_ggemm_bf16p(const GTask *__restrict__ tasks, int ntasks, double alpha,
-                                                    const __nv_bfloat16 *__restrict__ pan, double *__restrict__ C,
-                                                    double *__restrict__ part) {
-  using T = Bf16Tile<WM, WN, MT, NT2>;
-  constexpr int TBM = T::TBM, TBN = T::TBN, TBK = T::TBK, LDS = T::LDS;
-  constexpr int CA = 3 * TBM * 4, CB = 3 * TBN * 4;  // 16-byte chunks per K tile
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-  __nv_bfloat16 *Bs = As + 2 * 3 * TBM * LDS;
-  __shared__ long long crow_s[TBM], ccol_s[TBN];
-  __shared__ GTask t;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int wm = warp / WN, wn = warp % WN;
-  const int g = lane >> 2, tg = lane & 3;
-  const long long cta = blockIdx.x;
-  if (tid == 0) t = tasks[find_task(tasks, ntasks, cta)];
-  __syncthreads();
-  const long long local = cta - t.cta_begin;
-  const long long z = local / t.tiles, tile = local - z * t.tiles;
-  const long long m0 = (tile / t.tiles_n) * TBM, n0 = (tile % t.tiles_n) * TBN;
-  const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
-  const bool split = t.ksplit > 1;
-  for (int i = tid; i < TBM; i += NT) crow_s[i] = (!split && m0 + i < t.M) ? t.crow[m0 + i] : 0;
-  for (int i = tid; i < TBN; i += NT) ccol_s[i] = (!split && n0 + i < t.N) ? t.ccol[n0 + i] : 0;
-  const __nv_bfloat16 *pa = pan + t.apan, *pb = pan + t.bpan;
-  const long long plane_a = t.mp * t.kp, plane_b = t.np * t.kp;
-  auto issue = [&](long long k0, int buf) {
-    __nv_bfloat16 *as = As + buf * 3 * TBM * LDS, *bs = Bs + buf * 3 * TBN * LDS;
-    for (int c = tid; c < CA; c += NT) {
-      const int sl = c / (TBM * 4), rem = c - sl * TBM * 4, row = rem >> 2, ch = rem & 3;
-      cp_async16(as + (sl * TBM + row) * LDS + ch * 8, pa + sl * plane_a + (m0 + row) * t.kp + k0 + ch * 8);
-    }
-    for (int c = tid; c < CB; c += NT) {
-      const int sl = c / (TBN * 4), rem = c - sl * TBN * 4, col = rem >> 2, ch = rem & 3;
-      cp_async16(bs + (sl * TBN + col) * LDS + ch * 8, pb + sl * plane_b + (n0 + col) * t.kp + k0 + ch * 8);
-    }
-    cp_async_commit();
-  };
-  float acc[MT][NT2][4];
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < NT2; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  if (kb < ke) issue(kb, 0);
-  int buf = 0;
-  for (long long k0 = kb; k0 < ke; k0 += TBK, buf ^= 1) {
-    if (k0 + TBK < ke) {
-      issue(k0 + TBK, buf ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const __nv_bfloat16 *as = As + buf * 3 * TBM * LDS, *bs = Bs + buf * 3 * TBN * LDS;
-#pragma unroll
-    for (int ks = 0; ks < TBK; ks += 16) {
-      unsigned a[3][MT][4], b[3][NT2][2];
-#pragma unroll
-      for (int sl = 0; sl < 3; ++sl) {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-          const int r0 = sl * TBM + wm * MT * 16 + mt * 16 + g;
-          const int c0 = ks + 2 * tg;
-          a[sl][mt][0] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0]);
-          a[sl][mt][1] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0]);
-          a[sl][mt][2] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0 + 8]);
-          a[sl][mt][3] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0 + 8]);
-        }
-#pragma unroll
-        for (int nt = 0; nt < NT2; ++nt) {
-          const int n = sl * TBN + wn * NT2 * 8 + nt * 8 + g;
-          b[sl][nt][0] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg]);
-          b[sl][nt][1] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg + 8]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3 - i; ++j)
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT2; ++nt)
-              asm volatile(
-                  "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                  "{%0,%1,%2,%3};\n"
-                  : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
-                  : "r"(a[i][mt][0]), "r"(a[i][mt][1]), "r"(a[i][mt][2]), "r"(a[i][mt][3]), "r"(b[j][nt][0]),
-                    "r"(b[j][nt][1]));
-    }
-    __syncthreads();  // the buffer is refilled two tiles later
-  }
-  const long long MN = t.M * t.N;
-#pragma unroll
-  for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < NT2; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int rl = wm * MT * 16 + mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int cl = wn * NT2 * 8 + nt * 8 + 2 * tg + (e & 1);
-        const long long m = m0 + rl, n = n0 + cl;
-        if (m >= t.M || n >= t.N) continue;
-        if (split)
-          part[t.part_off + z * MN + m * t.N + n] = (double)acc[mt][nt][e];
-        else
-          C[crow_s[rl] + ccol_s[cl]] += alpha * (double)acc[mt][nt][e];
-      }
-}
-
-template <int WM, int WN, int MT, int NT2>
-void launch_bf16p(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
-                  const __nv_bfloat16 *pan, double *C, double *part) {
-  constexpr size_t smem = Bf16Tile<WM, WN, MT, NT2>::kSmem;
-  static std::mutex mu;
-  static bool done[64] = {};
-  int dev = 0;
-  FNOCC_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) throw std::runtime_error("grouped_gemm: device index out of range");
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!done[dev]) {
-      FNOCC_CUDA(cudaFuncSetAttribute(k_ggemm_bf16p<WM, WN, MT, NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-      done[dev] = true;
-    }
-  }
-  k_ggemm_bf16p<WM, WN, MT, NT2><<<grid, NT, smem, s>>>(tasks, ntasks, alpha, pan, C, part);
-}
-
 // C[crow(m) + ccol(n)] += alpha * sum_z part[task][z][m, n], z in order, for
 // the tasks whose reduction was split
 __global__ void k_greduce(const GTask *__restrict__ tasks, const int *__restrict__ split_ids, int nsplit,
@@ -584,31 +395,6 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0], L.stream));
   }
   const unsigned grid = (unsigned)g.ncta;
-  if (g.packed) {
-    // tensor-core path on packed panels: pack A and B once, then the tiles
-    if (!L.panels) throw std::runtime_error("grouped_gemm: no panel arena");
-    L.panels->reserve(sizeof(__nv_bfloat16) * 3 * (size_t)(g.npa + g.npb));
-    __nv_bfloat16 *pan = L.panels->as<__nv_bfloat16>();
-    k_pack_a<<<blocks_for(g.npa, 256), 256, 0, L.stream>>>(g.tasks, g.ntasks, g.npa, A, pan);
-    FNOCC_CUDA(cudaGetLastError());
-    k_pack_b<<<blocks_for(g.npb, 256), 256, 0, L.stream>>>(g.tasks, g.ntasks, g.npb, B, pan);
-    FNOCC_CUDA(cudaGetLastError());
-    if (L.counter) *L.counter += 2;
-    switch (g.shape) {
-#define FNOCC_P(i, wm, wn, mt, nt) \
-  case kGShapeBf16 + i:           \
-    launch_bf16p<wm, wn, mt, nt>(grid, L.stream, g.tasks, g.ntasks, alpha, pan, C, part); break;
-      FNOCC_P(0, 2, 4, 2, 2)
-      FNOCC_P(1, 2, 4, 1, 1)
-      FNOCC_P(2, 8, 1, 1, 2)
-      FNOCC_P(3, 1, 8, 1, 2)
-      FNOCC_P(4, 4, 2, 1, 1)
-      FNOCC_P(5, 1, 8, 1, 1)
-#undef FNOCC_P
-      default:
-        throw std::runtime_error("grouped_gemm: packed panels need a tensor-core shape");
-    }
-  } else {
 #define FNOCC_G(i, ty, tm, tn) \
   case i: k_ggemm<ty, tm, tn><<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part); break;
   switch (g.shape) {
@@ -634,7 +420,6 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
 #undef FNOCC_B
     default:
       throw std::runtime_error("grouped_gemm: bad shape");
-  }
   }
 #undef FNOCC_G
   FNOCC_CUDA(cudaGetLastError());
