@@ -350,7 +350,8 @@ __global__ void k_greduce(const GTask *__restrict__ tasks, const int *__restrict
 
 // (TY, TM, TN) of the FP64 shapes
 constexpr int kShapeDims[kGShapes][3] = {{16, 4, 4}, {16, 8, 2}, {16, 2, 8}, {16, 8, 1}, {16, 1, 8},
-                                         {16, 2, 2}, {16, 1, 1}, {64, 2, 1}, {256, 1, 1}, {4, 1, 2}};
+                                         {16, 2, 2}, {16, 1, 1}, {64, 2, 1}, {256, 1, 1}, {4, 1, 2},
+                                         {8, 1, 4},  {2, 1, 1},  {32, 1, 1}, {128, 1, 1}};
 // (WM, WN, MT, NT2) of the BF16x3 shapes: 64x64, 32x32, 128x16, 16x128, 64x16, 16x64
 constexpr int kBf16Dims[kGShapesBf16][4] = {{2, 4, 2, 2}, {2, 4, 1, 1}, {8, 1, 1, 2},
                                             {1, 8, 1, 2}, {4, 2, 1, 1}, {1, 8, 1, 1}};
@@ -408,6 +409,10 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_G(7, 64, 2, 1)
     FNOCC_G(8, 256, 1, 1)
     FNOCC_G(9, 4, 1, 2)
+    FNOCC_G(10, 8, 1, 4)
+    FNOCC_G(11, 2, 1, 1)
+    FNOCC_G(12, 32, 1, 1)
+    FNOCC_G(13, 128, 1, 1)
 #define FNOCC_B(i, wm, wn, mt, nt) \
   case kGShapeBf16 + i:           \
     launch_bf16<wm, wn, mt, nt>(grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part); break;
