@@ -52,9 +52,9 @@ def measured_bf16_peak():
 # Iteration counts and algorithmic flops per evaluation of one converged step
 # of this workload, as the library measured them on a GB300; the reference
 # arm uses them to turn its timed oracle sample into seconds per solve.
-REFERENCE_COUNTS = {"cc_iters": 21, "sigma": {"ip": 169, "ea": 136, "dip": 170, "dea": 109},
-                    "flops_per_residual": 9.11e9,
-                    "flops_per_sigma": {"ip": 7.0e8, "ea": 2.7e9, "dip": 2.9e9, "dea": 3.8e10}}
+REFERENCE_COUNTS = {"cc_iters": 21, "sigma": {"ip": 88, "ea": 89, "dip": 110, "dea": 74},
+                    "flops_per_residual": 1.297e9,
+                    "flops_per_sigma": {"ip": 1.94e8, "ea": 4.27e8, "dip": 4.77e8, "dea": 5.35e9}}
 
 
 def config(threshold, seed):
