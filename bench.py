@@ -172,6 +172,23 @@ def cpu_baseline(threshold, gpu_counts):
                        % (t_fno, t_res, cores, o, v, gpu_counts["cc_iters"], sig_equiv))}
 
 
+def replica_seed(rank):
+    """Independent replicas: every rank solves its own seeded system (no
+    collective on the data path)."""
+    return rank
+
+
+def max_over_ranks(seconds, world, device=None):
+    """Whole-job time of replicas: the slowest rank's (all-reduce MAX)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -310,7 +327,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    seed = rank  # independent replicas: every rank solves its own seeded system
+    seed = replica_seed(rank)
     h, eri = synth.hamiltonian(NE, NORB, seed=seed)
     nocc = NE // 2
     h_dev = torch.from_numpy(h).to(dev)
@@ -402,10 +419,8 @@ def main():
     ctx.profile(False)
     clocks = sampler.stop()
     total = sum(times)
+    total = max_over_ranks(total, world, dev)
     if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
         dist.barrier()
     # end to end: host buffers through the C ABI, copies and read-back inside
     e2e_times = []
@@ -416,10 +431,7 @@ def main():
         step(False)
         e2e_times.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, world, dev)
     accuracy = None
     if args.precision == "mixed":
         # every root against the same solve in FP64 (outside the timed region)
@@ -449,10 +461,7 @@ def main():
             e1.synchronize()
             ml_times.append(e0.elapsed_time(e1) / 1e3)
         ml_total = sum(ml_times)
-        if world > 1:
-            t = torch.tensor([ml_total], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ml_total = float(t.item())
+        ml_total = max_over_ranks(ml_total, world, dev)
         mixed_learned = {
             "value": ml_total / (len(VARIANTS) * args.steps * world), "unit": "s",
             "ms_per_step": 1e3 * ml_total / args.steps,
