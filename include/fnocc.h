@@ -364,6 +364,16 @@ long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char 
  * (packed or not), operands, intermediates and coefficients, planned with
  * the cost model at sizes (o, v); amortize > 0 marks R-independent steps as
  * cached. Same return convention as fnocc_equation_text. */
+/* Host-only consistency check of the executable plan of the same equation
+ * at sizes (o, v) (not in the paper; a test of the library's own
+ * bookkeeping): for every grouped contraction step with at most max_work
+ * multiply-adds and every tile shape, the (A, B, C) element offsets its
+ * tasks address (flat tables) must equal, as a multiset, those of the
+ * spin-allowed blocks decoded through the per-group offset tables, and the
+ * tasks' CTA ranges must tile the grid. Returns the number of
+ * inconsistencies (0 = consistent) or -1 on bad arguments. No GPU needed. */
+long fnocc_plan_selfcheck(int kind, int variant, int out_comp, int in_comp, int o, int v, double max_work);
+
 long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, int v, double amortize,
                      char *buf, size_t len);
 

@@ -114,6 +114,8 @@ SIGNATURES = {
     "fnocc_plan_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
     "fnocc_profile": (ctypes.c_int, [_cp, ctypes.c_int]),
+    "fnocc_plan_selfcheck": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double]),
     "fnocc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_cp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_ulonglong]),
     "fnocc_mlp_destroy": (None, [_cp]),
@@ -208,6 +210,13 @@ def equation_text(kind, variant=0, out_comp=0, in_comp=0):
     buf = ctypes.create_string_buffer(n + 1)
     lib.fnocc_equation_text(kind, var, out_comp, in_comp, buf, n + 1)
     return buf.value.decode()
+
+
+def plan_selfcheck(kind, variant=0, out_comp=0, in_comp=0, o=4, v=6, max_work=2e6):
+    """Inconsistencies of the executable plan's grouped tasks against its
+    spin blocks (host only); see fnocc_plan_selfcheck."""
+    lib = load_library()
+    return int(lib.fnocc_plan_selfcheck(kind, VARIANTS.get(variant, variant), out_comp, in_comp, o, v, max_work))
 
 
 def plan_text(kind, variant=0, out_comp=0, in_comp=0, o=10, v=30, amortize=0.0):

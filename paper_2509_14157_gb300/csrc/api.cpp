@@ -1811,6 +1811,32 @@ long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char 
   }
 }
 
+long fnocc_plan_selfcheck(int kind, int variant, int out_comp, int in_comp, int o, int v, double max_work) {
+  try {
+    if (o <= 0 || v <= 0 || o > 64 || v > 128) return -1;
+    static const int kSpace[4][3][2] = {{{1, 0}, {2, 1}, {3, 2}}, {{0, 1}, {1, 2}, {2, 3}},
+                                        {{2, 0}, {3, 1}, {4, 2}}, {{0, 2}, {1, 3}, {2, 4}}};
+    static const int kMs2[4] = {1, 1, 0, 0};
+    int rd[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    if (kind == 0 && out_comp >= 0 && out_comp <= 3) {
+      ExecEquation e(cc_equation(out_comp), o, v, rd, 0.0, 0.0, 0, true);
+      return (long)e.self_check(max_work);
+    }
+    if (kind == 1 && variant >= 0 && variant <= 3 && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2) {
+      for (int k = 0; k < 3; ++k) {
+        rd[k][0] = kSpace[variant][k][0];
+        rd[k][1] = kSpace[variant][k][1];
+      }
+      ExecEquation e(eom_equation(variant, out_comp, in_comp), o, v, rd, kSigmaAmortize, kCacheCapDoubles,
+                     kMs2[variant], true);
+      return (long)e.self_check(max_work);
+    }
+    return -1;
+  } catch (...) {
+    return -1;
+  }
+}
+
 long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, int v, double amortize, char *buf,
                      size_t len) {
   try {

@@ -3,6 +3,7 @@
 #include "engine.hpp"
 
 #include <algorithm>
+#include <tuple>
 #include <functional>
 #include <map>
 #include <mutex>
@@ -301,11 +302,18 @@ struct TableBuilder {
     return total;
   }
 
-  void upload(DevBuf &buf) {
+  // device copy (or, for host-only plans, a host copy kept in `keep`)
+  void upload(DevBuf &buf, bool host_only, std::vector<long long> &keep) {
     if (host.empty()) host.push_back(0);
-    buf.reserve(host.size() * sizeof(long long));
-    FNOCC_CUDA(cudaMemcpy(buf.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice));
-    const long long *base = buf.as<long long>();
+    const long long *base;
+    if (host_only) {
+      keep = host;
+      base = keep.data();
+    } else {
+      buf.reserve(host.size() * sizeof(long long));
+      FNOCC_CUDA(cudaMemcpy(buf.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice));
+      base = buf.as<long long>();
+    }
     for (auto &p : pend)
       for (size_t g = 0; g < p.offs.size(); ++g) p.map->tab[g] = base + p.offs[g];
   }
@@ -415,8 +423,8 @@ void build_tasks(const TableBuilder &tb, ExecStep &e, std::vector<long long> &fl
 }  // namespace
 
 ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize,
-                           double cache_cap, int r_charge)
-    : nh_(eq.nh), np_(eq.np), o_(o), v_(v) {
+                           double cache_cap, int r_charge, bool host_only)
+    : nh_(eq.nh), np_(eq.np), o_(o), v_(v), host_only_(host_only) {
   TableBuilder tb;
   std::vector<long long> flat_host;
   Storage outs = output_storage(nh_, np_, o, v);
@@ -599,7 +607,7 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
     terms_.push_back(std::move(et));
   }
   (void)rdims;
-  tb.upload(tables_);
+  tb.upload(tables_, host_only_, host_tables_);
   build_launches(flat_host);
 }
 
@@ -608,9 +616,15 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
 // tiles than two per SM, CTA, partial and reduction offsets.
 void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
   if (flat_host.empty()) return;
-  flat_.reserve(sizeof(long long) * flat_host.size());
-  FNOCC_CUDA(cudaMemcpy(flat_.p, flat_host.data(), sizeof(long long) * flat_host.size(), cudaMemcpyHostToDevice));
-  const long long *fb = flat_.as<long long>();
+  const long long *fb;
+  if (host_only_) {
+    host_flat_ = flat_host;
+    fb = host_flat_.data();
+  } else {
+    flat_.reserve(sizeof(long long) * flat_host.size());
+    FNOCC_CUDA(cudaMemcpy(flat_.p, flat_host.data(), sizeof(long long) * flat_host.size(), cudaMemcpyHostToDevice));
+    fb = flat_.as<long long>();
+  }
   constexpr long long kWantCta = 2 * 152;
   constexpr long long kPartCap = 1LL << 27;  // doubles of split partials per launch
   std::vector<GTask> gt;
@@ -706,11 +720,21 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
     }
   const size_t tbytes = sizeof(GTask) * gt.size(), ibytes = sizeof(int) * sid.size();
   const size_t ioff = (tbytes + 255) / 256 * 256;
-  gtasks_.reserve(ioff + std::max<size_t>(ibytes, 8));
-  FNOCC_CUDA(cudaMemcpy(gtasks_.p, gt.data(), tbytes, cudaMemcpyHostToDevice));
-  if (ibytes) FNOCC_CUDA(cudaMemcpy((char *)gtasks_.p + ioff, sid.data(), ibytes, cudaMemcpyHostToDevice));
-  const GTask *tb = reinterpret_cast<const GTask *>(gtasks_.p);
-  const int *ib = reinterpret_cast<const int *>((char *)gtasks_.p + ioff);
+  const GTask *tb;
+  const int *ib;
+  if (host_only_) {
+    host_gt_ = gt;
+    host_sid_ = sid;
+    if (host_sid_.empty()) host_sid_.push_back(0);
+    tb = host_gt_.data();
+    ib = host_sid_.data();
+  } else {
+    gtasks_.reserve(ioff + std::max<size_t>(ibytes, 8));
+    FNOCC_CUDA(cudaMemcpy(gtasks_.p, gt.data(), tbytes, cudaMemcpyHostToDevice));
+    if (ibytes) FNOCC_CUDA(cudaMemcpy((char *)gtasks_.p + ioff, sid.data(), ibytes, cudaMemcpyHostToDevice));
+    tb = reinterpret_cast<const GTask *>(gtasks_.p);
+    ib = reinterpret_cast<const int *>((char *)gtasks_.p + ioff);
+  }
   for (auto &f : fix) {
     f.gl->tasks = tb + f.t0;
     f.gl->split_ids = ib + f.s0;
@@ -843,6 +867,79 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
     }
   }
   if (refresh) cache_version_ = version;
+}
+
+namespace {
+long long host_map_off(const DMap &mp, long long m) {
+  long long off = 0;
+  for (int g = mp.ng - 1; g >= 0; --g) {
+    const long long q = m / mp.n[g];
+    off += mp.tab[g][m - q * mp.n[g]];
+    m = q;
+  }
+  return off;
+}
+DMap host_sub(const DMap &full, const std::vector<std::pair<long long, long long>> &seg) {
+  DMap m = full;
+  for (size_t g = 0; g < seg.size(); ++g) {
+    m.tab[g] = full.tab[g] + seg[g].first;
+    m.n[g] = seg[g].second;
+  }
+  return m;
+}
+}  // namespace
+
+// Every grouped step of a host-only plan: the (A, B, C) element-offset
+// triples its tasks address, for every tile shape's task list, against the
+// triples of the spin-allowed blocks decoded through the per-group tables.
+long long ExecEquation::self_check(double max_work) const {
+  if (!host_only_) throw std::runtime_error("self_check needs a host-only plan");
+  long long bad = 0;
+  using Trip = std::tuple<long long, long long, long long>;
+  for (const ExecTerm &t : terms_)
+    for (const ExecStep &s : t.steps) {
+      if (!s.grouped) continue;
+      double work = 0;
+      for (auto &tr : s.tasks) work += double(tr.M) * double(tr.N) * double(tr.K);
+      if (work > max_work) continue;
+      std::vector<Trip> ref;
+      auto add_ref = [&](long long M, long long N, long long K, const DMap &ar, const DMap &ac, const DMap &br,
+                         const DMap &bc, const DMap &cr, const DMap &cc) {
+        for (long long m = 0; m < M; ++m)
+          for (long long n = 0; n < N; ++n)
+            for (long long k = 0; k < K; ++k)
+              ref.emplace_back(host_map_off(ar, m) + host_map_off(ac, k), host_map_off(br, k) + host_map_off(bc, n),
+                               host_map_off(cr, m) + host_map_off(cc, n));
+      };
+      if (s.blocked) {
+        for (const SubGemm &b : s.blocks)
+          if (b.M > 0 && b.N > 0 && b.K > 0)
+            add_ref(b.M, b.N, b.K, host_sub(s.arow, b.mseg), host_sub(s.acol, b.kseg), host_sub(s.brow, b.kseg),
+                    host_sub(s.bcol, b.nseg), host_sub(s.crow, b.mseg), host_sub(s.ccol, b.nseg));
+      } else {
+        add_ref(s.M, s.N, s.K, s.arow, s.acol, s.brow, s.bcol, s.crow, s.ccol);
+      }
+      std::sort(ref.begin(), ref.end());
+      for (int shape = 0; shape < kGShapesAll; ++shape) {
+        const GroupedLaunch &gl = s.gl[shape];
+        std::vector<Trip> got;
+        long long ctas = 0;
+        for (int i = 0; i < gl.ntasks; ++i) {
+          const GTask &g = gl.tasks[i];
+          if (g.cta_begin != ctas) ++bad;  // CTA ranges must tile the grid in order
+          ctas += g.tiles * g.ksplit;
+          if ((long long)g.ksplit * g.kchunk < g.K) ++bad;  // the splits cover K
+          for (long long m = 0; m < g.M; ++m)
+            for (long long n = 0; n < g.N; ++n)
+              for (long long k = 0; k < g.K; ++k)
+                got.emplace_back(g.arow[m] + g.acol[k], g.brow[k] + g.bcol[n], g.crow[m] + g.ccol[n]);
+        }
+        if (ctas != gl.ncta) ++bad;
+        std::sort(got.begin(), got.end());
+        if (got != ref) ++bad;
+      }
+    }
+  return bad;
 }
 
 }  // namespace fnocc

@@ -71,8 +71,14 @@ class ExecEquation {
   // rdims: (nh, np) of the three EOM input components (ignored for CC)
   // amortize > 0: R-independent steps are cached (see plan_term)
   // r_charge: 2*M_s change of the EOM vectors (their spin sector); 0 for CC.
+  // host_only: tables and launch descriptors stay in host memory (no
+  // device needed; the plan cannot run, only self_check it)
   ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize = 0.0,
-               double cache_cap = 0.0, int r_charge = 0);
+               double cache_cap = 0.0, int r_charge = 0, bool host_only = false);
+  // host-only plans: number of inconsistencies between the grouped tasks of
+  // every tile shape and the spin-allowed blocks (steps above max_work
+  // multiply-adds skipped); 0 = consistent
+  long long self_check(double max_work) const;
   // Y (dense output accumulator [o^nh v^np]) += sum of terms. version: the
   // cached R-independent intermediates are recomputed when it changes.
   void run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch,
@@ -91,6 +97,10 @@ class ExecEquation {
  private:
   void build_launches(const std::vector<long long> &flat_host);
   int nh_, np_, o_, v_;
+  bool host_only_ = false;
+  std::vector<long long> host_tables_, host_flat_;
+  std::vector<GTask> host_gt_;
+  std::vector<int> host_sid_;
   std::vector<ExecTerm> terms_;
   DevBuf tables_;
   DevBuf flat_;    // flat offset tables of the grouped steps

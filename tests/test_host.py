@@ -142,3 +142,17 @@ def test_xfno_matches_oracle():
     e = [-1.2001, -1.2004, -1.2011]
     assert abs(pkg.xfno_extrapolate(f, e) - xfno.extrapolate(f, e)) < 1e-14
     assert abs(pkg.xfno_extrapolate([1.0], [-3.0]) + 3.0) < 1e-15
+
+
+@pytest.mark.parametrize("o,v", [(4, 6), (6, 4)])
+def test_grouped_tasks_cover_the_spin_blocks_exactly(o, v):
+    """Host-only plans of every CCSDT rank and every EOM block: the flat
+    tables of the grouped tasks address exactly the operand offsets of the
+    spin-allowed blocks, for every tile shape (no GPU)."""
+    import paper_2509_14157_gb300 as pkg
+    for rank in range(4):
+        assert pkg.plan_selfcheck(0, 0, rank, 0, o, v) == 0, rank
+    for var in ("ip", "ea", "dip", "dea"):
+        for oc in range(3):
+            for ic in range(3):
+                assert pkg.plan_selfcheck(1, var, oc, ic, o, v) == 0, (var, oc, ic)
