@@ -320,6 +320,14 @@ fnocc_status fnocc_mlp_loss_grad(fnocc_mlp *mlp, const float *x, const float *t,
  * be NULL). One epoch with batch >= n is exactly one Adam step on loss_grad. */
 fnocc_status fnocc_mlp_train(fnocc_mlp *mlp, const float *x, const float *t, const float *w, long long n,
                              int epochs, int batch, float lr, unsigned long long seed, double *history);
+/* Parameter file of a network (a trained guess kept for later runs): the
+ * 8-byte tag "FNOCCMLP", int32 version (1), nin, width, nout, int64
+ * param_count, then the FP32 parameters in the get_params layout, all in the
+ * host's byte order. load requires a network of the same shape and resets
+ * its optimiser state; a missing, foreign, mismatched or truncated file
+ * returns FNOCC_E_INVALID and leaves the parameters unchanged. */
+fnocc_status fnocc_mlp_save(fnocc_mlp *mlp, const char *path);
+fnocc_status fnocc_mlp_load(fnocc_mlp *mlp, const char *path);
 
 /* Features [dim x 8] of every element of the variant's packed operator space
  * (components concatenated as in eom_sigma): orbital-energy difference D,

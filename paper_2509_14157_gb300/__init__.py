@@ -127,6 +127,8 @@ SIGNATURES = {
     "fnocc_mlp_loss_grad": (ctypes.c_int, [_cp, _fp, _fp, _fp, ctypes.c_longlong, _dp, _fp]),
     "fnocc_mlp_train": (ctypes.c_int, [_cp, _fp, _fp, _fp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_float, ctypes.c_ulonglong, _dp]),
+    "fnocc_mlp_save": (ctypes.c_int, [_cp, ctypes.c_char_p]),
+    "fnocc_mlp_load": (ctypes.c_int, [_cp, ctypes.c_char_p]),
     "fnocc_eom_features": (ctypes.c_int, [_cp, ctypes.c_int, _fp]),
     "fnocc_eom_diagonal": (ctypes.c_int, [_cp, ctypes.c_int, _dp]),
     "fnocc_set_guess_model": (ctypes.c_int, [_cp, _cp]),
@@ -305,6 +307,14 @@ class Mlp:
         self._check(self.lib.fnocc_mlp_train(self._h, xp, tp, wp, x.shape[0], int(epochs), int(batch),
                                              float(lr), int(seed), hist.ctypes.data_as(_dp)))
         return hist[:epochs]
+
+    def save(self, path):
+        """Write the parameters to a file (fnocc_mlp_save)."""
+        self._check(self.lib.fnocc_mlp_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Read parameters written by save() for a network of this shape."""
+        self._check(self.lib.fnocc_mlp_load(self._h, os.fsencode(path)))
 
 
 class Context:

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -591,6 +592,18 @@ fnocc_status mlp_guarded(fnocc_mlp *m, F &&fn) {
   }
 }
 
+// parameter file: 8-byte tag, then int32 version, nin, width, nout, int64
+// parameter count, then the FP32 parameters (host byte order, the layout of
+// fnocc_mlp_get_params)
+constexpr char kMlpTag[8] = {'F', 'N', 'O', 'C', 'C', 'M', 'L', 'P'};
+constexpr int32_t kMlpVersion = 1;
+
+struct MlpFileHeader {
+  char tag[8];
+  int32_t version, nin, width, nout;
+  int64_t nparam;
+};
+
 }  // namespace
 
 extern "C" {
@@ -681,6 +694,50 @@ fnocc_status fnocc_mlp_train(fnocc_mlp *m, const float *x, const float *t, const
     return FNOCC_E_INVALID;
   return mlp_guarded(m, [&]() -> fnocc_status {
     m->net->train(x, t, w, n, epochs, batch, lr, seed, history);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status fnocc_mlp_save(fnocc_mlp *m, const char *path) {
+  if (!m || !path) return FNOCC_E_INVALID;
+  return mlp_guarded(m, [&]() -> fnocc_status {
+    const fnocc::Mlp &net = *m->net;
+    std::vector<float> p(net.nparam());
+    net.get_params(p.data());
+    MlpFileHeader hd{};
+    std::memcpy(hd.tag, kMlpTag, sizeof(hd.tag));
+    hd.version = kMlpVersion;
+    hd.nin = net.nin();
+    hd.width = net.width();
+    hd.nout = net.nout();
+    hd.nparam = (int64_t)p.size();
+    FILE *f = std::fopen(path, "wb");
+    if (!f) throw std::runtime_error(std::string("cannot open ") + path + " for writing");
+    const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+    if (std::fclose(f) != 0 || !ok) throw std::runtime_error(std::string("cannot write ") + path);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status fnocc_mlp_load(fnocc_mlp *m, const char *path) {
+  if (!m || !path) return FNOCC_E_INVALID;
+  return mlp_guarded(m, [&]() -> fnocc_status {
+    fnocc::Mlp &net = *m->net;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) throw std::runtime_error(std::string("cannot open ") + path);
+    MlpFileHeader hd{};
+    std::vector<float> p(net.nparam());
+    bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1;
+    const bool match = ok && std::memcmp(hd.tag, kMlpTag, sizeof(hd.tag)) == 0 && hd.version == kMlpVersion &&
+                       hd.nin == net.nin() && hd.width == net.width() && hd.nout == net.nout() &&
+                       hd.nparam == (int64_t)p.size();
+    ok = match && std::fread(p.data(), sizeof(float), p.size(), f) == p.size();
+    std::fclose(f);
+    if (!match)
+      throw std::runtime_error(std::string(path) + ": not a parameter file of this network's shape");
+    if (!ok) throw std::runtime_error(std::string(path) + ": truncated");
+    net.set_params(p.data());
+    net.reset_optimizer();
     return FNOCC_OK;
   });
 }

@@ -29,6 +29,7 @@ class Mlp {
   Mlp &operator=(const Mlp &) = delete;
   size_t nparam() const { return nparam_; }
   int nin() const { return nin_; }
+  int width() const { return width_; }
   int nout() const { return nout_; }
   int device() const { return device_; }
   // parameters: W1 [nin x width], b1, W2 [width x width], b2, W3 [width x nout], b3

@@ -76,6 +76,40 @@ def test_one_training_step_is_one_adam_step(pkg):
     net.close()
 
 
+def test_parameter_file_round_trip(pkg, tmp_path):
+    """A trained network written to a file and read into a fresh one gives the
+    same parameters and outputs; a file of another shape, a truncated file and
+    a foreign file are rejected without touching the parameters."""
+    params, x, t, w = case(n=700, seed=4)
+    net = pkg.Mlp(0, WIDTH, seed=1)
+    net.set_params(params)
+    net.train(x, t, w, epochs=2, batch=256, lr=1e-3)
+    path = tmp_path / "guess.bin"
+    net.save(path)
+    assert path.stat().st_size == 32 + 4 * net.nparam
+    other = pkg.Mlp(0, WIDTH, seed=7)
+    other.load(path)
+    assert np.array_equal(other.get_params(), net.get_params())
+    assert np.array_equal(other.forward(x[:50]), net.forward(x[:50]))
+    wide = pkg.Mlp(0, 2 * WIDTH, seed=1)
+    wide_before = wide.get_params()
+    with pytest.raises(pkg.FnoccError):
+        wide.load(path)
+    assert np.array_equal(wide.get_params(), wide_before)
+    cut = tmp_path / "cut.bin"
+    cut.write_bytes(path.read_bytes()[:-4])
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a network" * 8)
+    fresh = pkg.Mlp(0, WIDTH, seed=7)
+    before = fresh.get_params()
+    for bad in (cut, junk, tmp_path / "missing.bin"):
+        with pytest.raises(pkg.FnoccError):
+            fresh.load(bad)
+        assert np.array_equal(fresh.get_params(), before)
+    for m in (net, other, wide, fresh):
+        m.close()
+
+
 @pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
 def test_features_match_oracle(pkg, variant):
     h, eri = synth.hamiltonian(6, 10, seed=0)
