@@ -296,8 +296,9 @@ def main():
     ap.add_argument("--impl", default="fnocc", choices=["fnocc", "reference"])
     ap.add_argument("--threshold", type=float, default=THRESHOLD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="mixed: BF16 three-slice tensor-core contractions, then FP64 refinement")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_tf32"],
+                    help="mixed: BF16 three-slice tensor-core contractions, then FP64 refinement; "
+                         "mixed_tf32: TF32 two-slice")
     ap.add_argument("--guess", default="diagonal", choices=["diagonal", "learned"],
                     help="learned: Davidson start and preconditioner from a network trained first (untimed)")
     ap.add_argument("--no-mixed-learned", action="store_true",
@@ -338,10 +339,10 @@ def main():
 
     counts = {"cc_iters": 0, "sigma": {}, "detail": {}, "flops_per_sigma": {}}
 
-    # mixed: BF16x3 products throughout the Davidson solves, converged to the
-    # 1e-6 Eh accuracy target (no FP64 refinement sweep); CCSDT refines in FP64
-    eom_kw = (dict(precision="mixed", switch_tol=0.0, tol_res=1e-6, tol_e=1e-8)
-              if args.precision == "mixed" else dict(precision="fp64"))
+    # mixed kinds: split products throughout the Davidson solves, converged to
+    # the 1e-6 Eh accuracy target (no FP64 refinement sweep); CCSDT refines in FP64
+    eom_kw = (dict(precision=args.precision, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8)
+              if args.precision != "fp64" else dict(precision="fp64"))
     guess_net = {}
 
     def train_guess():
@@ -433,7 +434,7 @@ def main():
     e2e_total = sum(e2e_times)
     e2e_total = max_over_ranks(e2e_total, world, dev)
     accuracy = None
-    if args.precision == "mixed":
+    if args.precision != "fp64":
         # every root against the same solve in FP64 (outside the timed region)
         _, mixed_e = step(True)
         _, ref_e = step(True, "fp64", dict(precision="fp64"))
@@ -485,6 +486,15 @@ def main():
         roof = {"bound": "tensor", "kernel": dominant + " (BF16 mma.sync, 6 slice products)",
                 "achieved": 6 * achieved if achieved else None, "peak": peak, "unit": "TFLOP/s",
                 "frac": 6 * achieved / peak if achieved else None, "traffic": None, "peak_basis": basis}
+    elif dominant.startswith("k_ggemm_tf32x3"):
+        # three TF32 slice products per FP64-equivalent multiply-add; TF32 peak =
+        # measured BF16 peak x the nominal dense ratio 1.1 / 2.25 PFLOP/s
+        peak, basis = measured_bf16_peak()
+        peak *= 1.1 / 2.25
+        roof = {"bound": "tensor", "kernel": dominant + " (TF32 mma.sync, 3 slice products)",
+                "achieved": 3 * achieved if achieved else None, "peak": peak, "unit": "TFLOP/s",
+                "frac": 3 * achieved / peak if achieved else None, "traffic": None,
+                "peak_basis": basis + " x 1.1/2.25 (nominal TF32/BF16)"}
     else:
         roof = {"bound": "alu", "kernel": dominant + " (FP64 FMA)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -499,7 +509,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "bf16x3->f32, f64 refinement",
+        "dtype": {"fp64": "f64", "mixed": "bf16x3->f32, f64 refinement",
+                  "mixed_tf32": "tf32x3->f32, f64 refinement"}[args.precision],
         "data": "synthetic", "config": dict(config(args.threshold, seed), precision=args.precision),
         "tflops": flops * world / total / 1e12 if total > 0 else None,
         "roofline": roof,

@@ -69,12 +69,14 @@ typedef enum { FNOCC_IP = 0, FNOCC_EA = 1, FNOCC_DIP = 2, FNOCC_DEA = 3 } fnocc_
 typedef enum { FNOCC_GUESS_KOOPMANS = 0, FNOCC_GUESS_DIAGONAL = 1, FNOCC_GUESS_LEARNED = 2 } fnocc_guess;
 typedef enum { FNOCC_CRIT_ABS = 0, FNOCC_CRIT_OCCT = 1 } fnocc_criterion;
 /* Arithmetic of the contractions (the single- and double-precision
- * algorithms of Sec. 1). MIXED runs the large contractions as BF16
- * three-slice split products on the tensor cores with FP32 accumulation
- * until the residual falls below switch_tol, then refines in FP64;
- * DIIS, Davidson orthogonalisation, the subspace problem and norms are
- * always FP64. */
-typedef enum { FNOCC_FP64 = 0, FNOCC_MIXED_BF16X3 = 1 } fnocc_precision;
+ * algorithms of Sec. 1). The MIXED kinds run the large contractions as split
+ * products on the tensor cores with FP32 accumulation until the residual
+ * falls below switch_tol, then refine in FP64: BF16X3 splits each operand
+ * (truncated to FP32) into three BF16 slices and sums six slice products
+ * (dropped terms below 2^-24 relative); TF32 splits it into two TF32
+ * slices and sums three products (about 2^-21 relative). DIIS, Davidson
+ * orthogonalisation, the subspace problem and norms are always FP64. */
+typedef enum { FNOCC_FP64 = 0, FNOCC_MIXED_BF16X3 = 1, FNOCC_MIXED_TF32 = 2 } fnocc_precision;
 
 typedef struct fnocc_ctx fnocc_ctx;
 
@@ -395,12 +397,13 @@ double fnocc_flop_count(const fnocc_ctx *ctx);
 
 /* Contraction-kernel timing: when enabled, every contraction launch is
  * bracketed by CUDA events on the context stream. Contractions run on one of
- * six kernel paths: 0 the grouped FP64 gather-GEMM (k_ggemm: all spin blocks
+ * eight kernel paths: 0 the grouped FP64 gather-GEMM (k_ggemm: all spin blocks
  * of a step in one launch), 1 the same with a split reduction and its
  * ordered sum (k_greduce), 2 the small-output kernel (<= 256 outputs) with
  * its reduction, 3 the row-parallel GEMV, 4 and 5 the grouped BF16
  * three-slice tensor-core kernel (k_ggemm_bf16x3) without / with a split
- * reduction. fnocc_profile_read returns, for one path (or all with path =
+ * reduction, 6 and 7 the grouped TF32 two-slice kernel (k_ggemm_tf32x3)
+ * without / with. fnocc_profile_read returns, for one path (or all with path =
  * -1), the summed device time (ms), the summed algorithmic flops (2*M*N*K)
  * and the number of launches, then resets those counters. */
 fnocc_status fnocc_profile(fnocc_ctx *ctx, int enable);

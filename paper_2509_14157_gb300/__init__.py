@@ -18,7 +18,7 @@ IP, EA, DIP, DEA = 0, 1, 2, 3
 VARIANTS = {"ip": IP, "ea": EA, "dip": DIP, "dea": DEA}
 GUESS = {"koopmans": 0, "diagonal": 1, "learned": 2}
 CRITERIA = {"abs": 0, "occt": 1}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_tf32": 2}  # mixed: BF16 three-slice split
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "E_INVALID", -2: "E_NOMEM", -3: "E_CUDA",
           -4: "E_STATE", -5: "E_NUMERIC", -6: "E_TIMEOUT"}
 # (holes, particles) of R1, R2, R3 per variant
@@ -376,7 +376,8 @@ class Context:
                     kept_fraction=info.kept_fraction, scf_iters=info.scf_iters, occ=occ)
 
     def set_precision(self, precision):
-        """Arithmetic of standalone residual / sigma calls: 'fp64' or 'mixed'."""
+        """Arithmetic of standalone residual / sigma calls: 'fp64', 'mixed'
+        (BF16 three-slice split products) or 'mixed_tf32' (TF32 two-slice)."""
         self._check(self.lib.fnocc_set_precision(self._h, PRECISION[precision]))
 
     @property
@@ -387,7 +388,8 @@ class Context:
         self._check(self.lib.fnocc_profile(self._h, 1 if enable else 0))
 
     PROFILE_PATHS = {0: "k_ggemm", 1: "k_ggemm_split+k_greduce", 2: "k_gemm_small+k_reduce_partials",
-                     3: "k_gemv_rows", 4: "k_ggemm_bf16x3", 5: "k_ggemm_bf16x3_split+k_greduce"}
+                     3: "k_gemv_rows", 4: "k_ggemm_bf16x3", 5: "k_ggemm_bf16x3_split+k_greduce",
+                     6: "k_ggemm_tf32x3", 7: "k_ggemm_tf32x3_split+k_greduce"}
 
     def profile_read(self, path=-1):
         """(device ms, algorithmic flops, launches) of one contraction kernel path

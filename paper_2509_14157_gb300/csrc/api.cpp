@@ -34,6 +34,8 @@ struct StatusError : std::runtime_error {
   StatusError(fnocc_status s, const std::string &m) : std::runtime_error(m), st(s) {}
 };
 
+bool valid_precision(int p) { return p == FNOCC_FP64 || p == FNOCC_MIXED_BF16X3 || p == FNOCC_MIXED_TF32; }
+
 DMap stride_map(std::initializer_list<std::pair<long long, long long>> dims, std::vector<long long> &host,
                 std::vector<std::pair<DMap *, std::vector<long long>>> &fix, DMap *m) {
   m->ng = (int)dims.size();
@@ -1085,7 +1087,7 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
     Timer timer;
     ccsdt_options o{1e-10, 1e-12, 200, 8, FNOCC_FP64, 1e-6};
     if (opt) o = *opt;
-    if (o.precision != FNOCC_FP64 && o.precision != FNOCC_MIXED_BF16X3)
+    if (!valid_precision(o.precision))
       throw StatusError(FNOCC_E_INVALID, "bad precision");
     if (o.switch_tol < 0) o.switch_tol = 0;
     struct PrecisionGuard {
@@ -1133,11 +1135,11 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
     bool conv = false;
     int it;
     for (it = 1; it <= o.maxiter; ++it) {
-      if (c->precision == FNOCC_MIXED_BF16X3) ++iters_mixed;
+      if (c->precision != FNOCC_FP64) ++iters_mixed;
       e = cc_residual_dev(c, c->tpk.d(), c->rpk.d());
       absmax_dev(c, tot, c->rpk.d(), &rmax, &rn);
       if (!std::isfinite(e) || !std::isfinite(rmax)) throw StatusError(FNOCC_E_NUMERIC, "NaN/Inf in CCSDT iterations");
-      if (c->precision == FNOCC_MIXED_BF16X3 && o.switch_tol > 0 && rmax < o.switch_tol) {
+      if (c->precision != FNOCC_FP64 && o.switch_tol > 0 && rmax < o.switch_tol) {
         // refinement: from here on every contraction is FP64; the iterate is kept
         c->precision = FNOCC_FP64;
         e_old = e;
@@ -1196,7 +1198,7 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
 }
 
 fnocc_status fnocc_set_precision(fnocc_ctx *c, int precision) {
-  if (!c || (precision != FNOCC_FP64 && precision != FNOCC_MIXED_BF16X3)) return FNOCC_E_INVALID;
+  if (!c || (!valid_precision(precision))) return FNOCC_E_INVALID;
   c->default_precision = precision;
   return FNOCC_OK;
 }
@@ -1281,7 +1283,7 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
     Timer timer;
     eom_options o{1e-8, 1e-10, 0, 200, 0, FNOCC_FP64, 1e-5};
     if (opt) o = *opt;
-    if (o.precision != FNOCC_FP64 && o.precision != FNOCC_MIXED_BF16X3)
+    if (!valid_precision(o.precision))
       throw StatusError(FNOCC_E_INVALID, "bad precision");
     if (o.switch_tol < 0) o.switch_tol = 0;
     struct PrecisionGuard {
@@ -1407,7 +1409,7 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
         sigma_dev(c, variant, dst, sdst);
         scale_mask(L, dim, sdst, mask);
         ++sigma_calls;
-        if (c->precision == FNOCC_MIXED_BF16X3) ++sigma_calls_mixed;
+        if (c->precision != FNOCC_FP64) ++sigma_calls_mixed;
       }
       // extend G
       int k1 = kb + 1;
@@ -1502,7 +1504,7 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
         if (!std::isfinite(nrm)) throw StatusError(FNOCC_E_NUMERIC, "NaN in Davidson residual");
         norms[r] = nrm;
       }
-      if (c->precision == FNOCC_MIXED_BF16X3 && o.switch_tol > 0) {
+      if (c->precision != FNOCC_FP64 && o.switch_tol > 0) {
         double mx = 0;
         for (double x : norms) mx = std::max(mx, x);
         if (mx < o.switch_tol) {

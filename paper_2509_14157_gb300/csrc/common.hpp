@@ -65,8 +65,8 @@ struct DMap {
 // Optional event timing of contraction launches (owned by a context), per
 // kernel path: 0 grouped FP64 GEMM, 1 the same with split reduction + ordered
 // sum, 2 small-output kernel + reduction, 3 GEMV, 4 / 5 grouped BF16x3 GEMM
-// without / with split reduction.
-constexpr int kGemmPaths = 6;
+// without / with split reduction, 6 / 7 grouped TF32x3 GEMM without / with.
+constexpr int kGemmPaths = 8;
 struct GemmProfile {
   bool enabled = false;
   std::vector<cudaEvent_t> pool;           // events, reused
@@ -83,7 +83,7 @@ struct Launch {
   uint64_t *counter;      // incremented per kernel launch
   GemmProfile *prof = nullptr;
   DevBuf *partials = nullptr;  // split-K partial sums (deterministic reduction)
-  int precision = 0;           // 0 FP64; 1 BF16 three-slice split on tensor cores (tiled path)
+  int precision = 0;  // 0 FP64; tensor-core split products (tiled path): 1 BF16 three-slice, 2 TF32 two-slice
 };
 
 // One sub-GEMM of a grouped launch: C[crow[m] + ccol[n]] += alpha *

@@ -823,7 +823,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
       if (s.gmax_a >= size(s.a_kind, s.a_inter) || s.gmax_b >= size(s.b_kind, s.b_inter) || s.gmax_c >= csize)
         throw std::runtime_error("engine: grouped index tables exceed operand bounds");
       ExecStep &ms = const_cast<ExecStep &>(s);
-      if (L.precision == 1 && s.gl[0].flops >= 1e5) {
+      if (L.precision != 0 && s.gl[0].flops >= 1e5) {
         grouped_gemm(L, s.gl[s.bf16_shape], s.alpha, A, B, C);
         continue;
       }

@@ -17,8 +17,8 @@
 // On this part FP64 FMA issue is about two per clock per SM, so an FP64 tile
 // is FMA-bound whatever its shape: shapes are chosen for the least padding
 // (padded multiply-adds cost full time) and for enough CTAs to occupy all SMs.
-// The mixed-precision kernel runs the same tasks on the tensor cores as BF16
-// three-slice split products with FP32 accumulation.
+// The mixed-precision kernels run the same tasks on the tensor cores as BF16
+// three-slice or TF32 two-slice split products with FP32 accumulation.
 #include "common.hpp"
 
 #include <cuda_bf16.h>
@@ -153,32 +153,142 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &s0, __nv_bfloat16
   s2 = __float2bfloat16_rn(r1 - __bfloat162float(s1));
 }
 
-// BF16 three-slice split on the tensor cores (mma.sync m16n8k16, FP32
-// accumulation): the six slice products with i + j <= 2. 8 warps as WM x WN,
-// each warp MT x NT2 mma tiles (16 x 8), so the block tile is
-// (WM*MT*16) x (WN*NT2*8); K tile 32. Software pipeline: the operand
-// gathers of K tile t+1 are in flight (registers) while the tensor cores
-// work on tile t, whose slices sit in one of two shared-memory buffers; one
-// barrier per K tile.
-template <int WM, int WN, int MT, int NT2>
-struct Bf16Tile {
-  static constexpr int TBM = WM * MT * 16, TBN = WN * NT2 * 8, TBK = 32, LDS = 40;  // padded row stride
-  static constexpr int EA = TBM * TBK / NT, EB = TBN * TBK / NT;  // gathered elements per thread and tile
-  static constexpr size_t kSmem = sizeof(__nv_bfloat16) * 2 * 3 * (TBM + TBN) * LDS;
-  static_assert(WM * WN == 8, "8 warps");
-  static_assert(EA * NT == TBM * TBK && EB * NT == TBN * TBK, "whole tiles per thread");
+// FP32 -> TF32 (11 significant bits) rounded to nearest, ties away from
+// zero, in integer arithmetic on the bit pattern (finite inputs)
+__device__ __forceinline__ unsigned tf32_rna(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
+
+// Split products on the tensor cores (mma.sync, FP32 accumulation). A policy
+// stages each FP32 operand as kSlices narrow slices, one shared-memory plane
+// per slice, and runs the slice products of one K tile of 32.
+//
+// Bf16x3: three BF16 slices (exact), the six products with i + j <= 2 on
+// m16n8k16; the dropped products are below 2^-24 of the full one.
+struct Bf16x3 {
+  using slice_t = __nv_bfloat16;
+  static constexpr int kSlices = 3, LDS = 40;  // padded row stride (slices)
+  __device__ static void stage(float x, slice_t *p, int plane) { split3(x, p[0], p[plane], p[2 * plane]); }
+  template <int TBM, int TBN, int MT, int NT2>
+  __device__ static void products(const slice_t *as, const slice_t *bs, int wm, int wn, int g, int tg,
+                                  float (&acc)[MT][NT2][4]) {
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 16) {
+      unsigned a[3][MT][4], b[3][NT2][2];
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          const int r0 = sl * TBM + wm * MT * 16 + mt * 16 + g;
+          const int c0 = ks + 2 * tg;
+          a[sl][mt][0] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0]);
+          a[sl][mt][1] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0]);
+          a[sl][mt][2] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0 + 8]);
+          a[sl][mt][3] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0 + 8]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT2; ++nt) {
+          const int n = sl * TBN + wn * NT2 * 8 + nt * 8 + g;
+          b[sl][nt][0] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg]);
+          b[sl][nt][1] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg + 8]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3 - i; ++j)
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT2; ++nt)
+              asm volatile(
+                  "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                  "{%0,%1,%2,%3};\n"
+                  : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
+                  : "r"(a[i][mt][0]), "r"(a[i][mt][1]), "r"(a[i][mt][2]), "r"(a[i][mt][3]), "r"(b[j][nt][0]),
+                    "r"(b[j][nt][1]));
+    }
+  }
 };
 
-template <int WM, int WN, int MT, int NT2>
-__global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ tasks, int ntasks, double alpha,
-                                                     const double *__restrict__ A, const double *__restrict__ B,
-                                                     double *__restrict__ C, double *__restrict__ part) {
-  using T = Bf16Tile<WM, WN, MT, NT2>;
+// Tf32x3: two TF32 slices (hi = x rounded to 11 significant bits, lo = the
+// exact remainder rounded likewise), the three products hi*hi, hi*lo, lo*hi
+// on m16n8k8; slice and dropped-product errors are about 2^-21 of the full
+// product.
+struct Tf32x3 {
+  using slice_t = unsigned;
+  static constexpr int kSlices = 2, LDS = 36;  // padded row stride (words): conflict-free fragment reads
+  __device__ static void stage(float x, slice_t *p, int plane) {
+    const unsigned hi = tf32_rna(x);
+    p[0] = hi;
+    p[plane] = tf32_rna(x - __uint_as_float(hi));
+  }
+  template <int TBM, int TBN, int MT, int NT2>
+  __device__ static void products(const slice_t *as, const slice_t *bs, int wm, int wn, int g, int tg,
+                                  float (&acc)[MT][NT2][4]) {
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 8) {
+      unsigned a[2][MT][4], b[2][NT2][2];
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          const int r0 = sl * TBM + wm * MT * 16 + mt * 16 + g;
+          a[sl][mt][0] = as[r0 * LDS + ks + tg];
+          a[sl][mt][1] = as[(r0 + 8) * LDS + ks + tg];
+          a[sl][mt][2] = as[r0 * LDS + ks + tg + 4];
+          a[sl][mt][3] = as[(r0 + 8) * LDS + ks + tg + 4];
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT2; ++nt) {
+          const int n = sl * TBN + wn * NT2 * 8 + nt * 8 + g;
+          b[sl][nt][0] = bs[n * LDS + ks + tg];
+          b[sl][nt][1] = bs[n * LDS + ks + tg + 4];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2 - i; ++j)
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT2; ++nt)
+              asm volatile(
+                  "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                  "{%0,%1,%2,%3};\n"
+                  : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
+                  : "r"(a[i][mt][0]), "r"(a[i][mt][1]), "r"(a[i][mt][2]), "r"(a[i][mt][3]), "r"(b[j][nt][0]),
+                    "r"(b[j][nt][1]));
+    }
+  }
+};
+
+// Tile of the split-product kernels: 8 warps as WM x WN, each warp MT x NT2
+// mma tiles (16 x 8), so the block tile is (WM*MT*16) x (WN*NT2*8); K tile
+// 32. Software pipeline: the operand gathers of K tile t+1 are in flight
+// (registers) while the tensor cores work on tile t, whose slices sit in one
+// of two shared-memory buffers; one barrier per K tile.
+template <class S, int WM, int WN, int MT, int NT2>
+struct SplitTile {
+  static constexpr int TBM = WM * MT * 16, TBN = WN * NT2 * 8, TBK = 32, LDS = S::LDS;
+  static constexpr int EA = TBM * TBK / NT, EB = TBN * TBK / NT;  // gathered elements per thread and tile
+  static constexpr size_t kSmem = sizeof(typename S::slice_t) * 2 * S::kSlices * (TBM + TBN) * LDS;
+  static_assert(WM * WN == 8, "8 warps");
+  static_assert(EA * NT == TBM * TBK && EB * NT == TBN * TBK, "whole tiles per thread");
+  static_assert(LDS >= TBK, "row stride covers the K tile");
+};
+
+template <class S, int WM, int WN, int MT, int NT2>
+__device__ __forceinline__ void ggemm_split(const GTask *__restrict__ tasks, int ntasks, double alpha,
+                                            const double *__restrict__ A, const double *__restrict__ B,
+                                            double *__restrict__ C, double *__restrict__ part) {
+  using T = SplitTile<S, WM, WN, MT, NT2>;
+  using slice_t = typename S::slice_t;
   constexpr int TBM = T::TBM, TBN = T::TBN, TBK = T::TBK, LDS = T::LDS, EA = T::EA, EB = T::EB;
+  constexpr int NS = S::kSlices;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // As[buf][slice][row][k], Bs[buf][slice][col][k]
-  __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-  __nv_bfloat16 *Bs = As + 2 * 3 * TBM * LDS;
+  slice_t *As = reinterpret_cast<slice_t *>(smem_raw);
+  slice_t *Bs = As + 2 * NS * TBM * LDS;
   __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN];
   __shared__ GTask t;
   const int tid = threadIdx.x;
@@ -232,59 +342,22 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
   if (kb < ke) load(kb);
   int buf = 0;
   for (long long k0 = kb; k0 < ke; k0 += TBK, buf ^= 1) {
-    __nv_bfloat16 *as = As + buf * 3 * TBM * LDS, *bs = Bs + buf * 3 * TBN * LDS;
+    slice_t *as = As + buf * NS * TBM * LDS, *bs = Bs + buf * NS * TBN * LDS;
 #pragma unroll
     for (int r = 0; r < EA; ++r) {
       const int idx = tid + NT * r;
       const int kk = idx % TBK, row = idx / TBK;
-      split3(f64_to_f32_trunc(ra[r]), as[row * LDS + kk], as[(TBM + row) * LDS + kk],
-             as[(2 * TBM + row) * LDS + kk]);
+      S::stage(f64_to_f32_trunc(ra[r]), &as[row * LDS + kk], TBM * LDS);
     }
 #pragma unroll
     for (int r = 0; r < EB; ++r) {
       const int idx = tid + NT * r;
       const int col = idx % TBN, kk = idx / TBN;
-      split3(f64_to_f32_trunc(rb[r]), bs[col * LDS + kk], bs[(TBN + col) * LDS + kk],
-             bs[(2 * TBN + col) * LDS + kk]);
+      S::stage(f64_to_f32_trunc(rb[r]), &bs[col * LDS + kk], TBN * LDS);
     }
     __syncthreads();
     if (k0 + TBK < ke) load(k0 + TBK);  // next tile's gathers overlap this tile's products
-#pragma unroll
-    for (int ks = 0; ks < TBK; ks += 16) {
-      unsigned a[3][MT][4], b[3][NT2][2];
-#pragma unroll
-      for (int sl = 0; sl < 3; ++sl) {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-          const int r0 = sl * TBM + wm * MT * 16 + mt * 16 + g;
-          const int c0 = ks + 2 * tg;
-          a[sl][mt][0] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0]);
-          a[sl][mt][1] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0]);
-          a[sl][mt][2] = *reinterpret_cast<const unsigned *>(&as[r0 * LDS + c0 + 8]);
-          a[sl][mt][3] = *reinterpret_cast<const unsigned *>(&as[(r0 + 8) * LDS + c0 + 8]);
-        }
-#pragma unroll
-        for (int nt = 0; nt < NT2; ++nt) {
-          const int n = sl * TBN + wn * NT2 * 8 + nt * 8 + g;
-          b[sl][nt][0] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg]);
-          b[sl][nt][1] = *reinterpret_cast<const unsigned *>(&bs[n * LDS + ks + 2 * tg + 8]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3 - i; ++j)
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT2; ++nt)
-              asm volatile(
-                  "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                  "{%0,%1,%2,%3};\n"
-                  : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
-                  : "r"(a[i][mt][0]), "r"(a[i][mt][1]), "r"(a[i][mt][2]), "r"(a[i][mt][3]), "r"(b[j][nt][0]),
-                    "r"(b[j][nt][1]));
-    }
+    S::template products<TBM, TBN, MT, NT2>(as, bs, wm, wn, g, tg, acc);
   }
   const long long MN = t.M * t.N;
 #pragma unroll
@@ -304,11 +377,27 @@ __global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ t
       }
 }
 
-// dynamic shared memory above the 48 KiB default, opted in once per device
 template <int WM, int WN, int MT, int NT2>
-void launch_bf16(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha, const double *A,
-                 const double *B, double *C, double *part) {
-  constexpr size_t smem = Bf16Tile<WM, WN, MT, NT2>::kSmem;
+__global__ void __launch_bounds__(NT) k_ggemm_bf16x3(const GTask *__restrict__ tasks, int ntasks, double alpha,
+                                                     const double *__restrict__ A, const double *__restrict__ B,
+                                                     double *__restrict__ C, double *__restrict__ part) {
+  ggemm_split<Bf16x3, WM, WN, MT, NT2>(tasks, ntasks, alpha, A, B, C, part);
+}
+
+template <int WM, int WN, int MT, int NT2>
+__global__ void __launch_bounds__(NT) k_ggemm_tf32x3(const GTask *__restrict__ tasks, int ntasks, double alpha,
+                                                     const double *__restrict__ A, const double *__restrict__ B,
+                                                     double *__restrict__ C, double *__restrict__ part) {
+  ggemm_split<Tf32x3, WM, WN, MT, NT2>(tasks, ntasks, alpha, A, B, C, part);
+}
+
+// dynamic shared memory above the 48 KiB default, opted in once per device
+// and kernel
+template <class S, int WM, int WN, int MT, int NT2>
+void launch_split(void (*kernel)(const GTask *, int, double, const double *, const double *, double *, double *),
+                  unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha, const double *A,
+                  const double *B, double *C, double *part) {
+  constexpr size_t smem = SplitTile<S, WM, WN, MT, NT2>::kSmem;
   static std::mutex mu;
   static bool done[64] = {};
   int dev = 0;
@@ -317,12 +406,22 @@ void launch_bf16(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, 
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!done[dev]) {
-      FNOCC_CUDA(cudaFuncSetAttribute(k_ggemm_bf16x3<WM, WN, MT, NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+      FNOCC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       done[dev] = true;
     }
   }
-  k_ggemm_bf16x3<WM, WN, MT, NT2><<<grid, NT, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
+  kernel<<<grid, NT, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
+}
+
+template <int WM, int WN, int MT, int NT2>
+void launch_tensor(int precision, unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
+                   const double *A, const double *B, double *C, double *part) {
+  if (precision == 2)
+    launch_split<Tf32x3, WM, WN, MT, NT2>(k_ggemm_tf32x3<WM, WN, MT, NT2>, grid, s, tasks, ntasks, alpha, A, B, C,
+                                          part);
+  else
+    launch_split<Bf16x3, WM, WN, MT, NT2>(k_ggemm_bf16x3<WM, WN, MT, NT2>, grid, s, tasks, ntasks, alpha, A, B, C,
+                                          part);
 }
 
 // C[crow(m) + ccol(n)] += alpha * sum_z part[task][z][m, n], z in order, for
@@ -413,9 +512,10 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_G(11, 2, 1, 1)
     FNOCC_G(12, 32, 1, 1)
     FNOCC_G(13, 128, 1, 1)
-#define FNOCC_B(i, wm, wn, mt, nt) \
-  case kGShapeBf16 + i:           \
-    launch_bf16<wm, wn, mt, nt>(grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part); break;
+#define FNOCC_B(i, wm, wn, mt, nt)                                                                   \
+  case kGShapeBf16 + i:                                                                              \
+    launch_tensor<wm, wn, mt, nt>(L.precision, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part); \
+    break;
     FNOCC_B(0, 2, 4, 2, 2)
     FNOCC_B(1, 2, 4, 1, 1)
     FNOCC_B(2, 8, 1, 1, 2)
@@ -438,7 +538,8 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0 + 1], L.stream));
     pr->pairs.push_back({e0, e0 + 1});
     pr->flops.push_back(g.flops);
-    pr->path.push_back((g.shape >= kGShapeBf16 ? 4 : 0) + (g.nsplit > 0 ? 1 : 0));
+    const int base = g.shape < kGShapeBf16 ? 0 : (L.precision == 2 ? 6 : 4);
+    pr->path.push_back(base + (g.nsplit > 0 ? 1 : 0));
     if (pr->pairs.size() >= 4096) pr->fold();
   }
 }
