@@ -288,6 +288,64 @@ def run_batch(args):
                       "data": "synthetic"}), flush=True)
 
 
+# larger system for the split-product accuracy check: 41 kept natural virtuals
+PC_NE, PC_NORB, PC_THRESHOLD, PC_ROOTS, PC_VARIANTS = 16, 80, 1e-6, 6, ("ip", "ea")
+
+
+def run_precision_check(args):
+    """Accuracy and speed of the split-product kinds on the larger system
+    (16 electrons / 80 orbitals, FNO occupation >= 1e-6: 41 kept natural
+    virtuals, o = 16 and v = 82 spin orbitals), 6 roots of IP and EA.
+    CCSDT in FP64, then in BF16x3 with FP64 refinement below 1e-6 (both from
+    MP2 amplitudes); then every variant's Davidson solve in FP64 (residual
+    1e-8) and kept in each split kind throughout (residual 1e-6, the 1e-6 Eh
+    target), each from the same converged amplitudes. Reports per-root total
+    energy errors of the split kinds against the FP64 solve and wall-clock
+    seconds of the synchronous library calls; one JSON line per finished
+    part, then a summary line. DEA is left out at this size: its dense R3
+    work tensor alone is o^2 v^4 doubles (93 GB)."""
+    import paper_2509_14157_gb300 as pkg
+    import synth
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    h, eri = synth.hamiltonian(PC_NE, PC_NORB, seed=0)
+    ctx = pkg.Context(0)
+    t0 = time.perf_counter()
+    fi = ctx.fno_truncate(h, eri, PC_NE // 2, PC_THRESHOLD)
+    o, v, _ = ctx.dims()
+    summary = {"mode": "precision_check", "electrons": PC_NE, "orbitals": PC_NORB, "fno_threshold": PC_THRESHOLD,
+               "nkept": fi["nkept"], "o": o, "v": v, "roots": PC_ROOTS, "fno_seconds": time.perf_counter() - t0,
+               "data": "synthetic", "ccsdt": {}, "eom": {}}
+    for prec in ("fp64", "mixed"):
+        t0 = time.perf_counter()
+        r = ctx.ccsdt_solve(precision=prec, switch_tol=1e-6)
+        part = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "iters_mixed": r["iters_mixed"],
+                "e_corr": r["e_corr"], "converged": r["converged"]}
+        summary["ccsdt"][prec] = part
+        emit({"part": "ccsdt", "precision": prec, **part})
+    summary["ccsdt"]["e_corr_diff"] = summary["ccsdt"]["mixed"]["e_corr"] - summary["ccsdt"]["fp64"]["e_corr"]
+    for var in PC_VARIANTS:
+        res = {}
+        for prec in ("fp64", "mixed", "mixed_tf32"):
+            kw = (dict(precision="fp64") if prec == "fp64"
+                  else dict(precision=prec, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8))
+            t0 = time.perf_counter()
+            r = ctx.eom_solve(var, PC_ROOTS, **kw)
+            res[prec] = {"seconds": time.perf_counter() - t0, "sigma_calls": r["sigma_calls"],
+                         "converged": r["converged"], "energies": [float(x) for x in r["energies"]]}
+            emit({"part": "eom", "variant": var, "precision": prec, **res[prec]})
+        ref = np.asarray(res["fp64"]["energies"])
+        for prec in ("mixed", "mixed_tf32"):
+            err = np.asarray(res[prec]["energies"]) - ref
+            res[prec]["max_abs_err_eh"] = float(np.max(np.abs(err)))
+            res[prec]["speedup_vs_fp64"] = res["fp64"]["seconds"] / res[prec]["seconds"]
+        summary["eom"][var] = res
+    emit(summary)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,6 +363,8 @@ def main():
                     help="skip the mixed-precision + learned-guess arm of the default run")
     ap.add_argument("--batch", action="store_true",
                     help="many uneven independent systems: batched (one stream per worker) vs one at a time")
+    ap.add_argument("--precision-check", action="store_true",
+                    help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP and EA x 6 roots")
     ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS),
                     help="one sigma product at the workload's size (profiling case)")
     args = ap.parse_args()
@@ -314,6 +374,8 @@ def main():
         return run_sigma_only(args)
     if args.batch:
         return run_batch(args)
+    if args.precision_check:
+        return run_precision_check(args)
 
     import torch
     import torch.distributed as dist
