@@ -289,13 +289,13 @@ def run_batch(args):
 
 
 # larger system for the split-product accuracy check: 41 kept natural virtuals
-PC_NE, PC_NORB, PC_THRESHOLD, PC_ROOTS, PC_VARIANTS = 16, 80, 1e-6, 6, ("ip", "ea")
+PC_NE, PC_NORB, PC_THRESHOLD, PC_ROOTS, PC_VARIANTS = 16, 80, 1e-6, 6, ("ip", "ea", "dip")
 
 
 def run_precision_check(args):
     """Accuracy and speed of the split-product kinds on the larger system
     (16 electrons / 80 orbitals, FNO occupation >= 1e-6: 41 kept natural
-    virtuals, o = 16 and v = 82 spin orbitals), 6 roots of IP and EA.
+    virtuals, o = 16 and v = 82 spin orbitals), 6 roots of IP, EA and DIP.
     CCSDT in FP64, then in BF16x3 with FP64 refinement below 1e-6 (both from
     MP2 amplitudes); then every variant's Davidson solve in FP64 (residual
     1e-8) and kept in each split kind throughout (residual 1e-6, the 1e-6 Eh
@@ -364,7 +364,7 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="many uneven independent systems: batched (one stream per worker) vs one at a time")
     ap.add_argument("--precision-check", action="store_true",
-                    help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP and EA x 6 roots")
+                    help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
     ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS),
                     help="one sigma product at the workload's size (profiling case)")
     args = ap.parse_args()
