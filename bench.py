@@ -346,6 +346,65 @@ def run_precision_check(args):
     ctx.close()
 
 
+# learned-guess check: (electrons, orbitals, FNO threshold, variant) of the
+# evaluation systems, 8 roots each
+GC_SYSTEMS = ((16, 80, 1e-6, "dip"), (12, 60, 1e-4, "dea"))
+GC_ROOTS = 8
+
+
+def run_guess_check(args):
+    """Davidson starts at a matched 1e-6 Eh target: the guess network is
+    trained as in the default run (12 seeded systems with 6 or 8 electrons,
+    outside every timed region), then DIP on 16 electrons / 80 orbitals
+    (FNO 1e-6: 41 kept virtuals) and DEA on 12 electrons / 60 orbitals (FNO
+    1e-4: 17 kept virtuals; DEA's dense R3 work tensor grows as o^2 v^4),
+    8 roots each, BF16x3 products throughout (residual 1e-6), from the
+    diagonal, Koopmans and learned starts. Reports products, iterations,
+    wall-clock seconds and the largest root difference to the Koopmans
+    solve; one JSON line per finished solve, then a summary line."""
+    import paper_2509_14157_gb300 as pkg
+    from paper_2509_14157_gb300 import learned
+    import synth
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    t0 = time.perf_counter()
+    X, T, W, info = learned.training_set(learned.seeded_training_systems(12), list(VARIANTS), NROOTS)
+    net, hist = learned.train_guess_model(X, T, W, epochs=30, batch=2048)
+    training = {"seconds": time.perf_counter() - t0, "samples": int(X.shape[0]),
+                "systems": len(set(i[0] for i in info)), "final_loss": float(hist[-1])}
+    emit({"part": "training", **training})
+    summary = {"mode": "guess_check", "roots": GC_ROOTS, "precision": "mixed (BF16x3), residual 1e-6",
+               "training": training, "data": "synthetic", "systems": []}
+    for ne, norb, thr, var in GC_SYSTEMS:
+        h, eri = synth.hamiltonian(ne, norb, seed=0)
+        ctx = pkg.Context(0)
+        fi = ctx.fno_truncate(h, eri, ne // 2, thr)
+        o, v, _ = ctx.dims()
+        cc = ctx.ccsdt_solve(precision="mixed", switch_tol=1e-6)
+        ctx.set_guess_model(net)
+        res = {}
+        for guess in ("diagonal", "koopmans", "learned"):
+            t0 = time.perf_counter()
+            r = ctx.eom_solve(var, GC_ROOTS, guess=guess, precision="mixed", switch_tol=0.0, tol_res=1e-6,
+                              tol_e=1e-8)
+            res[guess] = {"seconds": time.perf_counter() - t0, "sigma_calls": r["sigma_calls"], "iters": r["iters"],
+                          "converged": r["converged"], "guess_used": r["guess_used"],
+                          "energies": [float(x) for x in r["energies"]]}
+            emit({"part": "eom", "electrons": ne, "variant": var, "guess": guess, **res[guess]})
+        ref = np.asarray(res["koopmans"]["energies"])
+        for guess in res:
+            res[guess]["max_root_diff_to_koopmans_eh"] = float(np.max(np.abs(np.asarray(res[guess]["energies"]) - ref)))
+        summary["systems"].append({"electrons": ne, "orbitals": norb, "fno_threshold": thr, "nkept": fi["nkept"],
+                                   "o": o, "v": v, "variant": var, "ccsdt_converged": cc["converged"],
+                                   "solves": res})
+        ctx.set_guess_model(None)
+        ctx.close()
+    net.close()
+    emit(summary)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,6 +422,9 @@ def main():
                     help="skip the mixed-precision + learned-guess arm of the default run")
     ap.add_argument("--batch", action="store_true",
                     help="many uneven independent systems: batched (one stream per worker) vs one at a time")
+    ap.add_argument("--guess-check", action="store_true",
+                    help="diagonal vs Koopmans vs learned Davidson start at a matched 1e-6 Eh target, 8 roots of "
+                         "DIP (16 electrons) and DEA (12 electrons)")
     ap.add_argument("--precision-check", action="store_true",
                     help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
     ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS),
@@ -376,6 +438,8 @@ def main():
         return run_batch(args)
     if args.precision_check:
         return run_precision_check(args)
+    if args.guess_check:
+        return run_guess_check(args)
 
     import torch
     import torch.distributed as dist
