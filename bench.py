@@ -261,19 +261,38 @@ def batch_systems(count=16):
     return out
 
 
+def batch_systems_large(count=32):
+    """Uneven seeded systems of the larger batch: 6-14 electrons, 20-40 kept
+    natural virtuals (nkeep), 8 dropped virtuals beyond them."""
+    import synth
+    out = []
+    for s in range(count):
+        ne = 6 + 2 * (s % 5)
+        kept = 20 + (13 * s) % 21
+        h, eri = synth.hamiltonian(ne, ne // 2 + kept + 8, seed=200 + s)
+        out.append(dict(h=h, eri=eri, nocc=ne // 2, nkeep=kept))
+    return out
+
+
 def run_batch(args):
-    """Throughput over many independent systems (IP and EA x 3 roots each):
-    fnocc_batch_solve with 4 workers (one context and stream each) against
-    the same call with one worker. Every system's roots must agree."""
+    """Throughput over many independent systems: fnocc_batch_solve with 4
+    workers (one context and stream each) against the same call with one
+    worker. Every system's roots must agree. Default: 16 small systems, IP
+    and EA x 3 roots, FP64. --batch-large: 32 systems of 6-14 electrons and
+    20-40 kept virtuals, IP and EA x 4 roots, BF16x3 products with FP64
+    refinement (CCSDT below 1e-6, Davidson below 1e-5)."""
     import paper_2509_14157_gb300 as pkg
-    systems = batch_systems()
+    large = args.batch_large
+    systems = batch_systems_large() if large else batch_systems()
     variants = ["ip", "ea"]
-    pkg.batch_solve(systems[:2], variants, BATCH_ROOTS, nworkers=2)  # warm: library, plans
+    nroots = 4 if large else BATCH_ROOTS
+    prec = "mixed" if large else "fp64"
+    pkg.batch_solve(systems[:2], variants, nroots, nworkers=2, precision=prec)  # warm: library, plans
     t0 = time.perf_counter()
-    om1, info1 = pkg.batch_solve(systems, variants, BATCH_ROOTS, nworkers=1)
+    om1, info1 = pkg.batch_solve(systems, variants, nroots, nworkers=1, precision=prec)
     t_seq = time.perf_counter() - t0
     t0 = time.perf_counter()
-    om4, info4 = pkg.batch_solve(systems, variants, BATCH_ROOTS, nworkers=4)
+    om4, info4 = pkg.batch_solve(systems, variants, nroots, nworkers=4, precision=prec)
     t_bat = time.perf_counter() - t0
     ok = [i for i, (a, b) in enumerate(zip(info1, info4)) if a["status"] == 0 and b["status"] == 0]
     solves = len(ok) * len(variants)
@@ -283,8 +302,11 @@ def run_batch(args):
                       "speedup": t_seq / t_bat if t_bat > 0 else None, "systems": len(systems),
                       "converged_systems": len(ok), "statuses": [i["status"] for i in info4],
                       "workers": 4, "max_root_diff_eh": diff,
-                      "config": {"workload": "16 seeded systems, 8/10/12 electrons, 8-14 kept natural virtuals "
-                                             "(nkeep), IP and EA x 3 roots", "precision": "fp64"},
+                      "config": ({"workload": "32 seeded systems, 6-14 electrons, 20-40 kept natural virtuals "
+                                              "(nkeep), IP and EA x 4 roots",
+                                  "precision": "BF16x3 products, FP64 refinement"} if large else
+                                 {"workload": "16 seeded systems, 8/10/12 electrons, 8-14 kept natural virtuals "
+                                              "(nkeep), IP and EA x 3 roots", "precision": "fp64"}),
                       "data": "synthetic"}), flush=True)
 
 
@@ -422,6 +444,9 @@ def main():
                     help="skip the mixed-precision + learned-guess arm of the default run")
     ap.add_argument("--batch", action="store_true",
                     help="many uneven independent systems: batched (one stream per worker) vs one at a time")
+    ap.add_argument("--batch-large", action="store_true",
+                    help="with --batch: 32 systems of 6-14 electrons and 20-40 kept virtuals, IP/EA x 4 roots, "
+                         "BF16x3 with FP64 refinement")
     ap.add_argument("--guess-check", action="store_true",
                     help="diagonal vs Koopmans vs learned Davidson start at a matched 1e-6 Eh target, 8 roots of "
                          "DIP (16 electrons) and DEA (12 electrons)")
