@@ -612,8 +612,15 @@ ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][
 }
 
 // Uploads the flat tables, then builds for every grouped step and tile shape
-// its GTask array: tiles, a split of the reduction when the step has fewer
-// tiles than two per SM, CTA, partial and reduction offsets.
+// its GTask array: tiles, a split of the reduction when the step has few
+// tiles, CTA, partial and reduction offsets.
+//
+// FP64 tiles are FMA-bound and several CTAs share an SM's FP64 pipe, so a
+// launch of c roughly equal CTAs that are all resident at once takes about
+// ceil(c / 152) CTA-times. The reduction split of the FP64 shapes starts
+// from two CTAs per SM and grows, up to about four per SM, while that lowers
+// ceil(c / 152) / c by more than 1 %; the shape estimate carries the same
+// factor.
 void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
   if (flat_host.empty()) return;
   const long long *fb;
@@ -625,8 +632,12 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
     FNOCC_CUDA(cudaMemcpy(flat_.p, flat_host.data(), sizeof(long long) * flat_host.size(), cudaMemcpyHostToDevice));
     fb = flat_.as<long long>();
   }
-  constexpr long long kWantCta = 2 * 152;
+  constexpr long long kSms = 152;
+  constexpr long long kWantCta = 2 * kSms;   // at least two CTAs per SM where the tiles allow
+  constexpr long long kFillCta = 4 * kSms;   // FP64 shapes: split at most up to four CTAs per SM
   constexpr long long kPartCap = 1LL << 27;  // doubles of split partials per launch
+  // CTA-times per CTA of a launch of c equal resident CTAs (smaller is better)
+  auto wave_cost = [](long long c) { return double((c + kSms - 1) / kSms) / double(std::max<long long>(1, c)); };
   std::vector<GTask> gt;
   std::vector<int> sid;
   struct Fix { GroupedLaunch *gl; size_t t0, s0; };
@@ -640,7 +651,15 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
         grouped_shape(shape, &tbm, &tbn, &tbk);
         long long T = 0;
         for (auto &tr : e.tasks) T += ((tr.M + tbm - 1) / tbm) * ((tr.N + tbn - 1) / tbn);
-        const long long want = T < kWantCta ? (kWantCta + T - 1) / T : 1;
+        // at least two CTAs per SM where the tiles allow it (one CTA's
+        // gathers overlap another's multiply-adds)
+        T = std::max<long long>(T, 1);
+        long long want = T < kWantCta ? (kWantCta + T - 1) / T : 1;
+        if (shape < kGShapeBf16 && T < kFillCta) {
+          const long long wmax = (kFillCta + T - 1) / T;
+          for (long long w = want + 1; w <= wmax; ++w)
+            if (wave_cost(T * w) < 0.99 * wave_cost(T * want)) want = w;
+        }
         GroupedLaunch &gl = e.gl[shape];
         gl.shape = shape;
         gl.ntasks = (int)e.tasks.size();
@@ -693,7 +712,7 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
         gl.padded = padded;
         gl.flops = flops;
         if (shape < kGShapeBf16) {
-          est[shape] = padded / double(std::max<long long>(1, std::min<long long>(cta, 152)));
+          est[shape] = padded * wave_cost(cta);
         } else {
           // tensor-core tiles: the cost is staging (gather, convert, split) of
           // the (tbm + tbn) x tbk operand panels of every K tile, two CTAs per SM
