@@ -482,8 +482,6 @@ std::vector<std::vector<int>> factor_anti_groups(const Factor &f) {
 
 bool contains(const std::vector<int> &v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
-double dim_of(int lab, int o, int v) { return lab_space(lab) == SP_O ? o : v; }
-
 double binom(int n, int k) {
   if (k < 0 || k > n) return 0;
   double r = 1;
