@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import cc, eom, fno, packing, wick, xfno
+from oracle import eom, fno, packing, wick, xfno
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 pkg = pytest.importorskip("paper_2509_14157_gb300")
