@@ -19,6 +19,7 @@ Between timed steps L2 is flushed by writing a 512 MB buffer.
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import math
@@ -515,15 +516,19 @@ def main():
         eom_kw = dict(eom_kw, guess="learned")
 
     def step(device_inputs, prec=args.precision, kw=eom_kw):
+        t0 = time.perf_counter()
         if device_inputs:
             ctx.fno_truncate_dev(h_dev.data_ptr(), eri_dev.data_ptr(), NORB, nocc, args.threshold)
         else:
             ctx.fno_truncate(h, eri, nocc, args.threshold)
+        counts["fno_seconds"] = round(time.perf_counter() - t0, 4)
         f0 = ctx.flops
         res = ctx.ccsdt_solve(precision=prec)
         if not res["converged"]:
             raise RuntimeError("CCSDT did not converge")
         counts["cc_iters"] = res["iters"]
+        counts["ccsdt_seconds"] = round(res["seconds"], 4)
+        counts["ccsdt_seconds_per_iter"] = round(res["seconds_per_iter"], 5)
         counts["flops_per_residual"] = (ctx.flops - f0) / max(1, res["iters"])
         out = {}
         for var in VARIANTS:
@@ -534,7 +539,8 @@ def main():
                 raise RuntimeError("%s-EOM did not converge" % var)
             counts["sigma"][var] = r["sigma_calls"]
             counts["detail"][var] = {"iters": r["iters"], "res_max": r["res_max"],
-                                     "complex_roots": r["complex_roots"], "seconds": round(r["seconds"], 3)}
+                                     "complex_roots": r["complex_roots"], "seconds": round(r["seconds"], 3),
+                                     "seconds_per_iter": round(r["seconds_per_iter"], 5)}
             out[var] = r["energies"]
         return res, out
 
@@ -584,6 +590,8 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_times)
     e2e_total = max_over_ranks(e2e_total, world, dev)
+    # solver statistics of the timed path (the arms below reuse `counts`)
+    path_counts = copy.deepcopy(counts)
     accuracy = None
     if args.precision != "fp64":
         # every root against the same solve in FP64 (outside the timed region)
@@ -673,11 +681,14 @@ def main():
         **({"mixed_learned": mixed_learned} if mixed_learned else {}),
         **({"guess": "learned", "guess_training": {k: v for k, v in guess_net.items() if k != "net"}}
            if args.guess == "learned" else {}),
-        "solver": {"ccsdt_iters": counts["cc_iters"], "sigma_calls": counts["sigma"], "eom": counts["detail"],
-                   "flops_per_residual": counts["flops_per_residual"], "flops_per_sigma": counts["flops_per_sigma"]},
+        "solver": {"fno_seconds": path_counts["fno_seconds"], "ccsdt_seconds": path_counts["ccsdt_seconds"],
+                   "ccsdt_seconds_per_iter": path_counts["ccsdt_seconds_per_iter"],
+                   "ccsdt_iters": path_counts["cc_iters"], "sigma_calls": path_counts["sigma"],
+                   "eom": path_counts["detail"], "flops_per_residual": path_counts["flops_per_residual"],
+                   "flops_per_sigma": path_counts["flops_per_sigma"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.threshold, counts)
+        line["cpu_baseline"] = cpu_baseline(args.threshold, path_counts)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
