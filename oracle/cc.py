@@ -5,8 +5,8 @@ of Eq. 7 come from the Wick term lists of oracle/wick.py evaluated on dense
 antisymmetric tensors. The equations keep f_ov and off-diagonal Fock blocks,
 so they hold for any reference (needed for the 3-electron FCI pin).
 
-Solver (reading Z11 of the paper's silent points: "the" solution is the one
-reached from T1 = 0, T2 = MP2, T3 = 0): Jacobi steps T += R / D with
+Solver (the paper does not say which CC solution it means; the reading here
+is the one reached from T1 = 0, T2 = MP2, T3 = 0): Jacobi steps T += R / D with
 orbital-energy denominators from diag(f), accelerated by DIIS on the packed
 amplitudes, until max|R| < tol_res and |dE| < tol_e.
 

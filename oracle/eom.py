@@ -1,16 +1,19 @@
 """Oracle: IP / EA / DIP / DEA EOM-CCSDT (Eq. 1-4) and the Davidson solver.
 
-Operator spaces (reading Z2 of the paper's silent points: every variant has
-three components; removal uses n = m..m+2 holes, attachment n = 0..2):
+Operator spaces (Eq. 3-4 as printed would drop 1p / 2p for attachment and
+4h2p for DIP; the reading here: every variant has three components, removal
+uses n = m..m+2 holes, attachment n = 0..2):
     IP  1h, 2h1p, 3h2p        EA  1p, 1h2p, 2h3p
     DIP 2h, 3h1p, 4h2p        DEA 2p, 1h3p, 2h4p
+and the excitation-energy variant the method builds on (Sec. 1):
+    EE  1h1p, 2h2p, 3h3p (M_s unchanged)
 sigma = <mu| (H-bar R)_c |Phi_0> from the Wick term lists (oracle/wick.py);
 the eigenvalue omega is the energy relative to the CC ground state, so the
 state's total energy is E_CC + omega.
 
-Spin sector (reading Z9): 2*M_s change of +1 for IP (a beta electron is
-removed) and EA (an alpha electron is added), 0 for DIP and DEA. The roots are
-the lowest Re(omega) in that sector.
+Spin sector (the paper names none): 2*M_s change of +1 for IP (a beta
+electron is removed) and EA (an alpha electron is added), 0 for DIP, DEA and
+EE. The roots are the lowest Re(omega) in that sector.
 
 Davidson (the paper names no eigensolver; this follows the standard
 non-symmetric Davidson method): orthonormal subspace V, projected matrix
@@ -35,7 +38,7 @@ import numpy as np
 
 from . import packing, wick
 
-SECTOR_MS2 = {"ip": 1, "ea": 1, "dip": 0, "dea": 0}
+SECTOR_MS2 = {"ip": 1, "ea": 1, "dip": 0, "dea": 0, "ee": 0}
 
 
 def comps(variant):

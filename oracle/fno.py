@@ -137,7 +137,8 @@ def mp2_vv_density(f, g, o):
 
 
 def choose_kept(occ_sorted, threshold, criterion="abs", nkeep=0, degen_rel=1e-10):
-    """Number of natural virtuals kept (Sec. 1.2 truncation; readings Z3-Z5).
+    """Number of natural virtuals kept (Sec. 1.2 truncation; the paper defines
+    neither of its two schemes, so both readings are offered below).
 
     occ_sorted: occupations in descending order.
     criterion 'abs': keep n_a >= threshold; 'occt': smallest prefix whose

@@ -290,11 +290,15 @@ def cc_terms(nh, t_ranks=(1, 2, 3)):
 
 # EOM operator spaces (reading of Eq. 3-4: three components per variant)
 #   variant -> list of (holes, particles) of R1, R2, R3
+# "ee" is the excitation-energy EOM-CCSDT (1h1p, 2h2p, 3h3p) that the
+# paper's Sec. 1 builds the particle-number-changing variants on; the same
+# product <mu| (H-bar R)_c |0> applies, R being an excitation operator.
 EOM_SPACES = {
     "ip": [(1, 0), (2, 1), (3, 2)],
     "ea": [(0, 1), (1, 2), (2, 3)],
     "dip": [(2, 0), (3, 1), (4, 2)],
     "dea": [(0, 2), (1, 3), (2, 4)],
+    "ee": [(1, 1), (2, 2), (3, 3)],
 }
 
 

@@ -2,7 +2,7 @@
 
 The paper extrapolates FNO energies obtained at three truncation thresholds
 towards the untruncated limit, but prints no formula (the fit data sit in its
-unavailable Supplementary Information). Reading Z8: a least-squares straight
+unavailable Supplementary Information). The reading here: a least-squares straight
 line E(f) through the points (f_k, E_k), where f_k is the fraction of the total
 natural-orbital occupation that was kept, evaluated at f = 1. It is applied to
 every total energy independently.

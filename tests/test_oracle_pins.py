@@ -5,7 +5,7 @@ and by mathematics, independent of the oracle's own formulas.
     against the Fock-space definition on random amplitudes (oracle/detspace.py);
   * CCSDT = FCI for three electrons; EOM-CCSDT = FCI for every root where
     the operator space spans the whole (N +- m) sector (IP, EA, DEA from two
-    electrons, DIP from four);
+    electrons, DIP from four; EE from two, its excited states);
   * MP2 energy and virtual-virtual density (Eq. 8-10) against second-order
     perturbation theory written out in determinant space;
   * RHF stationarity; invariance of CCSDT under the FNO rotation at
@@ -68,7 +68,7 @@ def test_cc_energy_equals_definition(small_system):
     assert abs(e - dso.cc_energy(amps, ham["e_ref"])) < 1e-12
 
 
-@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
 def test_eom_sigma_equals_definition(small_system, variant):
     ham, amps, dso = small_system
     o, v = ham["o"], ham["v"]
@@ -136,6 +136,17 @@ def test_eom_two_electron_reference_is_fci(two_electron, variant, nelec, ms2):
     roots, dim = _dense_roots(variant, act, res, len(fci))
     assert dim == len(fci)  # the operator space spans the whole sector
     assert np.max(np.abs(roots - fci)) < 1e-8
+
+
+def test_ee_two_electron_reference_is_fci(two_electron):
+    """EE from a two-electron reference: 1h1p and 2h2p span every other
+    determinant of the N = 2, M_s = 0 sector, so E_CC + omega are the excited
+    FCI energies (the ground state is the reference's own root)."""
+    act, res = two_electron
+    fci = detspace.fci_energies(act["hso"], act["g"], 2, 0)
+    roots, dim = _dense_roots("ee", act, res, len(fci) - 1)
+    assert dim == len(fci) - 1
+    assert np.max(np.abs(roots - fci[1:])) < 1e-8
 
 
 def test_dip_four_electron_reference_is_fci():
@@ -268,7 +279,7 @@ def test_size_extensivity_of_ccsdt():
     assert abs(e["ab"] - e["a"] - e["b"]) < 1e-10
 
 
-@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
 def test_noninteracting_limit_is_koopmans(variant):
     n, nocc = 5, 2
     eps = np.array([-1.3, -0.7, 0.4, 0.9, 1.6])
