@@ -20,6 +20,7 @@
  *     T_n has nh = np = n. EOM components (R1, R2, R3) per variant:
  *       IP  (1,0) (2,1) (3,2)     EA  (0,1) (1,2) (2,3)
  *       DIP (2,0) (3,1) (4,2)     DEA (0,2) (1,3) (2,4)
+ *       EE  (1,1) (2,2) (3,3)
  *     An EOM vector is R1, R2, R3 concatenated.
  *   - Operator normalisation: T_n = (1/n!)^2 sum t a^+..i and
  *     R = 1/(nh! np!) sum r a^+..a^+ i..i, i.e. one packed coefficient per
@@ -57,7 +58,9 @@ typedef enum {
   FNOCC_E_TIMEOUT = -6       /* a bounded device wait expired */
 } fnocc_status;
 
-typedef enum { FNOCC_IP = 0, FNOCC_EA = 1, FNOCC_DIP = 2, FNOCC_DEA = 3 } fnocc_variant;
+/* EE: excitation energies (the N-conserving EOM-CCSDT of Sec. 1 that the
+ * four particle-number-changing variants build on). */
+typedef enum { FNOCC_IP = 0, FNOCC_EA = 1, FNOCC_DIP = 2, FNOCC_DEA = 3, FNOCC_EE = 4 } fnocc_variant;
 /* KOOPMANS (recommended): unit vectors on the lowest diagonal entries of the
  * principal block; DIAGONAL: of the whole space (its non-principal unit
  * vectors also carry spin multiplicities the principal block cannot form);
@@ -188,9 +191,9 @@ fnocc_status ccsdt_residual_dev(fnocc_ctx *ctx, const double *t1, const double *
 
 /* EOM-CCSDT (Eq. 1-4) ----------------------------------------------------------
  * Lowest nroots roots (by real part) of H-bar in the variant's operator space
- * and target spin sector (IP, EA: 2*dM_s = +1; DIP, DEA: 0), by
+ * and target spin sector (IP, EA: 2*dM_s = +1; DIP, DEA, EE: 0), by
  * non-symmetric Davidson. Roots are counted among eigenstates with weight
- * >= 1e-6 in the principal block (1h, 1p, 2h or 2p): the sector also holds
+ * >= 1e-6 in the principal block (1h, 1p, 2h, 2p or 1h1p): the sector also holds
  * states of spin multiplicities the principal block cannot form (quartet
  * 2h1p of IP, quintet 3h1p of DIP, ...), which have no principal weight and
  * which a Davidson started on principal determinants reaches only through
@@ -206,7 +209,7 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *ctx, int variant, int nroots, int guess,
 fnocc_status fnocc_set_precision(fnocc_ctx *ctx, int precision);
 
 /* sigma = (H-bar R)_c for a packed EOM vector (host pointers). R is taken in
- * the variant's target spin sector (2*dM_s = +1 for IP/EA, 0 for DIP/DEA):
+ * the variant's target spin sector (2*dM_s = +1 for IP/EA, 0 for DIP/DEA/EE):
  * components outside it do not contribute, and sigma is returned in that
  * sector (zero elsewhere). Likewise every call treats ground-state amplitudes
  * as M_s-conserving. */

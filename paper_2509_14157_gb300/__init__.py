@@ -14,8 +14,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfnocc.so")
 
-IP, EA, DIP, DEA = 0, 1, 2, 3
-VARIANTS = {"ip": IP, "ea": EA, "dip": DIP, "dea": DEA}
+IP, EA, DIP, DEA, EE = 0, 1, 2, 3, 4
+VARIANTS = {"ip": IP, "ea": EA, "dip": DIP, "dea": DEA, "ee": EE}
 GUESS = {"koopmans": 0, "diagonal": 1, "learned": 2}
 CRITERIA = {"abs": 0, "occt": 1}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_tf32": 2}  # mixed: BF16 three-slice split

@@ -167,7 +167,7 @@ struct fnocc_ctx {
   std::vector<double> virt_occ;
 
   // EOM
-  std::unique_ptr<ExecEquation> eom_eq[4][3][3];
+  std::unique_ptr<ExecEquation> eom_eq[kEomVariants][3][3];
   DevBuf rd[3], sy[3];
   uint64_t hbar_version = 0;
   // the dressed operators and dense T2/T3 hold the stored amplitudes' H-bar
@@ -175,7 +175,7 @@ struct fnocc_ctx {
   bool hbar_valid = false;
   int plan_o = -1, plan_v = -1;  // shape the contraction plans were built for
   int cache_precision = 0;  // arithmetic of the cached R-independent intermediates
-  uint64_t eq_seen[4][3][3] = {};  // H-bar version whose cached flops were counted
+  uint64_t eq_seen[kEomVariants][3][3] = {};  // H-bar version whose cached flops were counted
   int last_variant = -1, last_nroots = 0;
   size_t last_dim = 0;
   DevBuf eom_vecs;
@@ -229,8 +229,11 @@ long long ipow(long long b, int e) {
   return r;
 }
 
-const int kEom[4][3][2] = {{{1, 0}, {2, 1}, {3, 2}}, {{0, 1}, {1, 2}, {2, 3}}, {{2, 0}, {3, 1}, {4, 2}}, {{0, 2}, {1, 3}, {2, 4}}};
-const int kSectorMs2[4] = {1, 1, 0, 0};
+// (holes, particles) of R1, R2, R3 per variant (IP, EA, DIP, DEA, EE) and the
+// sector's 2*M_s change
+const int kEom[kEomVariants][3][2] = {{{1, 0}, {2, 1}, {3, 2}}, {{0, 1}, {1, 2}, {2, 3}}, {{2, 0}, {3, 1}, {4, 2}},
+                                      {{0, 2}, {1, 3}, {2, 4}}, {{1, 1}, {2, 2}, {3, 3}}};
+const int kSectorMs2[kEomVariants] = {1, 1, 0, 0, 0};
 // R-independent EOM intermediates are cached per H-bar: the planner charges
 // them 1/kSigmaAmortize of their cost (a Davidson solve takes ~100 products);
 // one cached intermediate may hold at most 2^28 doubles (2 GiB).
@@ -1204,7 +1207,7 @@ fnocc_status fnocc_set_precision(fnocc_ctx *c, int precision) {
 }
 
 fnocc_status fnocc_eom_sizes(const fnocc_ctx *c, int variant, size_t *sizes) {
-  if (!c || !sizes || variant < 0 || variant > 3) return FNOCC_E_INVALID;
+  if (!c || !sizes || variant < 0 || variant >= kEomVariants) return FNOCC_E_INVALID;
   if (!c->have_ham) return FNOCC_E_STATE;
   eom_sizes(c, variant, sizes);
   return FNOCC_OK;
@@ -1213,7 +1216,7 @@ fnocc_status fnocc_eom_sizes(const fnocc_ctx *c, int variant, size_t *sizes) {
 fnocc_status eom_sigma_dev(fnocc_ctx *c, int variant, const double *r, double *s) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
-    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    if (variant < 0 || variant >= kEomVariants) throw StatusError(FNOCC_E_INVALID, "bad variant");
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     prepare_hbar(c);
@@ -1228,7 +1231,7 @@ fnocc_status eom_sigma_dev(fnocc_ctx *c, int variant, const double *r, double *s
 fnocc_status eom_sigma(fnocc_ctx *c, int variant, const double *r, double *s) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
-    if (variant < 0 || variant > 3 || !r || !s) throw StatusError(FNOCC_E_INVALID, "bad argument");
+    if (variant < 0 || variant >= kEomVariants || !r || !s) throw StatusError(FNOCC_E_INVALID, "bad argument");
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     size_t sz[3];
@@ -1272,7 +1275,7 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
                             double *energies, double *omegas, eom_info *out) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
-    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    if (variant < 0 || variant >= kEomVariants) throw StatusError(FNOCC_E_INVALID, "bad variant");
     if (nroots <= 0 || !energies) throw StatusError(FNOCC_E_INVALID, "bad nroots or null energies");
     if (guess != FNOCC_GUESS_KOOPMANS && guess != FNOCC_GUESS_DIAGONAL && guess != FNOCC_GUESS_LEARNED)
       throw StatusError(FNOCC_E_INVALID, "bad guess");
@@ -1620,7 +1623,7 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, c
 fnocc_status fnocc_eom_features(fnocc_ctx *c, int variant, float *features) {
   if (!c || !features) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
-    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    if (variant < 0 || variant >= kEomVariants) throw StatusError(FNOCC_E_INVALID, "bad variant");
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     size_t sz[3];
@@ -1638,7 +1641,7 @@ fnocc_status fnocc_eom_features(fnocc_ctx *c, int variant, float *features) {
 fnocc_status fnocc_eom_diagonal(fnocc_ctx *c, int variant, double *diag) {
   if (!c || !diag) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
-    if (variant < 0 || variant > 3) throw StatusError(FNOCC_E_INVALID, "bad variant");
+    if (variant < 0 || variant >= kEomVariants) throw StatusError(FNOCC_E_INVALID, "bad variant");
     require_ham(c);
     FNOCC_CUDA(cudaSetDevice(c->device));
     prepare_hbar(c);
@@ -1727,7 +1730,7 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
                                double *omegas, fnocc_system_result *results) {
   if (nsys <= 0 || !systems || nvariants <= 0 || !variants || nroots <= 0 || !omegas) return FNOCC_E_INVALID;
   for (int k = 0; k < nvariants; ++k)
-    if (variants[k] < 0 || variants[k] > 3) return FNOCC_E_INVALID;
+    if (variants[k] < 0 || variants[k] >= kEomVariants) return FNOCC_E_INVALID;
   for (int s = 0; s < nsys; ++s)
     if (!systems[s].h || !systems[s].eri || systems[s].n <= 1 || systems[s].nocc <= 0 || systems[s].nocc >= systems[s].n)
       return FNOCC_E_INVALID;
@@ -1797,7 +1800,7 @@ long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char 
       if (out_comp < 0 || out_comp > 3) return -1;
       s = equation_to_string(cc_equation(out_comp));
     } else if (kind == 1) {
-      if (variant < 0 || variant > 3 || out_comp < 0 || out_comp > 2 || in_comp < 0 || in_comp > 2) return -1;
+      if (variant < 0 || variant >= kEomVariants || out_comp < 0 || out_comp > 2 || in_comp < 0 || in_comp > 2) return -1;
       s = equation_to_string(eom_equation(variant, out_comp, in_comp));
     } else {
       return -1;
@@ -1816,21 +1819,18 @@ long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char 
 long fnocc_plan_selfcheck(int kind, int variant, int out_comp, int in_comp, int o, int v, double max_work) {
   try {
     if (o <= 0 || v <= 0 || o > 64 || v > 128) return -1;
-    static const int kSpace[4][3][2] = {{{1, 0}, {2, 1}, {3, 2}}, {{0, 1}, {1, 2}, {2, 3}},
-                                        {{2, 0}, {3, 1}, {4, 2}}, {{0, 2}, {1, 3}, {2, 4}}};
-    static const int kMs2[4] = {1, 1, 0, 0};
     int rd[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     if (kind == 0 && out_comp >= 0 && out_comp <= 3) {
       ExecEquation e(cc_equation(out_comp), o, v, rd, 0.0, 0.0, 0, true);
       return (long)e.self_check(max_work);
     }
-    if (kind == 1 && variant >= 0 && variant <= 3 && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2) {
+    if (kind == 1 && variant >= 0 && variant < kEomVariants && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2) {
       for (int k = 0; k < 3; ++k) {
-        rd[k][0] = kSpace[variant][k][0];
-        rd[k][1] = kSpace[variant][k][1];
+        rd[k][0] = kEom[variant][k][0];
+        rd[k][1] = kEom[variant][k][1];
       }
       ExecEquation e(eom_equation(variant, out_comp, in_comp), o, v, rd, kSigmaAmortize, kCacheCapDoubles,
-                     kMs2[variant], true);
+                     kSectorMs2[variant], true);
       return (long)e.self_check(max_work);
     }
     return -1;
@@ -1846,7 +1846,7 @@ long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, in
     Equation eq;
     if (kind == 0 && out_comp >= 0 && out_comp <= 3)
       eq = cc_equation(out_comp);
-    else if (kind == 1 && variant >= 0 && variant <= 3 && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2)
+    else if (kind == 1 && variant >= 0 && variant < kEomVariants && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2)
       eq = eom_equation(variant, out_comp, in_comp);
     else
       return -1;

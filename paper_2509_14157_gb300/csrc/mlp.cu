@@ -272,7 +272,7 @@ uint64_t splitmix64(uint64_t &x) {
 // otherwise (the pair's <pq||pq> averaged over the spin of q); x2 highest
 // hole energy; x3 lowest particle energy; x4 mean particle energy; x5 sum over
 // particles of log10 of their virtual's natural occupation; x6 component
-// (0, 1, 2); x7 variant (0..3). Every feature depends on spatial orbitals
+// (0, 1, 2); x7 variant (0..4). Every feature depends on spatial orbitals
 // only, so a preconditioner built from them treats all spin couplings of a
 // spatial configuration alike. g: antisymmetrised <pq||rs> of the n active
 // spin orbitals (alpha even), occupied first.

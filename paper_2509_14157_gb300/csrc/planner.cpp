@@ -390,11 +390,12 @@ std::vector<TMulti> cluster_products(int maxn) {
   return out;
 }
 
-const int kEomSpaces[4][3][2] = {
+const int kEomSpaces[kEomVariants][3][2] = {
     {{1, 0}, {2, 1}, {3, 2}},  // IP
     {{0, 1}, {1, 2}, {2, 3}},  // EA
     {{2, 0}, {3, 1}, {4, 2}},  // DIP
     {{0, 2}, {1, 3}, {2, 4}},  // DEA
+    {{1, 1}, {2, 2}, {3, 3}},  // EE
 };
 
 }  // namespace

@@ -55,6 +55,8 @@ Equation cc_equation(int rank);
 // EOM: variant 0..3 (IP, EA, DIP, DEA), output component and input component (0..2).
 Equation eom_equation(int variant, int out_comp, int in_comp);
 // (nh, np) of component c of a variant.
+// EOM variants: 0 IP, 1 EA, 2 DIP, 3 DEA, 4 EE (excitation energies)
+constexpr int kEomVariants = 5;
 void eom_component(int variant, int comp, int *nh, int *np);
 
 std::string equation_to_string(const Equation &eq);

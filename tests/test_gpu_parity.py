@@ -86,7 +86,7 @@ def test_ccsdt_residual_zero_amplitudes(pkg):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
 def test_eom_sigma_random(pkg, variant):
     nocc, n = 3, 10
     h, eri = synth.random_symmetric_mo_hamiltonian(n, 29)
@@ -145,6 +145,23 @@ def test_ccsdt_and_eom_small_system(pkg):
     ctx.close()
 
 
+def test_ee_roots_small_system(pkg):
+    """Excitation energies (EE, 1h1p / 2h2p / 3h3p) of 4 electrons in 6
+    orbitals: three roots against the oracle's Davidson, solved live."""
+    h, eri = synth.hamiltonian(4, 6, seed=0)
+    ref = fno.fno_truncate(h, eri, 2, 0.0)
+    f, g, o, v = ref["f"], ref["g"], ref["o"], ref["v"]
+    rcc = cc.ccsdt(f, g, o, v)
+    rr = eom.eom_ccsdt("ee", f, g, o, v, rcc["t1"], rcc["t2"], rcc["t3"], 3)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, 2, 0.0)
+    assert ctx.ccsdt_solve()["converged"]
+    gr = ctx.eom_solve("ee", 3)
+    assert gr["converged"] and rr["converged"]
+    assert np.max(np.abs(gr["omegas"] - rr["omega"])) < E_TOL
+    ctx.close()
+
+
 def test_c1_solve_against_oracle_fixture(pkg):
     """6 electrons / 10 orbitals, FNO 1e-4, CCSDT and three roots of each
     variant, against values the oracle wrote (tests/golden/make_golden.py)."""
@@ -199,7 +216,7 @@ def test_c2_residual_sampled(c2_system):
         assert np.max(np.abs(got[r - 1][idx] - val)) < AMP_TOL, r
 
 
-@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
 def test_c2_sigma_sampled(c2_system, variant):
     ref, ctx = c2_system
     f, g, o, v = ref["f"], ref["g"], ref["o"], ref["v"]

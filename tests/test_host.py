@@ -122,7 +122,7 @@ def test_planner_cc_equations_match_oracle(system, rank):
     assert np.max(np.abs(got - ref)) < 1e-12
 
 
-@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
 def test_planner_eom_equations_match_oracle(system, variant):
     ham, t = system
     o, v = ham["o"], ham["v"]
@@ -152,7 +152,7 @@ def test_grouped_tasks_cover_the_spin_blocks_exactly(o, v):
     import paper_2509_14157_gb300 as pkg
     for rank in range(4):
         assert pkg.plan_selfcheck(0, 0, rank, 0, o, v) == 0, rank
-    for var in ("ip", "ea", "dip", "dea"):
+    for var in ("ip", "ea", "dip", "dea", "ee"):
         for oc in range(3):
             for ic in range(3):
                 assert pkg.plan_selfcheck(1, var, oc, ic, o, v) == 0, (var, oc, ic)

@@ -187,7 +187,7 @@ def test_cc_plans_execute_to_oracle(system, rank):
     assert np.max(np.abs(got - ref)) < 1e-12
 
 
-@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
 def test_eom_plans_execute_to_oracle(system, variant):
     ham, t = system
     o, v = ham["o"], ham["v"]
