@@ -214,6 +214,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_solve_only(args):
+    """One variant's converged solve at the workload's size: FNO, CCSDT, then
+    the variant's NROOTS lowest roots (warm-up solve first, then the timed
+    one); wall-clock seconds of the synchronous calls, products, iterations
+    and algorithmic flops."""
+    import paper_2509_14157_gb300 as pkg
+    import synth
+    h, eri = synth.hamiltonian(NE, NORB, seed=0)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, NE // 2, args.threshold)
+    kw = (dict(precision="fp64") if args.precision == "fp64"
+          else dict(precision=args.precision, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8))
+    cc = ctx.ccsdt_solve()
+    ctx.eom_solve(args.solve_only, NROOTS, **kw)
+    f0 = ctx.flops
+    t0 = time.perf_counter()
+    r = ctx.eom_solve(args.solve_only, NROOTS, **kw)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"solve_only": args.solve_only, "precision": args.precision, "seconds": dt,
+                      "sigma_calls": r["sigma_calls"], "iters": r["iters"], "converged": r["converged"],
+                      "omegas": [float(x) for x in r["omegas"]], "ccsdt_iters": cc["iters"],
+                      "tflops": (ctx.flops - f0) / dt / 1e12}), flush=True)
+    ctx.close()
+
+
 def run_sigma_only(args):
     """Profiling case: FNO setup, random amplitudes, two warm sigma products of
     one variant (the second with the R-independent intermediates cached, as
@@ -453,13 +478,17 @@ def main():
                          "DIP (16 electrons) and DEA (12 electrons)")
     ap.add_argument("--precision-check", action="store_true",
                     help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
-    ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS),
+    ap.add_argument("--solve-only", default=None, choices=list(VARIANTS) + ["ee"],
+                    help="FNO, CCSDT and one Davidson solve of this variant (4 roots) at the workload's size")
+    ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS) + ["ee"],
                     help="one sigma product at the workload's size (profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.sigma_only:
         return run_sigma_only(args)
+    if args.solve_only:
+        return run_solve_only(args)
     if args.batch:
         return run_batch(args)
     if args.precision_check:
