@@ -1742,14 +1742,20 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return systems[a].n > systems[b].n; });
   std::atomic<int> next(0);
   std::vector<fnocc_status> st(nsys, FNOCC_OK);
+  std::vector<char> attempted(nsys, 0);
+  std::atomic<int> create_status(FNOCC_OK);
+  // a worker whose context cannot be created leaves the queue to the others;
+  // systems no worker reached get that worker's status after the join
   auto worker = [&]() {
     fnocc_ctx *c = nullptr;
-    if (fnocc_create(&c, device, nullptr) != FNOCC_OK) {
-      for (int q; (q = next.fetch_add(1)) < nsys;) st[order[q]] = FNOCC_E_CUDA;
+    const fnocc_status cs = fnocc_create(&c, device, nullptr);
+    if (cs != FNOCC_OK) {
+      create_status.store(cs);
       return;
     }
     for (int q; (q = next.fetch_add(1)) < nsys;) {
       const int s = order[q];
+      attempted[s] = 1;
       const fnocc_system &sys = systems[s];
       Timer timer;
       fno_options fo{FNOCC_CRIT_ABS, sys.nkeep, 200, 1e-12, 1e-10};
@@ -1784,8 +1790,18 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
     fnocc_destroy(c);
   };
   std::vector<std::thread> pool;
-  for (int w = 0; w < nworkers; ++w) pool.emplace_back(worker);
+  try {
+    for (int w = 0; w < nworkers; ++w) pool.emplace_back(worker);
+  } catch (const std::exception &) {
+    // no more threads: the started workers drain the queue; none started, this one does
+  }
+  if (pool.empty()) worker();
   for (auto &t : pool) t.join();
+  for (int s = 0; s < nsys; ++s)
+    if (!attempted[s]) {
+      st[s] = create_status.load() != FNOCC_OK ? (fnocc_status)create_status.load() : FNOCC_E_CUDA;
+      if (results) results[s] = fnocc_system_result{st[s], 0, 0.0, 0.0, 0, 0, 0.0};
+    }
   fnocc_status out = FNOCC_OK;
   for (int s = 0; s < nsys; ++s)
     if (st[s] < 0) return st[s];
