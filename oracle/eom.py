@@ -262,3 +262,18 @@ def sigma_matrix(variant, f, g, o, v, t1, t2, t3):
         e[k] = 1.0
         cols.append(sigma_packed(variant, f, g, o, v, t1, t2, t3, e)[idx])
     return np.array(cols).T
+
+
+def left_sigma_packed(variant, f, g, o, v, t1, t2, t3, lvec):
+    """Left product lambda_nu = sum_mu L_mu <mu| (H-bar tau_nu)_c |0> (the row
+    vector L times the product matrix), written out from its definition: one
+    right product per element nu of the target sector, each dotted with L.
+    O(dim) products: small systems only. Elements outside the sector are 0."""
+    mask = ms_mask(variant, o, v)
+    out = np.zeros(len(mask))
+    e = np.zeros(len(mask))
+    for k in np.where(mask)[0]:
+        e[k] = 1.0
+        out[k] = lvec[mask] @ sigma_packed(variant, f, g, o, v, t1, t2, t3, e)[mask]
+        e[k] = 0.0
+    return out

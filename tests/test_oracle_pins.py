@@ -161,6 +161,33 @@ def test_dip_four_electron_reference_is_fci():
     assert np.max(np.abs(roots - fci)) < 1e-8
 
 
+def test_left_product_is_the_transposed_product(two_electron):
+    """The left product is L times the product matrix: its dense matrix is
+    the transpose of the right one, the left eigenvalues equal the right
+    ones, and left and right eigenvectors of distinct roots are
+    biorthogonal."""
+    act, res = two_electron
+    f, g, o, v = act["f"], act["g"], act["o"], act["v"]
+    variant = "ip"
+    mask = eom.ms_mask(variant, o, v)
+    idx = np.where(mask)[0]
+    m = eom.sigma_matrix(variant, f, g, o, v, res["t1"], res["t2"], res["t3"])
+    rng = np.random.default_rng(5)
+    lvec = np.zeros(len(mask))
+    lvec[idx] = rng.normal(size=len(idx))
+    lam = eom.left_sigma_packed(variant, f, g, o, v, res["t1"], res["t2"], res["t3"], lvec)
+    assert np.max(np.abs(lam[idx] - m.T @ lvec[idx])) < 1e-12
+    assert np.all(lam[~mask] == 0)
+    wr, vr = np.linalg.eig(m)
+    wl, vl = np.linalg.eig(m.T)
+    assert np.max(np.abs(np.sort(wr.real) - np.sort(wl.real))) < 1e-10
+    order_r, order_l = np.argsort(wr.real), np.argsort(wl.real)
+    overlap = vl[:, order_l].T @ vr[:, order_r]
+    off = overlap - np.diag(np.diag(overlap))
+    gaps = np.min(np.abs(np.subtract.outer(wr.real, wr.real)) + np.eye(len(wr)) * 1e9)
+    assert gaps > 1e-8 and np.max(np.abs(off)) < 1e-8
+
+
 def test_davidson_matches_dense_diagonalisation():
     h, eri = synth.hamiltonian(4, 5, seed=2)
     act = fno.fno_truncate(h, eri, 2, 0.0)
