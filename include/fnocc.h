@@ -364,7 +364,10 @@ fnocc_status fno_truncate_dev(fnocc_ctx *ctx, const double *h_dev, const double 
 /* Text of the term list the library derived for one projected equation
  * (host only, no GPU needed): kind 0 = CCSDT residual of rank out_comp
  * (0 = energy, 1..3), with variant and in_comp ignored; kind 1 = EOM product
- * block sigma_{out_comp} <- R_{in_comp} of `variant` (components 0..2).
+ * block sigma_{out_comp} <- R_{in_comp} of `variant` (components 0..2);
+ * kind 2 = left product block lambda_{out_comp} <- L_{in_comp}, the
+ * transpose of block sigma_{in_comp} <- R_{out_comp} (lambda = L times the
+ * product matrix; L enters as the factors r1..r3, not in the paper).
  * Terms are over the T1-similarity-transformed Hamiltonian (f, v) and T2, T3;
  * each line is "coef factor[...] ...", a representative of an orbit of
  * output-index permutations whose full antisymmetriser the caller applies.
@@ -372,11 +375,6 @@ fnocc_status fno_truncate_dev(fnocc_ctx *ctx, const double *h_dev, const double 
  * -1 on bad arguments. */
 long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char *buf, size_t len);
 
-/* Text of the contraction plan the library builds for the same equation
- * (host only): for every term its GEMM steps with their index groups
- * (packed or not), operands, intermediates and coefficients, planned with
- * the cost model at sizes (o, v); amortize > 0 marks R-independent steps as
- * cached. Same return convention as fnocc_equation_text. */
 /* Host-only consistency check of the executable plan of the same equation
  * at sizes (o, v) (not in the paper; a test of the library's own
  * bookkeeping): for every grouped contraction step with at most max_work
@@ -387,6 +385,11 @@ long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char 
  * inconsistencies (0 = consistent) or -1 on bad arguments. No GPU needed. */
 long fnocc_plan_selfcheck(int kind, int variant, int out_comp, int in_comp, int o, int v, double max_work);
 
+/* Text of the contraction plan the library builds for the same equation
+ * (host only): for every term its GEMM steps with their index groups
+ * (packed or not), operands, intermediates and coefficients, planned with
+ * the cost model at sizes (o, v); amortize > 0 marks R-independent steps as
+ * cached. Same return convention as fnocc_equation_text. */
 long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, int v, double amortize,
                      char *buf, size_t len);
 

@@ -1809,18 +1809,29 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
   return out;
 }
 
+namespace {
+
+// kind 0: CCSDT rank out_comp; 1: right EOM block; 2: left EOM block
+bool equation_of(int kind, int variant, int out_comp, int in_comp, Equation *eq) {
+  if (kind == 0) {
+    if (out_comp < 0 || out_comp > 3) return false;
+    *eq = cc_equation(out_comp);
+    return true;
+  }
+  if ((kind != 1 && kind != 2) || variant < 0 || variant >= kEomVariants || out_comp < 0 || out_comp > 2 ||
+      in_comp < 0 || in_comp > 2)
+    return false;
+  *eq = kind == 1 ? eom_equation(variant, out_comp, in_comp) : eom_left_equation(variant, out_comp, in_comp);
+  return true;
+}
+
+}  // namespace
+
 long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char *buf, size_t len) {
   try {
-    std::string s;
-    if (kind == 0) {
-      if (out_comp < 0 || out_comp > 3) return -1;
-      s = equation_to_string(cc_equation(out_comp));
-    } else if (kind == 1) {
-      if (variant < 0 || variant >= kEomVariants || out_comp < 0 || out_comp > 2 || in_comp < 0 || in_comp > 2) return -1;
-      s = equation_to_string(eom_equation(variant, out_comp, in_comp));
-    } else {
-      return -1;
-    }
+    Equation eq;
+    if (!equation_of(kind, variant, out_comp, in_comp, &eq)) return -1;
+    std::string s = equation_to_string(eq);
     if (buf && len > 0) {
       size_t n = std::min(len - 1, s.size());
       std::memcpy(buf, s.data(), n);
@@ -1840,16 +1851,14 @@ long fnocc_plan_selfcheck(int kind, int variant, int out_comp, int in_comp, int 
       ExecEquation e(cc_equation(out_comp), o, v, rd, 0.0, 0.0, 0, true);
       return (long)e.self_check(max_work);
     }
-    if (kind == 1 && variant >= 0 && variant < kEomVariants && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2) {
-      for (int k = 0; k < 3; ++k) {
-        rd[k][0] = kEom[variant][k][0];
-        rd[k][1] = kEom[variant][k][1];
-      }
-      ExecEquation e(eom_equation(variant, out_comp, in_comp), o, v, rd, kSigmaAmortize, kCacheCapDoubles,
-                     kSectorMs2[variant], true);
-      return (long)e.self_check(max_work);
+    Equation eq;
+    if (kind == 0 || !equation_of(kind, variant, out_comp, in_comp, &eq)) return -1;
+    for (int k = 0; k < 3; ++k) {
+      rd[k][0] = kEom[variant][k][0];
+      rd[k][1] = kEom[variant][k][1];
     }
-    return -1;
+    ExecEquation e(eq, o, v, rd, kSigmaAmortize, kCacheCapDoubles, kSectorMs2[variant], true);
+    return (long)e.self_check(max_work);
   } catch (...) {
     return -1;
   }
@@ -1860,12 +1869,7 @@ long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, in
   try {
     if (o <= 0 || v <= 0) return -1;
     Equation eq;
-    if (kind == 0 && out_comp >= 0 && out_comp <= 3)
-      eq = cc_equation(out_comp);
-    else if (kind == 1 && variant >= 0 && variant < kEomVariants && out_comp >= 0 && out_comp <= 2 && in_comp >= 0 && in_comp <= 2)
-      eq = eom_equation(variant, out_comp, in_comp);
-    else
-      return -1;
+    if (!equation_of(kind, variant, out_comp, in_comp, &eq)) return -1;
     std::ostringstream os;
     os.precision(17);
     auto groups = [&](const std::vector<DimGroup> &gs) {

@@ -415,7 +415,10 @@ Equation cc_equation(int rank) {
   return reduce_orbits(rank, rank, acc);
 }
 
-Equation eom_equation(int variant, int out_comp, int in_comp) {
+namespace {
+
+// Every full term of <mu_out| (H~ e^{T2+T3} R_in)_c |0> before orbit reduction.
+std::map<std::vector<int>, Frac> eom_terms(int variant, int out_comp, int in_comp) {
   int nh, np, rh, rp;
   eom_component(variant, out_comp, &nh, &np);
   eom_component(variant, in_comp, &rh, &rp);
@@ -426,7 +429,93 @@ Equation eom_equation(int variant, int out_comp, int in_comp) {
     xs.push_back(excitation_string(TK_R1 + in_comp, rh, rp));
     expand_into(nh, np, xs, m.w, acc);
   }
-  return reduce_orbits(nh, np, acc);
+  return acc;
+}
+
+}  // namespace
+
+Equation eom_equation(int variant, int out_comp, int in_comp) {
+  int nh, np;
+  eom_component(variant, out_comp, &nh, &np);
+  return reduce_orbits(nh, np, eom_terms(variant, out_comp, in_comp));
+}
+
+// Left product lambda_out <- L_in as the transpose of sigma_in <- R_out. With
+// packed vectors, lambda[nu] = sum_{mu sorted} L[mu] d sigma[mu] / d r[nu];
+// in dense antisymmetric tensors sum_{mu sorted} = 1 / (nh! np!) sum_mu, and
+// d / d r[nu] sums d / d R[nu'] over the signed permutations nu' of nu. So
+// each full term of sigma_in <- R_out becomes, with L[mu] on the old
+// projection indices and the slots of R as the new projection indices, a term
+// of weight c / (nh! np!); its copies under all signed permutations of the new
+// hole and particle indices make the list closed under them, and the
+// antisymmetriser the caller applies to the output then yields every signed
+// permutation once, as the derivative requires.
+Equation eom_left_equation(int variant, int out_comp, int in_comp) {
+  int nh, np, rh, rp;
+  eom_component(variant, in_comp, &nh, &np);   // projection of the right block = shape of L
+  eom_component(variant, out_comp, &rh, &rp);  // input of the right block = shape of lambda
+  const std::map<std::vector<int>, Frac> right = eom_terms(variant, in_comp, out_comp);
+  const int rkind = TK_R1 + out_comp, lkind = TK_R1 + in_comp;
+  const Frac norm(1, factorial(nh) * factorial(np));
+  std::vector<int> hp(rh), pp(rp);
+  std::map<std::vector<int>, Frac> acc;
+  for (auto &kv : right) {
+    if (kv.second.zero()) continue;
+    std::vector<Factor> fs = decode(kv.first);
+    int ri = -1;
+    for (int k = 0; k < (int)fs.size(); ++k)
+      if (fs[k].kind == rkind) {
+        if (ri >= 0) throw std::runtime_error("planner: two EOM vectors in one term");
+        ri = k;
+      }
+    if (ri < 0 || fs[ri].groups.size() != 2 || (int)fs[ri].groups[0].size() != rh ||
+        (int)fs[ri].groups[1].size() != rp)
+      throw std::runtime_error("planner: malformed EOM vector factor");
+    const Factor rf = fs[ri];
+    fs.erase(fs.begin() + ri);
+    // old projection indices become dummies joined to L; R's slots become the
+    // new projection indices (holes 0..rh-1, particles rh..)
+    std::map<int, int> base;
+    for (int id = 0; id < nh + np; ++id) {
+      const int sp = id < nh ? SP_O : SP_V;
+      base[make_label(id, sp)] = make_label(64 + 160 + id, sp);
+    }
+    std::vector<int> rslot;  // R slot label (after the rename above) per new index
+    for (int k = 0; k < rh; ++k) rslot.push_back(rf.groups[0][k]);
+    for (int k = 0; k < rp; ++k) rslot.push_back(rf.groups[1][k]);
+    for (int &lab : rslot)
+      if (base.count(lab)) lab = base[lab];
+    Factor lf;
+    lf.kind = lkind;
+    lf.groups.resize(2);
+    for (int id = 0; id < nh; ++id) lf.groups[0].push_back(base[make_label(id, SP_O)]);
+    for (int id = nh; id < nh + np; ++id) lf.groups[1].push_back(base[make_label(id, SP_V)]);
+    for (auto &f : fs)
+      for (auto &g : f.groups)
+        for (int &lab : g)
+          if (base.count(lab)) lab = base[lab];
+    fs.push_back(lf);
+    std::iota(hp.begin(), hp.end(), 0);
+    do {
+      std::iota(pp.begin(), pp.end(), 0);
+      do {
+        std::map<int, int> ext;  // R slot label -> new projection index under this permutation
+        for (int k = 0; k < rh; ++k) ext[rslot[k]] = make_label(hp[k], SP_O);
+        for (int k = 0; k < rp; ++k) ext[rslot[rh + k]] = make_label(rh + pp[k], SP_V);
+        std::vector<Factor> t = fs;
+        for (auto &f : t)
+          for (auto &g : f.groups)
+            for (int &lab : g) {
+              auto it = ext.find(lab);
+              if (it != ext.end()) lab = it->second;
+            }
+        Canon c = canonical(t);
+        auto &slot = acc[c.code];
+        slot = slot + kv.second * norm * Frac(c.sign * perm_parity(hp) * perm_parity(pp));
+      } while (std::next_permutation(pp.begin(), pp.end()));
+    } while (std::next_permutation(hp.begin(), hp.end()));
+  }
+  return reduce_orbits(rh, rp, acc);
 }
 
 std::string equation_to_string(const Equation &eq) {

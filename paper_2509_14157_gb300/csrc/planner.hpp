@@ -54,6 +54,10 @@ struct Equation {
 Equation cc_equation(int rank);
 // EOM: variant 0..3 (IP, EA, DIP, DEA), output component and input component (0..2).
 Equation eom_equation(int variant, int out_comp, int in_comp);
+// Left EOM product block lambda_{out_comp} <- L_{in_comp}: the transpose of
+// the right block sigma_{in_comp} <- R_{out_comp}; L enters as the EOM vector
+// of component in_comp (the same tensor kinds as R).
+Equation eom_left_equation(int variant, int out_comp, int in_comp);
 // (nh, np) of component c of a variant.
 // EOM variants: 0 IP, 1 EA, 2 DIP, 3 DEA, 4 EE (excitation energies)
 constexpr int kEomVariants = 5;

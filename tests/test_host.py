@@ -137,6 +137,28 @@ def test_planner_eom_equations_match_oracle(system, variant):
         assert np.max(np.abs(got - ref[oc])) < 1e-12, (variant, oc)
 
 
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
+def test_planner_left_eom_equations_match_oracle(system, variant):
+    """Left product blocks lambda_out <- L_in (the planner's transposed terms)
+    against the oracle's L times the product matrix, in the target sector."""
+    ham, t = system
+    o, v = ham["o"], ham["v"]
+    comps = wick.EOM_SPACES[variant]
+    mask = eom.ms_mask(variant, o, v)
+    lvec = synth.random_packed(len(mask), 31, 0.3) * mask
+    ls = eom.split(variant, o, v, lvec)
+    amps = {"t1": np.zeros((o, v)), "t2": t[2], "t3": t[3], "r1": ls[0], "r2": ls[1], "r3": ls[2]}
+    ref = eom.left_sigma_packed(variant, ham["f"], ham["g"], o, v, amps["t1"], t[2], t[3], lvec)
+    got = []
+    for oc, (nh, np_) in enumerate(comps):
+        dense = sum(_evaluate(_parse(pkg.equation_text(2, variant, oc, ic)), ham["f"], ham["g"], amps, o, v)
+                    for ic in range(3))
+        got.append(packing.pack(dense, nh, np_, o, v))
+    got = np.concatenate(got)
+    # (the random T of this fixture does not conserve M_s, so only the sector is compared)
+    assert np.max(np.abs(got[mask] - ref[mask])) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
 def test_xfno_matches_oracle():
     f = [0.999, 0.9975, 0.995]
     e = [-1.2001, -1.2004, -1.2011]
@@ -152,7 +174,8 @@ def test_grouped_tasks_cover_the_spin_blocks_exactly(o, v):
     import paper_2509_14157_gb300 as pkg
     for rank in range(4):
         assert pkg.plan_selfcheck(0, 0, rank, 0, o, v) == 0, rank
-    for var in ("ip", "ea", "dip", "dea", "ee"):
-        for oc in range(3):
-            for ic in range(3):
-                assert pkg.plan_selfcheck(1, var, oc, ic, o, v) == 0, (var, oc, ic)
+    for kind in (1, 2):  # right and left (transposed) EOM products
+        for var in ("ip", "ea", "dip", "dea", "ee"):
+            for oc in range(3):
+                for ic in range(3):
+                    assert pkg.plan_selfcheck(kind, var, oc, ic, o, v) == 0, (kind, var, oc, ic)

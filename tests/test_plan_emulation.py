@@ -201,3 +201,25 @@ def test_eom_plans_execute_to_oracle(system, variant):
         got = sum(emu.run(parse_plan(pkg.plan_text(1, variant, oc, ic, o=10, v=50, amortize=100.0)))
                   for ic in range(3))
         assert np.max(np.abs(got - ref[oc])) < 1e-12, (variant, oc)
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
+def test_left_eom_plans_execute_to_oracle(system, variant):
+    """Plans of the transposed (left) product blocks, executed step by step,
+    against the oracle's L times the product matrix in the target sector."""
+    ham, t = system
+    o, v = ham["o"], ham["v"]
+    comps = wick.EOM_SPACES[variant]
+    mask = eom.ms_mask(variant, o, v)
+    lvec = synth.random_packed(len(mask), 37, 0.3) * mask
+    ls = eom.split(variant, o, v, lvec)
+    amps = {"t1": np.zeros((o, v)), "t2": t[2], "t3": t[3], "r1": ls[0], "r2": ls[1], "r3": ls[2]}
+    emu = Emulator(ham["f"], ham["g"], amps, o, v)
+    ref = eom.left_sigma_packed(variant, ham["f"], ham["g"], o, v, amps["t1"], t[2], t[3], lvec)
+    got = []
+    for oc, (nh, np_) in enumerate(comps):
+        dense = sum(emu.run(parse_plan(pkg.plan_text(2, variant, oc, ic, o=10, v=50, amortize=100.0)))
+                    for ic in range(3))
+        got.append(packing.pack(dense, nh, np_, o, v))
+    got = np.concatenate(got)
+    assert np.max(np.abs(got[mask] - ref[mask])) < 1e-12 * max(1.0, np.max(np.abs(ref)))
