@@ -216,6 +216,21 @@ fnocc_status fnocc_set_precision(fnocc_ctx *ctx, int precision);
 fnocc_status eom_sigma(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
 fnocc_status eom_sigma_dev(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
 
+/* Left product lambda = L^T H-bar, lambda_nu = sum_mu L_mu <mu| (H-bar tau_nu)_c
+ * |0> with tau_nu the operator of packed element nu (not in the paper, which
+ * names the left vectors L1-L3 only as rate-determining six-index
+ * quantities): the transpose of eom_sigma's matrix, same layouts, sector
+ * and conventions, evaluated from transposed term lists (fnocc_equation_text
+ * kind 2) on the same engine. */
+fnocc_status eom_left_sigma(fnocc_ctx *ctx, int variant, const double *l, double *lambda);
+fnocc_status eom_left_sigma_dev(fnocc_ctx *ctx, int variant, const double *l, double *lambda);
+/* Left eigenvectors: eom_ccsdt_solve with the left product. The eigenvalues
+ * are those of the right problem; fnocc_get_block(11..13) then returns the
+ * left vectors L1..L3 (unnormalised against the right ones). */
+fnocc_status eom_ccsdt_solve_left(fnocc_ctx *ctx, int variant, int nroots, int guess,
+                                  const eom_options *opt, double *energies, double *omegas,
+                                  eom_info *out);
+
 /* Packed sizes of the three EOM components of a variant for the loaded
  * Hamiltonian (sizes[3]). */
 fnocc_status fnocc_eom_sizes(const fnocc_ctx *ctx, int variant, size_t *sizes);

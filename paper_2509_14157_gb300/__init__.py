@@ -96,8 +96,12 @@ SIGNATURES = {
     "ccsdt_residual_dev": (ctypes.c_int, [_cp, _vp, _vp, _vp, _vp, _vp, _vp, _dp]),
     "eom_ccsdt_solve": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(EomOptions), _dp, _dp, ctypes.POINTER(EomInfo)]),
+    "eom_ccsdt_solve_left": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(EomOptions), _dp, _dp, ctypes.POINTER(EomInfo)]),
     "eom_sigma": (ctypes.c_int, [_cp, ctypes.c_int, _dp, _dp]),
     "eom_sigma_dev": (ctypes.c_int, [_cp, ctypes.c_int, _vp, _vp]),
+    "eom_left_sigma": (ctypes.c_int, [_cp, ctypes.c_int, _dp, _dp]),
+    "eom_left_sigma_dev": (ctypes.c_int, [_cp, ctypes.c_int, _vp, _vp]),
     "fnocc_eom_sizes": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "fnocc_set_amplitudes": (ctypes.c_int, [_cp, _dp, _dp, _dp]),
     "fnocc_dims": (ctypes.c_int, [_cp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]),
@@ -455,17 +459,27 @@ class Context:
     def eom_sigma_dev(self, variant, r_ptr, s_ptr):
         self._check(self.lib.eom_sigma_dev(self._h, VARIANTS.get(variant, variant), r_ptr, s_ptr))
 
+    def eom_left_sigma(self, variant, lvec):
+        """lambda = L^T H-bar (eom_left_sigma)."""
+        var = VARIANTS.get(variant, variant)
+        lvec, lp = _arr(lvec)
+        out = np.zeros_like(lvec)
+        self._check(self.lib.eom_left_sigma(self._h, var, lp, out.ctypes.data_as(_dp)))
+        return out
+
     def eom_solve(self, variant, nroots, guess="koopmans", tol_res=1e-8, tol_e=1e-10, max_sub=0,
-                  maxiter=200, nguess=0, precision="fp64", switch_tol=1e-5):
+                  maxiter=200, nguess=0, precision="fp64", switch_tol=1e-5, left=False):
+        """Lowest roots (eom_ccsdt_solve); left=True solves for the left
+        eigenvectors with the left product (eom_ccsdt_solve_left)."""
         var = VARIANTS.get(variant, variant)
         self._last_sizes = self.eom_sizes(var)
         opt = EomOptions(tol_res, tol_e, max_sub, maxiter, nguess, PRECISION[precision], switch_tol)
         info = EomInfo()
         en = np.zeros(nroots)
         om = np.zeros(nroots)
-        st = self._check(self.lib.eom_ccsdt_solve(self._h, var, int(nroots), GUESS[guess], ctypes.byref(opt),
-                                                  en.ctypes.data_as(_dp), om.ctypes.data_as(_dp),
-                                                  ctypes.byref(info)), allow=(0, 1))
+        solve = self.lib.eom_ccsdt_solve_left if left else self.lib.eom_ccsdt_solve
+        st = self._check(solve(self._h, var, int(nroots), GUESS[guess], ctypes.byref(opt),
+                               en.ctypes.data_as(_dp), om.ctypes.data_as(_dp), ctypes.byref(info)), allow=(0, 1))
         return dict(energies=en, omegas=om, iters=info.iters, sigma_calls=info.sigma_calls,
                     seconds=info.seconds, seconds_per_iter=info.seconds_per_iter,
                     complex_roots=info.complex_roots, res_max=info.res_max, converged=(st == 0),

@@ -168,6 +168,8 @@ struct fnocc_ctx {
 
   // EOM
   std::unique_ptr<ExecEquation> eom_eq[kEomVariants][3][3];
+  std::unique_ptr<ExecEquation> eom_left_eq[kEomVariants][3][3];  // transposed blocks (left product)
+  bool eom_left = false;  // the Davidson applies the left product (eom_ccsdt_solve_left)
   DevBuf rd[3], sy[3];
   uint64_t hbar_version = 0;
   // the dressed operators and dense T2/T3 hold the stored amplitudes' H-bar
@@ -176,6 +178,7 @@ struct fnocc_ctx {
   int plan_o = -1, plan_v = -1;  // shape the contraction plans were built for
   int cache_precision = 0;  // arithmetic of the cached R-independent intermediates
   uint64_t eq_seen[kEomVariants][3][3] = {};  // H-bar version whose cached flops were counted
+  uint64_t eq_seen_left[kEomVariants][3][3] = {};
   int last_variant = -1, last_nroots = 0;
   size_t last_dim = 0;
   DevBuf eom_vecs;
@@ -270,6 +273,9 @@ void install_hamiltonian(fnocc_ctx *c, int nocc, int nact_spatial) {
     c->dress_plan.build(c->n, c->n);
     for (int r = 0; r < 4; ++r) c->cc_eq[r].reset();
     for (auto &a : c->eom_eq)
+      for (auto &b : a)
+        for (auto &e : b) e.reset();
+    for (auto &a : c->eom_left_eq)
       for (auto &b : a)
         for (auto &e : b) e.reset();
     c->plan_o = c->o;
@@ -386,24 +392,24 @@ void require_ham(fnocc_ctx *c) {
 
 // ---- EOM sigma --------------------------------------------------------------
 
-uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic);
+uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic, bool left);
 
 void eom_sizes(const fnocc_ctx *c, int var, size_t *s) {
   for (int k = 0; k < 3; ++k) s[k] = (size_t)binom_ll(c->o, kEom[var][k][0]) * binom_ll(c->v, kEom[var][k][1]);
 }
 
-void ensure_eom_plans(fnocc_ctx *c, int var) {
+void ensure_eom_plans(fnocc_ctx *c, int var, bool left) {
   int rd[3][2];
   for (int k = 0; k < 3; ++k) {
     rd[k][0] = kEom[var][k][0];
     rd[k][1] = kEom[var][k][1];
   }
+  auto &eqs = left ? c->eom_left_eq[var] : c->eom_eq[var];
   for (int oc = 0; oc < 3; ++oc)
     for (int ic = 0; ic < 3; ++ic)
-      if (!c->eom_eq[var][oc][ic])
-        c->eom_eq[var][oc][ic].reset(
-            new ExecEquation(eom_equation(var, oc, ic), c->o, c->v, rd, kSigmaAmortize, kCacheCapDoubles,
-                             kSectorMs2[var]));
+      if (!eqs[oc][ic])
+        eqs[oc][ic].reset(new ExecEquation(left ? eom_left_equation(var, oc, ic) : eom_equation(var, oc, ic), c->o,
+                                           c->v, rd, kSigmaAmortize, kCacheCapDoubles, kSectorMs2[var]));
 }
 
 // prepares dressed operators and dense T2/T3 from the stored amplitudes
@@ -422,16 +428,20 @@ void prepare_hbar(fnocc_ctx *c) {
   c->hbar_valid = true;
 }
 
-uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic) { return c->eq_seen[var][oc][ic]; }
+uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic, bool left) {
+  return left ? c->eq_seen_left[var][oc][ic] : c->eq_seen[var][oc][ic];
+}
 
-void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s) {
+// s = (H-bar x)_c, or with left = true the left product s = x^T H-bar
+void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = false) {
   if (c->precision != c->cache_precision) {  // cached intermediates follow the arithmetic in use
     ++c->hbar_version;
     c->cache_precision = c->precision;
   }
   Launch L = c->L();
   const int o = c->o, v = c->v;
-  ensure_eom_plans(c, var);
+  ensure_eom_plans(c, var, left);
+  auto &eqs = left ? c->eom_left_eq[var] : c->eom_eq[var];
   size_t sz[3];
   eom_sizes(c, var, sz);
   size_t off = 0;
@@ -462,10 +472,10 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s) {
     c->sy[oc].reserve(sizeof(double) * dn);
     FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, c->stream));
     for (int ic = 0; ic < 3; ++ic) {
-      ExecEquation &eq = *c->eom_eq[var][oc][ic];
-      if (eq.cache_doubles() > 0 && eq_version(c, var, oc, ic) != c->hbar_version) flops += eq.cached_flops();
+      ExecEquation &eq = *eqs[oc][ic];
+      if (eq.cache_doubles() > 0 && eq_version(c, var, oc, ic, left) != c->hbar_version) flops += eq.cached_flops();
       eq.run(L, ops, c->sy[oc].d(), dn, c->scratch, c->hbar_version);
-      eq_version(c, var, oc, ic) = c->hbar_version;
+      eq_version(c, var, oc, ic, left) = c->hbar_version;
       flops += eq.flops();
     }
     antisym_pack(L, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
@@ -1213,7 +1223,10 @@ fnocc_status fnocc_eom_sizes(const fnocc_ctx *c, int variant, size_t *sizes) {
   return FNOCC_OK;
 }
 
-fnocc_status eom_sigma_dev(fnocc_ctx *c, int variant, const double *r, double *s) {
+
+namespace {
+
+fnocc_status product_dev(fnocc_ctx *c, int variant, const double *r, double *s, bool left) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
     if (variant < 0 || variant >= kEomVariants) throw StatusError(FNOCC_E_INVALID, "bad variant");
@@ -1221,14 +1234,14 @@ fnocc_status eom_sigma_dev(fnocc_ctx *c, int variant, const double *r, double *s
     FNOCC_CUDA(cudaSetDevice(c->device));
     prepare_hbar(c);
     c->precision = c->default_precision;
-    sigma_dev(c, variant, r, s);
+    sigma_dev(c, variant, r, s, left);
     c->precision = FNOCC_FP64;
     sync(c);
     return FNOCC_OK;
   });
 }
 
-fnocc_status eom_sigma(fnocc_ctx *c, int variant, const double *r, double *s) {
+fnocc_status product_host(fnocc_ctx *c, int variant, const double *r, double *s, bool left) {
   if (!c) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
     if (variant < 0 || variant >= kEomVariants || !r || !s) throw StatusError(FNOCC_E_INVALID, "bad argument");
@@ -1243,12 +1256,30 @@ fnocc_status eom_sigma(fnocc_ctx *c, int variant, const double *r, double *s) {
     FNOCC_CUDA(cudaMemcpyAsync(x.p, r, sizeof(double) * dim, cudaMemcpyHostToDevice, c->stream));
     prepare_hbar(c);
     c->precision = c->default_precision;
-    sigma_dev(c, variant, x.d(), y.d());
+    sigma_dev(c, variant, x.d(), y.d(), left);
     c->precision = FNOCC_FP64;
     FNOCC_CUDA(cudaMemcpyAsync(s, y.p, sizeof(double) * dim, cudaMemcpyDeviceToHost, c->stream));
     sync(c);
     return FNOCC_OK;
   });
+}
+
+}  // namespace
+
+fnocc_status eom_sigma(fnocc_ctx *c, int variant, const double *r, double *s) {
+  return product_host(c, variant, r, s, false);
+}
+
+fnocc_status eom_sigma_dev(fnocc_ctx *c, int variant, const double *r, double *s) {
+  return product_dev(c, variant, r, s, false);
+}
+
+fnocc_status eom_left_sigma(fnocc_ctx *c, int variant, const double *l, double *lambda) {
+  return product_host(c, variant, l, lambda, true);
+}
+
+fnocc_status eom_left_sigma_dev(fnocc_ctx *c, int variant, const double *l, double *lambda) {
+  return product_dev(c, variant, l, lambda, true);
 }
 
 // features [dim x kMlpFeatures] of the variant's operator space (device)
@@ -1409,7 +1440,7 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       if (sig_src) {
         axpby(L, dim, 0.0, sdst, 1.0 / nrm, sdst);
       } else {
-        sigma_dev(c, variant, dst, sdst);
+        sigma_dev(c, variant, dst, sdst, c->eom_left);
         scale_mask(L, dim, sdst, mask);
         ++sigma_calls;
         if (c->precision != FNOCC_FP64) ++sigma_calls_mixed;
@@ -1600,6 +1631,17 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
     }
     return conv ? FNOCC_OK : FNOCC_NOT_CONVERGED;
   });
+}
+
+fnocc_status eom_ccsdt_solve_left(fnocc_ctx *c, int variant, int nroots, int guess, const eom_options *opt,
+                                  double *energies, double *omegas, eom_info *out) {
+  if (!c) return FNOCC_E_INVALID;
+  struct LeftGuard {
+    fnocc_ctx *c;
+    ~LeftGuard() { c->eom_left = false; }
+  } guard{c};
+  c->eom_left = true;
+  return eom_ccsdt_solve(c, variant, nroots, guess, opt, energies, omegas, out);
 }
 
 fnocc_status eom_ccsdt_solve(fnocc_ctx *c, int variant, int nroots, int guess, const eom_options *opt,

@@ -145,6 +145,47 @@ def test_ccsdt_and_eom_small_system(pkg):
     ctx.close()
 
 
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
+def test_left_product_is_transposed(pkg, variant):
+    """L . sigma(x) = lambda(L) . x for random sector vectors (the left product
+    is the transpose of the right one); for IP and EA also the left product
+    against the oracle's L times the product matrix (one oracle product per
+    sector element, too slow for the larger spaces)."""
+    nocc, n = 2, 5
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 41)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    ctx = pkg.Context(0)
+    ctx.set_mo_hamiltonian(h, eri, nocc)
+    t = random_amplitudes(o, v, seed=220)
+    ctx.set_amplitudes(*t)
+    lvec = random_eom_vector(variant, o, v, seed=11)
+    lam = ctx.eom_left_sigma(variant, lvec)
+    for seed in (12, 13):
+        x = random_eom_vector(variant, o, v, seed=seed)
+        a, b = lvec @ ctx.eom_sigma(variant, x), lam @ x
+        assert abs(a - b) < 1e-11 * max(1.0, abs(a)), (a, b)
+    if variant in ("ip", "ea"):
+        td = [packing.unpack(t[r - 1], r, r, o, v) for r in (1, 2, 3)]
+        ref = eom.left_sigma_packed(variant, ham["f"], ham["g"], o, v, *td, lvec)
+        assert np.max(np.abs(lam - ref)) < AMP_TOL
+    ctx.close()
+
+
+def test_left_roots_equal_right_roots(pkg):
+    """Left eigenvalues of 4 electrons in 6 orbitals equal the right ones."""
+    h, eri = synth.hamiltonian(4, 6, seed=0)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, 2, 0.0)
+    assert ctx.ccsdt_solve()["converged"]
+    for variant in ("ip", "ee"):
+        r = ctx.eom_solve(variant, 3)
+        l = ctx.eom_solve(variant, 3, left=True)
+        assert r["converged"] and l["converged"]
+        assert np.max(np.abs(l["omegas"] - r["omegas"])) < E_TOL, variant
+    ctx.close()
+
+
 def test_ee_roots_small_system(pkg):
     """Excitation energies (EE, 1h1p / 2h2p / 3h3p) of 4 electrons in 6
     orbitals: three roots against the oracle's Davidson, solved live."""
