@@ -137,11 +137,24 @@ def test_planner_eom_equations_match_oracle(system, variant):
         assert np.max(np.abs(got - ref[oc])) < 1e-12, (variant, oc)
 
 
+@pytest.fixture(scope="module")
+def left_system():
+    # o = v = 4: every component of every variant is non-empty, and the
+    # oracle's left product (one product per sector element) stays quick
+    nocc, n = 2, 4
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 9)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    t = {r: packing.unpack(synth.random_packed(packing.packed_size(r, r, o, v), 13 + r, 0.1), r, r, o, v)
+         for r in (2, 3)}
+    return ham, t
+
+
 @pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
-def test_planner_left_eom_equations_match_oracle(system, variant):
+def test_planner_left_eom_equations_match_oracle(left_system, variant):
     """Left product blocks lambda_out <- L_in (the planner's transposed terms)
     against the oracle's L times the product matrix, in the target sector."""
-    ham, t = system
+    ham, t = left_system
     o, v = ham["o"], ham["v"]
     comps = wick.EOM_SPACES[variant]
     mask = eom.ms_mask(variant, o, v)

@@ -203,11 +203,22 @@ def test_eom_plans_execute_to_oracle(system, variant):
         assert np.max(np.abs(got - ref[oc])) < 1e-12, (variant, oc)
 
 
+@pytest.fixture(scope="module")
+def left_system():
+    nocc, n = 2, 4  # o = v = 4: every component non-empty, quick oracle left products
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 19)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    t = {r: packing.unpack(synth.random_packed(packing.packed_size(r, r, o, v), 80 + r, 0.1), r, r, o, v)
+         for r in (2, 3)}
+    return ham, t
+
+
 @pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
-def test_left_eom_plans_execute_to_oracle(system, variant):
+def test_left_eom_plans_execute_to_oracle(left_system, variant):
     """Plans of the transposed (left) product blocks, executed step by step,
     against the oracle's L times the product matrix in the target sector."""
-    ham, t = system
+    ham, t = left_system
     o, v = ham["o"], ham["v"]
     comps = wick.EOM_SPACES[variant]
     mask = eom.ms_mask(variant, o, v)
