@@ -120,6 +120,8 @@ SIGNATURES = {
     "fnocc_profile": (ctypes.c_int, [_cp, ctypes.c_int]),
     "fnocc_plan_selfcheck": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_double]),
+    "fnocc_plan_stats": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "fnocc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_cp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_ulonglong]),
     "fnocc_mlp_destroy": (None, [_cp]),
@@ -223,6 +225,18 @@ def plan_selfcheck(kind, variant=0, out_comp=0, in_comp=0, o=4, v=6, max_work=2e
     spin blocks (host only); see fnocc_plan_selfcheck."""
     lib = load_library()
     return int(lib.fnocc_plan_selfcheck(kind, VARIANTS.get(variant, variant), out_comp, in_comp, o, v, max_work))
+
+
+def plan_stats(kind, variant=0, out_comp=0, in_comp=0, o=10, v=30):
+    """Host-only plan statistics (fnocc_plan_stats) as a dict."""
+    lib = load_library()
+    out = (ctypes.c_double * 8)()
+    st = lib.fnocc_plan_stats(kind, VARIANTS.get(variant, variant), out_comp, in_comp, o, v, out)
+    if st != 0:
+        raise ValueError("bad plan request")
+    keys = ("grouped_steps", "grouped_flops", "padded_flops", "model_seconds", "small_launch_steps",
+            "small_launch_flops", "other_steps", "other_flops")
+    return dict(zip(keys, list(out)))
 
 
 def plan_text(kind, variant=0, out_comp=0, in_comp=0, o=10, v=30, amortize=0.0):

@@ -1906,6 +1906,26 @@ long fnocc_plan_selfcheck(int kind, int variant, int out_comp, int in_comp, int 
   }
 }
 
+fnocc_status fnocc_plan_stats(int kind, int variant, int out_comp, int in_comp, int o, int v, double *stats) {
+  try {
+    if (!stats || o <= 0 || v <= 0 || o > 64 || v > 128) return FNOCC_E_INVALID;
+    Equation eq;
+    if (!equation_of(kind, variant, out_comp, in_comp, &eq)) return FNOCC_E_INVALID;
+    int rd[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    if (kind != 0)
+      for (int k = 0; k < 3; ++k) {
+        rd[k][0] = kEom[variant][k][0];
+        rd[k][1] = kEom[variant][k][1];
+      }
+    ExecEquation e(eq, o, v, rd, kind == 0 ? 0.0 : kSigmaAmortize, kind == 0 ? 0.0 : kCacheCapDoubles,
+                   kind == 0 ? 0 : kSectorMs2[variant], true);
+    e.stats(stats);
+    return FNOCC_OK;
+  } catch (...) {
+    return FNOCC_E_INVALID;
+  }
+}
+
 long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, int v, double amortize, char *buf,
                      size_t len) {
   try {

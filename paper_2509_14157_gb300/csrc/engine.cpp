@@ -911,6 +911,34 @@ DMap host_sub(const DMap &full, const std::vector<std::pair<long long, long long
 // Every grouped step of a host-only plan: the (A, B, C) element-offset
 // triples its tasks address, for every tile shape's task list, against the
 // triples of the spin-allowed blocks decoded through the per-group tables.
+void ExecEquation::stats(double out[8]) const {
+  // model time of one launch on the FP64 pipe: padded multiply-adds of its
+  // busiest SM, ceil(c / 152) CTA-times of padded / c each, at 2 FMA per
+  // clock per SM and 2.07 GHz
+  constexpr double kSmFlops = 2.0 * 2.0 * 2.07e9;
+  for (int k = 0; k < 8; ++k) out[k] = 0;
+  for (const ExecTerm &t : terms_)
+    for (const ExecStep &e : t.steps) {
+      if (e.constant) continue;  // cached: once per H-bar, not per product
+      if (!e.grouped) {
+        out[6] += 1;
+        out[7] += 2.0 * double(e.M) * double(e.N) * double(e.K);
+        continue;
+      }
+      const GroupedLaunch &g = e.gl[e.default_shape];
+      const double c = double(std::max<long long>(1, g.ncta));
+      const double waves = std::ceil(c / 152.0);
+      out[0] += 1;
+      out[1] += g.flops;
+      out[2] += g.padded;
+      out[3] += g.padded * waves / c / kSmFlops;
+      if (g.ncta < 152) {
+        out[4] += 1;
+        out[5] += g.flops;
+      }
+    }
+}
+
 long long ExecEquation::self_check(double max_work) const {
   if (!host_only_) throw std::runtime_error("self_check needs a host-only plan");
   long long bad = 0;

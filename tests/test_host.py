@@ -172,6 +172,25 @@ def test_planner_left_eom_equations_match_oracle(left_system, variant):
     assert np.max(np.abs(got[mask] - ref[mask])) < 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
+def test_plan_stats_are_consistent():
+    """Host-only plan statistics: padded work covers the algorithmic work,
+    the model time is at least the algorithmic work at the FP64 peak, and
+    the DEA product's grouped flops match the algorithmic count the library
+    reports for it (5.3e9 at o = 10, v = 30)."""
+    peak = 152 * 2 * 2 * 2.07e9
+    tot = 0.0
+    for oc in range(3):
+        for ic in range(3):
+            s = pkg.plan_stats(1, "dea", oc, ic, o=10, v=30)
+            assert s["padded_flops"] >= s["grouped_flops"] >= 0
+            assert s["model_seconds"] >= s["grouped_flops"] / peak * (1 - 1e-12)
+            assert s["small_launch_flops"] <= s["grouped_flops"]
+            tot += s["grouped_flops"] + s["other_flops"]
+    assert 5.2e9 < tot < 5.45e9
+    with pytest.raises(ValueError):
+        pkg.plan_stats(1, "dea", 3, 0)
+
+
 def test_xfno_matches_oracle():
     f = [0.999, 0.9975, 0.995]
     e = [-1.2001, -1.2004, -1.2011]
