@@ -36,6 +36,7 @@ def denominators(f, o, rank):
 
 
 def residuals(f, g, o, v, t1, t2, t3):
+    """Dense residuals <Phi^n| (H e^T)_c |0>, n = 1..3 (Eq. 6), from the Wick terms."""
     amps = {"t1": t1, "t2": t2, "t3": t3}
     return [wick.evaluate(wick.cc_terms(n), n, n, f, g, amps, o, v) for n in (1, 2, 3)]
 
@@ -47,6 +48,7 @@ def energy(f, g, o, v, t1, t2, t3=None):
 
 
 def residuals_packed(f, g, o, v, p1, p2, p3):
+    """Eq. 6 residuals of packed amplitudes, returned packed."""
     t1 = packing.unpack(p1, 1, 1, o, v)
     t2 = packing.unpack(p2, 2, 2, o, v)
     t3 = packing.unpack(p3, 3, 3, o, v)

@@ -91,6 +91,7 @@ class FockSpace:
         return self.assemble(terms)
 
     def vacuum(self, nocc_orbs):
+        """Occupation-number vector of the reference |Phi_0> (the orbitals nocc_orbs filled)."""
         v = np.zeros(self.dim)
         v[sum(1 << p for p in nocc_orbs)] = 1.0
         return v
@@ -152,6 +153,7 @@ class DefinitionOracle:
         return self._project(chi, rank, rank)
 
     def cc_energy(self, amps, e_ref):
+        """Correlation energy <Phi_0| e^{-T} H e^{T} |Phi_0> - E_ref (the definition behind Eq. 7)."""
         t = self.cluster(amps)
         chi = _exp_apply(t, self.h @ _exp_apply(t, self.ref), -1.0)
         return float(self.ref @ chi) - e_ref

@@ -42,10 +42,12 @@ SECTOR_MS2 = {"ip": 1, "ea": 1, "dip": 0, "dea": 0, "ee": 0}
 
 
 def comps(variant):
+    """(holes, particles) of R1, R2, R3 of the variant (Eq. 3-4 as read here)."""
     return wick.EOM_SPACES[variant]
 
 
 def sizes(variant, o, v):
+    """Packed sizes of the three components."""
     return [packing.packed_size(nh, np_, o, v) for nh, np_ in comps(variant)]
 
 
@@ -62,12 +64,14 @@ def ms_mask(variant, o, v):
 
 
 def split(variant, o, v, vec):
+    """Packed EOM vector -> dense antisymmetric components."""
     s = sizes(variant, o, v)
     parts = np.split(vec, np.cumsum(s)[:-1])
     return [packing.unpack(p, nh, np_, o, v) for p, (nh, np_) in zip(parts, comps(variant))]
 
 
 def sigma_dense(variant, f, g, o, v, t1, t2, t3, rs):
+    """sigma_out = sum_in <mu_out| (H-bar R_in)_c |0> (Eq. 1-4) on dense components."""
     amps = {"t1": t1, "t2": t2, "t3": t3, "r1": rs[0], "r2": rs[1], "r3": rs[2]}
     out = []
     for oc, (nh, np_) in enumerate(comps(variant)):
@@ -79,6 +83,7 @@ def sigma_dense(variant, f, g, o, v, t1, t2, t3, rs):
 
 
 def sigma_packed(variant, f, g, o, v, t1, t2, t3, vec):
+    """sigma of a packed EOM vector, returned packed (Eq. 1-4)."""
     rs = split(variant, o, v, vec)
     out = sigma_dense(variant, f, g, o, v, t1, t2, t3, rs)
     return np.concatenate([packing.pack(x, nh, np_, o, v) for x, (nh, np_) in zip(out, comps(variant))])

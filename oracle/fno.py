@@ -89,6 +89,7 @@ def spin_orbital_integrals(eri_mo):
 
 
 def spin_orbital_one_body(h_mo):
+    """Spatial one-body matrix -> spin orbitals (alpha even, beta odd; Sec. 1.2)."""
     n = h_mo.shape[0]
     out = np.zeros((2 * n, 2 * n))
     out[0::2, 0::2] = h_mo
@@ -97,6 +98,7 @@ def spin_orbital_one_body(h_mo):
 
 
 def transform_eri(eri, c1, c2, c3, c4):
+    """(pq|rs) transformed index by index with the coefficient matrices c1..c4 (Sec. 1.2)."""
     return np.einsum("pqrs,pa,qb,rc,sd->abcd", eri, c1, c2, c3, c4, optimize=True)
 
 

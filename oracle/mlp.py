@@ -40,6 +40,7 @@ def unpack(params, width, nin=NIN, nout=NOUT):
 
 
 def pack(layers):
+    """Concatenated parameter vector of the weight and bias arrays."""
     return np.concatenate([np.ravel(x) for x in layers])
 
 

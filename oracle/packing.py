@@ -26,6 +26,7 @@ def _perm_sign(perm):
 
 
 def packed_size(nh, np_, o, v):
+    """Number of unique elements: C(o, nh) C(v, np)."""
     return math.comb(o, nh) * math.comb(v, np_)
 
 

@@ -71,22 +71,26 @@ class Factor:
 
 
 def fock_factor(ps, qs):
+    """One-body part f_pq {p+ q} of the normal-ordered Hamiltonian, spaces ps, qs."""
     return Factor("f", [(ps, True, 0), (qs, False, 1)], ((0,), (1,)), Fraction(1))
 
 
 def v_factor(sp):
+    """Two-body part 1/4 <pq||rs> {p+ q+ s r}, spaces sp = "pqrs"."""
     p, q, r, s = sp
     return Factor("v", [(p, True, 0), (q, True, 1), (s, False, 3), (r, False, 2)],
                   ((0, 1), (2, 3)), Fraction(1, 4))
 
 
 def amp_factor(name, nh, np_):
+    """Excitation operator 1/(nh! np!) sum x a+.. i.. (T_n, or an EOM component)."""
     ops = [("v", True, nh + k) for k in range(np_)] + [("o", False, k) for k in reversed(range(nh))]
     groups = (tuple(range(nh)), tuple(range(nh, nh + np_)))
     return Factor(name, ops, groups, Fraction(1, math.factorial(nh) * math.factorial(np_)))
 
 
 def hamiltonian_factors():
+    """Every occupied/virtual block of the normal-ordered Hamiltonian."""
     out = [fock_factor(a, b) for a in "ov" for b in "ov"]
     out += [v_factor("".join(s)) for s in itertools.product("ov", repeat=4)]
     return out

@@ -16,6 +16,7 @@ import numpy as np
 
 
 def extrapolate(kept_fraction, energy):
+    """Least-squares line E(f) through the points, evaluated at f = 1 (Sec. 2, read as stated above)."""
     f = np.asarray(kept_fraction, dtype=np.float64)
     e = np.asarray(energy, dtype=np.float64)
     if len(f) != len(e) or len(f) == 0:
