@@ -93,6 +93,7 @@ def fake_gpu(monkeypatch):
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _Stream())
     monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
     monkeypatch.setattr(FakeContext, "PROFILE_PATHS", dict(pkg.Context.PROFILE_PATHS))
     monkeypatch.setattr(pkg, "Context", FakeContext)
     monkeypatch.setattr(learned, "training_set", lambda *a, **k: (
