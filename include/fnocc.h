@@ -409,13 +409,15 @@ long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, in
                      char *buf, size_t len);
 
 /* Host-only statistics of the executable plan of the same equation at sizes
- * (o, v) (not in the paper; an analysis aid, no GPU needed). stats[8]:
+ * (o, v) (not in the paper; an analysis aid, no GPU needed). stats[10]:
  * [0] grouped FP64 steps run per product (cached R-independent steps
  * excluded), [1] their algorithmic flops, [2] their padded flops at the
  * estimated tile shapes, [3] their model time in seconds on the FP64 pipe
  * (per launch: padded flops x ceil(CTAs / 152) / CTAs at 2 FMA per clock per
  * SM and 2.07 GHz), [4] steps with fewer than 152 CTAs, [5] their flops,
- * [6] other (small-output or GEMV) steps, [7] their flops. The timed shape
+ * [6] other (small-output or GEMV) steps, [7] their flops, [8] doubles of
+ * intermediate scratch, [9] doubles of cached R-independent intermediates
+ * (device memory of the plan besides its operands). The timed shape
  * of large steps may differ at run time. Returns FNOCC_E_INVALID on bad
  * arguments. */
 fnocc_status fnocc_plan_stats(int kind, int variant, int out_comp, int in_comp, int o, int v, double *stats);

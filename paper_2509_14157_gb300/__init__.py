@@ -230,12 +230,12 @@ def plan_selfcheck(kind, variant=0, out_comp=0, in_comp=0, o=4, v=6, max_work=2e
 def plan_stats(kind, variant=0, out_comp=0, in_comp=0, o=10, v=30):
     """Host-only plan statistics (fnocc_plan_stats) as a dict."""
     lib = load_library()
-    out = (ctypes.c_double * 8)()
+    out = (ctypes.c_double * 10)()
     st = lib.fnocc_plan_stats(kind, VARIANTS.get(variant, variant), out_comp, in_comp, o, v, out)
     if st != 0:
         raise ValueError("bad plan request")
     keys = ("grouped_steps", "grouped_flops", "padded_flops", "model_seconds", "small_launch_steps",
-            "small_launch_flops", "other_steps", "other_flops")
+            "small_launch_flops", "other_steps", "other_flops", "scratch_doubles", "cache_doubles")
     return dict(zip(keys, list(out)))
 
 

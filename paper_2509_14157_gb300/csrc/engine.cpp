@@ -911,12 +911,14 @@ DMap host_sub(const DMap &full, const std::vector<std::pair<long long, long long
 // Every grouped step of a host-only plan: the (A, B, C) element-offset
 // triples its tasks address, for every tile shape's task list, against the
 // triples of the spin-allowed blocks decoded through the per-group tables.
-void ExecEquation::stats(double out[8]) const {
+void ExecEquation::stats(double out[10]) const {
   // model time of one launch on the FP64 pipe: padded multiply-adds of its
   // busiest SM, ceil(c / 152) CTA-times of padded / c each, at 2 FMA per
   // clock per SM and 2.07 GHz
   constexpr double kSmFlops = 2.0 * 2.0 * 2.07e9;
-  for (int k = 0; k < 8; ++k) out[k] = 0;
+  for (int k = 0; k < 10; ++k) out[k] = 0;
+  out[8] = double(scratch_need_);
+  out[9] = double(cache_need_);
   for (const ExecTerm &t : terms_)
     for (const ExecStep &e : t.steps) {
       if (e.constant) continue;  // cached: once per H-bar, not per product

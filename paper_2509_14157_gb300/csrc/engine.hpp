@@ -81,7 +81,7 @@ class ExecEquation {
   long long self_check(double max_work) const;
   // plan statistics of the FP64 grouped steps at their estimated tile
   // shapes (no device needed): see fnocc_plan_stats
-  void stats(double out[8]) const;
+  void stats(double out[10]) const;
   // Y (dense output accumulator [o^nh v^np]) += sum of terms. version: the
   // cached R-independent intermediates are recomputed when it changes.
   void run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch,
