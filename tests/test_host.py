@@ -191,6 +191,24 @@ def test_plan_stats_are_consistent():
         pkg.plan_stats(1, "dea", 3, 0)
 
 
+def test_plans_build_at_the_largest_workload():
+    """Every CCSDT rank and every right and left product block builds its
+    executable plan host-only at the largest workload (16 electrons, 41 kept
+    virtuals: o = 16, v = 82), with 64-bit tables and grids in range, and
+    its small grouped steps check out against the spin blocks."""
+    o, v = 16, 82
+    for rank in range(4):
+        s = pkg.plan_stats(0, 0, rank, 0, o=o, v=v)
+        assert s["padded_flops"] >= s["grouped_flops"] > 0 or rank == 0
+    for kind in (1, 2):
+        for var in ("ip", "ea", "dip", "ee"):
+            for oc in range(3):
+                for ic in range(3):
+                    s = pkg.plan_stats(kind, var, oc, ic, o=o, v=v)
+                    assert s["padded_flops"] >= s["grouped_flops"] >= 0
+    assert pkg.plan_selfcheck(1, "ea", 2, 2, o, v, max_work=1e5) == 0
+
+
 def test_xfno_matches_oracle():
     f = [0.999, 0.9975, 0.995]
     e = [-1.2001, -1.2004, -1.2011]
