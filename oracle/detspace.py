@@ -191,9 +191,9 @@ def fci_energies(hso, gso, nelec, ms2, nroots=None):
     fs = FockSpace(m)
     h = fs.hamiltonian(hso, gso)
     st = fs.states
-    n_e = np.bitwise_count(st)
+    n_e = np.bitwise_count(st).astype(np.int64)  # signed: na - nb below may be negative
     alpha_mask = sum(1 << p for p in range(0, m, 2))
-    na = np.bitwise_count(st & alpha_mask)
+    na = np.bitwise_count(st & alpha_mask).astype(np.int64)
     nb = n_e - na
     sel = np.where((n_e == nelec) & (na - nb == ms2))[0]
     hs = h[sel][:, sel].toarray()
