@@ -149,13 +149,7 @@ def test_ee_two_electron_reference_is_fci(two_electron):
     assert np.max(np.abs(roots - fci[1:])) < 1e-8
 
 
-def test_ee_three_electron_reference_is_fci():
-    """EE from an open-shell three-electron reference (0a, 0b, 1a) in 4
-    spatial orbitals: 1h1p, 2h2p and 3h3p of every spin change span every
-    other three-electron determinant, CCSDT is exact and T3 is active, so
-    E_CC + omega over the whole operator space are all FCI energies of N = 3
-    except the ground state (the sector masks assume an even number of
-    occupied spin orbitals, so the space is taken whole here)."""
+def _three_electron_reference():
     h, eri = synth.random_symmetric_mo_hamiltonian(4, 3, scale_h=0.1, scale_eri=0.03)
     hso, g = _so_hamiltonian(h, eri)
     o = 3
@@ -163,13 +157,40 @@ def test_ee_three_electron_reference_is_fci():
     v = hso.shape[0] - o
     res = cc.ccsdt(f, g, o, v)
     assert res["converged"] and np.max(np.abs(res["t3"])) > 1e-8
-    dim = sum(eom.sizes("ee", o, v))
+    return hso, g, f, e_ref, o, v, res
+
+
+def _whole_space_roots(variant, f, g, o, v, res):
+    dim = sum(eom.sizes(variant, o, v))
     cols = []
     for k in range(dim):
         e = np.zeros(dim)
         e[k] = 1.0
-        cols.append(eom.sigma_packed("ee", f, g, o, v, res["t1"], res["t2"], res["t3"], e))
-    roots = np.sort(e_ref + res["e_corr"] + np.linalg.eigvals(np.array(cols).T).real)
+        cols.append(eom.sigma_packed(variant, f, g, o, v, res["t1"], res["t2"], res["t3"], e))
+    return np.sort(np.linalg.eigvals(np.array(cols).T).real), dim
+
+
+def test_ip_three_electron_reference_is_fci():
+    """IP from the open-shell three-electron reference: 1h, 2h1p and 3h2p of
+    every spin change span all two-electron determinants, with T3 active,
+    so E_CC + omega are all FCI energies of N = 2."""
+    hso, g, f, e_ref, o, v, res = _three_electron_reference()
+    w, dim = _whole_space_roots("ip", f, g, o, v, res)
+    fci = np.sort(np.concatenate([detspace.fci_energies(hso, g, 2, ms2) for ms2 in (-2, 0, 2)]))
+    assert dim == len(fci)
+    assert np.max(np.abs(e_ref + res["e_corr"] + w - fci)) < 1e-8
+
+
+def test_ee_three_electron_reference_is_fci():
+    """EE from an open-shell three-electron reference (0a, 0b, 1a) in 4
+    spatial orbitals: 1h1p, 2h2p and 3h3p of every spin change span every
+    other three-electron determinant, CCSDT is exact and T3 is active, so
+    E_CC + omega over the whole operator space are all FCI energies of N = 3
+    except the ground state (the sector masks assume an even number of
+    occupied spin orbitals, so the space is taken whole here)."""
+    hso, g, f, e_ref, o, v, res = _three_electron_reference()
+    w, dim = _whole_space_roots("ee", f, g, o, v, res)
+    roots = e_ref + res["e_corr"] + w
     fci = np.sort(np.concatenate([detspace.fci_energies(hso, g, 3, ms2) for ms2 in (-3, -1, 1, 3)]))
     assert dim == len(fci) - 1
     ground = int(np.argmin(np.abs(fci - (e_ref + res["e_corr"]))))
