@@ -228,12 +228,13 @@ def run_solve_only(args):
     kw = (dict(precision="fp64") if args.precision == "fp64"
           else dict(precision=args.precision, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8))
     cc = ctx.ccsdt_solve()
+    kw["left"] = args.left
     ctx.eom_solve(args.solve_only, NROOTS, **kw)
     f0 = ctx.flops
     t0 = time.perf_counter()
     r = ctx.eom_solve(args.solve_only, NROOTS, **kw)
     dt = time.perf_counter() - t0
-    print(json.dumps({"solve_only": args.solve_only, "precision": args.precision, "seconds": dt,
+    print(json.dumps({"solve_only": args.solve_only, "left": args.left, "precision": args.precision, "seconds": dt,
                       "sigma_calls": r["sigma_calls"], "iters": r["iters"], "converged": r["converged"],
                       "omegas": [float(x) for x in r["omegas"]], "ccsdt_iters": cc["iters"],
                       "tflops": (ctx.flops - f0) / dt / 1e12}), flush=True)
@@ -254,18 +255,19 @@ def run_sigma_only(args):
     ctx.set_amplitudes(*[rng.normal(0, 0.01, s) for s in ctx.amp_sizes()])
     ctx.set_precision(args.precision)
     dim = sum(ctx.eom_sizes(args.sigma_only))
+    product = ctx.eom_left_sigma_dev if args.left else ctx.eom_sigma_dev
     x = torch.from_numpy(rng.normal(0, 0.1, dim)).cuda()
     s = torch.empty_like(x)
     for _ in range(2):
-        ctx.eom_sigma_dev(args.sigma_only, x.data_ptr(), s.data_ptr())
+        product(args.sigma_only, x.data_ptr(), s.data_ptr())
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("sig")
     t0 = time.perf_counter()
-    ctx.eom_sigma_dev(args.sigma_only, x.data_ptr(), s.data_ptr())
+    product(args.sigma_only, x.data_ptr(), s.data_ptr())
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     torch.cuda.nvtx.range_pop()
-    print(json.dumps({"sigma_only": args.sigma_only, "precision": args.precision, "seconds": dt,
+    print(json.dumps({"sigma_only": args.sigma_only, "left": args.left, "precision": args.precision, "seconds": dt,
                       "flops_all_calls": ctx.flops}), flush=True)
     ctx.close()
 
@@ -481,6 +483,8 @@ def main():
                     help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
     ap.add_argument("--solve-only", default=None, choices=list(VARIANTS) + ["ee"],
                     help="FNO, CCSDT and one Davidson solve of this variant (4 roots) at the workload's size")
+    ap.add_argument("--left", action="store_true",
+                    help="with --sigma-only / --solve-only: the left product / left eigenvectors")
     ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS) + ["ee"],
                     help="one sigma product at the workload's size (profiling case)")
     args = ap.parse_args()

@@ -473,6 +473,9 @@ class Context:
     def eom_sigma_dev(self, variant, r_ptr, s_ptr):
         self._check(self.lib.eom_sigma_dev(self._h, VARIANTS.get(variant, variant), r_ptr, s_ptr))
 
+    def eom_left_sigma_dev(self, variant, l_ptr, lam_ptr):
+        self._check(self.lib.eom_left_sigma_dev(self._h, VARIANTS.get(variant, variant), l_ptr, lam_ptr))
+
     def eom_left_sigma(self, variant, lvec):
         """lambda = L^T H-bar (eom_left_sigma)."""
         var = VARIANTS.get(variant, variant)
