@@ -74,6 +74,25 @@ class FakeContext:
     def set_guess_model(self, m):
         pass
 
+    # product-timing modes
+    def amp_sizes(self):
+        return [4, 6, 4]
+
+    def set_amplitudes(self, *t):
+        pass
+
+    def set_precision(self, p):
+        pass
+
+    def eom_sizes(self, variant):
+        return [2, 3, 4]
+
+    def eom_sigma_dev(self, variant, x, s):
+        self.calls = getattr(self, "calls", []) + [("right", variant)]
+
+    def eom_left_sigma_dev(self, variant, x, s):
+        self.calls = getattr(self, "calls", []) + [("left", variant)]
+
     def close(self):
         pass
 
@@ -94,6 +113,9 @@ def fake_gpu(monkeypatch):
     monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _Stream())
     monkeypatch.setattr(torch.cuda, "Event", _Event)
     monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.cuda.nvtx, "range_push", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda.nvtx, "range_pop", lambda *a, **k: None)
     monkeypatch.setattr(FakeContext, "PROFILE_PATHS", dict(pkg.Context.PROFILE_PATHS))
     monkeypatch.setattr(pkg, "Context", FakeContext)
     monkeypatch.setattr(learned, "training_set", lambda *a, **k: (
@@ -152,3 +174,12 @@ def test_reference_line_carries_the_contract(fake_gpu, monkeypatch, capsys):
         assert key in line, key
     assert line["e2e"] == {"value": 100.0, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert fake_gpu["counts"] is bench.REFERENCE_COUNTS
+
+
+@pytest.mark.parametrize("argv,key", [(["--sigma-only", "dea"], "sigma_only"),
+                                      (["--sigma-only", "ee", "--left"], "sigma_only"),
+                                      (["--solve-only", "ee", "--left"], "solve_only"),
+                                      (["--solve-only", "ip", "--precision", "mixed_tf32"], "solve_only")])
+def test_timing_modes_run(fake_gpu, monkeypatch, capsys, argv, key):
+    line = _run(monkeypatch, capsys, argv)
+    assert line[key] == argv[1] and line["left"] == ("--left" in argv) and line["seconds"] >= 0
