@@ -74,6 +74,9 @@ class FakeContext:
     def set_guess_model(self, m):
         pass
 
+    def dims(self):
+        return 4, 8, -1.0
+
     # product-timing modes
     def amp_sizes(self):
         return [4, 6, 4]
@@ -118,6 +121,14 @@ def fake_gpu(monkeypatch):
     monkeypatch.setattr(torch.cuda.nvtx, "range_pop", lambda *a, **k: None)
     monkeypatch.setattr(FakeContext, "PROFILE_PATHS", dict(pkg.Context.PROFILE_PATHS))
     monkeypatch.setattr(pkg, "Context", FakeContext)
+
+    def fake_batch_solve(systems, variants, nroots, nworkers=4, precision="fp64", **kw):
+        om = np.zeros((len(systems), len(variants), nroots))
+        info = [dict(status=0, nkept=4, e_rhf=-1.0, e_ccsdt=-1.1, ccsdt_iters=10, sigma_calls=50, seconds=0.1)
+                for _ in systems]
+        return om, info
+
+    monkeypatch.setattr(pkg, "batch_solve", fake_batch_solve)
     monkeypatch.setattr(learned, "training_set", lambda *a, **k: (
         np.zeros((4, 8), np.float32), np.zeros((4, 2), np.float32), np.ones((4, 2), np.float32), [(0,)]))
     monkeypatch.setattr(learned, "train_guess_model", lambda *a, **k: (_Net(), [0.5]))
@@ -179,7 +190,16 @@ def test_reference_line_carries_the_contract(fake_gpu, monkeypatch, capsys):
 @pytest.mark.parametrize("argv,key", [(["--sigma-only", "dea"], "sigma_only"),
                                       (["--sigma-only", "ee", "--left"], "sigma_only"),
                                       (["--solve-only", "ee", "--left"], "solve_only"),
-                                      (["--solve-only", "ip", "--precision", "mixed_tf32"], "solve_only")])
+                                      (["--solve-only", "ip", "--precision", "mixed_tf32"], "solve_only"),
+                                      (["--precision-check"], "mode"),
+                                      (["--guess-check"], "mode"),
+                                      (["--batch"], "metric"),
+                                      (["--batch", "--batch-large"], "metric")])
 def test_timing_modes_run(fake_gpu, monkeypatch, capsys, argv, key):
-    line = _run(monkeypatch, capsys, argv)
-    assert line[key] == argv[1] and line["left"] == ("--left" in argv) and line["seconds"] >= 0
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    bench.main()
+    lines = [json.loads(l) for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    line = lines[-1]
+    assert key in line
+    if key in ("sigma_only", "solve_only"):
+        assert line[key] == argv[1] and line["left"] == ("--left" in argv) and line["seconds"] >= 0
