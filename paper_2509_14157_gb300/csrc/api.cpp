@@ -1,4 +1,7 @@
-// C ABI of libfnocc (include/fnocc.h): context, FNO setup, CCSDT and EOM-CCSDT.
+// C ABI of libfnocc (include/fnocc.h): context, FNO setup (Sec. 1.2, Eq.
+// 8-10), CCSDT (Eq. 5-7), EOM-CCSDT products and Davidson solves (Eq. 1-4)
+// for IP / EA / DIP / DEA and the EE and left-vector extensions, XFNO
+// (Sec. 2), batching and the learned Davidson start.
 #include "../../include/fnocc.h"
 #include "mlp.hpp"
 

@@ -1,3 +1,8 @@
+// Small dense host linear algebra (see linalg.hpp): the k x k projected
+// eigenproblem of the non-symmetric Davidson (roots of Eq. 1-4; the paper
+// names no eigensolver) by the textbook Hessenberg reduction and shifted QR,
+// and the DIIS linear systems of the CCSDT iterations. O(k^3), k <= a few
+// hundred; all vector-length work stays on the device.
 #include "linalg.hpp"
 
 #include <algorithm>
