@@ -8,6 +8,10 @@
  *   - CCSDT ground state: Eq. 5-7.
  *   - EOM-CCSDT for IP / EA / DIP / DEA: Eq. 1-4.
  *   - XFNO extrapolation over three thresholds: Sec. 2.
+ *   - Extensions on the same machinery: the excitation-energy variant EE
+ *     (the EOM-CC the four variants build on, Sec. 1), left products and
+ *     left eigenvectors, mixed-precision split products, batching of
+ *     independent systems and a learned Davidson start.
  *
  * Conventions used by every call:
  *   - Everything is IEEE double, row-major, C-contiguous.
