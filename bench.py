@@ -647,6 +647,7 @@ def main():
         _, ref_e = step(True)
         step(True, "mixed", kw)
         ml_times = []
+        ml_flops0 = ctx.flops
         for _ in range(args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
@@ -659,8 +660,10 @@ def main():
             ml_times.append(e0.elapsed_time(e1) / 1e3)
         ml_total = sum(ml_times)
         ml_total = max_over_ranks(ml_total, world, dev)
+        ml_flops = ctx.flops - ml_flops0
         mixed_learned = {
             "value": ml_total / (len(VARIANTS) * args.steps * world), "unit": "s",
+            "tflops": ml_flops * world / ml_total / 1e12 if ml_total > 0 else None,
             "ms_per_step": 1e3 * ml_total / args.steps,
             "config": "BF16x3 products, Davidson to 1e-6 Eh without FP64 refinement, learned start and "
                       "preconditioner; CCSDT mixed then FP64",

@@ -176,6 +176,7 @@ def test_default_line_carries_the_contract(fake_gpu, monkeypatch, capsys):
     assert line["solver"]["sigma_calls"] == {v: 88 for v in bench.VARIANTS}
     assert fake_gpu["counts"]["sigma"] == {v: 88 for v in bench.VARIANTS}
     assert line["mixed_learned"]["sigma_calls"] == {v: 60 for v in bench.VARIANTS}
+    assert line["tflops"] > 0 and line["mixed_learned"]["tflops"] > 0
 
 
 def test_reference_line_carries_the_contract(fake_gpu, monkeypatch, capsys):
