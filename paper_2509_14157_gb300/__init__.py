@@ -170,6 +170,7 @@ def _arr(x):
 
 
 def xfno_extrapolate(kept_fraction, energy):
+    """XFNO extrapolation (Sec. 2): least-squares line E(f) at f = 1 (xfno_extrapolate)."""
     lib = load_library()
     f, fp = _arr(kept_fraction)
     e, ep = _arr(energy)
@@ -273,6 +274,7 @@ class Mlp:
         self.width = width
 
     def close(self):
+        """Releases the network's device memory."""
         if self._h:
             self.lib.fnocc_mlp_destroy(self._h)
             self._h = _cp()
@@ -290,24 +292,29 @@ class Mlp:
 
     @property
     def nparam(self):
+        """Number of FP32 parameters (fnocc_mlp_param_count)."""
         return int(self.lib.fnocc_mlp_param_count(self._h))
 
     def get_params(self):
+        """Parameters as a host FP32 array (get_params layout)."""
         p = np.zeros(self.nparam, dtype=np.float32)
         self._check(self.lib.fnocc_mlp_get_params(self._h, p.ctypes.data_as(_fp), p.size))
         return p
 
     def set_params(self, p):
+        """Sets the parameters and resets the optimiser state."""
         p, pp = _farr(p)
         self._check(self.lib.fnocc_mlp_set_params(self._h, pp, p.size))
 
     def forward(self, x, bf16=False):
+        """Network outputs [n x 2] for features [n x 8]; bf16=True: the tensor-core inference path."""
         x, xp = _farr(x, self.NIN)
         y = np.zeros((x.shape[0], self.NOUT), dtype=np.float32)
         self._check(self.lib.fnocc_mlp_forward(self._h, xp, x.shape[0], y.ctypes.data_as(_fp), 1 if bf16 else 0))
         return y
 
     def loss_grad(self, x, t, w):
+        """Weighted mean-squared loss and its gradient at the current parameters."""
         x, xp = _farr(x, self.NIN)
         t, tp = _farr(t, self.NOUT)
         w, wp = _farr(w, self.NOUT)
@@ -318,6 +325,7 @@ class Mlp:
         return loss.value, g
 
     def train(self, x, t, w, epochs=20, batch=4096, lr=1e-3, seed=0):
+        """Minibatch Adam on the library's kernels; returns the mean loss per epoch."""
         x, xp = _farr(x, self.NIN)
         t, tp = _farr(t, self.NOUT)
         w, wp = _farr(w, self.NOUT)
@@ -346,6 +354,7 @@ class Context:
             raise FnoccError(st, "fnocc_create failed")
 
     def close(self):
+        """Destroys the context and frees its device memory."""
         if self._h:
             self.lib.fnocc_destroy(self._h)
             self._h = _cp()
@@ -364,14 +373,17 @@ class Context:
 
     @property
     def launches(self):
+        """Kernel launches issued so far (fnocc_launch_count)."""
         return int(self.lib.fnocc_launch_count(self._h))
 
     def dims(self):
+        """(o, v, E_ref): active occupied / virtual spin orbitals and the reference energy."""
         o, v, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         self._check(self.lib.fnocc_dims(self._h, ctypes.byref(o), ctypes.byref(v), ctypes.byref(e)))
         return o.value, v.value, e.value
 
     def fno_truncate(self, h, eri, nocc, threshold, criterion="abs", nkeep=0):
+        """RHF, MP2 natural orbitals, truncation and the active Hamiltonian (Sec. 1.2, Eq. 8-10)."""
         h, hp = _arr(h)
         eri, ep = _arr(eri)
         n = h.shape[0]
@@ -400,9 +412,11 @@ class Context:
 
     @property
     def flops(self):
+        """Algorithmic flops of the contraction steps run so far (fnocc_flop_count)."""
         return float(self.lib.fnocc_flop_count(self._h))
 
     def profile(self, enable=True):
+        """Per-launch event timing of the contraction kernels on / off (fnocc_profile)."""
         self._check(self.lib.fnocc_profile(self._h, 1 if enable else 0))
 
     PROFILE_PATHS = {0: "k_ggemm", 1: "k_ggemm_split+k_greduce", 2: "k_gemm_small+k_reduce_partials",
@@ -418,11 +432,13 @@ class Context:
         return ms.value, fl.value, int(n.value)
 
     def set_mo_hamiltonian(self, h_mo, eri_mo, nocc):
+        """Loads an MO-basis Hamiltonian directly (no RHF or FNO step)."""
         h, hp = _arr(h_mo)
         e, ep = _arr(eri_mo)
         self._check(self.lib.fnocc_set_mo_hamiltonian(self._h, hp, ep, h.shape[0], int(nocc)))
 
     def ccsdt_solve(self, tol_res=1e-10, tol_e=1e-12, maxiter=200, diis=8, precision="fp64", switch_tol=1e-6):
+        """CCSDT ground state (Eq. 5-7) by Jacobi + DIIS iterations."""
         opt = CcsdtOptions(tol_res, tol_e, maxiter, diis, PRECISION[precision], switch_tol)
         info = CcsdtInfo()
         st = self._check(self.lib.ccsdt_solve(self._h, ctypes.byref(opt), ctypes.byref(info)), allow=(0, 1))
@@ -431,11 +447,13 @@ class Context:
                     iters_mixed=info.iters_mixed)
 
     def amp_sizes(self):
+        """Packed sizes of T1, T2, T3."""
         from math import comb
         o, v, _ = self.dims()
         return [comb(o, r) * comb(v, r) for r in (1, 2, 3)]
 
     def ccsdt_residual(self, t1, t2, t3):
+        """CCSDT residuals (Eq. 6) and energy of packed host amplitudes."""
         sizes = self.amp_sizes()
         ins = [_arr(t) for t in (t1, t2, t3)]
         outs = [np.zeros(s) for s in sizes]
@@ -445,12 +463,14 @@ class Context:
         return outs, e.value
 
     def ccsdt_residual_dev(self, t1_ptr, t2_ptr, t3_ptr, r1_ptr, r2_ptr, r3_ptr):
+        """ccsdt_residual on device pointers."""
         e = ctypes.c_double()
         self._check(self.lib.ccsdt_residual_dev(self._h, t1_ptr, t2_ptr, t3_ptr, r1_ptr, r2_ptr, r3_ptr,
                                                 ctypes.byref(e)))
         return e.value
 
     def set_amplitudes(self, t1, t2, t3):
+        """Stores ground-state amplitudes (packed, host) for the EOM products."""
         ins = [_arr(t) for t in (t1, t2, t3)]
         self._check(self.lib.fnocc_set_amplitudes(self._h, ins[0][1], ins[1][1], ins[2][1]))
 
@@ -459,11 +479,13 @@ class Context:
         self._check(self.lib.fnocc_multi_dot(self._h, x_ptr, y_ptr, int(n), int(ld), int(nvec), dots_ptr))
 
     def eom_sizes(self, variant):
+        """Packed sizes of the variant's three EOM components."""
         sz = (ctypes.c_size_t * 3)()
         self._check(self.lib.fnocc_eom_sizes(self._h, VARIANTS.get(variant, variant), sz))
         return [int(x) for x in sz]
 
     def eom_sigma(self, variant, r):
+        """sigma = (H-bar R)_c of a packed host vector (Eq. 1-4)."""
         var = VARIANTS.get(variant, variant)
         r, rp = _arr(r)
         s = np.zeros_like(r)
@@ -471,9 +493,11 @@ class Context:
         return s
 
     def eom_sigma_dev(self, variant, r_ptr, s_ptr):
+        """eom_sigma on device pointers."""
         self._check(self.lib.eom_sigma_dev(self._h, VARIANTS.get(variant, variant), r_ptr, s_ptr))
 
     def eom_left_sigma_dev(self, variant, l_ptr, lam_ptr):
+        """eom_left_sigma on device pointers."""
         self._check(self.lib.eom_left_sigma_dev(self._h, VARIANTS.get(variant, variant), l_ptr, lam_ptr))
 
     def eom_left_sigma(self, variant, lvec):
@@ -503,6 +527,7 @@ class Context:
                     sigma_calls_mixed=info.sigma_calls_mixed, guess_used=info.guess_used)
 
     def eom_features(self, variant):
+        """Per-element features [dim x 8] of the learned guess."""
         var = VARIANTS.get(variant, variant)
         dim = sum(self.eom_sizes(var))
         f = np.zeros((dim, Mlp.NIN), dtype=np.float32)
@@ -517,6 +542,7 @@ class Context:
         return d
 
     def set_guess_model(self, mlp):
+        """Attaches the network FNOCC_GUESS_LEARNED uses (None detaches)."""
         self._guess_model = mlp  # keep the network alive while attached
         self._check(self.lib.fnocc_set_guess_model(self._h, mlp._h if mlp is not None else None))
 
