@@ -3,8 +3,8 @@
 Workload (one step): the seeded synthetic closed-shell Hamiltonian with 10
 electrons in 48 spatial orbitals (synth.hamiltonian(10, 48, seed)), frozen
 natural orbitals kept at occupation >= 1e-4, the CCSDT ground state, and the
-four lowest roots of IP-, EA-, DIP- and DEA-EOM-CCSDT (Davidson, diagonal
-guess, residual 1e-8, |d omega| 1e-10). A step is 4 EOM solves; `value` is
+four lowest roots of IP-, EA-, DIP- and DEA-EOM-CCSDT (Davidson from the
+Koopmans guess, residual 1e-8, |d omega| 1e-10). A step is 4 EOM solves; `value` is
 step time / 4.
 
   value  device-resident inputs (h, eri already in HBM), device time of the
@@ -467,7 +467,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_tf32"],
                     help="mixed: BF16 three-slice tensor-core contractions, then FP64 refinement; "
                          "mixed_tf32: TF32 two-slice")
-    ap.add_argument("--guess", default="diagonal", choices=["diagonal", "learned"],
+    ap.add_argument("--guess", default="koopmans", choices=["koopmans", "learned"],
                     help="learned: Davidson start and preconditioner from a network trained first (untimed)")
     ap.add_argument("--no-mixed-learned", action="store_true",
                     help="skip the mixed-precision + learned-guess arm of the default run")
@@ -530,8 +530,8 @@ def main():
 
     # mixed kinds: split products throughout the Davidson solves, converged to
     # the 1e-6 Eh accuracy target (no FP64 refinement sweep); CCSDT refines in FP64
-    eom_kw = (dict(precision=args.precision, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8)
-              if args.precision != "fp64" else dict(precision="fp64"))
+    eom_kw = (dict(precision=args.precision, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8, guess="koopmans")
+              if args.precision != "fp64" else dict(precision="fp64", guess="koopmans"))
     guess_net = {}
 
     def train_guess():
@@ -640,7 +640,7 @@ def main():
                     "per_root_err_eh": {v: [float(x) for x in np.asarray(mixed_e[v]) - np.asarray(ref_e[v])]
                                         for v in VARIANTS}}
     mixed_learned = None
-    if args.precision == "fp64" and args.guess == "diagonal" and not args.no_mixed_learned:
+    if args.precision == "fp64" and args.guess == "koopmans" and not args.no_mixed_learned:
         # the BF16x3 + learned-guess arm on the same inputs, at the 1e-6 Eh target
         info = train_guess()
         kw = dict(precision="mixed", switch_tol=0.0, tol_res=1e-6, tol_e=1e-8, guess="learned")
