@@ -1,0 +1,76 @@
+"""The oracle's pins catch plausible mistakes (CPU, no GPU).
+
+Each case plants one mistake in a copy of the oracle's arithmetic - a
+dropped term, a flipped sign, integrals read in the wrong index order, a
+wrong evaluation point - and checks that the independent reference the
+pins use (the Fock-space definition, or the closed form on linear data) no
+longer agrees. A pin that still passed here would not protect the
+oracle against that mistake.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import detspace, fno, packing, wick, xfno
+
+
+@pytest.fixture(scope="module")
+def small():
+    nocc, n = 2, 5
+    h, eri = synth.random_symmetric_mo_hamiltonian(n, 21)
+    ham = fno.mo_hamiltonian(h, eri, nocc)
+    o, v = ham["o"], ham["v"]
+    amps = {}
+    for r in (1, 2, 3):
+        x = synth.random_packed(math.comb(o, r) * math.comb(v, r), 40 + r, 0.1)
+        amps[r] = packing.unpack(x * synth.packed_ms_mask(r, r, o, v, 0), r, r, o, v)
+    return ham, amps, detspace.DefinitionOracle(ham["hso"], ham["g"], o)
+
+
+def _largest_term(terms, nh, np_, ham, a, o, v):
+    sizes = [np.max(np.abs(wick.evaluate((t,), nh, np_, ham["f"], ham["g"], a, o, v))) for t in terms]
+    return int(np.argmax(sizes))
+
+
+@pytest.mark.parametrize("mistake", ["drop", "sign"])
+def test_cc_definition_pin_catches_a_bad_term(small, mistake):
+    ham, amps, dso = small
+    o, v = ham["o"], ham["v"]
+    a = {"t1": amps[1], "t2": amps[2], "t3": amps[3]}
+    terms = list(wick.cc_terms(3))
+    k = _largest_term(terms, 3, 3, ham, a, o, v)
+    if mistake == "drop":
+        del terms[k]
+    else:
+        terms[k] = (terms[k][0], -terms[k][1])
+    got = wick.evaluate(tuple(terms), 3, 3, ham["f"], ham["g"], a, o, v)
+    ref = dso.cc_residual(amps, 3)
+    assert np.max(np.abs(got - ref)) > 1e-6
+
+
+def test_eom_definition_pin_catches_a_misordered_integral(small):
+    ham, amps, dso = small
+    o, v = ham["o"], ham["v"]
+    comps = wick.EOM_SPACES["ip"]
+    rs = [packing.unpack(synth.random_packed(packing.packed_size(nh, np_, o, v), 90 + k, 0.3), nh, np_, o, v)
+          for k, (nh, np_) in enumerate(comps)]
+    a = {"t1": amps[1], "t2": amps[2], "t3": amps[3], "r1": rs[0], "r2": rs[1], "r3": rs[2]}
+    terms = wick.eom_terms("ip", 1, 1)
+    # <pq||rs> read in chemists' order (<pr||qs>): the index-order mistake
+    gbad = ham["g"].transpose(0, 2, 1, 3)
+    got = wick.evaluate(terms, 2, 1, ham["f"], gbad, a, o, v)
+    ref = dso.eom_sigma(amps, [(rs[k],) + comps[k] for k in range(3)], 2, 1) - sum(
+        wick.evaluate(wick.eom_terms("ip", 1, ic), 2, 1, ham["f"], ham["g"], a, o, v) for ic in (0, 2))
+    good = wick.evaluate(terms, 2, 1, ham["f"], ham["g"], a, o, v)
+    assert np.max(np.abs(good - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(got - ref)) > 1e-6
+
+
+def test_xfno_pin_catches_the_wrong_evaluation_point():
+    f = np.array([0.999, 0.9975, 0.995])
+    e = -1.2 + 0.4 * (1 - f)          # linear data: the extrapolation must return -1.2
+    assert abs(xfno.extrapolate(f, e) + 1.2) < 1e-12
+    slope, icpt = np.polyfit(f, e, 1)
+    assert abs(icpt + 1.2) > 1e-3      # evaluating at f = 0 instead of 1 would fail the pin
