@@ -2,9 +2,10 @@
 
 Each case plants one mistake in a copy of the oracle's arithmetic - a
 dropped term, a flipped sign, integrals read in the wrong index order, a
-wrong evaluation point - and checks that the independent reference the
-pins use (the Fock-space definition, or the closed form on linear data) no
-longer agrees. A pin that still passed here would not protect the
+wrong evaluation point, a wrong-signed gradient block, a dropped factor -
+and checks that the independent reference the pins use (the Fock-space
+definition, the closed form on linear data, finite differences, second-order
+perturbation theory in determinant space) no longer agrees. A pin that still passed here would not protect the
 oracle against that mistake.
 """
 import math
@@ -74,3 +75,51 @@ def test_xfno_pin_catches_the_wrong_evaluation_point():
     assert abs(xfno.extrapolate(f, e) + 1.2) < 1e-12
     slope, icpt = np.polyfit(f, e, 1)
     assert abs(icpt + 1.2) > 1e-3      # evaluating at f = 0 instead of 1 would fail the pin
+
+
+def test_mlp_gradient_pin_catches_a_wrong_layer_gradient():
+    """The finite-difference pin of the guess network's gradient rejects a
+    gradient whose hidden-layer bias block has the wrong sign."""
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    width, n = 5, 7
+    nparam = mlp.NIN * width + width + width * width + width + width * mlp.NOUT + mlp.NOUT
+    params = rng.normal(0, 0.5, nparam)
+    x, t = rng.normal(0, 1.0, (n, mlp.NIN)), rng.normal(0, 1.0, (n, mlp.NOUT))
+    w = rng.uniform(0.2, 1.5, (n, mlp.NOUT))
+    _, g = mlp.loss_grad(params, x, t, w, width)
+    bad = g.copy()
+    b1 = slice(mlp.NIN * width, mlp.NIN * width + width)   # first bias block (parameter layout)
+    bad[b1] = -bad[b1]
+    h = 1e-6
+    fd = np.array([(mlp.loss_grad(params + h * e, x, t, w, width)[0]
+                    - mlp.loss_grad(params - h * e, x, t, w, width)[0]) / (2 * h) for e in np.eye(nparam)])
+    tol = 1e-7 * max(1.0, np.max(np.abs(fd)))
+    assert np.max(np.abs(g - fd)) < tol
+    assert np.max(np.abs(bad - fd)) > tol
+
+
+def test_mp2_density_pin_catches_a_dropped_half():
+    """Second-order perturbation theory in determinant space rejects the
+    vv density without the 1/2 of Eq. 10."""
+    h, eri = synth.hamiltonian(4, 5, seed=2)
+    scf = fno.rhf(h, eri, 2)
+    act = fno.active_hamiltonian(h, eri, scf["c"], 2)
+    hso, g, o = act["hso"], act["g"], act["o"]
+    d = fno.mp2_vv_density(act["f"], g, o)
+    fs = detspace.FockSpace(hso.shape[0])
+    hmat = fs.hamiltonian(hso, g)
+    ref = fs.vacuum(range(o))
+    eso = np.repeat(scf["eps"], 2)
+    occ_energy = np.array([eso[[p for p in range(len(eso)) if (s >> p) & 1]].sum() for s in fs.states])
+    hv = hmat @ ref
+    e0 = occ_energy[int(np.argmax(ref))]
+    n_e = np.bitwise_count(fs.states)
+    psi1 = np.zeros(fs.dim)
+    sel = (n_e == o) & (ref == 0) & (np.abs(hv) > 0)
+    psi1[sel] = -hv[sel] / (occ_energy[sel] - e0)
+    vir = list(range(o, hso.shape[0]))
+    dd = np.array([[psi1 @ (fs.string([(a, True), (b, False)]) @ psi1) for b in vir] for a in vir])
+    tol = 1e-10 * np.max(np.abs(d))
+    assert np.max(np.abs(dd - d)) < tol
+    assert np.max(np.abs(dd - 2 * d)) > tol
