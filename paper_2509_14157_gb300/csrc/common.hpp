@@ -104,7 +104,7 @@ struct GTask {
 
 // A grouped launch: tasks ordered by cta_begin (device array) plus the list
 // of tasks with a split reduction.
-constexpr int kGShapes = 14;           // FP64 tile shapes
+constexpr int kGShapes = 19;           // FP64 tile shapes (14 with a K tile of 16, 5 of them again with 8)
 constexpr int kGShapeBf16 = kGShapes;  // first BF16 three-slice split shape (mixed precision)
 constexpr int kGShapesBf16 = 6;        // BF16x3 tiles 64x64, 32x32, 128x16, 16x128, 64x16, 16x64
 constexpr int kGShapesAll = kGShapes + kGShapesBf16;

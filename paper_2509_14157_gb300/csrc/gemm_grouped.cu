@@ -45,13 +45,15 @@ __device__ __forceinline__ int find_task(const GTask *tasks, int ntasks, long lo
 }
 
 // FP64 tile kernel: threads as TY x TX (TX = 256 / TY), each a TM x TN
-// micro-tile; the block covers (TY*TM) x (TX*TN) outputs; K staged 16 at a
-// time through shared memory.
-template <int TY, int TM, int TN>
+// micro-tile; the block covers (TY*TM) x (TX*TN) outputs; K staged BKG at a
+// time through shared memory (16, or 8 for the short reductions of single
+// spin blocks, e.g. K = 5, where a 16-wide K tile would pad 3.2x).
+template <int TY, int TM, int TN, int BKG = 16>
 __global__ void __launch_bounds__(NT) k_ggemm(const GTask *__restrict__ tasks, int ntasks, double alpha,
                                               const double *__restrict__ A, const double *__restrict__ B,
                                               double *__restrict__ C, double *__restrict__ part) {
-  constexpr int TX = NT / TY, TBM = TY * TM, TBN = TX * TN, BKG = 16;
+  static_assert(2 * BKG <= NT, "index staging uses 2 * BKG threads");
+  constexpr int TX = NT / TY, TBM = TY * TM, TBN = TX * TN;
   __shared__ double As[BKG][TBM];
   __shared__ double Bs[BKG][TBN];
   __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[BKG], brow_s[BKG];
@@ -447,10 +449,13 @@ __global__ void k_greduce(const GTask *__restrict__ tasks, const int *__restrict
   C[t.crow[m] + t.ccol[n]] += alpha * s;
 }
 
-// (TY, TM, TN) of the FP64 shapes
-constexpr int kShapeDims[kGShapes][3] = {{16, 4, 4}, {16, 8, 2}, {16, 2, 8}, {16, 8, 1}, {16, 1, 8},
-                                         {16, 2, 2}, {16, 1, 1}, {64, 2, 1}, {256, 1, 1}, {4, 1, 2},
-                                         {8, 1, 4},  {2, 1, 1},  {32, 1, 1}, {128, 1, 1}};
+// (TY, TM, TN, K tile) of the FP64 shapes; the last five repeat shapes 0,
+// 6, 8, 11 and 12 with a K tile of 8
+constexpr int kShapeDims[kGShapes][4] = {
+    {16, 4, 4, 16}, {16, 8, 2, 16}, {16, 2, 8, 16}, {16, 8, 1, 16}, {16, 1, 8, 16}, {16, 2, 2, 16},
+    {16, 1, 1, 16}, {64, 2, 1, 16}, {256, 1, 1, 16}, {4, 1, 2, 16},  {8, 1, 4, 16},  {2, 1, 1, 16},
+    {32, 1, 1, 16}, {128, 1, 1, 16}, {16, 4, 4, 8},  {16, 1, 1, 8},  {256, 1, 1, 8}, {2, 1, 1, 8},
+    {32, 1, 1, 8}};
 // (WM, WN, MT, NT2) of the BF16x3 shapes: 64x64, 32x32, 128x16, 16x128, 64x16, 16x64
 constexpr int kBf16Dims[kGShapesBf16][4] = {{2, 4, 2, 2}, {2, 4, 1, 1}, {8, 1, 1, 2},
                                             {1, 8, 1, 2}, {4, 2, 1, 1}, {1, 8, 1, 1}};
@@ -471,7 +476,7 @@ void grouped_shape(int shape, int *tbm, int *tbn, int *tbk) {
   const int ty = kShapeDims[shape][0], tx = NT / ty;
   *tbm = ty * kShapeDims[shape][1];
   *tbn = tx * kShapeDims[shape][2];
-  *tbk = 16;
+  *tbk = kShapeDims[shape][3];
 }
 
 void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const double *A, const double *B, double *C) {
@@ -495,23 +500,28 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0], L.stream));
   }
   const unsigned grid = (unsigned)g.ncta;
-#define FNOCC_G(i, ty, tm, tn) \
-  case i: k_ggemm<ty, tm, tn><<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part); break;
+#define FNOCC_G(i, ty, tm, tn, bk) \
+  case i: k_ggemm<ty, tm, tn, bk><<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part); break;
   switch (g.shape) {
-    FNOCC_G(0, 16, 4, 4)
-    FNOCC_G(1, 16, 8, 2)
-    FNOCC_G(2, 16, 2, 8)
-    FNOCC_G(3, 16, 8, 1)
-    FNOCC_G(4, 16, 1, 8)
-    FNOCC_G(5, 16, 2, 2)
-    FNOCC_G(6, 16, 1, 1)
-    FNOCC_G(7, 64, 2, 1)
-    FNOCC_G(8, 256, 1, 1)
-    FNOCC_G(9, 4, 1, 2)
-    FNOCC_G(10, 8, 1, 4)
-    FNOCC_G(11, 2, 1, 1)
-    FNOCC_G(12, 32, 1, 1)
-    FNOCC_G(13, 128, 1, 1)
+    FNOCC_G(0, 16, 4, 4, 16)
+    FNOCC_G(1, 16, 8, 2, 16)
+    FNOCC_G(2, 16, 2, 8, 16)
+    FNOCC_G(3, 16, 8, 1, 16)
+    FNOCC_G(4, 16, 1, 8, 16)
+    FNOCC_G(5, 16, 2, 2, 16)
+    FNOCC_G(6, 16, 1, 1, 16)
+    FNOCC_G(7, 64, 2, 1, 16)
+    FNOCC_G(8, 256, 1, 1, 16)
+    FNOCC_G(9, 4, 1, 2, 16)
+    FNOCC_G(10, 8, 1, 4, 16)
+    FNOCC_G(11, 2, 1, 1, 16)
+    FNOCC_G(12, 32, 1, 1, 16)
+    FNOCC_G(13, 128, 1, 1, 16)
+    FNOCC_G(14, 16, 4, 4, 8)
+    FNOCC_G(15, 16, 1, 1, 8)
+    FNOCC_G(16, 256, 1, 1, 8)
+    FNOCC_G(17, 2, 1, 1, 8)
+    FNOCC_G(18, 32, 1, 1, 8)
 #define FNOCC_B(i, wm, wn, mt, nt)                                                                   \
   case kGShapeBf16 + i:                                                                              \
     launch_tensor<wm, wn, mt, nt>(L.precision, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part); \
