@@ -178,7 +178,7 @@ def test_plan_stats_are_consistent():
     the DEA product's grouped flops match the algorithmic count the library
     reports for it (5.3e9 at o = 10, v = 30)."""
     peak = 152 * 2 * 2 * 2.07e9
-    tot = 0.0
+    tot = padded = grouped = 0.0
     for oc in range(3):
         for ic in range(3):
             s = pkg.plan_stats(1, "dea", oc, ic, o=10, v=30)
@@ -186,7 +186,11 @@ def test_plan_stats_are_consistent():
             assert s["model_seconds"] >= s["grouped_flops"] / peak * (1 - 1e-12)
             assert s["small_launch_flops"] <= s["grouped_flops"]
             tot += s["grouped_flops"] + s["other_flops"]
+            padded += s["padded_flops"]
+            grouped += s["grouped_flops"]
     assert 5.2e9 < tot < 5.45e9
+    # the tile set keeps the padding of this product low (1.40 with 16-wide K tiles only)
+    assert padded / grouped < 1.25
     with pytest.raises(ValueError):
         pkg.plan_stats(1, "dea", 3, 0)
 
