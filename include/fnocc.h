@@ -396,11 +396,14 @@ long fnocc_equation_text(int kind, int variant, int out_comp, int in_comp, char 
 
 /* Host-only consistency check of the executable plan of the same equation
  * at sizes (o, v) (not in the paper; a test of the library's own
- * bookkeeping): for every grouped contraction step with at most max_work
- * multiply-adds and every tile shape, the (A, B, C) element offsets its
- * tasks address (flat tables) must equal, as a multiset, those of the
- * spin-allowed blocks decoded through the per-group offset tables, and the
- * tasks' CTA ranges must tile the grid. Returns the number of
+ * bookkeeping): for every grouped contraction step and every tile shape,
+ * the launch descriptors must be consistent (CTA ranges tile the grid,
+ * tiles match the shape, reduction splits cover K without empty splits in
+ * whole K tiles, partial sums and their ordered reduction tile their
+ * buffers); for steps with at most max_work multiply-adds the (A, B, C)
+ * element offsets the tasks address (flat tables) must also equal, as a
+ * multiset, those of the spin-allowed blocks decoded through the per-group
+ * offset tables. Returns the number of
  * inconsistencies (0 = consistent) or -1 on bad arguments. No GPU needed. */
 long fnocc_plan_selfcheck(int kind, int variant, int out_comp, int in_comp, int o, int v, double max_work);
 

@@ -950,6 +950,32 @@ long long ExecEquation::self_check(double max_work) const {
       if (!s.grouped) continue;
       double work = 0;
       for (auto &tr : s.tasks) work += double(tr.M) * double(tr.N) * double(tr.K);
+      // launch descriptors of every shape: checked for every step
+      for (int shape = 0; shape < kGShapesAll; ++shape) {
+        const GroupedLaunch &gl = s.gl[shape];
+        int tbm, tbn, tbk;
+        grouped_shape(shape, &tbm, &tbn, &tbk);
+        long long ctas = 0, part = 0, red = 0;
+        int nsplit = 0;
+        for (int i = 0; i < gl.ntasks; ++i) {
+          const GTask &g = gl.tasks[i];
+          if (g.cta_begin != ctas) ++bad;  // CTA ranges must tile the grid in order
+          ctas += g.tiles * g.ksplit;
+          if ((long long)g.ksplit * g.kchunk < g.K) ++bad;  // the splits cover K
+          if (g.ksplit > 1 && (long long)(g.ksplit - 1) * g.kchunk >= g.K) ++bad;  // no empty split
+          if (g.kchunk % tbk != 0) ++bad;  // whole K tiles per split
+          // the kernel's tiling of this shape
+          if (g.tiles_n != (g.N + tbn - 1) / tbn || g.tiles != ((g.M + tbm - 1) / tbm) * g.tiles_n) ++bad;
+          if (g.ksplit > 1) {  // partial sums and their ordered reduction tile their buffers in order
+            ++nsplit;
+            if (g.part_off != part || g.red_begin != red) ++bad;
+            part += (long long)g.ksplit * g.M * g.N;
+            red += g.M * g.N;
+          }
+        }
+        if (ctas != gl.ncta) ++bad;
+        if (part != gl.part_need || red != gl.nred || nsplit != gl.nsplit) ++bad;
+      }
       if (work > max_work) continue;
       std::vector<Trip> ref;
       auto add_ref = [&](long long M, long long N, long long K, const DMap &ar, const DMap &ac, const DMap &br,
@@ -972,18 +998,13 @@ long long ExecEquation::self_check(double max_work) const {
       for (int shape = 0; shape < kGShapesAll; ++shape) {
         const GroupedLaunch &gl = s.gl[shape];
         std::vector<Trip> got;
-        long long ctas = 0;
         for (int i = 0; i < gl.ntasks; ++i) {
           const GTask &g = gl.tasks[i];
-          if (g.cta_begin != ctas) ++bad;  // CTA ranges must tile the grid in order
-          ctas += g.tiles * g.ksplit;
-          if ((long long)g.ksplit * g.kchunk < g.K) ++bad;  // the splits cover K
           for (long long m = 0; m < g.M; ++m)
             for (long long n = 0; n < g.N; ++n)
               for (long long k = 0; k < g.K; ++k)
                 got.emplace_back(g.arow[m] + g.acol[k], g.brow[k] + g.bcol[n], g.crow[m] + g.ccol[n]);
         }
-        if (ctas != gl.ncta) ++bad;
         std::sort(got.begin(), got.end());
         if (got != ref) ++bad;
       }

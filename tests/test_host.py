@@ -195,6 +195,21 @@ def test_plan_stats_are_consistent():
         pkg.plan_stats(1, "dea", 3, 0)
 
 
+def test_launch_descriptors_at_the_benchmark_size():
+    """Every grouped step of every CCSDT rank and every right and left
+    product block at the benchmark's size (o = 10, v = 30): the launch
+    descriptors of all tile shapes (including the split reductions of the
+    large steps) are consistent; the small steps' tables match the spin
+    blocks element by element."""
+    bad = sum(pkg.plan_selfcheck(0, 0, r, 0, 10, 30, 2e5) for r in range(1, 4))
+    for kind in (1, 2):
+        for var in ("ip", "ea", "dip", "dea", "ee"):
+            for oc in range(3):
+                for ic in range(3):
+                    bad += pkg.plan_selfcheck(kind, var, oc, ic, 10, 30, 2e5)
+    assert bad == 0
+
+
 def test_plans_build_at_the_largest_workload():
     """Every CCSDT rank and every right and left product block builds its
     executable plan host-only at the largest workload (16 electrons, 41 kept
