@@ -505,3 +505,43 @@ def test_en_shift_from_spatial_coulomb_and_exchange():
         fh = tuple(sorted(i ^ 1 for i in hs))
         fp = tuple(sorted(a ^ 1 for a in ps))
         assert np.allclose(feats[r], feats[rows[(comp, fh, fp)]])
+
+
+def _random_tuples(o, v, nh, np_, count, seed):
+    """Output elements in any index order (unsorted, repeated indices
+    included), so that a transposed gather in the sampled evaluation shows."""
+    rng = np.random.default_rng(seed)
+    hs = rng.integers(0, o, size=(count, nh))
+    ps = rng.integers(0, v, size=(count, np_))
+    return np.concatenate([hs, ps], axis=1)
+
+
+@pytest.mark.parametrize("rank", [1, 2, 3])
+def test_sampled_cc_residual_equals_definition(small_system, rank):
+    """wick.evaluate_at (the checker of the large parity cases) against the
+    Fock-space definition at arbitrary output elements."""
+    ham, amps, dso = small_system
+    o, v = ham["o"], ham["v"]
+    a = {"t1": amps[1], "t2": amps[2], "t3": amps[3]}
+    ref = dso.cc_residual(amps, rank)
+    tup = _random_tuples(o, v, rank, rank, 400, 60 + rank)
+    got = wick.evaluate_at(wick.cc_terms(rank), rank, rank, ham["f"], ham["g"], a, o, v, tup)
+    want = ref[tuple(tup.T)]
+    assert np.max(np.abs(got - want)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea", "ee"])
+def test_sampled_eom_sigma_equals_definition(small_system, variant):
+    ham, amps, dso = small_system
+    o, v = ham["o"], ham["v"]
+    comps = wick.EOM_SPACES[variant]
+    rs = [packing.unpack(synth.random_packed(packing.packed_size(nh, np_, o, v), 95 + k, 0.3), nh, np_, o, v)
+          for k, (nh, np_) in enumerate(comps)]
+    a = {"t1": amps[1], "t2": amps[2], "t3": amps[3], "r1": rs[0], "r2": rs[1], "r3": rs[2]}
+    for oc, (nh, np_) in enumerate(comps):
+        ref = dso.eom_sigma(amps, [(rs[k],) + comps[k] for k in range(3)], nh, np_)
+        tup = _random_tuples(o, v, nh, np_, 300, 70 + oc)
+        got = sum(wick.evaluate_at(wick.eom_terms(variant, oc, ic), nh, np_, ham["f"], ham["g"], a, o, v, tup)
+                  for ic in range(3))
+        want = ref[tuple(tup.T)]
+        assert np.max(np.abs(got - want)) < 1e-12 * max(1.0, np.max(np.abs(ref))), (variant, oc)

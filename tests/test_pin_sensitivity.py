@@ -123,3 +123,21 @@ def test_mp2_density_pin_catches_a_dropped_half():
     tol = 1e-10 * np.max(np.abs(d))
     assert np.max(np.abs(dd - d)) < tol
     assert np.max(np.abs(dd - 2 * d)) > tol
+
+
+def test_sampled_evaluation_pin_catches_a_transposed_gather(small):
+    """The sampled-element checker of the large parity cases, with its two
+    hole columns swapped (a transposed external gather), no longer matches
+    the Fock-space definition, while the correct gather does."""
+    ham, amps, dso = small
+    o, v = ham["o"], ham["v"]
+    a = {"t1": amps[1], "t2": amps[2], "t3": amps[3]}
+    ref = dso.cc_residual(amps, 2)
+    rng = np.random.default_rng(8)
+    tup = np.concatenate([rng.integers(0, o, (200, 2)), rng.integers(0, v, (200, 2))], axis=1)
+    good = wick.evaluate_at(wick.cc_terms(2), 2, 2, ham["f"], ham["g"], a, o, v, tup)
+    bad = wick.evaluate_at(wick.cc_terms(2), 2, 2, ham["f"], ham["g"], a, o, v, tup[:, [1, 0, 2, 3]])
+    want = ref[tuple(tup.T)]
+    tol = 1e-12 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(good - want)) < tol
+    assert np.max(np.abs(bad - want)) > 1e-6
