@@ -212,6 +212,30 @@ fnocc_status eom_ccsdt_solve(fnocc_ctx *ctx, int variant, int nroots, int guess,
  * default FP64). The solvers take theirs from their options. */
 fnocc_status fnocc_set_precision(fnocc_ctx *ctx, int precision);
 
+/* Tile shape of the grouped contraction kernel (not in the paper; a test
+ * and analysis facility of the library). shape -1 (the default) lets the
+ * library choose per contraction step (least padded work per busy SM,
+ * large FP64 steps timed once and the fastest kept); 0 <= shape < the count
+ * returned by fnocc_tile_shape_count forces one shape for every grouped step
+ * of the matching arithmetic: shapes below the first mixed-precision shape
+ * (the FP64 tiles) apply to FP64 contractions, the others to the split
+ * products. Results do not depend on the shape beyond FP64 reassociation.
+ * Returns FNOCC_E_INVALID for other values. */
+fnocc_status fnocc_set_tile_shape(fnocc_ctx *ctx, int shape);
+/* Number of tile shapes (FP64 shapes first, then the split-product shapes);
+ * fnocc_tile_shape_first_mixed gives the index of the first split-product
+ * shape. */
+int fnocc_tile_shape_count(void);
+int fnocc_tile_shape_first_mixed(void);
+/* Process-wide switch of the tile-shape timing (on by default): when on, an
+ * FP64 contraction step above 1e8 padded flops times its candidate shapes
+ * once and keeps the fastest, so two runs can pick different shapes and
+ * their FP64 sums can differ in the last bits (each shape sums in a fixed
+ * order). Off: every step runs its estimated shape and repeated runs are
+ * bitwise identical. Takes effect for contraction steps issued after the
+ * call. */
+fnocc_status fnocc_set_autotune(int enable);
+
 /* sigma = (H-bar R)_c for a packed EOM vector (host pointers). R is taken in
  * the variant's target spin sector (2*dM_s = +1 for IP/EA, 0 for DIP/DEA/EE):
  * components outside it do not contribute, and sigma is returned in that
@@ -267,7 +291,11 @@ fnocc_status fnocc_multi_dot(fnocc_ctx *ctx, const double *x, const double *Y, s
  * exits. Limit: nvec <= 64; larger nvec (or nvec < 1, n = 0, ld < n, a NULL
  * pointer) returns FNOCC_E_INVALID without touching the GPU.
  * The first call on a device, with that device current, looks up the
- * scratch's device address; make that first call before any stream capture.
+ * scratch's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. Every call waits for its stream
+ * (cudaStreamSynchronize) before it returns. A CUDA error already pending on
+ * the calling thread when the call starts is left in place for the caller
+ * and the call returns FNOCC_E_CUDA without launching anything.
  * Every call shares the one array: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * The array keeps the last call's partial sums; each call overwrites every
@@ -428,6 +456,14 @@ long fnocc_plan_text(int kind, int variant, int out_comp, int in_comp, int o, in
  * of large steps may differ at run time. Returns FNOCC_E_INVALID on bad
  * arguments. */
 fnocc_status fnocc_plan_stats(int kind, int variant, int out_comp, int in_comp, int o, int v, double *stats);
+
+/* FP64 throughput of device `device` (not in the paper; the denominators
+ * of the FP64 roofline fractions): best of five timed launches of
+ * register-only chains of independent FP64 FMAs (fma_tflops) and of FP64
+ * tensor-core products mma.sync m8n8k4 (dmma_tflops) on every SM, 2 flops
+ * per multiply-add. Needs no context; allocates and frees a small buffer and
+ * a stream of its own and takes about a second. */
+fnocc_status fnocc_fp64_peak(int device, double *fma_tflops, double *dmma_tflops);
 
 /* Count of kernel launches issued by the context so far. */
 uint64_t fnocc_launch_count(const fnocc_ctx *ctx);

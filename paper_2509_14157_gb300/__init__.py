@@ -111,6 +111,11 @@ SIGNATURES = {
                                         ctypes.POINTER(FnoOptions), ctypes.POINTER(FnoInfo), _dp]),
     "fnocc_flop_count": (ctypes.c_double, [_cp]),
     "fnocc_set_precision": (ctypes.c_int, [_cp, ctypes.c_int]),
+    "fnocc_set_tile_shape": (ctypes.c_int, [_cp, ctypes.c_int]),
+    "fnocc_tile_shape_count": (ctypes.c_int, []),
+    "fnocc_tile_shape_first_mixed": (ctypes.c_int, []),
+    "fnocc_set_autotune": (ctypes.c_int, [ctypes.c_int]),
+    "fnocc_fp64_peak": (ctypes.c_int, [ctypes.c_int, _dp, _dp]),
     "fnocc_multi_dot": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp]),
     "fnocc_multi_dot_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp, _vp]),
     "fnocc_equation_text": (ctypes.c_long, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -207,6 +212,27 @@ def batch_solve(systems, variants, nroots, device=0, nworkers=4, cc_tol_res=1e-1
     out = [dict(status=r.status, nkept=r.nkept, e_rhf=r.e_rhf, e_ccsdt=r.e_ccsdt, ccsdt_iters=r.ccsdt_iters,
                 sigma_calls=r.sigma_calls, seconds=r.seconds) for r in res]
     return om, out
+
+
+def tile_shapes():
+    """(number of tile shapes, index of the first split-product shape)."""
+    lib = load_library()
+    return int(lib.fnocc_tile_shape_count()), int(lib.fnocc_tile_shape_first_mixed())
+
+
+def fp64_peak(device=0):
+    """Measured FP64 throughput of the device in TFLOP/s: (FMA, mma.sync m8n8k4)."""
+    lib = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = lib.fnocc_fp64_peak(int(device), ctypes.byref(a), ctypes.byref(b))
+    if st != 0:
+        raise FnoccError(st, "fnocc_fp64_peak failed")
+    return a.value, b.value
+
+
+def set_autotune(enable):
+    """Process-wide switch of the FP64 tile-shape timing (fnocc_set_autotune)."""
+    load_library().fnocc_set_autotune(1 if enable else 0)
 
 
 def equation_text(kind, variant=0, out_comp=0, in_comp=0):
@@ -409,6 +435,10 @@ class Context:
         """Arithmetic of standalone residual / sigma calls: 'fp64', 'mixed'
         (BF16 three-slice split products) or 'mixed_tf32' (TF32 two-slice)."""
         self._check(self.lib.fnocc_set_precision(self._h, PRECISION[precision]))
+
+    def set_tile_shape(self, shape):
+        """Forces one grouped-GEMM tile shape (-1: the library's choice)."""
+        self._check(self.lib.fnocc_set_tile_shape(self._h, int(shape)))
 
     @property
     def flops(self):

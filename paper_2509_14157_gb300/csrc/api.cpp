@@ -139,7 +139,9 @@ struct fnocc_ctx {
   double flops_total = 0;
   int precision = 0;          // fnocc_precision of the contractions currently issued
   int default_precision = 0;  // for standalone residual / sigma calls
-  Launch L() { return Launch{stream, &launches, &prof, &partials, precision}; }
+  int sms = 152;              // multiprocessors of the device (read at creation)
+  int force_shape = -1;       // fnocc_set_tile_shape
+  Launch L() { return Launch{stream, &launches, &prof, &partials, precision, sms, force_shape}; }
 
   // active Hamiltonian (spin orbitals, bare)
   bool have_ham = false;
@@ -334,7 +336,7 @@ void dress(fnocc_ctx *c, const double *t1) {
 void ensure_cc_plans(fnocc_ctx *c) {
   int rd[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   for (int r = 0; r < 4; ++r)
-    if (!c->cc_eq[r]) c->cc_eq[r].reset(new ExecEquation(cc_equation(r), c->o, c->v, rd));
+    if (!c->cc_eq[r]) c->cc_eq[r].reset(new ExecEquation(cc_equation(r), c->o, c->v, rd, 0.0, 0.0, 0, false, c->sms));
 }
 
 // residual of packed amplitudes tp (device) into rp (device); returns E_corr
@@ -412,7 +414,8 @@ void ensure_eom_plans(fnocc_ctx *c, int var, bool left) {
     for (int ic = 0; ic < 3; ++ic)
       if (!eqs[oc][ic])
         eqs[oc][ic].reset(new ExecEquation(left ? eom_left_equation(var, oc, ic) : eom_equation(var, oc, ic), c->o,
-                                           c->v, rd, kSigmaAmortize, kCacheCapDoubles, kSectorMs2[var]));
+                                           c->v, rd, kSigmaAmortize, kCacheCapDoubles, kSectorMs2[var], false,
+                                           c->sms));
 }
 
 // prepares dressed operators and dense T2/T3 from the stored amplitudes
@@ -653,6 +656,8 @@ fnocc_status fnocc_create(fnocc_ctx **out, int device, void *cuda_stream) {
     if (device < 0 || device >= ndev) throw StatusError(FNOCC_E_INVALID, "invalid device index");
     FNOCC_CUDA(cudaSetDevice(device));
     c->device = device;
+    FNOCC_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
+    if (c->sms < 1) c->sms = 1;
     if (cuda_stream) {
       c->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -1218,6 +1223,20 @@ fnocc_status fnocc_set_precision(fnocc_ctx *c, int precision) {
   c->default_precision = precision;
   return FNOCC_OK;
 }
+
+fnocc_status fnocc_set_tile_shape(fnocc_ctx *c, int shape) {
+  if (!c || shape < -1 || shape >= fnocc_tile_shape_count()) return FNOCC_E_INVALID;
+  c->force_shape = shape;
+  return FNOCC_OK;
+}
+
+int fnocc_tile_shape_count(void) { return kGShapesAll; }
+
+fnocc_status fnocc_set_autotune(int enable) {
+  ExecEquation::autotune = enable != 0;
+  return FNOCC_OK;
+}
+int fnocc_tile_shape_first_mixed(void) { return kGShapeBf16; }
 
 fnocc_status fnocc_eom_sizes(const fnocc_ctx *c, int variant, size_t *sizes) {
   if (!c || !sizes || variant < 0 || variant >= kEomVariants) return FNOCC_E_INVALID;

@@ -84,6 +84,8 @@ struct Launch {
   GemmProfile *prof = nullptr;
   DevBuf *partials = nullptr;  // split-K partial sums (deterministic reduction)
   int precision = 0;  // 0 FP64; tensor-core split products (tiled path): 1 BF16 three-slice, 2 TF32 two-slice
+  int sms = 152;       // streaming multiprocessors of the device (grid sizing)
+  int force_shape = -1;  // >= 0: every grouped step of the matching arithmetic runs this tile shape
 };
 
 // One sub-GEMM of a grouped launch: C[crow[m] + ccol[n]] += alpha *

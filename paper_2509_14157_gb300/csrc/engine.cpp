@@ -423,8 +423,8 @@ void build_tasks(const TableBuilder &tb, ExecStep &e, std::vector<long long> &fl
 }  // namespace
 
 ExecEquation::ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize,
-                           double cache_cap, int r_charge, bool host_only)
-    : nh_(eq.nh), np_(eq.np), o_(o), v_(v), host_only_(host_only) {
+                           double cache_cap, int r_charge, bool host_only, int sms)
+    : nh_(eq.nh), np_(eq.np), o_(o), v_(v), sms_(sms > 0 ? sms : 152), host_only_(host_only) {
   TableBuilder tb;
   std::vector<long long> flat_host;
   Storage outs = output_storage(nh_, np_, o, v);
@@ -632,12 +632,12 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
     FNOCC_CUDA(cudaMemcpy(flat_.p, flat_host.data(), sizeof(long long) * flat_host.size(), cudaMemcpyHostToDevice));
     fb = flat_.as<long long>();
   }
-  constexpr long long kSms = 152;
-  constexpr long long kWantCta = 2 * kSms;   // at least two CTAs per SM where the tiles allow
-  constexpr long long kFillCta = 4 * kSms;   // FP64 shapes: split at most up to four CTAs per SM
+  const long long kSms = std::max(1, sms_);
+  const long long kWantCta = 2 * kSms;   // at least two CTAs per SM where the tiles allow
+  const long long kFillCta = 4 * kSms;   // FP64 shapes: split at most up to four CTAs per SM
   constexpr long long kPartCap = 1LL << 27;  // doubles of split partials per launch
   // CTA-times per CTA of a launch of c equal resident CTAs (smaller is better)
-  auto wave_cost = [](long long c) { return double((c + kSms - 1) / kSms) / double(std::max<long long>(1, c)); };
+  auto wave_cost = [kSms](long long c) { return double((c + kSms - 1) / kSms) / double(std::max<long long>(1, c)); };
   std::vector<GTask> gt;
   std::vector<int> sid;
   struct Fix { GroupedLaunch *gl; size_t t0, s0; };
@@ -719,7 +719,7 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
           double staged = 0;
           for (size_t i = gt.size() - e.tasks.size(); i < gt.size(); ++i)
             staged += double(gt[i].tiles) * double((gt[i].K + tbk - 1) / tbk) * double((tbm + tbn) * tbk);
-          est[shape] = staged / double(std::max<long long>(1, std::min<long long>(cta, 2 * 152)));
+          est[shape] = staged / double(std::max<long long>(1, std::min<long long>(cta, 2 * kSms)));
         }
       }
       int bbest = kGShapeBf16;
@@ -843,7 +843,12 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         throw std::runtime_error("engine: grouped index tables exceed operand bounds");
       ExecStep &ms = const_cast<ExecStep &>(s);
       if (L.precision != 0 && s.gl[0].flops >= 1e5) {
-        grouped_gemm(L, s.gl[s.bf16_shape], s.alpha, A, B, C);
+        const bool forced = L.force_shape >= kGShapeBf16 && L.force_shape < kGShapesAll;
+        grouped_gemm(L, s.gl[forced ? L.force_shape : s.bf16_shape], s.alpha, A, B, C);
+        continue;
+      }
+      if (L.precision == 0 && L.force_shape >= 0 && L.force_shape < kGShapes) {
+        grouped_gemm(L, s.gl[L.force_shape], s.alpha, A, B, C);
         continue;
       }
       const bool tune = autotune && L.precision == 0 && ms.tuned_shape < 0 && ms.cand.size() > 1 &&
@@ -913,7 +918,7 @@ DMap host_sub(const DMap &full, const std::vector<std::pair<long long, long long
 // triples of the spin-allowed blocks decoded through the per-group tables.
 void ExecEquation::stats(double out[10]) const {
   // model time of one launch on the FP64 pipe: padded multiply-adds of its
-  // busiest SM, ceil(c / 152) CTA-times of padded / c each, at 2 FMA per
+  // busiest SM, ceil(c / sms) CTA-times of padded / c each, at 2 FMA per
   // clock per SM and 2.07 GHz
   constexpr double kSmFlops = 2.0 * 2.0 * 2.07e9;
   for (int k = 0; k < 10; ++k) out[k] = 0;
@@ -929,12 +934,12 @@ void ExecEquation::stats(double out[10]) const {
       }
       const GroupedLaunch &g = e.gl[e.default_shape];
       const double c = double(std::max<long long>(1, g.ncta));
-      const double waves = std::ceil(c / 152.0);
+      const double waves = std::ceil(c / double(sms_));
       out[0] += 1;
       out[1] += g.flops;
       out[2] += g.padded;
       out[3] += g.padded * waves / c / kSmFlops;
-      if (g.ncta < 152) {
+      if (g.ncta < sms_) {
         out[4] += 1;
         out[5] += g.flops;
       }

@@ -73,8 +73,10 @@ class ExecEquation {
   // r_charge: 2*M_s change of the EOM vectors (their spin sector); 0 for CC.
   // host_only: tables and launch descriptors stay in host memory (no
   // device needed; the plan cannot run, only self_check it)
+  // sms: streaming multiprocessors of the device the plan runs on (reduction
+  // splits and the wave model of the shape choice)
   ExecEquation(const Equation &eq, int o, int v, const int rdims[3][2], double amortize = 0.0,
-               double cache_cap = 0.0, int r_charge = 0, bool host_only = false);
+               double cache_cap = 0.0, int r_charge = 0, bool host_only = false, int sms = 152);
   // host-only plans: number of inconsistencies between the grouped tasks of
   // every tile shape and the spin-allowed blocks (steps above max_work
   // multiply-adds skipped); 0 = consistent
@@ -100,6 +102,7 @@ class ExecEquation {
  private:
   void build_launches(const std::vector<long long> &flat_host);
   int nh_, np_, o_, v_;
+  int sms_ = 152;
   bool host_only_ = false;
   std::vector<long long> host_tables_, host_flat_;
   std::vector<GTask> host_gt_;

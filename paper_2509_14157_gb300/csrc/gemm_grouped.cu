@@ -12,7 +12,11 @@
 // The CTAs of all tasks form one grid: CTA c finds its task by binary search
 // over the tasks' first-CTA offsets, then its tile and reduction slice. A task
 // with few tiles splits its reduction; those partial products go to a buffer
-// and a second launch adds them in a fixed order (deterministic results).
+// and a second launch adds them in a fixed order, so that for a given tile
+// shape the results are bitwise reproducible (no atomics). The shape itself
+// may be picked from timings (see ExecEquation::autotune); another shape sums
+// in another order, so autotuned FP64 results can differ in the last bits
+// between runs unless the shape is fixed.
 //
 // On this part FP64 FMA issue is about two per clock per SM, so an FP64 tile
 // is FMA-bound whatever its shape: shapes are chosen for the least padding
@@ -24,7 +28,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <array>
 #include <mutex>
+#include <utility>
 
 namespace fnocc {
 
@@ -462,6 +468,39 @@ constexpr int kBf16Dims[kGShapesBf16][4] = {{2, 4, 2, 2}, {2, 4, 1, 1}, {8, 1, 1
 
 inline unsigned blocks_for(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 
+// Launchers of every shape, instantiated from the two tables above so that a
+// shape's index and its template arguments cannot drift apart.
+using ShapeLaunch = void (*)(unsigned, cudaStream_t, const GTask *, int, double, const double *, const double *,
+                             double *, double *);
+using SplitShapeLaunch = void (*)(int, unsigned, cudaStream_t, const GTask *, int, double, const double *,
+                                  const double *, double *, double *);
+
+template <int I>
+void launch_fp64_shape(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha, const double *A,
+                       const double *B, double *C, double *part) {
+  k_ggemm<kShapeDims[I][0], kShapeDims[I][1], kShapeDims[I][2], kShapeDims[I][3]>
+      <<<grid, NT, 0, s>>>(tasks, ntasks, alpha, A, B, C, part);
+}
+
+template <int I>
+void launch_split_shape(int precision, unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
+                        const double *A, const double *B, double *C, double *part) {
+  launch_tensor<kBf16Dims[I][0], kBf16Dims[I][1], kBf16Dims[I][2], kBf16Dims[I][3]>(precision, grid, s, tasks,
+                                                                                     ntasks, alpha, A, B, C, part);
+}
+
+template <size_t... I>
+constexpr std::array<ShapeLaunch, sizeof...(I)> fp64_launchers(std::index_sequence<I...>) {
+  return {{&launch_fp64_shape<(int)I>...}};
+}
+template <size_t... I>
+constexpr std::array<SplitShapeLaunch, sizeof...(I)> split_launchers(std::index_sequence<I...>) {
+  return {{&launch_split_shape<(int)I>...}};
+}
+
+constexpr auto kFp64Launch = fp64_launchers(std::make_index_sequence<kGShapes>{});
+constexpr auto kSplitLaunch = split_launchers(std::make_index_sequence<kGShapesBf16>{});
+
 }  // namespace
 
 void grouped_shape(int shape, int *tbm, int *tbn, int *tbk) {
@@ -500,43 +539,12 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0], L.stream));
   }
   const unsigned grid = (unsigned)g.ncta;
-#define FNOCC_G(i, ty, tm, tn, bk) \
-  case i: k_ggemm<ty, tm, tn, bk><<<grid, NT, 0, L.stream>>>(g.tasks, g.ntasks, alpha, A, B, C, part); break;
-  switch (g.shape) {
-    FNOCC_G(0, 16, 4, 4, 16)
-    FNOCC_G(1, 16, 8, 2, 16)
-    FNOCC_G(2, 16, 2, 8, 16)
-    FNOCC_G(3, 16, 8, 1, 16)
-    FNOCC_G(4, 16, 1, 8, 16)
-    FNOCC_G(5, 16, 2, 2, 16)
-    FNOCC_G(6, 16, 1, 1, 16)
-    FNOCC_G(7, 64, 2, 1, 16)
-    FNOCC_G(8, 256, 1, 1, 16)
-    FNOCC_G(9, 4, 1, 2, 16)
-    FNOCC_G(10, 8, 1, 4, 16)
-    FNOCC_G(11, 2, 1, 1, 16)
-    FNOCC_G(12, 32, 1, 1, 16)
-    FNOCC_G(13, 128, 1, 1, 16)
-    FNOCC_G(14, 16, 4, 4, 8)
-    FNOCC_G(15, 16, 1, 1, 8)
-    FNOCC_G(16, 256, 1, 1, 8)
-    FNOCC_G(17, 2, 1, 1, 8)
-    FNOCC_G(18, 32, 1, 1, 8)
-#define FNOCC_B(i, wm, wn, mt, nt)                                                                   \
-  case kGShapeBf16 + i:                                                                              \
-    launch_tensor<wm, wn, mt, nt>(L.precision, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part); \
-    break;
-    FNOCC_B(0, 2, 4, 2, 2)
-    FNOCC_B(1, 2, 4, 1, 1)
-    FNOCC_B(2, 8, 1, 1, 2)
-    FNOCC_B(3, 1, 8, 1, 2)
-    FNOCC_B(4, 4, 2, 1, 1)
-    FNOCC_B(5, 1, 8, 1, 1)
-#undef FNOCC_B
-    default:
-      throw std::runtime_error("grouped_gemm: bad shape");
-  }
-#undef FNOCC_G
+  if (g.shape >= 0 && g.shape < kGShapes)
+    kFp64Launch[g.shape](grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
+  else if (g.shape >= kGShapeBf16 && g.shape < kGShapesAll)
+    kSplitLaunch[g.shape - kGShapeBf16](L.precision, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
+  else
+    throw std::runtime_error("grouped_gemm: bad shape");
   FNOCC_CUDA(cudaGetLastError());
   if (L.counter) ++*L.counter;
   if (g.nsplit > 0) {

@@ -988,7 +988,7 @@ int gather_gemm(const Launch &L, long long M, long long N, long long K, double a
     if (pr->pairs.size() >= 4096) pr->fold();
   };
   p.atomic = 0;
-  const long long want = 2 * 152;
+  const long long want = 2 * (long long)L.sms;
   const long long O = M * N;
   // GEMV shape with enough rows: one thread per row
   if (N == 1 && M >= 2048) {
@@ -1003,7 +1003,7 @@ int gather_gemm(const Launch &L, long long M, long long N, long long K, double a
   if (O <= 256) {
     // FP64 issue is slow per SM: spread K over about two blocks per SM
     // (chunks of at least 64) so that the whole GPU works on the few outputs
-    long long nblk = std::min<long long>(std::max<long long>(1, p.K / 64), 2 * 152);
+    long long nblk = std::min<long long>(std::max<long long>(1, p.K / 64), 2 * (long long)L.sms);
     long long kchunk = (p.K + nblk - 1) / nblk;
     nblk = (p.K + kchunk - 1) / kchunk;
     p.kchunk = kchunk;
@@ -1164,7 +1164,7 @@ void multi_dot(const Launch &L, long long n, const double *x, const double *Y, l
 void lincomb(const Launch &L, long long n, const double *X, long long ld, int k, const double *coef_dev, double *y,
              bool accumulate) {
   if (n <= 0) return;
-  const int grid = (int)std::min<long long>(blocks_for(n, 256), 152 * 8);
+  const int grid = (int)std::min<long long>(blocks_for(n, 256), (long long)L.sms * 8);
   k_lincomb<<<grid, 256, sizeof(double) * std::max(k, 1), L.stream>>>(n, X, ld, k, coef_dev, y, accumulate ? 1 : 0);
   post(L);
 }

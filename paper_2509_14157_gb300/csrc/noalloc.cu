@@ -59,6 +59,9 @@ extern "C" fnocc_status fnocc_multi_dot_noalloc(const double *x, const double *Y
                                                 double *dots, void *stream) {
   if (!x || !Y || !dots || n == 0 || ld < n) return FNOCC_E_INVALID;
   if (nvec < 1 || nvec > kMaxVec) return FNOCC_E_INVALID;  // beyond the fixed scratch
+  // an error left pending by the caller's own work stays theirs to read: do
+  // not launch, and do not clear it, so the checks below see only this call
+  if (cudaPeekAtLastError() != cudaSuccess) return FNOCC_E_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FNOCC_E_CUDA;
   double *part = nullptr;
