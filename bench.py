@@ -40,8 +40,17 @@ import numpy as np  # noqa: E402
 NE, NORB, THRESHOLD, NROOTS = 10, 48, 1e-4, 4
 VARIANTS = ("ip", "ea", "dip", "dea")
 METRIC = "s per converged EOM-CCSDT solve"
-# FP64 FMA issue on this part: 2 FMA per clock per SM (measured), 152 SMs, 2070 MHz max
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 FMA issue derived from unit counts and clocks (2 FMA per clock per SM,
+# 152 SMs, 2070 MHz max): reported beside the measured figure
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def measured_fp64_peak(device=0):
+    """FP64 peak measured on this device by the library's probe
+    (fnocc_fp64_peak): FMA chains and mma.sync m8n8k4, TFLOP/s."""
+    import paper_2509_14157_gb300 as pkg
+    fma, dmma = pkg.fp64_peak(device)
+    return fma, dmma, "measured in this run (fnocc_fp64_peak: register-only FP64 FMA chains on every SM)"
 
 
 def measured_bf16_peak():
@@ -136,42 +145,160 @@ def read_traffic():
     return float(m_b.group(1))
 
 
-def cpu_baseline(threshold, gpu_counts):
-    """The oracle, as it stands, on a bounded sample of the workload.
+# one term in SAMPLE_STRIDE of every block of the oracle's Wick term lists
+# is timed (at least one per block), see OracleSample
+SAMPLE_STRIDE = 16
 
-    Sample: the oracle's FNO setup and one full evaluation of its CCSDT
-    residual (all Wick terms, einsum on dense tensors) at the benchmark's
-    size, i.e. one CCSDT iteration of the workload. A converged step needs
-    cc_iters residuals and the sigma products of four Davidson solves; the
-    sigma products are costed as residual evaluations scaled by the ratio of
-    the algorithmic flops the library measured for a sigma product of that
-    variant and for a residual (gpu_counts). Result: estimated oracle seconds
-    per converged EOM solve."""
-    import synth
-    from oracle import cc as occ, fno as ofno, packing
-    t0 = time.time()
-    h, eri = synth.hamiltonian(NE, NORB, seed=0)
-    act = ofno.fno_truncate(h, eri, NE // 2, threshold)
-    t_fno = time.time() - t0
-    f, g, o, v = act["f"], act["g"], act["o"], act["v"]
-    rng = np.random.default_rng(0)
-    t = [packing.unpack(rng.normal(0, 0.01, math.comb(o, r) * math.comb(v, r)), r, r, o, v) for r in (1, 2, 3)]
-    from oracle import wick
-    for r in (1, 2, 3):
-        wick.cc_terms(r)  # term derivation is setup, not timed
-    t1 = time.time()
-    occ.residuals(f, g, o, v, *t)
-    t_res = time.time() - t1
-    fr = gpu_counts["flops_per_residual"]
-    sig_equiv = sum(gpu_counts["sigma"][k] * gpu_counts["flops_per_sigma"][k] / fr for k in VARIANTS)
-    est = t_fno + t_res * (gpu_counts["cc_iters"] + sig_equiv)
+
+class OracleSample:
+    """The oracle, as it stands, on a bounded sample of one converged step.
+
+    A converged step is the oracle's FNO setup, cc_iters CCSDT iterations
+    (one residual evaluation of Eq. 6 each, plus the packing of the
+    amplitudes) and, per variant, sigma_calls EOM products (Eq. 1-4, plus
+    the unpacking of R and packing of sigma). Every residual and product is a
+    sum over Wick terms evaluated as dense einsums, grouped in blocks (one
+    per residual rank or product block); within a block the terms share the
+    output shape. The sample: the FNO setup, the packing steps, and a seeded
+    random choice of ceil(T / SAMPLE_STRIDE) of the T terms of every block
+    (at least one), all timed on the host cores. A block is estimated as its
+    output allocation plus (sampled time - allocation) x T / sampled terms;
+    a residual or product as the sum of its blocks and packing steps. The
+    GPU path's own call counts (iterations, products) turn these measured
+    parts into seconds per converged solve."""
+
+    def __init__(self, threshold, stride=SAMPLE_STRIDE, seed=0):
+        import synth
+        from oracle import fno as ofno, packing, wick
+        self.packing, self.wick = packing, wick
+        t0 = time.perf_counter()
+        h, eri = synth.hamiltonian(NE, NORB, seed=0)
+        act = ofno.fno_truncate(h, eri, NE // 2, threshold)
+        self.t_fno = time.perf_counter() - t0
+        self.f, self.g, self.o, self.v = act["f"], act["g"], act["o"], act["v"]
+        o, v = self.o, self.v
+        rng = np.random.default_rng(seed)
+        self.amps = {"t%d" % r: packing.unpack(rng.normal(0, 0.01, math.comb(o, r) * math.comb(v, r)), r, r, o, v)
+                     for r in (1, 2, 3)}
+        self.blocks = {}  # (part, out_comp, in_comp) -> (terms, nh, np)
+        for r in (1, 2, 3):
+            self.blocks[("residual", r, 0)] = (wick.cc_terms(r), r, r)
+        self.blocks[("residual", 0, 0)] = (wick.cc_terms(0), 0, 0)  # the energy of Eq. 7
+        self.eom_amps = {}
+        for var in VARIANTS:
+            comps = wick.EOM_SPACES[var]
+            for oc, (nh, np_) in enumerate(comps):
+                for ic in range(3):
+                    self.blocks[(var, oc, ic)] = (wick.eom_terms(var, oc, ic), nh, np_)
+            self.eom_amps[var] = [rng.normal(0, 0.1, math.comb(o, nh) * math.comb(v, np_)) for nh, np_ in comps]
+        # the work items: sampled terms of every block, then the packing steps
+        self.items = []
+        for key, (terms, nh, np_) in self.blocks.items():
+            m = max(1, -(-len(terms) // stride))
+            pick = np.sort(rng.choice(len(terms), size=m, replace=False))
+            self.items.append(("terms", key, tuple(int(k) for k in pick)))
+        self.items.append(("pack_t", None, None))
+        for var in VARIANTS:
+            self.items.append(("pack_r", var, None))
+        self.times = {}
+
+    def _amps_for(self, part):
+        if part == "residual":
+            return self.amps
+        rs = [self.packing.unpack(x, nh, np_, self.o, self.v)
+              for x, (nh, np_) in zip(self.eom_amps[part], self.wick.EOM_SPACES[part])]
+        return dict(self.amps, r1=rs[0], r2=rs[1], r3=rs[2])
+
+    def run(self, items):
+        """Times the given work items on the host cores."""
+        o, v, pk = self.o, self.v, self.packing
+        cache = {}
+        for kind, key, pick in items:
+            if kind == "terms":
+                terms, nh, np_ = self.blocks[key]
+                if key[0] not in cache:
+                    cache = {key[0]: self._amps_for(key[0])}  # dense inputs: setup, not timed
+                amps = cache[key[0]]
+                t0 = time.perf_counter()
+                np.zeros((o,) * nh + (v,) * np_)
+                t_alloc = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                self.wick.evaluate(tuple(terms[k] for k in pick), nh, np_, self.f, self.g, amps, o, v)
+                self.times[(kind, key)] = (t_alloc, time.perf_counter() - t0, len(pick), len(terms))
+            elif kind == "pack_t":
+                t0 = time.perf_counter()
+                for r in (1, 2, 3):
+                    pk.unpack(pk.pack(self.amps["t%d" % r], r, r, o, v), r, r, o, v)
+                self.times[(kind, key)] = time.perf_counter() - t0
+            else:
+                comps = self.wick.EOM_SPACES[key]
+                t0 = time.perf_counter()
+                for x, (nh, np_) in zip(self.eom_amps[key], comps):
+                    pk.pack(pk.unpack(x, nh, np_, o, v), nh, np_, o, v)
+                self.times[(kind, key)] = time.perf_counter() - t0
+
+    def seconds_sampled(self):
+        tot = self.t_fno
+        for k, x in self.times.items():
+            tot += x[1] if k[0] == "terms" else x
+        return tot
+
+    def estimate(self, counts):
+        """Oracle seconds per residual and per product (from the measured
+        sample) and per converged solve (with the GPU path's call counts)."""
+        part_s = {}
+        for (kind, key), x in self.times.items():
+            if kind == "terms":
+                t_alloc, t, m, total = x
+                part_s[key[0]] = part_s.get(key[0], 0.0) + t_alloc + max(t - t_alloc, 0.0) * total / m
+            elif kind == "pack_t":
+                part_s["residual"] = part_s.get("residual", 0.0) + x
+            else:
+                part_s[key] = part_s.get(key, 0.0) + x
+        step = self.t_fno + counts["cc_iters"] * part_s["residual"] + sum(
+            counts["sigma"][var] * part_s[var] for var in VARIANTS)
+        return part_s, step / len(VARIANTS)
+
+
+def cpu_baseline(threshold, gpu_counts):
+    """The oracle timed on a bounded sample of the workload (OracleSample),
+    scaled to seconds per converged solve with the GPU path's own iteration
+    and product counts."""
+    smp = OracleSample(threshold)
+    smp.run(smp.items)
+    part_s, per_solve = smp.estimate(gpu_counts)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": est / len(VARIANTS), "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": ("oracle FNO setup (%.1f s) and one full CCSDT residual evaluation (%.1f s, all Wick terms as "
-                       "dense einsum, %d threads available) at o=%d, v=%d; per converged step %d residuals plus "
-                       "sigma products costed as %.1f residual-equivalents (library-measured flop ratio); "
-                       "estimate = (setup + residual x (iterations + equivalents)) / 4 solves"
-                       % (t_fno, t_res, cores, o, v, gpu_counts["cc_iters"], sig_equiv))}
+    return {"value": per_solve, "unit": "s", "cores": cores, "kind": "oracle",
+            "sampled_seconds": round(smp.seconds_sampled(), 2),
+            "oracle_s_per_ccsdt_iter": part_s["residual"],
+            "oracle_s_per_sigma": {var: part_s[var] for var in VARIANTS},
+            "sample": ("oracle (dense einsum over Wick terms, %d threads available) at o=%d, v=%d: FNO setup, "
+                       "the packing steps, and 1 in %d Wick terms of every residual and product block (seeded, "
+                       "at least one per block), %.1f s measured; each block scaled by its term count, each "
+                       "residual / product by the GPU path's counts of this step (%d CCSDT iterations, "
+                       "products %s); per converged solve = step / 4 (an estimate built from measured parts)"
+                       % (cores, smp.o, smp.v, SAMPLE_STRIDE, smp.seconds_sampled(), gpu_counts["cc_iters"],
+                          json.dumps(gpu_counts["sigma"])))}
+
+
+def oracle_root_errors(roots, threshold, seed):
+    """Total-energy error of every root against the roots the oracle wrote
+    for this workload (tests/golden/c2_oracle.json, written by
+    tests/golden/make_c2_golden.py), or None when no fixture covers it."""
+    path = os.path.join(HERE, "tests", "golden", "c2_oracle.json")
+    if seed != 0 or threshold != 1e-4 or (NE, NORB) != (10, 48) or not os.path.exists(path):
+        return None
+    gold = json.load(open(path))
+    out = {"fixture": "tests/golden/c2_oracle.json", "per_root_err_eh": {}}
+    for var in VARIANTS:
+        if var not in gold.get("eom", {}) or var not in roots:
+            continue
+        ref = gold["e_ref"] + gold["e_ccsdt_corr"] + np.asarray(gold["eom"][var]["omega"])
+        got = np.asarray(roots[var])[:len(ref)]
+        out["per_root_err_eh"][var] = [float(x) for x in got - ref]
+    errs = [abs(x) for v in out["per_root_err_eh"].values() for x in v]
+    out["max_abs_err_eh"] = max(errs) if errs else None
+    return out
 
 
 def replica_seed(rank):
@@ -192,26 +319,49 @@ def max_over_ranks(seconds, world, device=None):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper ships no code) on the host
+    cores. Setup (oracle FNO, dense inputs, term derivation) is untimed; each
+    warm-up step evaluates one sampled term; the timed steps share the
+    OracleSample work items round-robin, so that the K steps together time
+    the whole sample once. value = the oracle's seconds per converged solve
+    estimated from those measured parts with the GPU path's call counts of
+    this workload (REFERENCE_COUNTS); ms_per_step = the measured wall time
+    of one timed step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # counts of a converged step at this workload (measured on the GPU path; kept fixed so the
-    # reference arm needs no GPU)
     counts = REFERENCE_COUNTS
-    t0 = time.time()
-    vals = []
-    base = None
-    for _ in range(max(1, args.steps)):
-        base = cpu_baseline(args.threshold, counts)
-        vals.append(base["value"])
-    value = statistics.median(vals)
+    t_all = time.time()
+    smp = OracleSample(args.threshold)
+    first = [it for it in smp.items if it[0] == "terms"][:1]
+    for _ in range(args.warmup):
+        smp.run(first)
+    steps = max(1, args.steps)
+    share = [smp.items[k::steps] for k in range(steps)]
+    step_s = []
+    for k in range(steps):
+        t0 = time.perf_counter()
+        smp.run(share[k])
+        step_s.append(time.perf_counter() - t0)
+    part_s, value = smp.estimate(counts)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    base = {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+            "sampled_seconds": round(smp.seconds_sampled(), 2),
+            "oracle_s_per_ccsdt_iter": part_s["residual"],
+            "oracle_s_per_sigma": {var: part_s[var] for var in VARIANTS},
+            "sample": ("oracle at o=%d, v=%d: FNO setup, packing steps and 1 in %d Wick terms of every residual "
+                       "and product block, timed over %d steps (%.1f s); scaled by term counts and by the GPU "
+                       "path's counts of a converged step (%d CCSDT iterations, products %s); per converged "
+                       "solve = step / 4 (an estimate built from measured parts)"
+                       % (smp.o, smp.v, SAMPLE_STRIDE, steps, sum(step_s), counts["cc_iters"],
+                          json.dumps(counts["sigma"])))}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * value * len(VARIANTS),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(step_s) / steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(args.threshold, 0),
-            "cpu_baseline": dict(base, value=value),
+            "data": "synthetic", "config": dict(config(args.threshold, 0), precision="fp64"),
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": time.time() - t0}
+            "wall_s": time.time() - t_all}
     print(json.dumps(line), flush=True)
 
 
@@ -583,6 +733,7 @@ def main():
 
     for _ in range(args.warmup):
         step(True)
+    fp64_fma, fp64_dmma, fp64_basis = measured_fp64_peak(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -592,14 +743,19 @@ def main():
     ctx.profile_read(-1)
     launches0, flops0 = ctx.launches, ctx.flops
     times = []
-    for _ in range(args.steps):
+    last_roots = {}
+    for k in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if k == args.steps - 1:
+            torch.cuda.nvtx.range_push("step")  # the last timed step, for launch lists
         e0.record(stream)
-        step(True)
+        _, last_roots["fp64"] = step(True)
         e1.record(stream)
+        if k == args.steps - 1:
+            torch.cuda.nvtx.range_pop()
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     torch.cuda.synchronize()
@@ -643,7 +799,9 @@ def main():
     if args.precision == "fp64" and args.guess == "koopmans" and not args.no_mixed_learned:
         # the BF16x3 + learned-guess arm on the same inputs, at the 1e-6 Eh target
         info = train_guess()
-        kw = dict(precision="mixed", switch_tol=0.0, tol_res=1e-6, tol_e=1e-8, guess="learned")
+        # split products until every residual norm is below 1e-5, then FP64
+        # refinement sweeps to residual 1e-6 / |d omega| 1e-8
+        kw = dict(precision="mixed", switch_tol=1e-5, tol_res=1e-6, tol_e=1e-8, guess="learned")
         _, ref_e = step(True)
         step(True, "mixed", kw)
         ml_times = []
@@ -665,8 +823,10 @@ def main():
             "value": ml_total / (len(VARIANTS) * args.steps * world), "unit": "s",
             "tflops": ml_flops * world / ml_total / 1e12 if ml_total > 0 else None,
             "ms_per_step": 1e3 * ml_total / args.steps,
-            "config": "BF16x3 products, Davidson to 1e-6 Eh without FP64 refinement, learned start and "
-                      "preconditioner; CCSDT mixed then FP64",
+            "config": "BF16x3 products until every Davidson residual is below 1e-5, then FP64 refinement "
+                      "sweeps to residual 1e-6 and |d omega| 1e-8; learned start and preconditioner; CCSDT "
+                      "BF16x3 then FP64 below 1e-6",
+            "vs_oracle": oracle_root_errors(ml_e, args.threshold, seed),
             "sigma_calls": dict(counts["sigma"]),
             "max_abs_err_eh": {v: float(np.max(np.abs(np.asarray(ml_e[v]) - np.asarray(ref_e[v]))))
                                for v in VARIANTS},
@@ -677,6 +837,7 @@ def main():
                                            "natural virtuals, IP/EA/DIP/DEA x 4 roots"}}
     solves = len(VARIANTS) * args.steps * world
     value = total / solves
+    parity = oracle_root_errors(last_roots["fp64"], args.threshold, seed) if args.precision == "fp64" else None
     achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
     traffic = read_traffic()
     if dominant.startswith("k_ggemm_bf16x3"):
@@ -696,10 +857,12 @@ def main():
                 "peak_basis": basis + " x 1.1/2.25 (nominal TF32/BF16)"}
     else:
         roof = {"bound": "alu", "kernel": dominant + " (FP64 FMA)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "peak": fp64_fma, "unit": "TFLOP/s",
+                "frac": achieved / fp64_fma if achieved else None,
                 "traffic": traffic if dominant == "k_ggemm" else None,
-                "peak_basis": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz"}
+                "peak_basis": fp64_basis, "peak_fp64_dmma_measured": fp64_dmma,
+                "peak_derived": FP64_PEAK_DERIVED_TFLOPS,
+                "frac_of_derived": achieved / FP64_PEAK_DERIVED_TFLOPS if achieved else None}
     roof.update({"launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / total if total else None,
                  "paths": {k: {"ms": round(x["ms"], 3),
                                "tflops": (x["flops"] / x["ms"] / 1e9) if x["ms"] else None,
@@ -717,6 +880,7 @@ def main():
                 "h2d_bytes_per_step": int(h.nbytes + eri.nbytes),
                 "d2h_bytes_per_step": int(8 * (len(VARIANTS) * NROOTS * 2 + (NORB - nocc)))},
         "gpu_launches": launches, "clocks": clocks,
+        **({"parity": parity} if parity else {}),
         **({"accuracy": accuracy} if accuracy else {}),
         **({"mixed_learned": mixed_learned} if mixed_learned else {}),
         **({"guess": "learned", "guess_training": {k: v for k, v in guess_net.items() if k != "net"}}

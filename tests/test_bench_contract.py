@@ -138,7 +138,28 @@ def fake_gpu(monkeypatch):
         seen["counts"] = counts
         return {"value": 100.0, "unit": "s", "cores": 1, "kind": "oracle", "sample": "stand-in"}
 
+    class FakeSample:
+        """Stand-in for the oracle sample: four work items, fixed estimate."""
+        o, v = 4, 8
+
+        def __init__(self, threshold):
+            self.items = [("terms", ("residual", 1, 0), (0,))] * 3 + [("pack_t", None, None)]
+            self.ran = 0
+
+        def run(self, items):
+            self.ran += len(items)
+            seen["sample_items_run"] = self.ran
+
+        def seconds_sampled(self):
+            return 1.0
+
+        def estimate(self, counts):
+            seen["counts"] = counts
+            return {"residual": 1.0, **{v: 1.0 for v in bench.VARIANTS}}, 100.0
+
     monkeypatch.setattr(bench, "cpu_baseline", fake_cpu_baseline)
+    monkeypatch.setattr(bench, "OracleSample", FakeSample)
+    monkeypatch.setattr(bench, "measured_fp64_peak", lambda device=0: (1.2, 1.0, "stand-in"))
     monkeypatch.setattr(bench, "NE", 2)      # small host arrays for the stand-in
     monkeypatch.setattr(bench, "NORB", 4)
     return seen
@@ -180,8 +201,11 @@ def test_default_line_carries_the_contract(fake_gpu, monkeypatch, capsys):
 
 
 def test_reference_line_carries_the_contract(fake_gpu, monkeypatch, capsys):
-    line = _run(monkeypatch, capsys, ["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    line = _run(monkeypatch, capsys, ["--impl", "reference", "--steps", "3", "--warmup", "2"])
     assert line["impl"] == "reference" and line["value"] == 100.0
+    # the timed steps share the sample's work items: every item runs once, plus one per warm-up step
+    assert fake_gpu["sample_items_run"] == 4 + 2
+    assert line["ms_per_step"] >= 0 and line["config"]["precision"] == "fp64"
     for key in ("metric", "unit", "higher_is_better", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["e2e"] == {"value": 100.0, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

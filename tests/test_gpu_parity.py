@@ -128,15 +128,17 @@ def test_ccsdt_and_eom_small_system(pkg):
     h, eri = synth.hamiltonian(4, 6, seed=0)
     ref = fno.fno_truncate(h, eri, 2, 0.0)
     f, g, o, v = ref["f"], ref["g"], ref["o"], ref["v"]
-    rcc = cc.ccsdt(f, g, o, v)
+    # both solves converged to max|R| < 1e-12, so that the amplitudes of the
+    # two agree well inside the 1e-10 bound
+    rcc = cc.ccsdt(f, g, o, v, tol_res=1e-12, tol_e=1e-13)
     ctx = pkg.Context(0)
     ctx.fno_truncate(h, eri, 2, 0.0)
-    gcc = ctx.ccsdt_solve()
+    gcc = ctx.ccsdt_solve(tol_res=1e-12, tol_e=1e-13)
     assert gcc["converged"]
     assert abs(gcc["e_corr"] - rcc["e_corr"]) < E_TOL
     for r in (1, 2, 3):
         got = ctx.get_block("t%d" % r)
-        assert np.max(np.abs(got - packing.pack(rcc["t%d" % r], r, r, o, v))) < 1e-8
+        assert np.max(np.abs(got - packing.pack(rcc["t%d" % r], r, r, o, v))) < AMP_TOL
     for variant in ("ip", "ea", "dip", "dea"):
         gr = ctx.eom_solve(variant, 2)
         rr = eom.eom_ccsdt(variant, f, g, o, v, rcc["t1"], rcc["t2"], rcc["t3"], 2)
@@ -278,3 +280,39 @@ def test_c2_sigma_sampled(c2_system, variant):
                   for ic in range(3))
         assert np.max(np.abs(got[off + idx] - val)) < AMP_TOL, (variant, oc)
         off += sizes[oc]
+
+
+def test_c2_solve_against_oracle_fixture(pkg):
+    """The benchmarked workload (10 electrons / 48 orbitals, FNO 1e-4; o = 10,
+    v = 30): FNO quantities, the CCSDT energy and amplitudes (converged to
+    max|R| < 1e-12 on both sides; every T1 element, sampled T2 and T3
+    elements and the block norms to 1e-10) and the four lowest roots of
+    every variant (1e-9 Eh) against values the oracle wrote
+    (tests/golden/make_c2_golden.py)."""
+    path = os.path.join(HERE, "golden", "c2_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle fixture not written")
+    gold = json.load(open(path))
+    h, eri = synth.hamiltonian(10, 48, seed=0)
+    ctx = pkg.Context(0)
+    info = ctx.fno_truncate(h, eri, 5, 1e-4)
+    assert info["nkept"] == gold["nkept"]
+    assert abs(info["e_rhf"] - gold["e_rhf"]) < E_TOL
+    assert abs(info["e_mp2"] - gold["e_mp2"]) < E_TOL
+    res = ctx.ccsdt_solve(tol_res=1e-12, tol_e=1e-13)
+    assert res["converged"]
+    assert abs(res["e_corr"] - gold["e_ccsdt_corr"]) < E_TOL
+    t = {r: ctx.get_block("t%d" % r) for r in (1, 2, 3)}
+    assert np.max(np.abs(t[1] - np.array(gold["t1"]))) < AMP_TOL
+    for r in (2, 3):
+        smp = gold["t_samples"]["t%d" % r]
+        assert np.max(np.abs(t[r][np.array(smp["index"])] - np.array(smp["value"]))) < AMP_TOL, r
+    for r in (1, 2, 3):
+        assert abs(np.linalg.norm(t[r]) - gold["t_norms"]["t%d" % r]) < AMP_TOL, r
+    assert gold["eom"], "fixture holds no EOM roots"
+    for variant, ent in gold["eom"].items():
+        assert ent["converged"], variant
+        r = ctx.eom_solve(variant, len(ent["omega"]))
+        assert r["converged"], variant
+        assert np.max(np.abs(r["omegas"] - np.array(ent["omega"]))) < E_TOL, variant
+    ctx.close()
