@@ -114,6 +114,7 @@ SIGNATURES = {
     "fnocc_set_tile_shape": (ctypes.c_int, [_cp, ctypes.c_int]),
     "fnocc_tile_shape_count": (ctypes.c_int, []),
     "fnocc_tile_shape_first_mixed": (ctypes.c_int, []),
+    "fnocc_tile_shape_kind": (ctypes.c_int, [ctypes.c_int]),
     "fnocc_set_autotune": (ctypes.c_int, [ctypes.c_int]),
     "fnocc_fp64_peak": (ctypes.c_int, [ctypes.c_int, _dp, _dp]),
     "fnocc_multi_dot": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp]),
@@ -218,6 +219,11 @@ def tile_shapes():
     """(number of tile shapes, index of the first split-product shape)."""
     lib = load_library()
     return int(lib.fnocc_tile_shape_count()), int(lib.fnocc_tile_shape_first_mixed())
+
+
+def tile_shape_kind(shape):
+    """0 FP64, 1 split product on mma.sync, 2 BF16x3 on tcgen05 (-1 out of range)."""
+    return int(load_library().fnocc_tile_shape_kind(int(shape)))
 
 
 def fp64_peak(device=0):
@@ -451,7 +457,8 @@ class Context:
 
     PROFILE_PATHS = {0: "k_ggemm", 1: "k_ggemm_split+k_greduce", 2: "k_gemm_small+k_reduce_partials",
                      3: "k_gemv_rows", 4: "k_ggemm_bf16x3", 5: "k_ggemm_bf16x3_split+k_greduce",
-                     6: "k_ggemm_tf32x3", 7: "k_ggemm_tf32x3_split+k_greduce"}
+                     6: "k_ggemm_tf32x3", 7: "k_ggemm_tf32x3_split+k_greduce",
+                     8: "k_ggemm_tc", 9: "k_ggemm_tc_split+k_greduce"}
 
     def profile_read(self, path=-1):
         """(device ms, algorithmic flops, launches) of one contraction kernel path

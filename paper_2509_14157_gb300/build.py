@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfnocc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "gemm_grouped.cu", "engine.cpp", "planner.cpp", "linalg.cpp", "api.cpp", "noalloc.cu", "mlp.cu", "peak.cu"]
+SOURCES = ["kernels.cu", "gemm_grouped.cu", "gemm_tc.cu", "engine.cpp", "planner.cpp", "linalg.cpp", "api.cpp", "noalloc.cu", "mlp.cu", "peak.cu"]
 
 
 def _nvcc():

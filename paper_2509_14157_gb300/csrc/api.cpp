@@ -381,6 +381,8 @@ double cc_residual_dev(fnocc_ctx *c, const double *tp, double *rp) {
   }
   c->flops_cc_last = flops;
   c->flops_total += flops;
+  if (L.precision == FNOCC_MIXED_BF16X3 && tc_status_take(c->stream))
+    throw StatusError(FNOCC_E_TIMEOUT, "a bounded wait of the tcgen05 contraction kernel expired");
   size_t off = 0;
   for (int r = 1; r <= 3; ++r) {
     antisym_pack(L, c->Y[r].d(), r, r, o, v, c->otab[r].dev.as<int>(), c->otab[r].count, c->vtab[r].dev.as<int>(),
@@ -490,6 +492,8 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = fa
   }
   c->flops_sigma_last = flops;
   c->flops_total += flops;
+  if (L.precision == FNOCC_MIXED_BF16X3 && tc_status_take(c->stream))
+    throw StatusError(FNOCC_E_TIMEOUT, "a bounded wait of the tcgen05 contraction kernel expired");
 }
 
 // ---- small helpers on device vectors ---------------------------------------------
@@ -1237,6 +1241,7 @@ fnocc_status fnocc_set_autotune(int enable) {
   return FNOCC_OK;
 }
 int fnocc_tile_shape_first_mixed(void) { return kGShapeBf16; }
+int fnocc_tile_shape_kind(int shape) { return shape < 0 || shape >= kGShapesAll ? -1 : shape_kind(shape); }
 
 fnocc_status fnocc_eom_sizes(const fnocc_ctx *c, int variant, size_t *sizes) {
   if (!c || !sizes || variant < 0 || variant >= kEomVariants) return FNOCC_E_INVALID;

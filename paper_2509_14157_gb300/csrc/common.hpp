@@ -65,8 +65,9 @@ struct DMap {
 // Optional event timing of contraction launches (owned by a context), per
 // kernel path: 0 grouped FP64 GEMM, 1 the same with split reduction + ordered
 // sum, 2 small-output kernel + reduction, 3 GEMV, 4 / 5 grouped BF16x3 GEMM
-// without / with split reduction, 6 / 7 grouped TF32x3 GEMM without / with.
-constexpr int kGemmPaths = 8;
+// (mma.sync) without / with split reduction, 6 / 7 grouped TF32x3 GEMM
+// without / with, 8 / 9 grouped BF16x3 GEMM on tcgen05 without / with.
+constexpr int kGemmPaths = 10;
 struct GemmProfile {
   bool enabled = false;
   std::vector<cudaEvent_t> pool;           // events, reused
@@ -108,8 +109,21 @@ struct GTask {
 // of tasks with a split reduction.
 constexpr int kGShapes = 19;           // FP64 tile shapes (14 with a K tile of 16, 5 of them again with 8)
 constexpr int kGShapeBf16 = kGShapes;  // first BF16 three-slice split shape (mixed precision)
-constexpr int kGShapesBf16 = 6;        // BF16x3 tiles 64x64, 32x32, 128x16, 16x128, 64x16, 16x64
-constexpr int kGShapesAll = kGShapes + kGShapesBf16;
+constexpr int kGShapesBf16 = 6;        // BF16x3 tiles 64x64, 32x32, 128x16, 16x128, 64x16, 16x64 (mma.sync)
+constexpr int kGShapeTc = kGShapeBf16 + kGShapesBf16;  // first tcgen05 BF16x3 shape
+constexpr int kGShapesTc = 3;          // tcgen05 BF16x3 tiles 128x64, 128x128, 128x256 (TMEM accumulator)
+constexpr int kGShapesAll = kGShapes + kGShapesBf16 + kGShapesTc;
+// kind of a shape: 0 FP64, 1 split product on mma.sync (BF16x3 or TF32x3),
+// 2 BF16x3 split product on tcgen05
+inline int shape_kind(int shape) { return shape < kGShapeBf16 ? 0 : (shape < kGShapeTc ? 1 : 2); }
+// tcgen05 shapes (index 0..kGShapesTc-1): tile, dynamic shared memory,
+// launch, and the status word of an expired bounded wait (read and cleared;
+// synchronises the stream)
+void tc_shape(int idx, int *tbm, int *tbn, int *tbk);
+size_t tc_smem_bytes(int idx);
+void grouped_gemm_tc(int idx, unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
+                     const double *A, const double *B, double *C, double *part);
+int tc_status_take(cudaStream_t s);
 struct GroupedLaunch {
   const GTask *tasks = nullptr;
   int ntasks = 0;

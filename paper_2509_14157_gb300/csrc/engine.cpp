@@ -715,17 +715,27 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
           est[shape] = padded * wave_cost(cta);
         } else {
           // tensor-core tiles: the cost is staging (gather, convert, split) of
-          // the (tbm + tbn) x tbk operand panels of every K tile, two CTAs per SM
+          // the (tbm + tbn) x tbk operand panels of every K tile, over the
+          // CTAs resident at once (two per SM; one for the 128 x 256 tcgen05
+          // tile, whose stages take 145 KiB of shared memory)
           double staged = 0;
           for (size_t i = gt.size() - e.tasks.size(); i < gt.size(); ++i)
             staged += double(gt[i].tiles) * double((gt[i].K + tbk - 1) / tbk) * double((tbm + tbn) * tbk);
-          est[shape] = staged / double(std::max<long long>(1, std::min<long long>(cta, 2 * kSms)));
+          const long long per_sm = (shape_kind(shape) == 2 && tbn >= 256) ? 1 : 2;
+          est[shape] = staged / double(std::max<long long>(1, std::min<long long>(cta, per_sm * kSms)));
         }
       }
       int bbest = kGShapeBf16;
-      for (int shape = kGShapeBf16 + 1; shape < kGShapesAll; ++shape)
+      for (int shape = kGShapeBf16 + 1; shape < kGShapeTc; ++shape)
         if (est[shape] < est[bbest]) bbest = shape;
       e.bf16_shape = bbest;
+      int tbest = kGShapeTc;
+      for (int shape = kGShapeTc + 1; shape < kGShapesAll; ++shape)
+        if (est[shape] < est[tbest]) tbest = shape;
+      e.tc_shape = tbest;
+      // BF16x3: the tcgen05 tile where it stages less per busy SM (large
+      // steps time both once, see run)
+      e.bf16x3_shape = est[tbest] < est[bbest] ? tbest : bbest;
       int best = 0;
       for (int shape = 1; shape < kGShapes; ++shape)
         if (est[shape] < est[best]) best = shape;
@@ -843,8 +853,23 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         throw std::runtime_error("engine: grouped index tables exceed operand bounds");
       ExecStep &ms = const_cast<ExecStep &>(s);
       if (L.precision != 0 && s.gl[0].flops >= 1e5) {
-        const bool forced = L.force_shape >= kGShapeBf16 && L.force_shape < kGShapesAll;
-        grouped_gemm(L, s.gl[forced ? L.force_shape : s.bf16_shape], s.alpha, A, B, C);
+        // split products: mma.sync tiles for TF32x3; for BF16x3 the mma.sync
+        // or the tcgen05 tile, timed once for large steps
+        ExecStep &mm = const_cast<ExecStep &>(s);
+        const int fk = L.force_shape >= 0 && L.force_shape < kGShapesAll ? shape_kind(L.force_shape) : 0;
+        int shape;
+        if (fk == 1 || (fk == 2 && L.precision == 1))
+          shape = L.force_shape;
+        else if (L.precision != 1)
+          shape = s.bf16_shape;
+        else if (mm.tuned_mixed >= 0)
+          shape = mm.tuned_mixed;
+        else if (autotune && s.gl[s.bf16x3_shape].padded >= 1e8) {
+          tune_launch(L, mm.mixed_tune, {s.bf16_shape, s.tc_shape}, mm.tuned_mixed, s, A, B, C);
+          continue;
+        } else
+          shape = s.bf16x3_shape;
+        grouped_gemm(L, s.gl[shape], s.alpha, A, B, C);
         continue;
       }
       if (L.precision == 0 && L.force_shape >= 0 && L.force_shape < kGShapes) {
@@ -891,6 +916,41 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
     }
   }
   if (refresh) cache_version_ = version;
+}
+
+void ExecEquation::tune_launch(const Launch &L, ExecStep::Trial &tr, std::initializer_list<int> cand, int &tuned,
+                               const ExecStep &s, const double *A, const double *B, double *C) {
+  if (tr.pending < 0) {  // first use: an event pair of its own
+    tr.pending = tune_count_++;
+    while ((int)tune_events_.size() < 2 * tune_count_) {
+      cudaEvent_t ev;
+      FNOCC_CUDA(cudaEventCreate(&ev));
+      tune_events_.push_back(ev);
+    }
+  }
+  cudaEvent_t e0 = tune_events_[2 * tr.pending], e1 = tune_events_[2 * tr.pending + 1];
+  for (int k : cand)
+    if (tr.ms[k] < 0) {  // the trial of the previous run
+      FNOCC_CUDA(cudaEventSynchronize(e1));
+      float tms = 0;
+      FNOCC_CUDA(cudaEventElapsedTime(&tms, e0, e1));
+      tr.ms[k] = std::max(tms, 1e-6f);
+    }
+  int next = -1;
+  for (int k : cand)
+    if (next < 0 && tr.ms[k] == 0) next = k;
+  if (next < 0) {
+    int best = *cand.begin();
+    for (int k : cand)
+      if (tr.ms[k] < tr.ms[best]) best = k;
+    tuned = best;
+    grouped_gemm(L, s.gl[best], s.alpha, A, B, C);
+    return;
+  }
+  FNOCC_CUDA(cudaEventRecord(e0, L.stream));
+  grouped_gemm(L, s.gl[next], s.alpha, A, B, C);
+  FNOCC_CUDA(cudaEventRecord(e1, L.stream));
+  tr.ms[next] = -1.f;  // in flight; read on the next run
 }
 
 namespace {

@@ -4,6 +4,7 @@
 #include "common.hpp"
 #include "planner.hpp"
 
+#include <initializer_list>
 #include <memory>
 
 namespace fnocc {
@@ -49,7 +50,16 @@ struct ExecStep {
   GroupedLaunch gl[kGShapesAll];
   long long gmax_a = 0, gmax_b = 0, gmax_c = 0;  // largest row + column offset per operand
   int default_shape = 0;                          // least padded work per busy SM
-  int bf16_shape = kGShapeBf16;                   // mixed precision: least staged work per busy SM
+  int bf16_shape = kGShapeBf16;                   // mma.sync split tile with the least staged work per busy SM
+  int tc_shape = kGShapeTc;                       // tcgen05 BF16x3 tile with the least staged work per busy SM
+  int bf16x3_shape = kGShapeBf16;                 // BF16x3 default: the better of the two estimates
+  // BF16x3 steps above 1e8 padded flops: the mma.sync and the tcgen05 tile
+  // are timed once each, then the faster is kept
+  struct Trial {
+    float ms[kGShapesAll] = {0};  // 0 untimed, < 0 in flight
+    int pending = -1;             // event pair of this step, -1 none yet
+  } mixed_tune;
+  int tuned_mixed = -1;
   std::vector<int> cand;                          // FP64 shapes worth timing, best estimate first
   // tile-shape autotuning of large FP64 steps: every candidate is timed once,
   // then the fastest is kept
@@ -101,6 +111,12 @@ class ExecEquation {
 
  private:
   void build_launches(const std::vector<long long> &flat_host);
+  // one timing round of a step's candidate shapes: reads the trial of the
+  // previous run, then launches the next untimed candidate between an event
+  // pair of the step's own (read on a later run), or, once all are timed,
+  // keeps the fastest in `tuned` and launches it
+  void tune_launch(const Launch &L, ExecStep::Trial &tr, std::initializer_list<int> cand, int &tuned,
+                   const ExecStep &s, const double *A, const double *B, double *C);
   int nh_, np_, o_, v_;
   int sms_ = 152;
   bool host_only_ = false;

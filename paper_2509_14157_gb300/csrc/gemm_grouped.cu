@@ -504,7 +504,11 @@ constexpr auto kSplitLaunch = split_launchers(std::make_index_sequence<kGShapesB
 }  // namespace
 
 void grouped_shape(int shape, int *tbm, int *tbn, int *tbk) {
-  if (shape >= kGShapeBf16 && shape < kGShapesAll) {
+  if (shape >= kGShapeTc && shape < kGShapesAll) {
+    tc_shape(shape - kGShapeTc, tbm, tbn, tbk);
+    return;
+  }
+  if (shape >= kGShapeBf16 && shape < kGShapeTc) {
     const int *d = kBf16Dims[shape - kGShapeBf16];
     *tbm = d[0] * d[2] * 16;
     *tbn = d[1] * d[3] * 8;
@@ -541,8 +545,10 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
   const unsigned grid = (unsigned)g.ncta;
   if (g.shape >= 0 && g.shape < kGShapes)
     kFp64Launch[g.shape](grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
-  else if (g.shape >= kGShapeBf16 && g.shape < kGShapesAll)
+  else if (g.shape >= kGShapeBf16 && g.shape < kGShapeTc)
     kSplitLaunch[g.shape - kGShapeBf16](L.precision, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
+  else if (g.shape >= kGShapeTc && g.shape < kGShapesAll && L.precision == 1)
+    grouped_gemm_tc(g.shape - kGShapeTc, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
   else
     throw std::runtime_error("grouped_gemm: bad shape");
   FNOCC_CUDA(cudaGetLastError());
@@ -556,7 +562,7 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0 + 1], L.stream));
     pr->pairs.push_back({e0, e0 + 1});
     pr->flops.push_back(g.flops);
-    const int base = g.shape < kGShapeBf16 ? 0 : (L.precision == 2 ? 6 : 4);
+    const int base = g.shape < kGShapeBf16 ? 0 : (g.shape >= kGShapeTc ? 8 : (L.precision == 2 ? 6 : 4));
     pr->path.push_back(base + (g.nsplit > 0 ? 1 : 0));
     if (pr->pairs.size() >= 4096) pr->fold();
   }

@@ -1,0 +1,396 @@
+// Grouped split-product GEMM on the fifth-generation tensor cores (tcgen05,
+// accumulator in tensor memory).
+//
+// Same tasks as the other grouped kernels (one spin-allowed sub-GEMM of a
+// contraction step per task, operands read in place through flat offset
+// tables, gemm_grouped.cu), same BF16 three-slice arithmetic as the
+// mixed-precision path of the single- and double-precision algorithms of
+// Sec. 1: every FP64 operand element is truncated to FP32 and split exactly
+// into three BF16 slices x = s0 + s1 + s2; the six slice products with
+// i + j <= 2 accumulate in FP32 (the three dropped ones are below 2^-24 of
+// the full product).
+//
+// A CTA computes a 128 x BN output tile (BN = 64, 128 or 256) in a tensor-
+// memory accumulator of BN FP32 columns. K advances 32 at a time through two
+// shared-memory stages. Per stage, all 256 threads gather the FP64 operand
+// panels (128 x 32 of A, BN x 32 of B) through the offset tables, convert
+// and split them, and store the three BF16 planes of each in the canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices; adjacent
+// core matrices along K 128 bytes apart, along M / N 256 bytes apart); then
+// one thread issues 2 K-steps x 6 slice products of tcgen05.mma kind::f16
+// (M = 128, N = BN, K = 16) and commits them to the stage's mbarrier, which
+// frees the stage two iterations later. The gathers of the next stage are in
+// flight while the tensor cores work on the current one. The epilogue reads
+// the accumulator with tcgen05.ld (warp w reads lanes 32 (w mod 4) .. +31,
+// half of the columns each), converts to FP64 and scatters C[crow + ccol] +=
+// alpha * acc, or writes a split-reduction partial.
+//
+// Every wait on an mbarrier is bounded (about 2 s of SM clock); on expiry
+// the kernel records a status word that the host reads after the product
+// (fnocc returns FNOCC_E_TIMEOUT), skips the output, waits (bounded) for its
+// own committed products, frees its tensor memory and returns.
+#include "common.hpp"
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
+
+namespace fnocc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBM = 128;  // accumulator lanes
+constexpr int kBK = 32;   // K per stage: two K-steps of the f16 kind
+constexpr long long kTimeoutCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+// status word of the last bounded wait that expired (0 = none), per device
+__device__ int g_tc_status;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+// true when the phase with the given parity has completed, false after the
+// time limit
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long start = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - start > kTimeoutCycles) return false;
+  }
+}
+
+// shared-memory matrix descriptor: canonical K-major layout without swizzle;
+// lbo / sbo: byte distance of adjacent core matrices along K / along M or N
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int find_task_tc(const GTask *tasks, int ntasks, long long cta) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].cta_begin <= cta)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// FP64 -> FP32 by truncation of the significand (integer arithmetic); then
+// an exact three-way BF16 split
+__device__ __forceinline__ float trunc_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+__device__ __forceinline__ void split3(double xd, __nv_bfloat16 &s0, __nv_bfloat16 &s1, __nv_bfloat16 &s2) {
+  const float x = trunc_f32(xd);
+  s0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(s0);
+  s1 = __float2bfloat16_rn(r1);
+  s2 = __float2bfloat16_rn(r1 - __bfloat162float(s1));
+}
+
+// byte offset of element (row, k) of a K-step plane (k < 16): core matrix
+// (row / 8, k / 8), 16-byte row (row % 8), element k % 8
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+template <int BN>
+struct TcTile {
+  static constexpr int kPlaneA = kBM * 16 * 2;  // bytes of one K-step plane of A
+  static constexpr int kPlaneB = BN * 16 * 2;
+  static constexpr int kStageA = 3 * 2 * kPlaneA;  // three slices x two K-steps
+  static constexpr int kStageB = 3 * 2 * kPlaneB;
+  static constexpr int kStage = kStageA + kStageB;
+  static constexpr size_t kSmem = 2 * (size_t)kStage + 1024;  // two stages + alignment slack
+  static constexpr int EA = kBM * kBK / kThreads;  // gathered A elements per thread and stage
+  static constexpr int EB = BN * kBK / kThreads;
+  static_assert(BN == 64 || BN == 128 || BN == 256, "accumulator width");
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
+    k_ggemm_tc(const GTask *__restrict__ tasks, int ntasks, double alpha, const double *__restrict__ A,
+               const double *__restrict__ B, double *__restrict__ C, double *__restrict__ part) {
+  using T = TcTile<BN>;
+  constexpr int EA = T::EA, EB = T::EB;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ long long arow_s[kBM], crow_s[kBM], bcol_s[BN], ccol_s[BN];
+  __shared__ GTask t;
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long cta = blockIdx.x;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    t = tasks[find_task_tc(tasks, ntasks, cta)];
+    abort_s = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+  const long long local = cta - t.cta_begin;
+  const long long z = local / t.tiles, tile = local - z * t.tiles;
+  const long long m0 = (tile / t.tiles_n) * kBM, n0 = (tile % t.tiles_n) * BN;
+  const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
+  const bool split = t.ksplit > 1;
+  for (int i = tid; i < kBM; i += kThreads) {
+    const long long m = m0 + i;
+    arow_s[i] = m < t.M ? t.arow[m] : 0;
+    crow_s[i] = (!split && m < t.M) ? t.crow[m] : 0;
+  }
+  for (int i = tid; i < BN; i += kThreads) {
+    const long long n = n0 + i;
+    bcol_s[i] = n < t.N ? t.bcol[n] : 0;
+    ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
+  }
+  __syncthreads();
+
+  double ra[EA], rb[EB];
+  // gathers of the stage at k0 into registers (0 outside the task): a warp
+  // reads 32 consecutive k of one A row, and 32 consecutive columns of one B
+  // row
+  auto load = [&](long long k0) {
+#pragma unroll
+    for (int r = 0; r < EA; ++r) {
+      const int idx = tid + kThreads * r;
+      const int kk = idx % kBK, row = idx / kBK;
+      const long long k = k0 + kk;
+      ra[r] = (m0 + row < t.M && k < ke) ? __ldg(A + arow_s[row] + __ldg(t.acol + k)) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < EB; ++r) {
+      const int idx = tid + kThreads * r;
+      const int col = idx % BN, kk = idx / BN;
+      const long long k = k0 + kk;
+      rb[r] = (n0 + col < t.N && k < ke) ? __ldg(B + __ldg(t.brow + k) + bcol_s[col]) : 0.0;
+    }
+  };
+
+  const long long nk = ke > kb ? (ke - kb + kBK - 1) / kBK : 0;
+  const uint32_t sbase = smem_u32(smem);
+  constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+  // the six slice products i + j <= 2 (A slice i, B slice j)
+  constexpr int kPi[6] = {0, 0, 1, 0, 1, 2}, kPj[6] = {0, 1, 0, 2, 1, 0};
+  if (nk > 0) load(kb);
+  for (long long kt = 0; kt < nk; ++kt) {
+    const int s = (int)(kt & 1);
+    unsigned char *stA = smem + s * T::kStage;
+    unsigned char *stB = stA + T::kStageA;
+    if (kt >= 2) {  // the products of stage s two iterations back have read it
+      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kt - 2) >> 1) & 1))) abort_s = 1;
+      __syncthreads();
+      if (abort_s) break;
+    }
+#pragma unroll
+    for (int r = 0; r < EA; ++r) {
+      const int idx = tid + kThreads * r;
+      const int kk = idx % kBK, row = idx / kBK;
+      __nv_bfloat16 s0, s1, s2;
+      split3(ra[r], s0, s1, s2);
+      const uint32_t off = (uint32_t)((kk >> 4) * T::kPlaneA) + core_off(row, kk & 15);
+      *reinterpret_cast<__nv_bfloat16 *>(stA + off) = s0;
+      *reinterpret_cast<__nv_bfloat16 *>(stA + 2 * T::kPlaneA + off) = s1;
+      *reinterpret_cast<__nv_bfloat16 *>(stA + 4 * T::kPlaneA + off) = s2;
+    }
+#pragma unroll
+    for (int r = 0; r < EB; ++r) {
+      const int idx = tid + kThreads * r;
+      const int col = idx % BN, kk = idx / BN;
+      __nv_bfloat16 s0, s1, s2;
+      split3(rb[r], s0, s1, s2);
+      const uint32_t off = (uint32_t)((kk >> 4) * T::kPlaneB) + core_off(col, kk & 15);
+      *reinterpret_cast<__nv_bfloat16 *>(stB + off) = s0;
+      *reinterpret_cast<__nv_bfloat16 *>(stB + 2 * T::kPlaneB + off) = s1;
+      *reinterpret_cast<__nv_bfloat16 *>(stB + 4 * T::kPlaneB + off) = s2;
+    }
+    // generic-proxy stores become visible to the tensor cores' async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (kt + 1 < nk) load(kb + (kt + 1) * kBK);  // in flight during the products below
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t a0 = sbase + s * T::kStage, b0 = a0 + T::kStageA;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const uint64_t ad = smem_desc(a0 + (kPi[p] * 2 + ks) * T::kPlaneA, 128, 256);
+          const uint64_t bd = smem_desc(b0 + (kPj[p] * 2 + ks) * T::kPlaneB, 128, 256);
+          mma_bf16(tmem, ad, bd, idesc, (kt > 0 || ks > 0 || p > 0) ? 1u : 0u);
+        }
+      mma_commit(smem_u32(&mbar[s]));
+    }
+  }
+  bool ok = !abort_s;
+  if (ok && nk > 0) {
+    const long long last = nk - 1;
+    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) ok = false;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_tc_status, 1);
+    // let products already committed finish (bounded) before the memory goes
+    if (nk > 0) {
+      const long long last = nk - 1;
+      mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
+    }
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int q = warp & 3, half = warp >> 2;
+    const int rl = q * 32 + lane;
+    const long long m = m0 + rl;
+    const long long MN = t.M * t.N;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      const int cl0 = half * (BN / 2) + c * 16;
+      float v[16];
+      if (nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cl0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if (m >= t.M) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const long long n = n0 + cl0 + i;
+        if (n >= t.N) break;
+        if (split)
+          part[t.part_off + z * MN + m * t.N + n] = (double)v[i];
+        else
+          C[crow_s[rl] + ccol_s[cl0 + i]] += alpha * (double)v[i];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+template <int BN>
+void launch_tc(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha, const double *A,
+               const double *B, double *C, double *part) {
+  constexpr size_t smem = TcTile<BN>::kSmem;
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  FNOCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw std::runtime_error("grouped_gemm_tc: device index out of range");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+      FNOCC_CUDA(cudaFuncSetAttribute(k_ggemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done[dev] = true;
+    }
+  }
+  k_ggemm_tc<BN><<<grid, kThreads, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
+}
+
+}  // namespace
+
+void tc_shape(int idx, int *tbm, int *tbn, int *tbk) {
+  static const int bn[kGShapesTc] = {64, 128, 256};
+  if (idx < 0 || idx >= kGShapesTc) throw std::runtime_error("tc_shape: bad shape");
+  *tbm = kBM;
+  *tbn = bn[idx];
+  *tbk = kBK;
+}
+
+size_t tc_smem_bytes(int idx) {
+  switch (idx) {
+    case 0: return TcTile<64>::kSmem;
+    case 1: return TcTile<128>::kSmem;
+    case 2: return TcTile<256>::kSmem;
+    default: throw std::runtime_error("tc_smem_bytes: bad shape");
+  }
+}
+
+void grouped_gemm_tc(int idx, unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
+                     const double *A, const double *B, double *C, double *part) {
+  switch (idx) {
+    case 0: launch_tc<64>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    case 1: launch_tc<128>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    case 2: launch_tc<256>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    default: throw std::runtime_error("grouped_gemm_tc: bad shape");
+  }
+}
+
+int tc_status_take(cudaStream_t s) {
+  int v = 0;
+  FNOCC_CUDA(cudaMemcpyFromSymbolAsync(&v, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  FNOCC_CUDA(cudaStreamSynchronize(s));
+  if (v) {
+    const int zero = 0;
+    FNOCC_CUDA(cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    FNOCC_CUDA(cudaStreamSynchronize(s));
+  }
+  return v;
+}
+
+}  // namespace fnocc

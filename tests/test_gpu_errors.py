@@ -83,7 +83,9 @@ def test_not_converged_fills_outputs(pkg):
     info = pkg.CcsdtInfo()
     st = lib.ccsdt_solve(ctx._h, ctypes.byref(opt), ctypes.byref(info))
     assert st == STATUS["NOT_CONVERGED"]
-    assert info.iters == 2 and math.isfinite(info.e_corr) and info.e_corr < 0 and info.res_max > 1e-10
+    # the energy of the second iterate (a large first Jacobi step can make it
+    # positive; it only has to be the iterate's, finite and filled in)
+    assert info.iters == 2 and math.isfinite(info.e_corr) and info.e_corr != 0.0 and info.res_max > 1e-10
     t2 = ctx.get_block("t2")
     assert np.all(np.isfinite(t2)) and np.max(np.abs(t2)) > 0
     res = ctx.ccsdt_solve(maxiter=2)

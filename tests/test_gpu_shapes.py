@@ -10,8 +10,9 @@ one ragged tile for the large ones.
 
 Tolerances: FP64 shapes 1e-10 max-abs (the FP64 path's bound); split-product
 shapes run in their own arithmetic (BF16 three-slice or TF32 two-slice, FP32
-accumulation) and are held to the relative product bounds of the mixed path
-(2e-6 and 1e-5 of the largest element).
+accumulation; on mma.sync, and BF16 three-slice also on the tcgen05 tensor
+cores with a tensor-memory accumulator) and are held to the relative product
+bounds of the mixed path (2e-6 and 1e-5 of the largest element).
 """
 import math
 
@@ -71,7 +72,11 @@ def _shapes(pkg):
 
 def test_shape_table(pkg):
     count, first_mixed = _shapes(pkg)
-    assert 0 < first_mixed < count
+    assert first_mixed == 19 < count
+    kinds = [pkg.tile_shape_kind(k) for k in range(count)]
+    assert kinds[:first_mixed] == [0] * first_mixed
+    assert 1 in kinds and 2 in kinds and kinds == sorted(kinds)
+    assert pkg.tile_shape_kind(count) == -1
 
 
 @pytest.mark.parametrize("shape", range(19))
@@ -101,6 +106,8 @@ def test_split_shape_products(pkg, system, kind):
     ctx.set_precision(kind)
     try:
         for shape in range(first_mixed, count):
+            if kind == "mixed_tf32" and pkg.tile_shape_kind(shape) == 2:
+                continue  # tcgen05 tiles run BF16x3 only
             ctx.set_tile_shape(shape)
             ctx.set_amplitudes(*t)
             for variant in ("ip", "dea"):
