@@ -301,6 +301,26 @@ def oracle_root_errors(roots, threshold, seed):
     return out
 
 
+def split_roofline(paths, step_s):
+    """Tensor-core roofline of the split-product kernels of a profiled
+    mixed-precision step: the tcgen05 BF16x3 kernel (k_ggemm_tc) and the
+    mma.sync one (k_ggemm_bf16x3), each at six BF16 slice products per
+    FP64-equivalent multiply-add, against the measured sustained BF16 peak."""
+    peak, basis = measured_bf16_peak()
+    out = {}
+    for name in ("k_ggemm_tc", "k_ggemm_bf16x3"):
+        ms_ = paths[name]["ms"] + paths[name + "_split+k_greduce"]["ms"]
+        fl_ = paths[name]["flops"] + paths[name + "_split+k_greduce"]["flops"]
+        n_ = paths[name]["launches"] + paths[name + "_split+k_greduce"]["launches"]
+        ach = 6 * fl_ / (ms_ / 1e3) / 1e12 if ms_ > 0 else None
+        out[name] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": ach / peak if ach else None, "launches": n_, "ms": round(ms_, 3),
+                     "share_of_step": (ms_ / 1e3) / step_s if step_s else None}
+    out["peak_basis"] = basis + "; six BF16 slice products per FP64-equivalent multiply-add"
+    out["paths"] = {k: {"ms": round(x["ms"], 3), "launches": x["launches"]} for k, x in paths.items()}
+    return out
+
+
 def replica_seed(rank):
     """Independent replicas: every rank solves its own seeded system (no
     collective on the data path)."""
@@ -739,8 +759,6 @@ def main():
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
-    ctx.profile(True)
-    ctx.profile_read(-1)
     launches0, flops0 = ctx.launches, ctx.flops
     times = []
     last_roots = {}
@@ -759,15 +777,25 @@ def main():
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     torch.cuda.synchronize()
+    launches = ctx.launches - launches0
+    flops = ctx.flops - flops0
+    # per-kernel timing: one more step of the same work with CUDA events
+    # around every contraction launch (plain launches: the timed steps replay
+    # the products' launch sequences as graphs, which per-launch events would
+    # break up)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(-1)
+    step(True)
+    torch.cuda.synchronize()
     paths = {}
     for pid, name in ctx.PROFILE_PATHS.items():
         ms_, fl_, n_ = ctx.profile_read(pid)
         paths[name] = {"ms": ms_, "flops": fl_, "launches": n_}
+    ctx.profile(False)
     dominant = max(paths, key=lambda k: paths[k]["ms"])
     gemm_ms, gemm_flops, gemm_n = paths[dominant]["ms"], paths[dominant]["flops"], paths[dominant]["launches"]
-    launches = ctx.launches - launches0
-    flops = ctx.flops - flops0
-    ctx.profile(False)
     clocks = sampler.stop()
     total = sum(times)
     total = max_over_ranks(total, world, dev)
@@ -819,6 +847,18 @@ def main():
         ml_total = sum(ml_times)
         ml_total = max_over_ranks(ml_total, world, dev)
         ml_flops = ctx.flops - ml_flops0
+        # per-kernel timing of the arm: one profiled step (plain launches)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(-1)
+        step(True, "mixed", kw)
+        torch.cuda.synchronize()
+        ml_paths = {}
+        for pid, name in ctx.PROFILE_PATHS.items():
+            ms_, fl_, n_ = ctx.profile_read(pid)
+            ml_paths[name] = {"ms": ms_, "flops": fl_, "launches": n_}
+        ctx.profile(False)
         mixed_learned = {
             "value": ml_total / (len(VARIANTS) * args.steps * world), "unit": "s",
             "tflops": ml_flops * world / ml_total / 1e12 if ml_total > 0 else None,
@@ -827,6 +867,7 @@ def main():
                       "sweeps to residual 1e-6 and |d omega| 1e-8; learned start and preconditioner; CCSDT "
                       "BF16x3 then FP64 below 1e-6",
             "vs_oracle": oracle_root_errors(ml_e, args.threshold, seed),
+            "roofline": split_roofline(ml_paths, ml_total / args.steps),
             "sigma_calls": dict(counts["sigma"]),
             "max_abs_err_eh": {v: float(np.max(np.abs(np.asarray(ml_e[v]) - np.asarray(ref_e[v]))))
                                for v in VARIANTS},
@@ -863,7 +904,9 @@ def main():
                 "peak_basis": fp64_basis, "peak_fp64_dmma_measured": fp64_dmma,
                 "peak_derived": FP64_PEAK_DERIVED_TFLOPS,
                 "frac_of_derived": achieved / FP64_PEAK_DERIVED_TFLOPS if achieved else None}
-    roof.update({"launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / total if total else None,
+    roof.update({"launches": gemm_n, "share_of_step": (gemm_ms / 1e3) / (total / args.steps) if total else None,
+                 "measured_on": "one profiled step after the timed ones (CUDA events around every "
+                                "contraction launch, plain launches)",
                  "paths": {k: {"ms": round(x["ms"], 3),
                                "tflops": (x["flops"] / x["ms"] / 1e9) if x["ms"] else None,
                                "launches": x["launches"]} for k, x in paths.items()}})

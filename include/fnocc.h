@@ -251,6 +251,18 @@ fnocc_status fnocc_set_autotune(int enable);
 fnocc_status eom_sigma(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
 fnocc_status eom_sigma_dev(fnocc_ctx *ctx, int variant, const double *r, double *sigma);
 
+/* Launch-sequence replay of the EOM products (not in the paper; a library
+ * facility, on by default): once a product's cached R-independent pieces
+ * are valid and none of its steps still times tile shapes, its launch
+ * sequence is captured in a CUDA graph on the context stream (per variant,
+ * direction and arithmetic) and replayed by later products of the same
+ * shape, with the input and output copied through two buffers of the
+ * vector's size held by the context (vectors above 2^26 elements run
+ * without a graph). Results are bitwise those of the plain launches. Off
+ * (enable = 0) frees the graphs; per-launch profiling (fnocc_profile)
+ * always runs the plain launches. */
+fnocc_status fnocc_set_graphs(fnocc_ctx *ctx, int enable);
+
 /* Left product lambda = L^T H-bar, lambda_nu = sum_mu L_mu <mu| (H-bar tau_nu)_c
  * |0> with tau_nu the operator of packed element nu (not in the paper, which
  * names the left vectors L1-L3 only as rate-determining six-index

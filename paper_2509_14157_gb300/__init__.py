@@ -116,6 +116,7 @@ SIGNATURES = {
     "fnocc_tile_shape_first_mixed": (ctypes.c_int, []),
     "fnocc_tile_shape_kind": (ctypes.c_int, [ctypes.c_int]),
     "fnocc_set_autotune": (ctypes.c_int, [ctypes.c_int]),
+    "fnocc_set_graphs": (ctypes.c_int, [_cp, ctypes.c_int]),
     "fnocc_fp64_peak": (ctypes.c_int, [ctypes.c_int, _dp, _dp]),
     "fnocc_multi_dot": (ctypes.c_int, [_cp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp]),
     "fnocc_multi_dot_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, _vp, _vp]),
@@ -441,6 +442,10 @@ class Context:
         """Arithmetic of standalone residual / sigma calls: 'fp64', 'mixed'
         (BF16 three-slice split products) or 'mixed_tf32' (TF32 two-slice)."""
         self._check(self.lib.fnocc_set_precision(self._h, PRECISION[precision]))
+
+    def set_graphs(self, enable):
+        """Graph replay of the EOM products' launch sequences (fnocc_set_graphs)."""
+        self._check(self.lib.fnocc_set_graphs(self._h, 1 if enable else 0))
 
     def set_tile_shape(self, shape):
         """Forces one grouped-GEMM tile shape (-1: the library's choice)."""

@@ -126,6 +126,26 @@ struct TransformPlan {
   }
 };
 
+// A captured product launch sequence and what it was captured against.
+struct ProductGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> key;
+  uint64_t launches = 0;  // kernel launches of one replay
+  ProductGraph() {}
+  ProductGraph(const ProductGraph &) = delete;
+  ProductGraph &operator=(const ProductGraph &) = delete;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key.clear();
+  }
+  ~ProductGraph() { reset(); }
+};
+
+// products of larger spaces are launch-bound no longer and keep their own
+// buffers: no graph (and no copies through the fixed buffers)
+const size_t kGraphMaxDim = size_t(1) << 26;
+
 }  // namespace
 
 struct fnocc_ctx {
@@ -188,6 +208,11 @@ struct fnocc_ctx {
   size_t last_dim = 0;
   DevBuf eom_vecs;
   double flops_cc_last = 0, flops_sigma_last = 0;
+  // captured product launch sequences [variant][left][precision] and their
+  // fixed input / output buffers
+  bool use_graphs = true;
+  ProductGraph graphs[kEomVariants][2][3];
+  DevBuf gx, gs;
 
   // fno scratch
   DevBuf eri_ao, h_ao, c_mo, dens, fock, jmat, kmat, ctmp, evals, evecs, work, diis_f, diis_e, t2full, w2full,
@@ -440,7 +465,37 @@ uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic, bool left) {
   return left ? c->eq_seen_left[var][oc][ic] : c->eq_seen[var][oc][ic];
 }
 
-// s = (H-bar x)_c, or with left = true the left product s = x^T H-bar
+// the launch sequence of one product: unpack x into the dense work tensors,
+// the nine blocks into the dense accumulators, antisymmetrise-pack into s
+void sigma_launches(fnocc_ctx *c, int var, const double *x, double *s, bool left, const Launch &L,
+                    const Operands &ops) {
+  const int o = c->o, v = c->v;
+  auto &eqs = left ? c->eom_left_eq[var] : c->eom_eq[var];
+  size_t sz[3];
+  eom_sizes(c, var, sz);
+  size_t off = 0;
+  for (int k = 0; k < 3; ++k) {
+    unpack(c, L, x + off, kEom[var][k][0], kEom[var][k][1], c->rd[k].d());
+    off += sz[k];
+  }
+  off = 0;
+  for (int oc = 0; oc < 3; ++oc) {
+    int nh = kEom[var][oc][0], np = kEom[var][oc][1];
+    long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
+    FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, c->stream));
+    for (int ic = 0; ic < 3; ++ic) eqs[oc][ic]->run(L, ops, c->sy[oc].d(), dn, c->scratch, c->hbar_version);
+    antisym_pack(L, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
+                 c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
+    off += sz[oc];
+  }
+}
+
+// s = (H-bar x)_c, or with left = true the left product s = x^T H-bar.
+// Once the cached R-independent pieces are valid and no step still times
+// its tile shapes, the launch sequence is captured in a CUDA graph (per
+// variant, direction and arithmetic) and replayed on later calls, with x
+// and s copied through fixed buffers: the few-microsecond launches of the
+// small products then run back to back. Per-launch profiling turns it off.
 void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = false) {
   if (c->precision != c->cache_precision) {  // cached intermediates follow the arithmetic in use
     ++c->hbar_version;
@@ -452,7 +507,7 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = fa
   auto &eqs = left ? c->eom_left_eq[var] : c->eom_eq[var];
   size_t sz[3];
   eom_sizes(c, var, sz);
-  size_t off = 0;
+  const size_t dim = sz[0] + sz[1] + sz[2];
   Operands ops;
   ops.f = c->fdr.d();
   ops.v = c->gd.d();
@@ -467,29 +522,66 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = fa
     int nh = kEom[var][k][0], np = kEom[var][k][1];
     long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
     c->rd[k].reserve(sizeof(double) * dn);
-    unpack(c, L, x + off, nh, np, c->rd[k].d());
+    c->sy[k].reserve(sizeof(double) * dn);
     ops.r[k] = c->rd[k].d();
     ops.r_size[k] = dn;
-    off += sz[k];
   }
-  off = 0;
   double flops = 0;
-  for (int oc = 0; oc < 3; ++oc) {
-    int nh = kEom[var][oc][0], np = kEom[var][oc][1];
-    long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
-    c->sy[oc].reserve(sizeof(double) * dn);
-    FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, c->stream));
+  bool graph = c->use_graphs && !c->prof.enabled && dim <= kGraphMaxDim;
+  for (int oc = 0; oc < 3; ++oc)
     for (int ic = 0; ic < 3; ++ic) {
       ExecEquation &eq = *eqs[oc][ic];
       if (eq.cache_doubles() > 0 && eq_version(c, var, oc, ic, left) != c->hbar_version) flops += eq.cached_flops();
-      eq.run(L, ops, c->sy[oc].d(), dn, c->scratch, c->hbar_version);
-      eq_version(c, var, oc, ic, left) = c->hbar_version;
       flops += eq.flops();
+      if (eq.needs_refresh(c->hbar_version) || eq.tuning_pending(L)) graph = false;
     }
-    antisym_pack(L, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
-                 c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
-    off += sz[oc];
+  if (!graph) {
+    sigma_launches(c, var, x, s, left, L, ops);
+  } else {
+    c->gx.reserve(sizeof(double) * dim);
+    c->gs.reserve(sizeof(double) * dim);
+    // everything the captured launches address, and how they were chosen
+    std::vector<uintptr_t> key = {(uintptr_t)c->hbar_version, (uintptr_t)L.precision, (uintptr_t)(L.force_shape + 1),
+                                  (uintptr_t)c->gx.p, (uintptr_t)c->gs.p, (uintptr_t)c->scratch.p,
+                                  (uintptr_t)c->partials.p, (uintptr_t)ops.f, (uintptr_t)ops.v, (uintptr_t)ops.t2,
+                                  (uintptr_t)ops.t3};
+    for (int k = 0; k < 3; ++k) {
+      key.push_back((uintptr_t)c->rd[k].p);
+      key.push_back((uintptr_t)c->sy[k].p);
+    }
+    for (int oc = 0; oc < 3; ++oc)
+      for (int ic = 0; ic < 3; ++ic) key.push_back((uintptr_t)eqs[oc][ic]->cache_ptr());
+    ProductGraph &g = c->graphs[var][left ? 1 : 0][L.precision];
+    if (!g.exec || g.key != key) {
+      g.reset();
+      cudaGraph_t gr = nullptr;
+      const uint64_t l0 = c->launches;
+      FNOCC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+      try {
+        sigma_launches(c, var, c->gx.d(), c->gs.d(), left, L, ops);
+      } catch (...) {
+        cudaStreamEndCapture(c->stream, &gr);
+        if (gr) cudaGraphDestroy(gr);
+        c->launches = l0;
+        throw;
+      }
+      FNOCC_CUDA(cudaStreamEndCapture(c->stream, &gr));
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t e = cudaGraphInstantiate(&ex, gr, 0);
+      cudaGraphDestroy(gr);
+      FNOCC_CUDA(e);
+      g.exec = ex;
+      g.key = key;
+      g.launches = c->launches - l0;
+      c->launches = l0;
+    }
+    FNOCC_CUDA(cudaMemcpyAsync(c->gx.p, x, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
+    FNOCC_CUDA(cudaGraphLaunch(g.exec, c->stream));
+    c->launches += g.launches;
+    FNOCC_CUDA(cudaMemcpyAsync(s, c->gs.p, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
   }
+  for (int oc = 0; oc < 3; ++oc)
+    for (int ic = 0; ic < 3; ++ic) eq_version(c, var, oc, ic, left) = c->hbar_version;
   c->flops_sigma_last = flops;
   c->flops_total += flops;
   if (L.precision == FNOCC_MIXED_BF16X3 && tc_status_take(c->stream))
@@ -1235,6 +1327,16 @@ fnocc_status fnocc_set_tile_shape(fnocc_ctx *c, int shape) {
 }
 
 int fnocc_tile_shape_count(void) { return kGShapesAll; }
+
+fnocc_status fnocc_set_graphs(fnocc_ctx *c, int enable) {
+  if (!c) return FNOCC_E_INVALID;
+  c->use_graphs = enable != 0;
+  if (!c->use_graphs)
+    for (auto &a : c->graphs)
+      for (auto &b : a)
+        for (auto &g : b) g.reset();
+  return FNOCC_OK;
+}
 
 fnocc_status fnocc_set_autotune(int enable) {
   ExecEquation::autotune = enable != 0;

@@ -918,6 +918,21 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
   if (refresh) cache_version_ = version;
 }
 
+bool ExecEquation::tuning_pending(const Launch &L) const {
+  if (!autotune || L.force_shape >= 0) return false;
+  for (const ExecTerm &t : terms_)
+    for (const ExecStep &s : t.steps) {
+      // cached R-independent steps do not run while the cache is valid
+      if (!s.grouped || s.b_kind < 0 || s.constant) continue;
+      if (L.precision == 0) {
+        if (s.tuned_shape < 0 && s.cand.size() > 1 && s.gl[s.default_shape].padded >= 1e8) return true;
+      } else if (L.precision == 1 && s.gl[0].flops >= 1e5) {
+        if (s.tuned_mixed < 0 && s.gl[s.bf16x3_shape].padded >= 1e8) return true;
+      }
+    }
+  return false;
+}
+
 void ExecEquation::tune_launch(const Launch &L, ExecStep::Trial &tr, std::initializer_list<int> cand, int &tuned,
                                const ExecStep &s, const double *A, const double *B, double *C) {
   if (tr.pending < 0) {  // first use: an event pair of its own

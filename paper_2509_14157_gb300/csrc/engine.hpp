@@ -98,6 +98,12 @@ class ExecEquation {
   // cached R-independent intermediates are recomputed when it changes.
   void run(const Launch &L, const Operands &ops, double *Y, long long y_size, DevBuf &scratch,
            uint64_t version = 0);
+  // true when a run with this version would recompute the cached
+  // R-independent intermediates
+  bool needs_refresh(uint64_t version) const { return cache_need_ > 0 && version != cache_version_; }
+  // true while a run under L would still time candidate tile shapes
+  bool tuning_pending(const Launch &L) const;
+  const void *cache_ptr() const { return cache_.p; }
   long long scratch_doubles() const { return scratch_need_; }
   long long cache_doubles() const { return cache_need_; }
   double flops() const { return flops_; }              // per run, cached steps excluded
