@@ -392,19 +392,28 @@ def run_solve_only(args):
     and algorithmic flops."""
     import paper_2509_14157_gb300 as pkg
     import synth
-    h, eri = synth.hamiltonian(NE, NORB, seed=0)
+    ne, norb, thr, nroots = (PC_NE, PC_NORB, PC_THRESHOLD, PC_ROOTS) if args.large else (
+        NE, NORB, args.threshold, NROOTS)
+    h, eri = synth.hamiltonian(ne, norb, seed=0)
     ctx = pkg.Context(0)
-    ctx.fno_truncate(h, eri, NE // 2, args.threshold)
+    ctx.fno_truncate(h, eri, ne // 2, thr)
     kw = (dict(precision="fp64") if args.precision == "fp64"
           else dict(precision=args.precision, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8))
-    cc = ctx.ccsdt_solve()
+    t0 = time.perf_counter()
+    cc = ctx.ccsdt_solve(precision="mixed" if args.large and args.precision != "fp64" else "fp64")
+    t_cc = time.perf_counter() - t0
     kw["left"] = args.left
-    ctx.eom_solve(args.solve_only, NROOTS, **kw)
+    if not args.large:  # warm solve (plans, cached pieces); the larger system times its first solve
+        ctx.eom_solve(args.solve_only, nroots, **kw)
     f0 = ctx.flops
     t0 = time.perf_counter()
-    r = ctx.eom_solve(args.solve_only, NROOTS, **kw)
+    r = ctx.eom_solve(args.solve_only, nroots, **kw)
     dt = time.perf_counter() - t0
+    o, v, _ = ctx.dims()
     print(json.dumps({"solve_only": args.solve_only, "left": args.left, "precision": args.precision, "seconds": dt,
+                      "system": {"electrons": ne, "orbitals": norb, "fno_threshold": thr, "o": o, "v": v,
+                                 "roots": nroots, "dim": int(sum(ctx.eom_sizes(args.solve_only)))},
+                      "ccsdt_seconds": t_cc, "energies": [float(x) for x in r["energies"]],
                       "sigma_calls": r["sigma_calls"], "iters": r["iters"], "converged": r["converged"],
                       "omegas": [float(x) for x in r["omegas"]], "ccsdt_iters": cc["iters"],
                       "tflops": (ctx.flops - f0) / dt / 1e12}), flush=True)
@@ -418,9 +427,10 @@ def run_sigma_only(args):
     import torch
     import paper_2509_14157_gb300 as pkg
     import synth
-    h, eri = synth.hamiltonian(NE, NORB, seed=0)
+    ne, norb, thr = (PC_NE, PC_NORB, PC_THRESHOLD) if args.large else (NE, NORB, args.threshold)
+    h, eri = synth.hamiltonian(ne, norb, seed=0)
     ctx = pkg.Context(0)
-    ctx.fno_truncate(h, eri, NE // 2, args.threshold)
+    ctx.fno_truncate(h, eri, ne // 2, thr)
     rng = np.random.default_rng(0)
     ctx.set_amplitudes(*[rng.normal(0, 0.01, s) for s in ctx.amp_sizes()])
     ctx.set_precision(args.precision)
@@ -653,6 +663,9 @@ def main():
                     help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
     ap.add_argument("--solve-only", default=None, choices=list(VARIANTS) + ["ee"],
                     help="FNO, CCSDT and one Davidson solve of this variant (4 roots) at the workload's size")
+    ap.add_argument("--large", action="store_true",
+                    help="with --sigma-only / --solve-only: the larger system (16 electrons / 80 orbitals, FNO "
+                         "1e-6: 41 kept natural virtuals, o = 16, v = 82), 6 roots; mixed solves run CCSDT mixed")
     ap.add_argument("--left", action="store_true",
                     help="with --sigma-only / --solve-only: the left product / left eigenvectors")
     ap.add_argument("--sigma-only", default=None, choices=list(VARIANTS) + ["ee"],

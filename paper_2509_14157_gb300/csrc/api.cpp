@@ -1528,49 +1528,69 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
         return score[a] > score[b] || (score[a] == score[b] && a < b);
       });
     if ((long long)order.size() > ng) order.resize(ng);
-    // subspace storage
+    // Subspace vectors hold the sector's elements only (the allowed packed
+    // indices in order: about a third of the packed space for the
+    // M_s-conserving variants), so that the subspace of the largest spaces
+    // fits next to the product's dense work tensors; products expand a
+    // vector into the packed layout and take the sector's part back.
+    const long long na = (long long)allowed.size();
+    long long na0 = 0;  // allowed elements of the principal block (they come first)
+    while (na0 < na && allowed[na0] < (long long)sz[0]) ++na0;
+    DevBuf aidx, dgc;
+    aidx.reserve(sizeof(long long) * na);
+    FNOCC_CUDA(cudaMemcpyAsync(aidx.p, allowed.data(), sizeof(long long) * na, cudaMemcpyHostToDevice, c->stream));
+    dgc.reserve(sizeof(double) * na);
+    gather_idx(L, na, aidx.as<long long>(), dg.d(), dgc.d());
+    sync(c);
+    dg.release();
+    mk.release();
+    auto cpos = [&](long long full) {  // position of an allowed packed index in the sector
+      return (long long)(std::lower_bound(allowed.begin(), allowed.end(), full) - allowed.begin());
+    };
+    DevBuf xfull, sfull;  // one product's input and output in the packed layout
+    xfull.reserve(sizeof(double) * dim);
+    sfull.reserve(sizeof(double) * dim);
+    // elements outside the sector stay zero: the products only write the
+    // allowed ones into xfull
+    FNOCC_CUDA(cudaMemsetAsync(xfull.p, 0, sizeof(double) * dim, c->stream));
     const int cap = max_sub + nr + 1;
     DevBuf Vb, Sb, xr, rr, tmp;
-    Vb.reserve(sizeof(double) * dim * cap);
-    Sb.reserve(sizeof(double) * dim * cap);
-    xr.reserve(sizeof(double) * dim * nr);
-    rr.reserve(sizeof(double) * dim * nr);
-    tmp.reserve(sizeof(double) * dim);
-    const unsigned char *mask = mk.as<unsigned char>();
+    Vb.reserve(sizeof(double) * na * cap);
+    Sb.reserve(sizeof(double) * na * cap);
+    xr.reserve(sizeof(double) * na * nr);
+    rr.reserve(sizeof(double) * na * nr);
+    tmp.reserve(sizeof(double) * na);
     int kb = 0, sigma_calls = 0;
     std::vector<double> G;  // kb x kb, row-major, G[i][j] = V_i . S_j
     std::vector<double> G1;  // kb x kb, principal-block overlaps V_i[0:sz0] . V_j[0:sz0]
-    const long long sz0 = (long long)sz[0];
-    auto vrow = [&](int i) { return Vb.d() + (size_t)i * dim; };
-    auto srow = [&](int i) { return Sb.d() + (size_t)i * dim; };
+    auto vrow = [&](int i) { return Vb.d() + (size_t)i * na; };
+    auto srow = [&](int i) { return Sb.d() + (size_t)i * na; };
     // Appends src, orthonormalised against the basis (Gram-Schmidt twice), and
     // its product: computed, or (restart) carried along linearly from sig_src.
     auto add_vector = [&](const double *src, const double *sig_src = nullptr) -> bool {
       double *dst = vrow(kb);
       double *sdst = srow(kb);
-      FNOCC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
-      scale_mask(L, dim, dst, mask);
-      if (sig_src) {
-        FNOCC_CUDA(cudaMemcpyAsync(sdst, sig_src, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
-        scale_mask(L, dim, sdst, mask);
-      }
+      FNOCC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * na, cudaMemcpyDeviceToDevice, c->stream));
+      if (sig_src)
+        FNOCC_CUDA(cudaMemcpyAsync(sdst, sig_src, sizeof(double) * na, cudaMemcpyDeviceToDevice, c->stream));
       for (int pass = 0; pass < 2 && kb > 0; ++pass) {
         c->small.reserve(sizeof(double) * std::max(64, kb));
-        multi_dot(L, dim, dst, Vb.d(), dim, kb, c->small.d(), c->red);
+        multi_dot(L, na, dst, Vb.d(), na, kb, c->small.d(), c->red);
         auto d = to_host(c, c->small.d(), kb);
         for (auto &x : d) x = -x;
-        combine_rows(c, dim, Vb.d(), kb, d, dst, true);
-        if (sig_src) combine_rows(c, dim, Sb.d(), kb, d, sdst, true);
+        combine_rows(c, na, Vb.d(), kb, d, dst, true);
+        if (sig_src) combine_rows(c, na, Sb.d(), kb, d, sdst, true);
       }
       double amax, nrm;
-      absmax_dev(c, dim, dst, &amax, &nrm);
+      absmax_dev(c, na, dst, &amax, &nrm);
       if (!(nrm > 1e-10)) return false;
-      axpby(L, dim, 0.0, dst, 1.0 / nrm, dst);
+      axpby(L, na, 0.0, dst, 1.0 / nrm, dst);
       if (sig_src) {
-        axpby(L, dim, 0.0, sdst, 1.0 / nrm, sdst);
+        axpby(L, na, 0.0, sdst, 1.0 / nrm, sdst);
       } else {
-        sigma_dev(c, variant, dst, sdst, c->eom_left);
-        scale_mask(L, dim, sdst, mask);
+        scatter_idx(L, na, aidx.as<long long>(), dst, xfull.d());
+        sigma_dev(c, variant, xfull.d(), sfull.d(), c->eom_left);
+        gather_idx(L, na, aidx.as<long long>(), sfull.d(), sdst);
         ++sigma_calls;
         if (c->precision != FNOCC_FP64) ++sigma_calls_mixed;
       }
@@ -1580,11 +1600,11 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       for (int i = 0; i < kb; ++i)
         for (int j = 0; j < kb; ++j) Gn[i * k1 + j] = G[i * kb + j];
       c->small.reserve(sizeof(double) * std::max(64, k1));
-      multi_dot(L, dim, srow(kb), Vb.d(), dim, k1, c->small.d(), c->red);  // V_i . S_new
+      multi_dot(L, na, srow(kb), Vb.d(), na, k1, c->small.d(), c->red);  // V_i . S_new
       auto col = to_host(c, c->small.d(), k1);
       for (int i = 0; i < k1; ++i) Gn[i * k1 + kb] = col[i];
       if (kb > 0) {
-        multi_dot(L, dim, vrow(kb), Sb.d(), dim, kb, c->small.d(), c->red);  // V_new . S_j
+        multi_dot(L, na, vrow(kb), Sb.d(), na, kb, c->small.d(), c->red);  // V_new . S_j
         auto row = to_host(c, c->small.d(), kb);
         for (int j = 0; j < kb; ++j) Gn[kb * k1 + j] = row[j];
       }
@@ -1592,17 +1612,17 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       std::vector<double> G1n((size_t)k1 * k1, 0.0);
       for (int i = 0; i < kb; ++i)
         for (int j = 0; j < kb; ++j) G1n[i * k1 + j] = G1[i * kb + j];
-      multi_dot(L, sz0, vrow(kb), Vb.d(), dim, k1, c->small.d(), c->red);  // principal overlaps
+      multi_dot(L, na0, vrow(kb), Vb.d(), na, k1, c->small.d(), c->red);  // principal overlaps
       auto pc = to_host(c, c->small.d(), k1);
       for (int i = 0; i < k1; ++i) G1n[i * k1 + kb] = G1n[kb * k1 + i] = pc[i];
       G1.swap(G1n);
       kb = k1;
       return true;
     };
-    auto add_unit = [&](long long idx) {
-      FNOCC_CUDA(cudaMemsetAsync(tmp.p, 0, sizeof(double) * dim, c->stream));
+    auto add_unit = [&](long long full) {
+      FNOCC_CUDA(cudaMemsetAsync(tmp.p, 0, sizeof(double) * na, c->stream));
       double one = 1.0;
-      FNOCC_CUDA(cudaMemcpyAsync(tmp.d() + idx, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      FNOCC_CUDA(cudaMemcpyAsync(tmp.d() + cpos(full), &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
       sync(c);
       return add_vector(tmp.d());
     };
@@ -1657,13 +1677,13 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
         if (nn == 0) nn = 1;
         for (double &a : y) a /= nn;
         ys[r] = y;
-        double *x = xr.d() + (size_t)r * dim;
-        double *res = rr.d() + (size_t)r * dim;
-        combine_rows(c, dim, Vb.d(), kb, y, x, false);
-        combine_rows(c, dim, Sb.d(), kb, y, res, false);
-        axpby(L, dim, -theta[r], x, 1.0, res);
+        double *x = xr.d() + (size_t)r * na;
+        double *res = rr.d() + (size_t)r * na;
+        combine_rows(c, na, Vb.d(), kb, y, x, false);
+        combine_rows(c, na, Sb.d(), kb, y, res, false);
+        axpby(L, na, -theta[r], x, 1.0, res);
         double amax, nrm;
-        absmax_dev(c, dim, res, &amax, &nrm);
+        absmax_dev(c, na, res, &amax, &nrm);
         if (!std::isfinite(nrm)) throw StatusError(FNOCC_E_NUMERIC, "NaN in Davidson residual");
         norms[r] = nrm;
       }
@@ -1676,12 +1696,12 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
           c->precision = FNOCC_FP64;
           ++c->hbar_version;
           DevBuf keep;
-          keep.reserve(sizeof(double) * dim * nr);
-          FNOCC_CUDA(cudaMemcpyAsync(keep.p, xr.p, sizeof(double) * dim * nr, cudaMemcpyDeviceToDevice, c->stream));
+          keep.reserve(sizeof(double) * na * nr);
+          FNOCC_CUDA(cudaMemcpyAsync(keep.p, xr.p, sizeof(double) * na * nr, cudaMemcpyDeviceToDevice, c->stream));
           kb = 0;
           G.clear();
           G1.clear();
-          for (int r = 0; r < nr; ++r) add_vector(keep.d() + (size_t)r * dim);
+          for (int r = 0; r < nr; ++r) add_vector(keep.d() + (size_t)r * na);
           have_old = false;
           continue;
         }
@@ -1707,8 +1727,8 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
         // products, formed as the same linear combinations (no new products)
         const int nkeep = std::min((int)idx.size(), 2 * nr);
         DevBuf kx, ks;
-        kx.reserve(sizeof(double) * dim * nkeep);
-        ks.reserve(sizeof(double) * dim * nkeep);
+        kx.reserve(sizeof(double) * na * nkeep);
+        ks.reserve(sizeof(double) * na * nkeep);
         for (int q = 0; q < nkeep; ++q) {
           int j = idx[q];
           std::vector<double> y(kb);
@@ -1718,17 +1738,17 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
           nn = std::sqrt(nn);
           if (nn == 0) nn = 1;
           for (double &t : y) t /= nn;
-          combine_rows(c, dim, Vb.d(), kb, y, kx.d() + (size_t)q * dim, false);
-          combine_rows(c, dim, Sb.d(), kb, y, ks.d() + (size_t)q * dim, false);
+          combine_rows(c, na, Vb.d(), kb, y, kx.d() + (size_t)q * na, false);
+          combine_rows(c, na, Sb.d(), kb, y, ks.d() + (size_t)q * na, false);
         }
         kb = 0;
         G.clear();
         G1.clear();
-        for (int q = 0; q < nkeep; ++q) add_vector(kx.d() + (size_t)q * dim, ks.d() + (size_t)q * dim);
+        for (int q = 0; q < nkeep; ++q) add_vector(kx.d() + (size_t)q * na, ks.d() + (size_t)q * na);
       }
       for (int r = 0; r < nr; ++r) {
         if (done[r]) continue;
-        precondition(L, dim, rr.d() + (size_t)r * dim, dg.d(), theta[r], mask, tmp.d());
+        precondition(L, na, rr.d() + (size_t)r * na, dgc.d(), theta[r], nullptr, tmp.d());
         add_vector(tmp.d());
       }
     }
@@ -1739,8 +1759,13 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       energies[r] = c->e_ref + c->e_corr + th;
       if (omegas) omegas[r] = th;
     }
+    // root vectors in the packed layout (zero outside the sector)
+    Vb.release();
+    Sb.release();
     c->eom_vecs.reserve(sizeof(double) * dim * nr);
-    FNOCC_CUDA(cudaMemcpyAsync(c->eom_vecs.p, xr.p, sizeof(double) * dim * nr, cudaMemcpyDeviceToDevice, c->stream));
+    FNOCC_CUDA(cudaMemsetAsync(c->eom_vecs.p, 0, sizeof(double) * dim * nr, c->stream));
+    for (int r = 0; r < nr; ++r)
+      scatter_idx(L, na, aidx.as<long long>(), xr.d() + (size_t)r * na, c->eom_vecs.d() + (size_t)r * dim);
     sync(c);
     c->last_variant = variant;
     c->last_nroots = nr;

@@ -177,7 +177,10 @@ void axpby(const Launch &L, long long n, double a, const double *x, double b, do
 void scale_mask(const Launch &L, long long n, double *x, const unsigned char *mask);       // x *= mask
 void jacobi_update(const Launch &L, long long n, const double *r, const double *d, double *t);  // t += r/d
 void precondition(const Launch &L, long long n, const double *r, const double *d, double theta,
-                  const unsigned char *mask, double *out);  // out = mask * r / (theta - d)
+                  const unsigned char *mask, double *out);  // out = mask * r / (theta - d) (mask NULL: 1)
+// dst[i] = src[idx[i]] and dst[idx[i]] = src[i] for i < n
+void gather_idx(const Launch &L, long long n, const long long *idx, const double *src, double *dst);
+void scatter_idx(const Launch &L, long long n, const long long *idx, const double *src, double *dst);
 // dots[j] = sum_i x[i] * Y[j*ld + i] for j < nvec  (reduction over i)
 void multi_dot(const Launch &L, long long n, const double *x, const double *Y, long long ld,
                int nvec, double *dots_dev, DevBuf &scratch);

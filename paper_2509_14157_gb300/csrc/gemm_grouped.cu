@@ -153,12 +153,23 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(sign | ((unsigned)e << 23) | mant);
 }
 
-// exact split of an FP32 value into three BF16 slices (8 significant bits each)
+// bits of a finite FP32 value rounded to BF16, round to nearest, ties to
+// even, in the upper half of the word (integer arithmetic only)
+__device__ __forceinline__ unsigned bf16_rne_bits(float x) {
+  const unsigned u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+}
+
+// exact split of an FP32 value into three BF16 slices (8 significant bits
+// each; every remainder is exact in FP32)
 __device__ __forceinline__ void split3(float x, __nv_bfloat16 &s0, __nv_bfloat16 &s1, __nv_bfloat16 &s2) {
-  s0 = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(s0);
-  s1 = __float2bfloat16_rn(r1);
-  s2 = __float2bfloat16_rn(r1 - __bfloat162float(s1));
+  const unsigned u0 = bf16_rne_bits(x);
+  const float r1 = x - __uint_as_float(u0);
+  const unsigned u1 = bf16_rne_bits(r1);
+  const float r2 = r1 - __uint_as_float(u1);
+  s0 = __ushort_as_bfloat16((unsigned short)(u0 >> 16));
+  s1 = __ushort_as_bfloat16((unsigned short)(u1 >> 16));
+  s2 = __ushort_as_bfloat16((unsigned short)(bf16_rne_bits(r2) >> 16));
 }
 
 // FP32 -> TF32 (11 significant bits) rounded to nearest, ties away from
@@ -298,6 +309,9 @@ __device__ __forceinline__ void ggemm_split(const GTask *__restrict__ tasks, int
   slice_t *As = reinterpret_cast<slice_t *>(smem_raw);
   slice_t *Bs = As + 2 * NS * TBM * LDS;
   __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN];
+  // reduction-index offsets of the K tiles in flight (a ring of three): read
+  // one tile ahead, so that no operand gather waits on a table load
+  __shared__ long long acol_r[3][TBK], brow_r[3][TBK];
   __shared__ GTask t;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -321,23 +335,35 @@ __device__ __forceinline__ void ggemm_split(const GTask *__restrict__ tasks, int
     bcol_s[i] = n < t.N ? t.bcol[n] : 0;
     ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
   }
+  // table entries of the K tile at k0 into ring slot q (threads 0 .. 2 TBK - 1)
+  auto load_tables = [&](long long k0, int q) {
+    if (tid < TBK) {
+      const long long k = k0 + tid;
+      acol_r[q][tid] = k < ke ? __ldg(t.acol + k) : 0;
+    } else if (tid < 2 * TBK) {
+      const long long k = k0 + tid - TBK;
+      brow_r[q][tid - TBK] = k < ke ? __ldg(t.brow + k) : 0;
+    }
+  };
+  load_tables(kb, 0);
+  load_tables(kb + TBK, 1);
   __syncthreads();
   double ra[EA], rb[EB];
   // gathers of the K tile at k0 into registers (0 outside the task)
-  auto load = [&](long long k0) {
+  auto load = [&](long long k0, int q) {
 #pragma unroll
     for (int r = 0; r < EA; ++r) {
       const int idx = tid + NT * r;
       const int kk = idx % TBK, row = idx / TBK;
       const long long k = k0 + kk;
-      ra[r] = (m0 + row < t.M && k < ke) ? __ldg(A + arow_s[row] + __ldg(t.acol + k)) : 0.0;
+      ra[r] = (m0 + row < t.M && k < ke) ? __ldg(A + arow_s[row] + acol_r[q][kk]) : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < EB; ++r) {
       const int idx = tid + NT * r;
       const int col = idx % TBN, kk = idx / TBN;
       const long long k = k0 + kk;
-      rb[r] = (n0 + col < t.N && k < ke) ? __ldg(B + __ldg(t.brow + k) + bcol_s[col]) : 0.0;
+      rb[r] = (n0 + col < t.N && k < ke) ? __ldg(B + brow_r[q][kk] + bcol_s[col]) : 0.0;
     }
   };
   float acc[MT][NT2][4];
@@ -347,9 +373,9 @@ __device__ __forceinline__ void ggemm_split(const GTask *__restrict__ tasks, int
     for (int j = 0; j < NT2; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  if (kb < ke) load(kb);
-  int buf = 0;
-  for (long long k0 = kb; k0 < ke; k0 += TBK, buf ^= 1) {
+  if (kb < ke) load(kb, 0);
+  int buf = 0, q = 0;
+  for (long long k0 = kb; k0 < ke; k0 += TBK, buf ^= 1, q = q == 2 ? 0 : q + 1) {
     slice_t *as = As + buf * NS * TBM * LDS, *bs = Bs + buf * NS * TBN * LDS;
 #pragma unroll
     for (int r = 0; r < EA; ++r) {
@@ -364,7 +390,9 @@ __device__ __forceinline__ void ggemm_split(const GTask *__restrict__ tasks, int
       S::stage(f64_to_f32_trunc(rb[r]), &bs[col * LDS + kk], TBN * LDS);
     }
     __syncthreads();
-    if (k0 + TBK < ke) load(k0 + TBK);  // next tile's gathers overlap this tile's products
+    const int q1 = q == 2 ? 0 : q + 1, q2 = q1 == 2 ? 0 : q1 + 1;
+    if (k0 + TBK < ke) load(k0 + TBK, q1);  // next tile's gathers overlap this tile's products
+    if (k0 + 2 * TBK < ke) load_tables(k0 + 2 * TBK, q2);
     S::template products<TBM, TBN, MT, NT2>(as, bs, wm, wn, g, tg, acc);
   }
   const long long MN = t.M * t.N;

@@ -134,12 +134,25 @@ __device__ __forceinline__ float trunc_f32(double x) {
   return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffu));
 }
 
-__device__ __forceinline__ void split3(double xd, __nv_bfloat16 &s0, __nv_bfloat16 &s1, __nv_bfloat16 &s2) {
+// bits of a finite FP32 value rounded to BF16 (8 significant bits), round
+// to nearest, ties to even, kept in the upper half of the word: integer
+// arithmetic only (no conversion unit)
+__device__ __forceinline__ uint32_t bf16_rne_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+}
+
+// x = s0 + s1 + s2 exactly (24 = 3 x 8 significant bits; each remainder is
+// exact in FP32); the BF16 slices as their 16-bit patterns
+__device__ __forceinline__ void split3(double xd, uint16_t &s0, uint16_t &s1, uint16_t &s2) {
   const float x = trunc_f32(xd);
-  s0 = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(s0);
-  s1 = __float2bfloat16_rn(r1);
-  s2 = __float2bfloat16_rn(r1 - __bfloat162float(s1));
+  const uint32_t u0 = bf16_rne_bits(x);
+  const float r1 = x - __uint_as_float(u0);
+  const uint32_t u1 = bf16_rne_bits(r1);
+  const float r2 = r1 - __uint_as_float(u1);
+  s0 = (uint16_t)(u0 >> 16);
+  s1 = (uint16_t)(u1 >> 16);
+  s2 = (uint16_t)(bf16_rne_bits(r2) >> 16);
 }
 
 // byte offset of element (row, k) of a K-step plane (k < 16): core matrix
@@ -170,6 +183,9 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ long long arow_s[kBM], crow_s[kBM], bcol_s[BN], ccol_s[BN];
+  // reduction-index offsets of the K tiles kt, kt + 1, kt + 2 (a ring): read
+  // one stage ahead, so that no operand gather waits on a table load
+  __shared__ long long acol_r[3][kBK], brow_r[3][kBK];
   __shared__ GTask t;
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ uint32_t tmem_base_s;
@@ -209,26 +225,38 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
     bcol_s[i] = n < t.N ? t.bcol[n] : 0;
     ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
   }
+  // table entries of the K tile at k0 into ring slot q (threads 0 .. 2 kBK - 1)
+  auto load_tables = [&](long long k0, int q) {
+    if (tid < kBK) {
+      const long long k = k0 + tid;
+      acol_r[q][tid] = k < ke ? __ldg(t.acol + k) : 0;
+    } else if (tid < 2 * kBK) {
+      const long long k = k0 + tid - kBK;
+      brow_r[q][tid - kBK] = k < ke ? __ldg(t.brow + k) : 0;
+    }
+  };
+  load_tables(kb, 0);
+  load_tables(kb + kBK, 1);
   __syncthreads();
 
   double ra[EA], rb[EB];
   // gathers of the stage at k0 into registers (0 outside the task): a warp
   // reads 32 consecutive k of one A row, and 32 consecutive columns of one B
   // row
-  auto load = [&](long long k0) {
+  auto load = [&](long long k0, int q) {
 #pragma unroll
     for (int r = 0; r < EA; ++r) {
       const int idx = tid + kThreads * r;
       const int kk = idx % kBK, row = idx / kBK;
       const long long k = k0 + kk;
-      ra[r] = (m0 + row < t.M && k < ke) ? __ldg(A + arow_s[row] + __ldg(t.acol + k)) : 0.0;
+      ra[r] = (m0 + row < t.M && k < ke) ? __ldg(A + arow_s[row] + acol_r[q][kk]) : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < EB; ++r) {
       const int idx = tid + kThreads * r;
       const int col = idx % BN, kk = idx / BN;
       const long long k = k0 + kk;
-      rb[r] = (n0 + col < t.N && k < ke) ? __ldg(B + __ldg(t.brow + k) + bcol_s[col]) : 0.0;
+      rb[r] = (n0 + col < t.N && k < ke) ? __ldg(B + brow_r[q][kk] + bcol_s[col]) : 0.0;
     }
   };
 
@@ -237,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
   constexpr uint32_t idesc = idesc_bf16(kBM, BN);
   // the six slice products i + j <= 2 (A slice i, B slice j)
   constexpr int kPi[6] = {0, 0, 1, 0, 1, 2}, kPj[6] = {0, 1, 0, 2, 1, 0};
-  if (nk > 0) load(kb);
+  if (nk > 0) load(kb, 0);
   for (long long kt = 0; kt < nk; ++kt) {
     const int s = (int)(kt & 1);
     unsigned char *stA = smem + s * T::kStage;
@@ -251,28 +279,29 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
     for (int r = 0; r < EA; ++r) {
       const int idx = tid + kThreads * r;
       const int kk = idx % kBK, row = idx / kBK;
-      __nv_bfloat16 s0, s1, s2;
+      uint16_t s0, s1, s2;
       split3(ra[r], s0, s1, s2);
       const uint32_t off = (uint32_t)((kk >> 4) * T::kPlaneA) + core_off(row, kk & 15);
-      *reinterpret_cast<__nv_bfloat16 *>(stA + off) = s0;
-      *reinterpret_cast<__nv_bfloat16 *>(stA + 2 * T::kPlaneA + off) = s1;
-      *reinterpret_cast<__nv_bfloat16 *>(stA + 4 * T::kPlaneA + off) = s2;
+      *reinterpret_cast<uint16_t *>(stA + off) = s0;
+      *reinterpret_cast<uint16_t *>(stA + 2 * T::kPlaneA + off) = s1;
+      *reinterpret_cast<uint16_t *>(stA + 4 * T::kPlaneA + off) = s2;
     }
 #pragma unroll
     for (int r = 0; r < EB; ++r) {
       const int idx = tid + kThreads * r;
       const int col = idx % BN, kk = idx / BN;
-      __nv_bfloat16 s0, s1, s2;
+      uint16_t s0, s1, s2;
       split3(rb[r], s0, s1, s2);
       const uint32_t off = (uint32_t)((kk >> 4) * T::kPlaneB) + core_off(col, kk & 15);
-      *reinterpret_cast<__nv_bfloat16 *>(stB + off) = s0;
-      *reinterpret_cast<__nv_bfloat16 *>(stB + 2 * T::kPlaneB + off) = s1;
-      *reinterpret_cast<__nv_bfloat16 *>(stB + 4 * T::kPlaneB + off) = s2;
+      *reinterpret_cast<uint16_t *>(stB + off) = s0;
+      *reinterpret_cast<uint16_t *>(stB + 2 * T::kPlaneB + off) = s1;
+      *reinterpret_cast<uint16_t *>(stB + 4 * T::kPlaneB + off) = s2;
     }
     // generic-proxy stores become visible to the tensor cores' async proxy
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (kt + 1 < nk) load(kb + (kt + 1) * kBK);  // in flight during the products below
+    if (kt + 1 < nk) load(kb + (kt + 1) * kBK, (int)((kt + 1) % 3));  // in flight during the products below
+    if (kt + 2 < nk) load_tables(kb + (kt + 2) * kBK, (int)((kt + 2) % 3));
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t a0 = sbase + s * T::kStage, b0 = a0 + T::kStageA;

@@ -543,7 +543,17 @@ __global__ void k_precondition(long long n, const double *r, const double *d, do
   if (i >= n) return;
   double den = theta - d[i];
   if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
-  out[i] = mask[i] ? r[i] / den : 0.0;
+  out[i] = (!mask || mask[i]) ? r[i] / den : 0.0;
+}
+
+__global__ void k_gather_idx(long long n, const long long *idx, const double *src, double *dst) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void k_scatter_idx(long long n, const long long *idx, const double *src, double *dst) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[idx[i]] = src[i];
 }
 
 // y[i] (+)= sum_j coef[j] * X[j * ld + i]: one streaming pass over the k
@@ -1133,6 +1143,18 @@ void axpby(const Launch &L, long long n, double a, const double *x, double b, do
 void scale_mask(const Launch &L, long long n, double *x, const unsigned char *mask) {
   if (n <= 0) return;
   k_scale_mask<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, x, mask);
+  post(L);
+}
+
+void gather_idx(const Launch &L, long long n, const long long *idx, const double *src, double *dst) {
+  if (n <= 0) return;
+  k_gather_idx<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, idx, src, dst);
+  post(L);
+}
+
+void scatter_idx(const Launch &L, long long n, const long long *idx, const double *src, double *dst) {
+  if (n <= 0) return;
+  k_scatter_idx<<<blocks_for(n, 256), 256, 0, L.stream>>>(n, idx, src, dst);
   post(L);
 }
 
