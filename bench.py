@@ -533,8 +533,10 @@ def run_precision_check(args):
     target), each from the same converged amplitudes. Reports per-root total
     energy errors of the split kinds against the FP64 solve and wall-clock
     seconds of the synchronous library calls; one JSON line per finished
-    part, then a summary line. DEA is left out at this size: its dense R3
-    work tensor alone is o^2 v^4 doubles (93 GB)."""
+    part, then a summary line. DEA (--pc-variants dea) fits at this size
+    (dense R3 work tensor and accumulator 93 GB each, sector-compressed
+    Davidson subspace) but its FP64 solve takes about a quarter of an hour,
+    so it is run on request."""
     import paper_2509_14157_gb300 as pkg
     import synth
 
@@ -557,9 +559,11 @@ def run_precision_check(args):
         summary["ccsdt"][prec] = part
         emit({"part": "ccsdt", "precision": prec, **part})
     summary["ccsdt"]["e_corr_diff"] = summary["ccsdt"]["mixed"]["e_corr"] - summary["ccsdt"]["fp64"]["e_corr"]
-    for var in PC_VARIANTS:
+    variants = tuple(args.pc_variants.split(",")) if args.pc_variants else PC_VARIANTS
+    kinds = tuple(args.pc_kinds.split(",")) if args.pc_kinds else ("mixed", "mixed_tf32")
+    for var in variants:
         res = {}
-        for prec in ("fp64", "mixed", "mixed_tf32"):
+        for prec in ("fp64",) + kinds:
             kw = (dict(precision="fp64") if prec == "fp64"
                   else dict(precision=prec, switch_tol=0.0, tol_res=1e-6, tol_e=1e-8))
             t0 = time.perf_counter()
@@ -568,7 +572,7 @@ def run_precision_check(args):
                          "converged": r["converged"], "energies": [float(x) for x in r["energies"]]}
             emit({"part": "eom", "variant": var, "precision": prec, **res[prec]})
         ref = np.asarray(res["fp64"]["energies"])
-        for prec in ("mixed", "mixed_tf32"):
+        for prec in kinds:
             err = np.asarray(res[prec]["energies"]) - ref
             res[prec]["max_abs_err_eh"] = float(np.max(np.abs(err)))
             res[prec]["speedup_vs_fp64"] = res["fp64"]["seconds"] / res[prec]["seconds"]
@@ -661,6 +665,11 @@ def main():
                          "DIP (16 electrons) and DEA (12 electrons)")
     ap.add_argument("--precision-check", action="store_true",
                     help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
+    ap.add_argument("--pc-variants", default=None,
+                    help="with --precision-check: comma-separated variants (default ip,ea,dip; dea fits on the "
+                         "device at this size, its FP64 solve takes about a quarter of an hour)")
+    ap.add_argument("--pc-kinds", default=None,
+                    help="with --precision-check: comma-separated split kinds (default mixed,mixed_tf32)")
     ap.add_argument("--solve-only", default=None, choices=list(VARIANTS) + ["ee"],
                     help="FNO, CCSDT and one Davidson solve of this variant (4 roots) at the workload's size")
     ap.add_argument("--large", action="store_true",
