@@ -691,6 +691,7 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
           ks = (tr.K + kchunk - 1) / kchunk;
           g.ksplit = (int)ks;
           g.kchunk = kchunk;
+          g.mfast = tr.N > tr.M ? 1 : 0;
           g.cta_begin = cta;
           cta += g.tiles * ks;
           if (ks > 1) {

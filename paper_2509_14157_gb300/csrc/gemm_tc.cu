@@ -171,6 +171,8 @@ struct TcTile {
   static constexpr size_t kSmem = 2 * (size_t)kStage + 1024;  // two stages + alignment slack
   static constexpr int EA = kBM * kBK / kThreads;  // gathered A elements per thread and stage
   static constexpr int EB = BN * kBK / kThreads;
+  static_assert(EA % 2 == 0 && EB % 2 == 0 && kBM * kBK / 64 == 8 * (EA / 2) && BN * kBK / 64 == 8 * (EB / 2),
+                "every core matrix of a stage taken by exactly one warp");
   static_assert(BN == 64 || BN == 128 || BN == 256, "accumulator width");
 };
 
@@ -212,7 +214,11 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
   const uint32_t tmem = tmem_base_s;
   const long long local = cta - t.cta_begin;
   const long long z = local / t.tiles, tile = local - z * t.tiles;
-  const long long m0 = (tile / t.tiles_n) * kBM, n0 = (tile % t.tiles_n) * BN;
+  // tile order: n fastest (consecutive CTAs share the A row tile), or m
+  // fastest where B is the larger operand (they share its column tile in L2)
+  const long long tiles_m = t.tiles / t.tiles_n;
+  const long long m0 = (t.mfast ? tile % tiles_m : tile / t.tiles_n) * kBM,
+                  n0 = (t.mfast ? tile / tiles_m : tile % t.tiles_n) * BN;
   const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
   const bool split = t.ksplit > 1;
   for (int i = tid; i < kBM; i += kThreads) {
@@ -240,23 +246,29 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
   __syncthreads();
 
   double ra[EA], rb[EB];
-  // gathers of the stage at k0 into registers (0 outside the task): a warp
-  // reads 32 consecutive k of one A row, and 32 consecutive columns of one B
-  // row
+  // Gathers of the stage at k0 into registers (0 outside the task). The
+  // stage's operand planes are sets of core matrices (8 rows x 8 k): A has
+  // 16 row groups x 4 k chunks, B has BN / 8 column groups x 4 k chunks, and
+  // warp w takes core matrices w, w + 8, w + 16, ...; lane l takes row l / 4
+  // of the core matrix and its k pair 2 (l mod 4), 2 (l mod 4) + 1, so that
+  // each later store of a warp fills one core matrix's 128 contiguous bytes
+  // (no bank conflict).
   auto load = [&](long long k0, int q) {
 #pragma unroll
-    for (int r = 0; r < EA; ++r) {
-      const int idx = tid + kThreads * r;
-      const int kk = idx % kBK, row = idx / kBK;
-      const long long k = k0 + kk;
-      ra[r] = (m0 + row < t.M && k < ke) ? __ldg(A + arow_s[row] + acol_r[q][kk]) : 0.0;
+    for (int j = 0; j < EA / 2; ++j) {
+      const int cm = warp + 8 * j, rg = cm & 15, kc = cm >> 4;
+      const int row = rg * 8 + (lane >> 2), kk = kc * 8 + 2 * (lane & 3);
+      const bool rok = m0 + row < t.M;
+      ra[2 * j] = (rok && k0 + kk < ke) ? __ldg(A + arow_s[row] + acol_r[q][kk]) : 0.0;
+      ra[2 * j + 1] = (rok && k0 + kk + 1 < ke) ? __ldg(A + arow_s[row] + acol_r[q][kk + 1]) : 0.0;
     }
 #pragma unroll
-    for (int r = 0; r < EB; ++r) {
-      const int idx = tid + kThreads * r;
-      const int col = idx % BN, kk = idx / BN;
-      const long long k = k0 + kk;
-      rb[r] = (n0 + col < t.N && k < ke) ? __ldg(B + brow_r[q][kk] + bcol_s[col]) : 0.0;
+    for (int j = 0; j < EB / 2; ++j) {
+      const int cm = warp + 8 * j, cg = cm % (BN / 8), kc = cm / (BN / 8);
+      const int col = cg * 8 + (lane >> 2), kk = kc * 8 + 2 * (lane & 3);
+      const bool cok = n0 + col < t.N;
+      rb[2 * j] = (cok && k0 + kk < ke) ? __ldg(B + brow_r[q][kk] + bcol_s[col]) : 0.0;
+      rb[2 * j + 1] = (cok && k0 + kk + 1 < ke) ? __ldg(B + brow_r[q][kk + 1] + bcol_s[col]) : 0.0;
     }
   };
 
@@ -275,27 +287,31 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
       __syncthreads();
       if (abort_s) break;
     }
+    // the three slices of each element pair as 32-bit words (element k in
+    // the low half), one core-matrix row chunk per lane
 #pragma unroll
-    for (int r = 0; r < EA; ++r) {
-      const int idx = tid + kThreads * r;
-      const int kk = idx % kBK, row = idx / kBK;
-      uint16_t s0, s1, s2;
-      split3(ra[r], s0, s1, s2);
-      const uint32_t off = (uint32_t)((kk >> 4) * T::kPlaneA) + core_off(row, kk & 15);
-      *reinterpret_cast<uint16_t *>(stA + off) = s0;
-      *reinterpret_cast<uint16_t *>(stA + 2 * T::kPlaneA + off) = s1;
-      *reinterpret_cast<uint16_t *>(stA + 4 * T::kPlaneA + off) = s2;
+    for (int j = 0; j < EA / 2; ++j) {
+      const int cm = warp + 8 * j, rg = cm & 15, kc = cm >> 4;
+      uint16_t a0, a1, a2, b0, b1, b2;
+      split3(ra[2 * j], a0, a1, a2);
+      split3(ra[2 * j + 1], b0, b1, b2);
+      const uint32_t off = (uint32_t)((kc >> 1) * T::kPlaneA + rg * 256 + (kc & 1) * 128 + (lane >> 2) * 16 +
+                                      (lane & 3) * 4);
+      *reinterpret_cast<uint32_t *>(stA + off) = (uint32_t)a0 | ((uint32_t)b0 << 16);
+      *reinterpret_cast<uint32_t *>(stA + 2 * T::kPlaneA + off) = (uint32_t)a1 | ((uint32_t)b1 << 16);
+      *reinterpret_cast<uint32_t *>(stA + 4 * T::kPlaneA + off) = (uint32_t)a2 | ((uint32_t)b2 << 16);
     }
 #pragma unroll
-    for (int r = 0; r < EB; ++r) {
-      const int idx = tid + kThreads * r;
-      const int col = idx % BN, kk = idx / BN;
-      uint16_t s0, s1, s2;
-      split3(rb[r], s0, s1, s2);
-      const uint32_t off = (uint32_t)((kk >> 4) * T::kPlaneB) + core_off(col, kk & 15);
-      *reinterpret_cast<uint16_t *>(stB + off) = s0;
-      *reinterpret_cast<uint16_t *>(stB + 2 * T::kPlaneB + off) = s1;
-      *reinterpret_cast<uint16_t *>(stB + 4 * T::kPlaneB + off) = s2;
+    for (int j = 0; j < EB / 2; ++j) {
+      const int cm = warp + 8 * j, cg = cm % (BN / 8), kc = cm / (BN / 8);
+      uint16_t a0, a1, a2, b0, b1, b2;
+      split3(rb[2 * j], a0, a1, a2);
+      split3(rb[2 * j + 1], b0, b1, b2);
+      const uint32_t off = (uint32_t)((kc >> 1) * T::kPlaneB + cg * 256 + (kc & 1) * 128 + (lane >> 2) * 16 +
+                                      (lane & 3) * 4);
+      *reinterpret_cast<uint32_t *>(stB + off) = (uint32_t)a0 | ((uint32_t)b0 << 16);
+      *reinterpret_cast<uint32_t *>(stB + 2 * T::kPlaneB + off) = (uint32_t)a1 | ((uint32_t)b1 << 16);
+      *reinterpret_cast<uint32_t *>(stB + 4 * T::kPlaneB + off) = (uint32_t)a2 | ((uint32_t)b2 << 16);
     }
     // generic-proxy stores become visible to the tensor cores' async proxy
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
