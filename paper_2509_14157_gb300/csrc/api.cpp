@@ -452,6 +452,9 @@ void prepare_hbar(fnocc_ctx *c) {
   Launch L = c->L();
   const int o = c->o, v = c->v;
   const double *tp = c->tpk.d();
+  // the residual accumulators (the T3 one is o^3 v^3 doubles) are dead
+  // while products run: their memory goes to the product's work tensors
+  for (int r = 0; r < 4; ++r) c->Y[r].release();
   dress(c, tp);
   c->t2d.reserve(sizeof(double) * ipow(o, 2) * ipow(v, 2));
   c->t3d.reserve(sizeof(double) * std::max<long long>(1, ipow(o, 3) * ipow(v, 3)));
