@@ -583,18 +583,18 @@ def run_precision_check(args):
 
 # learned-guess check: (electrons, orbitals, FNO threshold, variant) of the
 # evaluation systems, 8 roots each
-GC_SYSTEMS = ((16, 80, 1e-6, "dip"), (12, 60, 1e-4, "dea"))
+GC_SYSTEMS = ((16, 80, 1e-6, "dip"), (12, 60, 1e-5, "dip"), (16, 80, 1e-5, "dea"), (12, 60, 1e-6, "dea"))
 GC_ROOTS = 8
 
 
 def run_guess_check(args):
     """Davidson starts at a matched 1e-6 Eh target: the guess network is
-    trained as in the default run (12 seeded systems with 6 or 8 electrons,
-    outside every timed region), then DIP on 16 electrons / 80 orbitals
-    (FNO 1e-6: 41 kept virtuals) and DEA on 12 electrons / 60 orbitals (FNO
-    1e-4: 17 kept virtuals; DEA's dense R3 work tensor grows as o^2 v^4),
-    8 roots each, BF16x3 products throughout (residual 1e-6), from the
-    diagonal, Koopmans and learned starts. Reports products, iterations,
+    trained on --gc-train seeded systems of 6-10 electrons (the default
+    run's 12; outside every timed region), then DIP and DEA on 12 and 16
+    electrons with 28-41 kept natural virtuals (16 e / 80 orbitals at FNO
+    1e-6 and 1e-5, 12 e / 60 orbitals at 1e-5 and 1e-6), 8 roots each, BF16x3
+    products throughout (residual 1e-6), from the diagonal, Koopmans and
+    learned starts. Reports products, iterations,
     wall-clock seconds and the largest root difference to the Koopmans
     solve; one JSON line per finished solve, then a summary line."""
     import paper_2509_14157_gb300 as pkg
@@ -605,7 +605,8 @@ def run_guess_check(args):
         print(json.dumps(d), flush=True)
 
     t0 = time.perf_counter()
-    X, T, W, info = learned.training_set(learned.seeded_training_systems(12), list(VARIANTS), NROOTS)
+    X, T, W, info = learned.training_set(learned.seeded_training_systems(args.gc_train, electrons=(6, 8, 10)),
+                                         list(VARIANTS), NROOTS)
     net, hist = learned.train_guess_model(X, T, W, epochs=30, batch=2048)
     training = {"seconds": time.perf_counter() - t0, "samples": int(X.shape[0]),
                 "systems": len(set(i[0] for i in info)), "final_loss": float(hist[-1])}
@@ -663,6 +664,8 @@ def main():
     ap.add_argument("--guess-check", action="store_true",
                     help="diagonal vs Koopmans vs learned Davidson start at a matched 1e-6 Eh target, 8 roots of "
                          "DIP (16 electrons) and DEA (12 electrons)")
+    ap.add_argument("--gc-train", type=int, default=12,
+                    help="with --guess-check: number of seeded training systems")
     ap.add_argument("--precision-check", action="store_true",
                     help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
     ap.add_argument("--pc-variants", default=None,

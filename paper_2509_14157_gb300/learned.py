@@ -75,13 +75,17 @@ def train_guess_model(X, T, W, width=256, epochs=30, batch=4096, lr=1e-3, seed=0
     return net, hist
 
 
-def seeded_training_systems(count=24, first_seed=100):
+def seeded_training_systems(count=24, first_seed=100, electrons=(6, 8)):
     """The training workload: small seeded synthetic closed-shell systems
-    (6 or 8 electrons, 10-12 orbitals, 4-6 kept natural virtuals)."""
+    cycling through the given electron counts (6 and 8 by default: 10-12
+    orbitals; 10 electrons: 12-14 orbitals), 4-6 kept natural virtuals (the
+    exact-diagonal target costs one product per element, which bounds the
+    size)."""
     import synth
     out = []
     for s in range(count):
-        ne, n = 6 + 2 * (s % 2), 10 + (s % 3)
+        ne = electrons[s % len(electrons)]
+        n = 10 + (s % 3) + max(0, ne - 8)
         h, eri = synth.hamiltonian(ne, n, seed=first_seed + s)
         out.append(dict(h=h, eri=eri, nocc=ne // 2, nkeep=4 + (s % 3), name="train%d" % s))
     return out
