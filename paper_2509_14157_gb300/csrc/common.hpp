@@ -103,7 +103,7 @@ struct GTask {
   long long cta_begin = 0;           // first CTA of this task in the grid
   long long part_off = 0;            // doubles, [ksplit][M][N]
   long long red_begin = 0;           // first output of this task in the reduction launch
-  int mfast = 0;                     // split-product kernels: tiles ordered with m fastest (consecutive CTAs
+  int mfast = 0;                     // tcgen05 kernel: tiles ordered with m fastest (consecutive CTAs
                                      // share a column tile of B, the larger operand)
 };
 

@@ -322,9 +322,7 @@ __device__ __forceinline__ void ggemm_split(const GTask *__restrict__ tasks, int
   __syncthreads();
   const long long local = cta - t.cta_begin;
   const long long z = local / t.tiles, tile = local - z * t.tiles;
-  const long long tiles_m = t.tiles / t.tiles_n;
-  const long long m0 = (t.mfast ? tile % tiles_m : tile / t.tiles_n) * TBM,
-                  n0 = (t.mfast ? tile / tiles_m : tile % t.tiles_n) * TBN;
+  const long long m0 = (tile / t.tiles_n) * TBM, n0 = (tile % t.tiles_n) * TBN;
   const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
   const bool split = t.ksplit > 1;
   for (int i = tid; i < TBM; i += NT) {
