@@ -443,11 +443,13 @@ def run_sigma_only(args):
     rng = np.random.default_rng(0)
     ctx.set_amplitudes(*[rng.normal(0, 0.01, s) for s in ctx.amp_sizes()])
     ctx.set_precision(args.precision)
+    if args.tile_shape >= 0:
+        ctx.set_tile_shape(args.tile_shape)
     dim = sum(ctx.eom_sizes(args.sigma_only))
     product = ctx.eom_left_sigma_dev if args.left else ctx.eom_sigma_dev
     x = torch.from_numpy(rng.normal(0, 0.1, dim)).cuda()
     s = torch.empty_like(x)
-    for _ in range(2):
+    for _ in range(args.warm):
         product(args.sigma_only, x.data_ptr(), s.data_ptr())
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("sig")
@@ -684,6 +686,11 @@ def main():
                     help="with --precision-check: comma-separated split kinds (default mixed,mixed_tf32)")
     ap.add_argument("--solve-only", default=None, choices=list(VARIANTS) + ["ee"],
                     help="FNO, CCSDT and one Davidson solve of this variant (4 roots) at the workload's size")
+    ap.add_argument("--warm", type=int, default=2,
+                    help="with --sigma-only: warm products before the timed one (tile-shape timing needs one "
+                         "per candidate)")
+    ap.add_argument("--tile-shape", type=int, default=-1,
+                    help="with --sigma-only: force one grouped-GEMM tile shape (fnocc_set_tile_shape)")
     ap.add_argument("--large", action="store_true",
                     help="with --sigma-only / --solve-only: the larger system (16 electrons / 80 orbitals, FNO "
                          "1e-6: 41 kept natural virtuals, o = 16, v = 82), 6 roots; mixed solves run CCSDT mixed")

@@ -229,9 +229,12 @@ int fnocc_tile_shape_count(void);
 int fnocc_tile_shape_first_mixed(void);
 /* Kind of a tile shape: 0 FP64 (CUDA-core FMA tiles), 1 split product on
  * mma.sync (BF16x3, or TF32x3 under FNOCC_MIXED_TF32), 2 BF16x3 split
- * product on the tcgen05 tensor cores with a tensor-memory accumulator
- * (128 x 64, 128 x 128, 128 x 256 tiles; used by FNOCC_MIXED_BF16X3 only:
- * forcing one under FNOCC_MIXED_TF32 leaves TF32 on its mma.sync tiles);
+ * product on the tcgen05 tensor cores with a tensor-memory accumulator,
+ * operands gathered by the kernel (128 x 64, 128 x 128, 128 x 256 tiles),
+ * 3 the same tiles fed by bulk copies from split BF16 panels that one
+ * packing launch per step writes (a panel buffer held by the context, up
+ * to 4 GiB per step); kinds 2 and 3 are used by FNOCC_MIXED_BF16X3 only
+ * (forcing one under FNOCC_MIXED_TF32 leaves TF32 on its mma.sync tiles);
  * -1 for an index out of range. */
 int fnocc_tile_shape_kind(int shape);
 /* Process-wide switch of the tile-shape timing (on by default): when on, an

@@ -463,7 +463,8 @@ class Context:
     PROFILE_PATHS = {0: "k_ggemm", 1: "k_ggemm_split+k_greduce", 2: "k_gemm_small+k_reduce_partials",
                      3: "k_gemv_rows", 4: "k_ggemm_bf16x3", 5: "k_ggemm_bf16x3_split+k_greduce",
                      6: "k_ggemm_tf32x3", 7: "k_ggemm_tf32x3_split+k_greduce",
-                     8: "k_ggemm_tc", 9: "k_ggemm_tc_split+k_greduce"}
+                     8: "k_ggemm_tc", 9: "k_ggemm_tc_split+k_greduce",
+                     10: "k_tc_pack+k_ggemm_tcp", 11: "k_tc_pack+k_ggemm_tcp_split+k_greduce"}
 
     def profile_read(self, path=-1):
         """(device ms, algorithmic flops, launches) of one contraction kernel path

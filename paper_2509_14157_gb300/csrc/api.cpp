@@ -161,7 +161,8 @@ struct fnocc_ctx {
   int default_precision = 0;  // for standalone residual / sigma calls
   int sms = 152;              // multiprocessors of the device (read at creation)
   int force_shape = -1;       // fnocc_set_tile_shape
-  Launch L() { return Launch{stream, &launches, &prof, &partials, precision, sms, force_shape}; }
+  DevBuf panels;               // split BF16 operand panels (tcgen05 panel tiles)
+  Launch L() { return Launch{stream, &launches, &prof, &partials, precision, sms, force_shape, &panels}; }
 
   // active Hamiltonian (spin orbitals, bare)
   bool have_ham = false;
@@ -546,7 +547,8 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = fa
     // everything the captured launches address, and how they were chosen
     std::vector<uintptr_t> key = {(uintptr_t)c->hbar_version, (uintptr_t)L.precision, (uintptr_t)(L.force_shape + 1),
                                   (uintptr_t)c->gx.p, (uintptr_t)c->gs.p, (uintptr_t)c->scratch.p,
-                                  (uintptr_t)c->partials.p, (uintptr_t)ops.f, (uintptr_t)ops.v, (uintptr_t)ops.t2,
+                                  (uintptr_t)c->partials.p, (uintptr_t)c->panels.p, (uintptr_t)ops.f,
+                                  (uintptr_t)ops.v, (uintptr_t)ops.t2,
                                   (uintptr_t)ops.t3};
     for (int k = 0; k < 3; ++k) {
       key.push_back((uintptr_t)c->rd[k].p);

@@ -66,8 +66,9 @@ struct DMap {
 // kernel path: 0 grouped FP64 GEMM, 1 the same with split reduction + ordered
 // sum, 2 small-output kernel + reduction, 3 GEMV, 4 / 5 grouped BF16x3 GEMM
 // (mma.sync) without / with split reduction, 6 / 7 grouped TF32x3 GEMM
-// without / with, 8 / 9 grouped BF16x3 GEMM on tcgen05 without / with.
-constexpr int kGemmPaths = 10;
+// without / with, 8 / 9 grouped BF16x3 GEMM on tcgen05 without / with,
+// 10 / 11 the panel form on tcgen05 (packing launch included) without / with.
+constexpr int kGemmPaths = 12;
 struct GemmProfile {
   bool enabled = false;
   std::vector<cudaEvent_t> pool;           // events, reused
@@ -87,6 +88,7 @@ struct Launch {
   int precision = 0;  // 0 FP64; tensor-core split products (tiled path): 1 BF16 three-slice, 2 TF32 two-slice
   int sms = 152;       // streaming multiprocessors of the device (grid sizing)
   int force_shape = -1;  // >= 0: every grouped step of the matching arithmetic runs this tile shape
+  DevBuf *panels = nullptr;  // split BF16 operand panels of the tcgen05 panel shapes
 };
 
 // One sub-GEMM of a grouped launch: C[crow[m] + ccol[n]] += alpha *
@@ -103,8 +105,12 @@ struct GTask {
   long long cta_begin = 0;           // first CTA of this task in the grid
   long long part_off = 0;            // doubles, [ksplit][M][N]
   long long red_begin = 0;           // first output of this task in the reduction launch
-  int mfast = 0;                     // tcgen05 kernel: tiles ordered with m fastest (consecutive CTAs
+  int mfast = 0;                     // tcgen05 kernels: tiles ordered with m fastest (consecutive CTAs
                                      // share a column tile of B, the larger operand)
+  // tcgen05 panel shapes: split BF16 panels of this task in the panel buffer
+  // (bytes), its first block of the packing launch and its 16-wide K steps
+  int ksteps = 0;
+  long long apanel = 0, bpanel = 0, pk_begin = 0;
 };
 
 // A grouped launch: tasks ordered by cta_begin (device array) plus the list
@@ -114,10 +120,15 @@ constexpr int kGShapeBf16 = kGShapes;  // first BF16 three-slice split shape (mi
 constexpr int kGShapesBf16 = 6;        // BF16x3 tiles 64x64, 32x32, 128x16, 16x128, 64x16, 16x64 (mma.sync)
 constexpr int kGShapeTc = kGShapeBf16 + kGShapesBf16;  // first tcgen05 BF16x3 shape
 constexpr int kGShapesTc = 3;          // tcgen05 BF16x3 tiles 128x64, 128x128, 128x256 (TMEM accumulator)
-constexpr int kGShapesAll = kGShapes + kGShapesBf16 + kGShapesTc;
+constexpr int kGShapeTcp = kGShapeTc + kGShapesTc;  // first tcgen05 panel shape
+constexpr int kGShapesTcp = 3;         // the same tiles fed from split BF16 panels by bulk copies
+constexpr int kGShapesAll = kGShapes + kGShapesBf16 + kGShapesTc + kGShapesTcp;
 // kind of a shape: 0 FP64, 1 split product on mma.sync (BF16x3 or TF32x3),
-// 2 BF16x3 split product on tcgen05
-inline int shape_kind(int shape) { return shape < kGShapeBf16 ? 0 : (shape < kGShapeTc ? 1 : 2); }
+// 2 BF16x3 split product on tcgen05 (operands gathered in the kernel),
+// 3 the same from split BF16 panels packed once per step
+inline int shape_kind(int shape) {
+  return shape < kGShapeBf16 ? 0 : (shape < kGShapeTc ? 1 : (shape < kGShapeTcp ? 2 : 3));
+}
 // tcgen05 shapes (index 0..kGShapesTc-1): tile, dynamic shared memory,
 // launch, and the status word of an expired bounded wait (read and cleared;
 // synchronises the stream)
@@ -126,6 +137,12 @@ size_t tc_smem_bytes(int idx);
 void grouped_gemm_tc(int idx, unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
                      const double *A, const double *B, double *C, double *part);
 int tc_status_take(cudaStream_t s);
+// tcgen05 panel shapes (index 0..kGShapesTcp-1): bytes of one 16-wide K step
+// of the A (128 rows) and B (BN columns) panels, three BF16 slices each;
+// packing launch (one CTA per panel block) and GEMM launch
+void tcp_block_bytes(int idx, long long *abytes, long long *bbytes);
+void grouped_gemm_tcp(int idx, unsigned grid, long long pack_blocks, cudaStream_t s, const GTask *tasks, int ntasks,
+                      double alpha, const double *A, const double *B, double *C, double *part, unsigned char *panels);
 struct GroupedLaunch {
   const GTask *tasks = nullptr;
   int ntasks = 0;
@@ -136,6 +153,7 @@ struct GroupedLaunch {
   int shape = 0;
   double flops = 0;      // algorithmic flops of the launch (profiling)
   double padded = 0;     // multiply-adds including tile padding x 2
+  long long pack_blocks = 0, panel_bytes = 0;  // tcgen05 panel shapes: packing grid and panel buffer
 };
 // rows, columns and K tile of a shape (FP64 and BF16x3 shapes)
 void grouped_shape(int shape, int *tbm, int *tbn, int *tbk);

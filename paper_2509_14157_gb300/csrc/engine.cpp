@@ -636,6 +636,7 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
   const long long kWantCta = 2 * kSms;   // at least two CTAs per SM where the tiles allow
   const long long kFillCta = 4 * kSms;   // FP64 shapes: split at most up to four CTAs per SM
   constexpr long long kPartCap = 1LL << 27;  // doubles of split partials per launch
+  constexpr long long kPanelCap = 1LL << 32;  // bytes of split BF16 panels per launch
   // CTA-times per CTA of a launch of c equal resident CTAs (smaller is better)
   auto wave_cost = [kSms](long long c) { return double((c + kSms - 1) / kSms) / double(std::max<long long>(1, c)); };
   std::vector<GTask> gt;
@@ -664,7 +665,9 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
         gl.shape = shape;
         gl.ntasks = (int)e.tasks.size();
         fix.push_back({&gl, gt.size(), sid.size()});
-        long long cta = 0, part = 0, red = 0;
+        long long cta = 0, part = 0, red = 0, pk_blocks = 0, pbytes = 0;
+        long long pa_bytes = 0, pb_bytes = 0;
+        if (shape_kind(shape) == 3) tcp_block_bytes(shape - kGShapeTcp, &pa_bytes, &pb_bytes);
         double padded = 0, flops = 0;
         for (size_t i = 0; i < e.tasks.size(); ++i) {
           const auto &tr = e.tasks[i];
@@ -692,6 +695,16 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
           g.ksplit = (int)ks;
           g.kchunk = kchunk;
           g.mfast = tr.N > tr.M ? 1 : 0;
+          if (shape_kind(shape) == 3) {
+            // split BF16 panels of the whole K range of the task, 256-byte aligned
+            g.ksteps = (int)((tr.K + 15) / 16);
+            g.apanel = pbytes;
+            pbytes += (tm * g.ksteps * pa_bytes + 255) / 256 * 256;
+            g.bpanel = pbytes;
+            pbytes += (g.tiles_n * g.ksteps * pb_bytes + 255) / 256 * 256;
+            g.pk_begin = pk_blocks;
+            pk_blocks += (tm + g.tiles_n) * g.ksteps;
+          }
           g.cta_begin = cta;
           cta += g.tiles * ks;
           if (ks > 1) {
@@ -712,7 +725,13 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
         gl.part_need = part;
         gl.padded = padded;
         gl.flops = flops;
-        if (shape < kGShapeBf16) {
+        gl.pack_blocks = pk_blocks;
+        gl.panel_bytes = pbytes;
+        if (shape_kind(shape) == 3) {
+          // panel tiles: chosen by timing only (large steps), or when forced;
+          // here ranked by padded work, excluded above the panel memory cap
+          est[shape] = pbytes <= kPanelCap ? padded : 1e300;
+        } else if (shape < kGShapeBf16) {
           est[shape] = padded * wave_cost(cta);
         } else {
           // tensor-core tiles: the cost is staging (gather, convert, split) of
@@ -731,9 +750,13 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
         if (est[shape] < est[bbest]) bbest = shape;
       e.bf16_shape = bbest;
       int tbest = kGShapeTc;
-      for (int shape = kGShapeTc + 1; shape < kGShapesAll; ++shape)
+      for (int shape = kGShapeTc + 1; shape < kGShapeTcp; ++shape)
         if (est[shape] < est[tbest]) tbest = shape;
       e.tc_shape = tbest;
+      int pbest = kGShapeTcp;
+      for (int shape = kGShapeTcp + 1; shape < kGShapesAll; ++shape)
+        if (est[shape] < est[pbest]) pbest = shape;
+      e.tcp_shape = est[pbest] < 1e300 ? pbest : -1;
       // BF16x3: the tcgen05 tile where it stages less per busy SM (large
       // steps time both once, see run)
       e.bf16x3_shape = est[tbest] < est[bbest] ? tbest : bbest;
@@ -859,14 +882,17 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         ExecStep &mm = const_cast<ExecStep &>(s);
         const int fk = L.force_shape >= 0 && L.force_shape < kGShapesAll ? shape_kind(L.force_shape) : 0;
         int shape;
-        if (fk == 1 || (fk == 2 && L.precision == 1))
+        if (fk == 1 || ((fk == 2 || fk == 3) && L.precision == 1))
           shape = L.force_shape;
         else if (L.precision != 1)
           shape = s.bf16_shape;
         else if (mm.tuned_mixed >= 0)
           shape = mm.tuned_mixed;
         else if (autotune && s.gl[s.bf16x3_shape].padded >= 1e8) {
-          tune_launch(L, mm.mixed_tune, {s.bf16_shape, s.tc_shape}, mm.tuned_mixed, s, A, B, C);
+          if (s.tcp_shape >= 0)
+            tune_launch(L, mm.mixed_tune, {s.bf16_shape, s.tc_shape, s.tcp_shape}, mm.tuned_mixed, s, A, B, C);
+          else
+            tune_launch(L, mm.mixed_tune, {s.bf16_shape, s.tc_shape}, mm.tuned_mixed, s, A, B, C);
           continue;
         } else
           shape = s.bf16x3_shape;

@@ -532,7 +532,12 @@ constexpr auto kSplitLaunch = split_launchers(std::make_index_sequence<kGShapesB
 }  // namespace
 
 void grouped_shape(int shape, int *tbm, int *tbn, int *tbk) {
-  if (shape >= kGShapeTc && shape < kGShapesAll) {
+  if (shape >= kGShapeTcp && shape < kGShapesAll) {
+    tc_shape(shape - kGShapeTcp, tbm, tbn, tbk);
+    *tbk = 16;  // one K step of the panels
+    return;
+  }
+  if (shape >= kGShapeTc && shape < kGShapeTcp) {
     tc_shape(shape - kGShapeTc, tbm, tbn, tbk);
     return;
   }
@@ -575,8 +580,14 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     kFp64Launch[g.shape](grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
   else if (g.shape >= kGShapeBf16 && g.shape < kGShapeTc)
     kSplitLaunch[g.shape - kGShapeBf16](L.precision, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
-  else if (g.shape >= kGShapeTc && g.shape < kGShapesAll && L.precision == 1)
+  else if (g.shape >= kGShapeTc && g.shape < kGShapeTcp && L.precision == 1)
     grouped_gemm_tc(g.shape - kGShapeTc, grid, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part);
+  else if (g.shape >= kGShapeTcp && g.shape < kGShapesAll && L.precision == 1) {
+    if (!L.panels) throw std::runtime_error("grouped_gemm: no panel buffer");
+    L.panels->reserve((size_t)std::max<long long>(g.panel_bytes, 256));
+    grouped_gemm_tcp(g.shape - kGShapeTcp, grid, g.pack_blocks, L.stream, g.tasks, g.ntasks, alpha, A, B, C, part,
+                     L.panels->as<unsigned char>());
+  }
   else
     throw std::runtime_error("grouped_gemm: bad shape");
   FNOCC_CUDA(cudaGetLastError());
@@ -590,7 +601,8 @@ void grouped_gemm(const Launch &L, const GroupedLaunch &g, double alpha, const d
     FNOCC_CUDA(cudaEventRecord(pr->pool[e0 + 1], L.stream));
     pr->pairs.push_back({e0, e0 + 1});
     pr->flops.push_back(g.flops);
-    const int base = g.shape < kGShapeBf16 ? 0 : (g.shape >= kGShapeTc ? 8 : (L.precision == 2 ? 6 : 4));
+    const int kind = shape_kind(g.shape);
+    const int base = kind == 0 ? 0 : (kind == 3 ? 10 : (kind == 2 ? 8 : (L.precision == 2 ? 6 : 4)));
     pr->path.push_back(base + (g.nsplit > 0 ? 1 : 0));
     if (pr->pairs.size() >= 4096) pr->fold();
   }

@@ -397,6 +397,267 @@ void launch_tc(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, do
   k_ggemm_tc<BN><<<grid, kThreads, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
 }
 
+
+// ---------------------------------------------------------------------------
+// Panel form: the operands of a step are gathered, truncated and split once
+// per step into BF16 panels laid out as the tensor cores read them, then a
+// GEMM kernel streams the panels into shared memory with bulk copies (TMA,
+// cp.async.bulk) through a ring of stages, one thread issuing the copies,
+// one thread issuing the products, all four warps draining the accumulator.
+// A panel block is one 16-wide K step of one tile: three BF16 slices, each
+// a K-step plane in the canonical K-major layout (core matrices 128 bytes
+// apart along K, 256 bytes along rows), so a stage is two contiguous copies.
+// ---------------------------------------------------------------------------
+
+constexpr int kPackThreads = 256;
+constexpr int kTcpThreads = 128;
+
+template <int BN>
+struct TcpTile {
+  static constexpr int kBlockA = 3 * kBM * 16 * 2;   // bytes of one A panel block (three slices)
+  static constexpr int kBlockB = 3 * BN * 16 * 2;
+  static constexpr int kStage = kBlockA + kBlockB;
+  static constexpr int kStages = BN >= 256 ? 5 : 4;   // 180 KiB / 96 KiB / 72 KiB of stages
+  static constexpr size_t kSmem = (size_t)kStages * kStage + 1024;
+};
+
+__device__ __forceinline__ int find_pack_task(const GTask *tasks, int ntasks, long long blk) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].pk_begin <= blk)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// One CTA per panel block: rows R (128 for A, BN for B) x 16 K of the task,
+// zero outside it, split into the three slice planes of the block.
+template <int BN>
+__global__ void __launch_bounds__(kPackThreads) k_tc_pack(const GTask *__restrict__ tasks, int ntasks,
+                                                          const double *__restrict__ A,
+                                                          const double *__restrict__ B,
+                                                          unsigned char *__restrict__ panels) {
+  __shared__ long long rowoff[BN > kBM ? BN : kBM];
+  __shared__ long long koff[16];
+  __shared__ GTask t;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long blk = blockIdx.x;
+  if (tid == 0) t = tasks[find_pack_task(tasks, ntasks, blk)];
+  __syncthreads();
+  const long long tiles_m = t.tiles / t.tiles_n;
+  long long local = blk - t.pk_begin;
+  const bool isA = local < tiles_m * t.ksteps;
+  if (!isA) local -= tiles_m * t.ksteps;
+  const long long tile = local / t.ksteps, ks = local - tile * t.ksteps;
+  const int R = isA ? kBM : BN;
+  const long long r0 = tile * R, k0 = ks * 16;
+  const long long nrows = isA ? t.M : t.N;
+  for (int i = tid; i < R; i += kPackThreads) {
+    const long long r = r0 + i;
+    rowoff[i] = r < nrows ? (isA ? t.arow[r] : t.bcol[r]) : -1;
+  }
+  if (tid < 16) {
+    const long long k = k0 + tid;
+    koff[tid] = k < t.K ? (isA ? t.acol[k] : t.brow[k]) : -1;
+  }
+  __syncthreads();
+  const double *src = isA ? A : B;
+  unsigned char *dst = panels + (isA ? t.apanel + (tile * t.ksteps + ks) * (long long)TcpTile<BN>::kBlockA
+                                     : t.bpanel + (tile * t.ksteps + ks) * (long long)TcpTile<BN>::kBlockB);
+  const int plane = R * 32;  // bytes of one slice plane
+  // core matrices (R / 8 row groups x 2 k chunks); warp w takes w, w + 8, ...;
+  // lane l: row l / 4 of the core matrix, k pair 2 (l mod 4), 2 (l mod 4) + 1
+  for (int cm = warp; cm < R / 4; cm += kPackThreads / 32) {
+    const int rg = cm >> 1, kc = cm & 1;
+    const int r = rg * 8 + (lane >> 2), kk = kc * 8 + 2 * (lane & 3);
+    double x0 = 0.0, x1 = 0.0;
+    const long long ro = rowoff[r];
+    if (ro >= 0) {
+      if (koff[kk] >= 0) x0 = __ldg(src + ro + koff[kk]);
+      if (koff[kk + 1] >= 0) x1 = __ldg(src + ro + koff[kk + 1]);
+    }
+    uint16_t a0, a1, a2, b0, b1, b2;
+    split3(x0, a0, a1, a2);
+    split3(x1, b0, b1, b2);
+    const int off = rg * 256 + kc * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
+    *reinterpret_cast<uint32_t *>(dst + off) = (uint32_t)a0 | ((uint32_t)b0 << 16);
+    *reinterpret_cast<uint32_t *>(dst + plane + off) = (uint32_t)a1 | ((uint32_t)b1 << 16);
+    *reinterpret_cast<uint32_t *>(dst + 2 * plane + off) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+  }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> shared, completion counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kTcpThreads, 1)
+    k_ggemm_tcp(const GTask *__restrict__ tasks, int ntasks, double alpha, double *__restrict__ C,
+                double *__restrict__ part, const unsigned char *__restrict__ panels) {
+  using T = TcpTile<BN>;
+  constexpr int S = T::kStages;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ long long crow_s[kBM], ccol_s[BN];
+  __shared__ GTask t;
+  __shared__ __align__(8) unsigned long long full[S], empty[S], done;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long cta = blockIdx.x;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+    }
+    mbar_init(smem_u32(&done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    t = tasks[find_task_tc(tasks, ntasks, cta)];
+    abort_s = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+  const long long local = cta - t.cta_begin;
+  const long long z = local / t.tiles, tile = local - z * t.tiles;
+  const long long tiles_m = t.tiles / t.tiles_n;
+  const long long mt = t.mfast ? tile % tiles_m : tile / t.tiles_n, nt = t.mfast ? tile / tiles_m : tile % t.tiles_n;
+  const long long m0 = mt * kBM, n0 = nt * BN;
+  const bool split = t.ksplit > 1;
+  for (int i = tid; i < kBM; i += kTcpThreads) {
+    const long long m = m0 + i;
+    crow_s[i] = (!split && m < t.M) ? t.crow[m] : 0;
+  }
+  for (int i = tid; i < BN; i += kTcpThreads) {
+    const long long n = n0 + i;
+    ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
+  }
+  __syncthreads();
+  // K steps of this CTA (the reduction chunk is a whole number of steps)
+  const long long ks0 = (z * t.kchunk) / 16;
+  const long long ks1 = min((long long)t.ksteps, ((z + 1) * t.kchunk + 15) / 16);
+  const long long nk = ks1 > ks0 ? ks1 - ks0 : 0;
+  const uint32_t sbase = smem_u32(smem);
+  constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+  constexpr int kPi[6] = {0, 0, 1, 0, 1, 2}, kPj[6] = {0, 1, 0, 2, 1, 0};
+  if (tid == 0 && nk > 0) {  // producer: bulk copies of the panel blocks into the ring
+    const unsigned char *pa = panels + t.apanel + (mt * t.ksteps + ks0) * (long long)T::kBlockA;
+    const unsigned char *pb = panels + t.bpanel + (nt * t.ksteps + ks0) * (long long)T::kBlockB;
+    long long it = 0;
+    for (; it < nk; ++it) {
+      const int s = (int)(it % S);
+      if (it >= S && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((it / S) - 1) & 1))) {
+        abort_s = 1;
+        break;
+      }
+      if (*(volatile int *)&abort_s) break;
+      const uint32_t a_dst = sbase + s * T::kStage, b_dst = a_dst + T::kBlockA;
+      mbar_expect_tx(smem_u32(&full[s]), (uint32_t)T::kStage);
+      bulk_g2s(a_dst, pa + it * T::kBlockA, (uint32_t)T::kBlockA, smem_u32(&full[s]));
+      bulk_g2s(b_dst, pb + it * T::kBlockB, (uint32_t)T::kBlockB, smem_u32(&full[s]));
+    }
+    if (it < nk && it > 0) {  // stopped early: copies already issued land before the memory goes
+      const long long last = it - 1;
+      mbar_wait(smem_u32(&full[last % S]), (uint32_t)((last / S) & 1));
+    }
+  } else if (tid == 32 && nk > 0) {  // products
+    long long it = 0;
+    for (; it < nk; ++it) {
+      const int s = (int)(it % S);
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / S) & 1)) || *(volatile int *)&abort_s) {
+        abort_s = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t a0 = sbase + s * T::kStage, b0 = a0 + T::kBlockA;
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const uint64_t ad = smem_desc(a0 + kPi[p] * (kBM * 32), 128, 256);
+        const uint64_t bd = smem_desc(b0 + kPj[p] * (BN * 32), 128, 256);
+        mma_bf16(tmem, ad, bd, idesc, (it > 0 || p > 0) ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&empty[s]));
+    }
+    mma_commit(smem_u32(&done));  // arrives once every product issued above has completed
+  }
+  __syncwarp();
+  bool ok = true;
+  if (nk > 0 && !mbar_wait(smem_u32(&done), 0u)) ok = false;
+  __syncthreads();
+  if (abort_s) ok = false;
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_tc_status, 1);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int rl = warp * 32 + lane;  // accumulator lane = output row
+    const long long m = m0 + rl;
+    const long long MN = t.M * t.N;
+#pragma unroll 1
+    for (int c = 0; c < BN / 16; ++c) {
+      float v[16];
+      if (nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if (m >= t.M) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const long long n = n0 + c * 16 + i;
+        if (n >= t.N) break;
+        if (split)
+          part[t.part_off + z * MN + m * t.N + n] = (double)v[i];
+        else
+          C[crow_s[rl] + ccol_s[c * 16 + i]] += alpha * (double)v[i];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+template <int BN>
+void launch_tcp(unsigned grid, long long pack_blocks, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
+                const double *A, const double *B, double *C, double *part, unsigned char *panels) {
+  constexpr size_t smem = TcpTile<BN>::kSmem;
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  FNOCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw std::runtime_error("grouped_gemm_tcp: device index out of range");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+      FNOCC_CUDA(cudaFuncSetAttribute(k_ggemm_tcp<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done[dev] = true;
+    }
+  }
+  if (pack_blocks > 0x7fffffffLL) throw std::runtime_error("grouped_gemm_tcp: packing grid too large");
+  k_tc_pack<BN><<<(unsigned)pack_blocks, kPackThreads, 0, s>>>(tasks, ntasks, A, B, panels);
+  FNOCC_CUDA(cudaGetLastError());
+  k_ggemm_tcp<BN><<<grid, kTcpThreads, smem, s>>>(tasks, ntasks, alpha, C, part, panels);
+}
+
 }  // namespace
 
 void tc_shape(int idx, int *tbm, int *tbn, int *tbk) {
@@ -423,6 +684,25 @@ void grouped_gemm_tc(int idx, unsigned grid, cudaStream_t s, const GTask *tasks,
     case 1: launch_tc<128>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
     case 2: launch_tc<256>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
     default: throw std::runtime_error("grouped_gemm_tc: bad shape");
+  }
+}
+
+void tcp_block_bytes(int idx, long long *abytes, long long *bbytes) {
+  switch (idx) {
+    case 0: *abytes = TcpTile<64>::kBlockA; *bbytes = TcpTile<64>::kBlockB; return;
+    case 1: *abytes = TcpTile<128>::kBlockA; *bbytes = TcpTile<128>::kBlockB; return;
+    case 2: *abytes = TcpTile<256>::kBlockA; *bbytes = TcpTile<256>::kBlockB; return;
+    default: throw std::runtime_error("tcp_block_bytes: bad shape");
+  }
+}
+
+void grouped_gemm_tcp(int idx, unsigned grid, long long pack_blocks, cudaStream_t s, const GTask *tasks, int ntasks,
+                      double alpha, const double *A, const double *B, double *C, double *part, unsigned char *panels) {
+  switch (idx) {
+    case 0: launch_tcp<64>(grid, pack_blocks, s, tasks, ntasks, alpha, A, B, C, part, panels); break;
+    case 1: launch_tcp<128>(grid, pack_blocks, s, tasks, ntasks, alpha, A, B, C, part, panels); break;
+    case 2: launch_tcp<256>(grid, pack_blocks, s, tasks, ntasks, alpha, A, B, C, part, panels); break;
+    default: throw std::runtime_error("grouped_gemm_tcp: bad shape");
   }
 }
 
