@@ -123,6 +123,7 @@ constexpr int kGShapesTc = 3;          // tcgen05 BF16x3 tiles 128x64, 128x128, 
 constexpr int kGShapeTcp = kGShapeTc + kGShapesTc;  // first tcgen05 panel shape
 constexpr int kGShapesTcp = 3;         // the same tiles fed from split BF16 panels by bulk copies
 constexpr int kGShapesAll = kGShapes + kGShapesBf16 + kGShapesTc + kGShapesTcp;
+constexpr long long kPanelCapBytes = 1LL << 32;  // split BF16 panels of one step at most (panel tiles)
 // kind of a shape: 0 FP64, 1 split product on mma.sync (BF16x3 or TF32x3),
 // 2 BF16x3 split product on tcgen05 (operands gathered in the kernel),
 // 3 the same from split BF16 panels packed once per step

@@ -636,7 +636,7 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
   const long long kWantCta = 2 * kSms;   // at least two CTAs per SM where the tiles allow
   const long long kFillCta = 4 * kSms;   // FP64 shapes: split at most up to four CTAs per SM
   constexpr long long kPartCap = 1LL << 27;  // doubles of split partials per launch
-  constexpr long long kPanelCap = 1LL << 32;  // bytes of split BF16 panels per launch
+  constexpr long long kPanelCap = kPanelCapBytes;
   // CTA-times per CTA of a launch of c equal resident CTAs (smaller is better)
   auto wave_cost = [kSms](long long c) { return double((c + kSms - 1) / kSms) / double(std::max<long long>(1, c)); };
   std::vector<GTask> gt;
@@ -889,10 +889,12 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         else if (mm.tuned_mixed >= 0)
           shape = mm.tuned_mixed;
         else if (autotune && s.gl[s.bf16x3_shape].padded >= 1e8) {
-          if (s.tcp_shape >= 0)
-            tune_launch(L, mm.mixed_tune, {s.bf16_shape, s.tc_shape, s.tcp_shape}, mm.tuned_mixed, s, A, B, C);
-          else
-            tune_launch(L, mm.mixed_tune, {s.bf16_shape, s.tc_shape}, mm.tuned_mixed, s, A, B, C);
+          // the mma.sync and gathering tcgen05 tiles of least staged volume,
+          // and every panel tile within the panel memory cap
+          std::vector<int> cand = {s.bf16_shape, s.tc_shape};
+          for (int k = kGShapeTcp; k < kGShapesAll; ++k)
+            if (s.gl[k].panel_bytes <= kPanelCapBytes) cand.push_back(k);
+          tune_launch(L, mm.mixed_tune, cand, mm.tuned_mixed, s, A, B, C);
           continue;
         } else
           shape = s.bf16x3_shape;
@@ -960,7 +962,7 @@ bool ExecEquation::tuning_pending(const Launch &L) const {
   return false;
 }
 
-void ExecEquation::tune_launch(const Launch &L, ExecStep::Trial &tr, std::initializer_list<int> cand, int &tuned,
+void ExecEquation::tune_launch(const Launch &L, ExecStep::Trial &tr, const std::vector<int> &cand, int &tuned,
                                const ExecStep &s, const double *A, const double *B, double *C) {
   if (tr.pending < 0) {  // first use: an event pair of its own
     tr.pending = tune_count_++;
@@ -982,7 +984,7 @@ void ExecEquation::tune_launch(const Launch &L, ExecStep::Trial &tr, std::initia
   for (int k : cand)
     if (next < 0 && tr.ms[k] == 0) next = k;
   if (next < 0) {
-    int best = *cand.begin();
+    int best = cand.front();
     for (int k : cand)
       if (tr.ms[k] < tr.ms[best]) best = k;
     tuned = best;

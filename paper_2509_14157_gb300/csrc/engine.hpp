@@ -122,7 +122,7 @@ class ExecEquation {
   // previous run, then launches the next untimed candidate between an event
   // pair of the step's own (read on a later run), or, once all are timed,
   // keeps the fastest in `tuned` and launches it
-  void tune_launch(const Launch &L, ExecStep::Trial &tr, std::initializer_list<int> cand, int &tuned,
+  void tune_launch(const Launch &L, ExecStep::Trial &tr, const std::vector<int> &cand, int &tuned,
                    const ExecStep &s, const double *A, const double *B, double *C);
   int nh_, np_, o_, v_;
   int sms_ = 152;
