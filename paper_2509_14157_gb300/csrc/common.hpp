@@ -119,7 +119,8 @@ constexpr int kGShapes = 19;           // FP64 tile shapes (14 with a K tile of 
 constexpr int kGShapeBf16 = kGShapes;  // first BF16 three-slice split shape (mixed precision)
 constexpr int kGShapesBf16 = 6;        // BF16x3 tiles 64x64, 32x32, 128x16, 16x128, 64x16, 16x64 (mma.sync)
 constexpr int kGShapeTc = kGShapeBf16 + kGShapesBf16;  // first tcgen05 BF16x3 shape
-constexpr int kGShapesTc = 3;          // tcgen05 BF16x3 tiles 128x64, 128x128, 128x256 (TMEM accumulator)
+constexpr int kGShapesTc = 5;          // tcgen05 BF16x3 tiles 128x64, 128x128, 128x256, and 32x128, 64x128
+                                       // computed transposed (TMEM accumulator)
 constexpr int kGShapeTcp = kGShapeTc + kGShapesTc;  // first tcgen05 panel shape
 constexpr int kGShapesTcp = 3;         // the same tiles fed from split BF16 panels by bulk copies
 constexpr int kGShapesAll = kGShapes + kGShapesBf16 + kGShapesTc + kGShapesTcp;

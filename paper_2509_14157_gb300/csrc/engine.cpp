@@ -749,10 +749,15 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
       for (int shape = kGShapeBf16 + 1; shape < kGShapeTc; ++shape)
         if (est[shape] < est[bbest]) bbest = shape;
       e.bf16_shape = bbest;
-      int tbest = kGShapeTc;
-      for (int shape = kGShapeTc + 1; shape < kGShapeTcp; ++shape)
+      // gathering tcgen05 tiles: the best with the rows of A on the
+      // accumulator lanes (the first three) and the best transposed one
+      int tbest = kGShapeTc, tbest_t = kGShapeTc + 3;
+      for (int shape = kGShapeTc + 1; shape < kGShapeTc + 3; ++shape)
         if (est[shape] < est[tbest]) tbest = shape;
-      e.tc_shape = tbest;
+      for (int shape = kGShapeTc + 4; shape < kGShapeTcp; ++shape)
+        if (est[shape] < est[tbest_t]) tbest_t = shape;
+      e.tc_shape = est[tbest_t] < est[tbest] ? tbest_t : tbest;
+      e.tc_shape_alt = est[tbest_t] < est[tbest] ? tbest : tbest_t;
       int pbest = kGShapeTcp;
       for (int shape = kGShapeTcp + 1; shape < kGShapesAll; ++shape)
         if (est[shape] < est[pbest]) pbest = shape;
@@ -891,7 +896,7 @@ void ExecEquation::run(const Launch &L, const Operands &ops, double *Y, long lon
         else if (autotune && s.gl[s.bf16x3_shape].padded >= 1e8) {
           // the mma.sync and gathering tcgen05 tiles of least staged volume,
           // and every panel tile within the panel memory cap
-          std::vector<int> cand = {s.bf16_shape, s.tc_shape};
+          std::vector<int> cand = {s.bf16_shape, s.tc_shape, s.tc_shape_alt};
           for (int k = kGShapeTcp; k < kGShapesAll; ++k)
             if (s.gl[k].panel_bytes <= kPanelCapBytes) cand.push_back(k);
           tune_launch(L, mm.mixed_tune, cand, mm.tuned_mixed, s, A, B, C);

@@ -52,6 +52,7 @@ struct ExecStep {
   int default_shape = 0;                          // least padded work per busy SM
   int bf16_shape = kGShapeBf16;                   // mma.sync split tile with the least staged work per busy SM
   int tc_shape = kGShapeTc;                       // tcgen05 BF16x3 tile with the least staged work per busy SM
+  int tc_shape_alt = kGShapeTc;                   // the best one of the other orientation (lanes on B's columns)
   int tcp_shape = -1;                             // tcgen05 panel tile with the least padded work (-1: panels too large)
   int bf16x3_shape = kGShapeBf16;                 // BF16x3 default: the better of the two estimates
   // BF16x3 steps above 1e8 padded flops: the mma.sync and the tcgen05 tile

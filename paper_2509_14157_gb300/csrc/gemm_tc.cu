@@ -173,10 +173,15 @@ struct TcTile {
   static constexpr int EB = BN * kBK / kThreads;
   static_assert(EA % 2 == 0 && EB % 2 == 0 && kBM * kBK / 64 == 8 * (EA / 2) && BN * kBK / 64 == 8 * (EB / 2),
                 "every core matrix of a stage taken by exactly one warp");
-  static_assert(BN == 64 || BN == 128 || BN == 256, "accumulator width");
+  static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "accumulator width");
 };
 
-template <int BN>
+// TR = false: the accumulator lanes (the tcgen05 M dimension) run over the
+// 128 rows of an A tile and its columns over BN columns of B; TR = true (for
+// steps with few rows): lanes over 128 columns of B and columns over BN
+// rows of A, i.e. the tile of C is computed transposed in tensor memory.
+// X is the operand on the lanes, Y the one on the columns.
+template <int BN, bool TR>
 __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
     k_ggemm_tc(const GTask *__restrict__ tasks, int ntasks, double alpha, const double *__restrict__ A,
                const double *__restrict__ B, double *__restrict__ C, double *__restrict__ part) {
@@ -184,10 +189,10 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
   constexpr int EA = T::EA, EB = T::EB;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ long long arow_s[kBM], crow_s[kBM], bcol_s[BN], ccol_s[BN];
+  __shared__ long long xrow_s[kBM], cx_s[kBM], yrow_s[BN], cy_s[BN];
   // reduction-index offsets of the K tiles kt, kt + 1, kt + 2 (a ring): read
   // one stage ahead, so that no operand gather waits on a table load
-  __shared__ long long acol_r[3][kBK], brow_r[3][kBK];
+  __shared__ long long xk_r[3][kBK], yk_r[3][kBK];
   __shared__ GTask t;
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ uint32_t tmem_base_s;
@@ -217,28 +222,35 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
   // tile order: n fastest (consecutive CTAs share the A row tile), or m
   // fastest where B is the larger operand (they share its column tile in L2)
   const long long tiles_m = t.tiles / t.tiles_n;
-  const long long m0 = (t.mfast ? tile % tiles_m : tile / t.tiles_n) * kBM,
-                  n0 = (t.mfast ? tile / tiles_m : tile % t.tiles_n) * BN;
+  constexpr int TBM = TR ? BN : kBM, TBN = TR ? kBM : BN;
+  const long long m0 = (t.mfast ? tile % tiles_m : tile / t.tiles_n) * TBM,
+                  n0 = (t.mfast ? tile / tiles_m : tile % t.tiles_n) * TBN;
+  const long long x0 = TR ? n0 : m0, y0 = TR ? m0 : n0;  // first X and Y index of the tile
+  const long long XN = TR ? t.N : t.M, YN = TR ? t.M : t.N;
+  const long long *xrow = TR ? t.bcol : t.arow, *yrow = TR ? t.arow : t.bcol;
+  const long long *cxt = TR ? t.ccol : t.crow, *cyt = TR ? t.crow : t.ccol;
+  const long long *xkt = TR ? t.brow : t.acol, *ykt = TR ? t.acol : t.brow;
+  const double *X = TR ? B : A, *Y = TR ? A : B;
   const long long kb = z * t.kchunk, ke = min(t.K, kb + t.kchunk);
   const bool split = t.ksplit > 1;
   for (int i = tid; i < kBM; i += kThreads) {
-    const long long m = m0 + i;
-    arow_s[i] = m < t.M ? t.arow[m] : 0;
-    crow_s[i] = (!split && m < t.M) ? t.crow[m] : 0;
+    const long long x = x0 + i;
+    xrow_s[i] = x < XN ? xrow[x] : 0;
+    cx_s[i] = (!split && x < XN) ? cxt[x] : 0;
   }
   for (int i = tid; i < BN; i += kThreads) {
-    const long long n = n0 + i;
-    bcol_s[i] = n < t.N ? t.bcol[n] : 0;
-    ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
+    const long long y = y0 + i;
+    yrow_s[i] = y < YN ? yrow[y] : 0;
+    cy_s[i] = (!split && y < YN) ? cyt[y] : 0;
   }
   // table entries of the K tile at k0 into ring slot q (threads 0 .. 2 kBK - 1)
   auto load_tables = [&](long long k0, int q) {
     if (tid < kBK) {
       const long long k = k0 + tid;
-      acol_r[q][tid] = k < ke ? __ldg(t.acol + k) : 0;
+      xk_r[q][tid] = k < ke ? __ldg(xkt + k) : 0;
     } else if (tid < 2 * kBK) {
       const long long k = k0 + tid - kBK;
-      brow_r[q][tid - kBK] = k < ke ? __ldg(t.brow + k) : 0;
+      yk_r[q][tid - kBK] = k < ke ? __ldg(ykt + k) : 0;
     }
   };
   load_tables(kb, 0);
@@ -258,17 +270,17 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
     for (int j = 0; j < EA / 2; ++j) {
       const int cm = warp + 8 * j, rg = cm & 15, kc = cm >> 4;
       const int row = rg * 8 + (lane >> 2), kk = kc * 8 + 2 * (lane & 3);
-      const bool rok = m0 + row < t.M;
-      ra[2 * j] = (rok && k0 + kk < ke) ? __ldg(A + arow_s[row] + acol_r[q][kk]) : 0.0;
-      ra[2 * j + 1] = (rok && k0 + kk + 1 < ke) ? __ldg(A + arow_s[row] + acol_r[q][kk + 1]) : 0.0;
+      const bool rok = x0 + row < XN;
+      ra[2 * j] = (rok && k0 + kk < ke) ? __ldg(X + xrow_s[row] + xk_r[q][kk]) : 0.0;
+      ra[2 * j + 1] = (rok && k0 + kk + 1 < ke) ? __ldg(X + xrow_s[row] + xk_r[q][kk + 1]) : 0.0;
     }
 #pragma unroll
     for (int j = 0; j < EB / 2; ++j) {
       const int cm = warp + 8 * j, cg = cm % (BN / 8), kc = cm / (BN / 8);
       const int col = cg * 8 + (lane >> 2), kk = kc * 8 + 2 * (lane & 3);
-      const bool cok = n0 + col < t.N;
-      rb[2 * j] = (cok && k0 + kk < ke) ? __ldg(B + brow_r[q][kk] + bcol_s[col]) : 0.0;
-      rb[2 * j + 1] = (cok && k0 + kk + 1 < ke) ? __ldg(B + brow_r[q][kk + 1] + bcol_s[col]) : 0.0;
+      const bool cok = y0 + col < YN;
+      rb[2 * j] = (cok && k0 + kk < ke) ? __ldg(Y + yk_r[q][kk] + yrow_s[col]) : 0.0;
+      rb[2 * j + 1] = (cok && k0 + kk + 1 < ke) ? __ldg(Y + yk_r[q][kk + 1] + yrow_s[col]) : 0.0;
     }
   };
 
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int q = warp & 3, half = warp >> 2;
     const int rl = q * 32 + lane;
-    const long long m = m0 + rl;
+    const long long x = x0 + rl;
     const long long MN = t.M * t.N;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
@@ -360,15 +372,15 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
       }
-      if (m >= t.M) continue;
+      if (x >= XN) continue;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const long long n = n0 + cl0 + i;
-        if (n >= t.N) break;
+        const long long y = y0 + cl0 + i;
+        if (y >= YN) break;
         if (split)
-          part[t.part_off + z * MN + m * t.N + n] = (double)v[i];
+          part[t.part_off + z * MN + (TR ? y * t.N + x : x * t.N + y)] = (double)v[i];
         else
-          C[crow_s[rl] + ccol_s[cl0 + i]] += alpha * (double)v[i];
+          C[cx_s[rl] + cy_s[cl0 + i]] += alpha * (double)v[i];
       }
     }
   }
@@ -378,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, BN <= 128 ? 2 : 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
 }
 
-template <int BN>
+template <int BN, bool TR>
 void launch_tc(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha, const double *A,
                const double *B, double *C, double *part) {
   constexpr size_t smem = TcTile<BN>::kSmem;
@@ -390,11 +402,11 @@ void launch_tc(unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, do
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!done[dev]) {
-      FNOCC_CUDA(cudaFuncSetAttribute(k_ggemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FNOCC_CUDA(cudaFuncSetAttribute(k_ggemm_tc<BN, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       done[dev] = true;
     }
   }
-  k_ggemm_tc<BN><<<grid, kThreads, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
+  k_ggemm_tc<BN, TR><<<grid, kThreads, smem, s>>>(tasks, ntasks, alpha, A, B, C, part);
 }
 
 
@@ -660,11 +672,14 @@ void launch_tcp(unsigned grid, long long pack_blocks, cudaStream_t s, const GTas
 
 }  // namespace
 
+// tiles (rows of C x columns of C) of the gathering shapes: 128 x 64,
+// 128 x 128, 128 x 256, and the transposed 32 x 128, 64 x 128
 void tc_shape(int idx, int *tbm, int *tbn, int *tbk) {
-  static const int bn[kGShapesTc] = {64, 128, 256};
+  static const int tm[kGShapesTc] = {kBM, kBM, kBM, 32, 64};
+  static const int tn[kGShapesTc] = {64, 128, 256, kBM, kBM};
   if (idx < 0 || idx >= kGShapesTc) throw std::runtime_error("tc_shape: bad shape");
-  *tbm = kBM;
-  *tbn = bn[idx];
+  *tbm = tm[idx];
+  *tbn = tn[idx];
   *tbk = kBK;
 }
 
@@ -673,6 +688,8 @@ size_t tc_smem_bytes(int idx) {
     case 0: return TcTile<64>::kSmem;
     case 1: return TcTile<128>::kSmem;
     case 2: return TcTile<256>::kSmem;
+    case 3: return TcTile<32>::kSmem;
+    case 4: return TcTile<64>::kSmem;
     default: throw std::runtime_error("tc_smem_bytes: bad shape");
   }
 }
@@ -680,9 +697,11 @@ size_t tc_smem_bytes(int idx) {
 void grouped_gemm_tc(int idx, unsigned grid, cudaStream_t s, const GTask *tasks, int ntasks, double alpha,
                      const double *A, const double *B, double *C, double *part) {
   switch (idx) {
-    case 0: launch_tc<64>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
-    case 1: launch_tc<128>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
-    case 2: launch_tc<256>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    case 0: launch_tc<64, false>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    case 1: launch_tc<128, false>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    case 2: launch_tc<256, false>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    case 3: launch_tc<32, true>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
+    case 4: launch_tc<64, true>(grid, s, tasks, ntasks, alpha, A, B, C, part); break;
     default: throw std::runtime_error("grouped_gemm_tc: bad shape");
   }
 }
