@@ -228,3 +228,33 @@ def test_timing_modes_run(fake_gpu, monkeypatch, capsys, argv, key):
     assert key in line
     if key in ("sigma_only", "solve_only"):
         assert line[key] == argv[1] and line["left"] == ("--left" in argv) and line["seconds"] >= 0
+
+
+def test_oracle_sample_covers_every_block_and_scales(monkeypatch):
+    """The CPU baseline's sample: every Wick-term block of the residual and
+    of every product has at least one sampled term (all of them at stride
+    1), and the estimate scales each block's measured time by its term
+    count and each residual / product by the given call counts."""
+    monkeypatch.setattr(bench, "NE", 4)
+    monkeypatch.setattr(bench, "NORB", 6)
+    smp = bench.OracleSample(1e-4, stride=1)
+    blocks = {it[1] for it in smp.items if it[0] == "terms"}
+    assert blocks == set(smp.blocks)
+    for kind, key, pick in smp.items:
+        if kind == "terms":
+            assert list(pick) == list(range(len(smp.blocks[key][0])))
+    smp = bench.OracleSample(1e-4, stride=4)
+    # injected times: every sampled block 2 s for m sampled terms (allocation 0)
+    smp.times = {}
+    for kind, key, pick in smp.items:
+        if kind == "terms":
+            smp.times[(kind, key)] = (0.0, 2.0, len(pick), len(smp.blocks[key][0]))
+        else:
+            smp.times[(kind, key)] = 0.5
+    smp.t_fno = 1.0
+    part_s, per_solve = smp.estimate({"cc_iters": 3, "sigma": {v: 10 for v in bench.VARIANTS}})
+    res = sum(2.0 * len(smp.blocks[k][0]) / len([p for it in smp.items if it[1] == k for p in it[2]])
+              for k in smp.blocks if k[0] == "residual") + 0.5
+    assert abs(part_s["residual"] - res) < 1e-9
+    step = 1.0 + 3 * part_s["residual"] + sum(10 * part_s[v] for v in bench.VARIANTS)
+    assert abs(per_solve - step / len(bench.VARIANTS)) < 1e-9
