@@ -55,13 +55,14 @@ class FakeContext:
     def fno_truncate_dev(self, *a, **k):
         return {"nkept": 15}
 
-    def fno_truncate(self, *a, **k):
-        return {"nkept": 15}
+    def fno_truncate(self, h, eri, nocc, threshold, **k):
+        return {"nkept": 15, "kept_fraction": threshold if 0 < threshold < 1 else 1.0}
 
     def ccsdt_solve(self, precision="fp64", **k):
         self.flops += 2e10
         self.launches += 100
-        return dict(converged=True, iters=21, seconds=0.5, seconds_per_iter=0.02, e_corr=-0.3, iters_mixed=0)
+        return dict(converged=True, iters=21, seconds=0.5, seconds_per_iter=0.02, e_corr=-0.3, e_tot=-21.3,
+                    iters_mixed=0)
 
     def eom_solve(self, var, nroots, **kw):
         self.flops += 1e9
@@ -218,6 +219,7 @@ def test_reference_line_carries_the_contract(fake_gpu, monkeypatch, capsys):
                                       (["--solve-only", "ip", "--precision", "mixed_tf32"], "solve_only"),
                                       (["--precision-check"], "mode"),
                                       (["--guess-check"], "mode"),
+                                      (["--xfno-check"], "mode"),
                                       (["--batch"], "metric"),
                                       (["--batch", "--batch-large"], "metric")])
 def test_timing_modes_run(fake_gpu, monkeypatch, capsys, argv, key):
