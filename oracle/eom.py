@@ -202,7 +202,9 @@ def davidson(apply, diag, mask, nroots, tol_res=1e-8, tol_e=1e-10, max_sub=None,
             xs.append(x)
             res.append(rv)
             norms.append(np.linalg.norm(rv))
-        done = [norms[r] < tol_res and theta_old is not None and abs(theta[r] - theta_old[r]) < tol_e
+        # |d omega| against the nearest previous Ritz value (near-degenerate
+        # roots may swap rank between iterations)
+        done = [norms[r] < tol_res and theta_old is not None and np.min(np.abs(theta[r] - theta_old)) < tol_e
                 for r in range(nroots)]
         if all(done):
             return dict(omega=theta, vectors=np.array(xs), iters=it, res=np.array(norms),

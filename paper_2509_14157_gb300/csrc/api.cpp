@@ -1715,7 +1715,11 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       std::vector<bool> done(nr);
       bool all = true;
       for (int r = 0; r < nr; ++r) {
-        done[r] = may_stop && norms[r] < o.tol_res && have_old && std::fabs(theta[r] - theta_old[r]) < o.tol_e;
+        // |d omega| against the nearest Ritz value of the previous iteration:
+        // near-degenerate roots that swap rank do not restart the test
+        double dth = INFINITY;
+        for (int q = 0; q < nr; ++q) dth = std::min(dth, std::fabs(theta[r] - theta_old[q]));
+        done[r] = may_stop && norms[r] < o.tol_res && have_old && dth < o.tol_e;
         all = all && done[r];
       }
       if (all) {
