@@ -209,6 +209,12 @@ struct fnocc_ctx {
   size_t last_dim = 0;
   DevBuf eom_vecs;
   double flops_cc_last = 0, flops_sigma_last = 0;
+  // side streams of a product's output components 1 and 2 (component 0 runs
+  // on the context stream), each with its own scratch, split partials and
+  // panels; fork and join events
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  DevBuf bscratch[2], bpartials[2], bpanels[2];
   // captured product launch sequences [variant][left][precision] and their
   // fixed input / output buffers
   bool use_graphs = true;
@@ -482,16 +488,38 @@ void sigma_launches(fnocc_ctx *c, int var, const double *x, double *s, bool left
     unpack(c, L, x + off, kEom[var][k][0], kEom[var][k][1], c->rd[k].d());
     off += sz[k];
   }
+  // the three output components are independent: components 1 and 2 run on
+  // the side streams beside component 0 (each with its own scratch), so that
+  // the small launches of different components share the GPU; per-launch
+  // profiling keeps them on the context stream (isolated kernel times)
+  const bool fork = !c->prof.enabled;
+  if (fork) {
+    FNOCC_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    for (auto sd : c->side) FNOCC_CUDA(cudaStreamWaitEvent(sd, c->ev_fork, 0));
+  }
   off = 0;
   for (int oc = 0; oc < 3; ++oc) {
     int nh = kEom[var][oc][0], np = kEom[var][oc][1];
     long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
-    FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, c->stream));
-    for (int ic = 0; ic < 3; ++ic) eqs[oc][ic]->run(L, ops, c->sy[oc].d(), dn, c->scratch, c->hbar_version);
-    antisym_pack(L, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
+    Launch Lb = L;
+    DevBuf *scr = &c->scratch;
+    if (fork && oc > 0) {
+      Lb.stream = c->side[oc - 1];
+      Lb.partials = &c->bpartials[oc - 1];
+      Lb.panels = &c->bpanels[oc - 1];
+      scr = &c->bscratch[oc - 1];
+    }
+    FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, Lb.stream));
+    for (int ic = 0; ic < 3; ++ic) eqs[oc][ic]->run(Lb, ops, c->sy[oc].d(), dn, *scr, c->hbar_version);
+    antisym_pack(Lb, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
                  c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
     off += sz[oc];
   }
+  if (fork)
+    for (int i = 0; i < 2; ++i) {
+      FNOCC_CUDA(cudaEventRecord(c->ev_join[i], c->side[i]));
+      FNOCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join[i], 0));
+    }
 }
 
 // s = (H-bar x)_c, or with left = true the left product s = x^T H-bar.
@@ -553,6 +581,11 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = fa
     for (int k = 0; k < 3; ++k) {
       key.push_back((uintptr_t)c->rd[k].p);
       key.push_back((uintptr_t)c->sy[k].p);
+    }
+    for (int k = 0; k < 2; ++k) {
+      key.push_back((uintptr_t)c->bscratch[k].p);
+      key.push_back((uintptr_t)c->bpartials[k].p);
+      key.push_back((uintptr_t)c->bpanels[k].p);
     }
     for (int oc = 0; oc < 3; ++oc)
       for (int ic = 0; ic < 3; ++ic) key.push_back((uintptr_t)eqs[oc][ic]->cache_ptr());
@@ -765,10 +798,15 @@ fnocc_status fnocc_create(fnocc_ctx **out, int device, void *cuda_stream) {
       FNOCC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
       c->own_stream = true;
     }
+    for (int i = 0; i < 2; ++i) {
+      FNOCC_CUDA(cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
+      FNOCC_CUDA(cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming));
+    }
+    FNOCC_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     return FNOCC_OK;
   });
   if (st != FNOCC_OK) {
-    delete c;
+    fnocc_destroy(c);
     return st;
   }
   *out = c;
@@ -779,10 +817,17 @@ void fnocc_destroy(fnocc_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto sd : c->side)
+    if (sd) cudaStreamSynchronize(sd);
   bool own = c->own_stream;
-  cudaStream_t s = c->stream;
+  cudaStream_t s = c->stream, side[2] = {c->side[0], c->side[1]};
   for (auto ev : c->prof.pool) cudaEventDestroy(ev);
+  for (auto ev : c->ev_join)
+    if (ev) cudaEventDestroy(ev);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
+  for (auto sd : side)
+    if (sd) cudaStreamDestroy(sd);
   if (own && s) cudaStreamDestroy(s);
 }
 

@@ -108,3 +108,21 @@ def test_solve_with_and_without_replay(pkg):
         roots.append(r["omegas"])
         c.close()
     assert np.max(np.abs(roots[0] - roots[1])) < 1e-12
+
+
+@pytest.mark.parametrize("variant", ["ip", "dea"])
+def test_side_streams_match_serial(ctx, variant):
+    """The three output components of a product run on three streams
+    (components 1 and 2 beside 0); with per-launch profiling they run one
+    after another on the context stream. Both orders give the same bits."""
+    o, v, _ = ctx.dims()
+    ctx.set_precision("fp64")
+    ctx.set_graphs(False)
+    x = vector(variant, o, v, 740)
+    ctx.eom_sigma(variant, x)
+    forked = ctx.eom_sigma(variant, x)
+    ctx.profile(True)
+    serial = ctx.eom_sigma(variant, x)
+    ctx.profile(False)
+    ctx.set_graphs(True)
+    assert np.array_equal(forked, serial)
