@@ -1740,7 +1740,12 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       if (c->precision != FNOCC_FP64 && o.switch_tol > 0) {
         double mx = 0;
         for (double x : norms) mx = std::max(mx, x);
-        if (mx < o.switch_tol) {
+        // refinement once every residual is below switch_tol, or after a
+        // quarter of the iteration budget in split arithmetic (the roots
+        // selected by principal weight can keep changing when satellites sit
+        // near the weight threshold, and the split products' rounding is of
+        // the size that moves them across it)
+        if (mx < o.switch_tol || it >= std::max(8, o.maxiter / 4)) {
           // refinement: FP64 from here on; rebuild the subspace from the Ritz
           // vectors with FP64 products (cached H-bar pieces recomputed too)
           c->precision = FNOCC_FP64;
