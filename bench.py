@@ -521,6 +521,7 @@ def run_batch(args):
                       "unit": "s", "higher_is_better": False, "sequential_value": t_seq / max(solves, 1),
                       "speedup": t_seq / t_bat if t_bat > 0 else None, "systems": len(systems),
                       "converged_systems": len(ok), "statuses": [i["status"] for i in info4],
+                      "messages": {str(s): i["message"] for s, i in enumerate(info4) if i["status"] != 0},
                       "workers": 4, "max_root_diff_eh": diff,
                       "config": ({"workload": "32 seeded systems, 6-14 electrons, 20-40 kept natural virtuals "
                                               "(nkeep), IP and EA x 4 roots",

@@ -356,6 +356,7 @@ typedef struct {
   double e_rhf, e_ccsdt;
   int ccsdt_iters, sigma_calls;
   double seconds;        /* wall time of this system's pipeline */
+  char message[128];     /* NUL-terminated text of the first failing call ("" when it succeeded) */
 } fnocc_system_result;
 
 fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems, int nvariants,

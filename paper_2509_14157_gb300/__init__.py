@@ -74,7 +74,7 @@ class System(ctypes.Structure):
 class SystemResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("nkept", ctypes.c_int), ("e_rhf", ctypes.c_double),
                 ("e_ccsdt", ctypes.c_double), ("ccsdt_iters", ctypes.c_int), ("sigma_calls", ctypes.c_int),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("message", ctypes.c_char * 128)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -212,7 +212,8 @@ def batch_solve(systems, variants, nroots, device=0, nworkers=4, cc_tol_res=1e-1
     if st == -1:
         raise FnoccError(st, "invalid batch request")
     out = [dict(status=r.status, nkept=r.nkept, e_rhf=r.e_rhf, e_ccsdt=r.e_ccsdt, ccsdt_iters=r.ccsdt_iters,
-                sigma_calls=r.sigma_calls, seconds=r.seconds) for r in res]
+                sigma_calls=r.sigma_calls, seconds=r.seconds, message=r.message.decode(errors="replace"))
+           for r in res]
     return om, out
 
 

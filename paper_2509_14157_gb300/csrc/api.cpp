@@ -11,6 +11,7 @@
 #include <thread>
 #include <cmath>
 #include <complex>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -2016,11 +2017,16 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
       fno_options fo{FNOCC_CRIT_ABS, sys.nkeep, 200, 1e-12, 1e-10};
       fno_info fi{};
       ccsdt_info ci{};
+      std::string msg;
       fnocc_status worst = fno_truncate(c, sys.h, sys.eri, sys.n, sys.nocc, sys.occ_threshold, &fo, &fi, nullptr);
+      if (worst != FNOCC_OK) msg = c->err;
       int sig = 0;
       if (worst >= 0) {
         fnocc_status cs = ccsdt_solve(c, cc_opt, &ci);
-        if (cs != FNOCC_OK) worst = cs;
+        if (cs != FNOCC_OK) {
+          worst = cs;
+          if (msg.empty()) msg = cs == FNOCC_NOT_CONVERGED ? "CCSDT did not converge" : c->err;
+        }
         if (cs >= 0)
           for (int k = 0; k < nvariants; ++k) {
             eom_info ei{};
@@ -2028,6 +2034,9 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
             fnocc_status es = eom_ccsdt_solve(c, variants[k], nroots, FNOCC_GUESS_KOOPMANS, eom_opt, en.data(),
                                               omegas + ((size_t)s * nvariants + k) * nroots, &ei);
             sig += ei.sigma_calls;
+            if (es != FNOCC_OK && msg.empty())
+              msg = es == FNOCC_NOT_CONVERGED ? "EOM variant " + std::to_string(variants[k]) + " did not converge"
+                                              : c->err;
             if (es < 0 || (es != FNOCC_OK && worst >= 0)) worst = es;
           }
       }
@@ -2040,6 +2049,7 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
         results[s].ccsdt_iters = ci.iters;
         results[s].sigma_calls = sig;
         results[s].seconds = timer.s();
+        std::snprintf(results[s].message, sizeof(results[s].message), "%s", msg.c_str());
       }
     }
     fnocc_destroy(c);
@@ -2055,7 +2065,10 @@ fnocc_status fnocc_batch_solve(int device, int nsys, const fnocc_system *systems
   for (int s = 0; s < nsys; ++s)
     if (!attempted[s]) {
       st[s] = create_status.load() != FNOCC_OK ? (fnocc_status)create_status.load() : FNOCC_E_CUDA;
-      if (results) results[s] = fnocc_system_result{st[s], 0, 0.0, 0.0, 0, 0, 0.0};
+      if (results) {
+        results[s] = fnocc_system_result{st[s], 0, 0.0, 0.0, 0, 0, 0.0, {0}};
+        std::snprintf(results[s].message, sizeof(results[s].message), "no worker context could be created");
+      }
     }
   fnocc_status out = FNOCC_OK;
   for (int s = 0; s < nsys; ++s)

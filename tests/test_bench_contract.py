@@ -125,7 +125,8 @@ def fake_gpu(monkeypatch):
 
     def fake_batch_solve(systems, variants, nroots, nworkers=4, precision="fp64", **kw):
         om = np.zeros((len(systems), len(variants), nroots))
-        info = [dict(status=0, nkept=4, e_rhf=-1.0, e_ccsdt=-1.1, ccsdt_iters=10, sigma_calls=50, seconds=0.1)
+        info = [dict(status=0, nkept=4, e_rhf=-1.0, e_ccsdt=-1.1, ccsdt_iters=10, sigma_calls=50, seconds=0.1,
+                     message="")
                 for _ in systems]
         return om, info
 
