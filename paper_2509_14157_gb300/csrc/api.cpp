@@ -65,7 +65,7 @@ struct MapSet {
   void upload() {
     if (host.empty()) host.push_back(0);
     dev.reserve(host.size() * sizeof(long long));
-    FNOCC_CUDA(cudaMemcpy(dev.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    copy_now(dev.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice);
     for (auto &f : fix)
       for (size_t g = 0; g < f.second.size(); ++g) f.first->tab[g] = dev.as<long long>() + f.second[g];
   }
@@ -131,6 +131,7 @@ struct TransformPlan {
 struct ProductGraph {
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> key;
+  std::vector<uintptr_t> failed;  // key of the last capture that failed
   uint64_t launches = 0;  // kernel launches of one replay
   ProductGraph() {}
   ProductGraph(const ProductGraph &) = delete;
@@ -494,9 +495,20 @@ void sigma_launches(fnocc_ctx *c, int var, const double *x, double *s, bool left
   // the small launches of different components share the GPU; per-launch
   // profiling keeps them on the context stream (isolated kernel times)
   const bool fork = !c->prof.enabled;
+  struct Join {  // the side streams rejoin the context stream also when a launch throws
+    fnocc_ctx *c;
+    bool armed;
+    ~Join() {
+      if (armed)
+        for (int i = 0; i < 2; ++i)
+          if (cudaEventRecord(c->ev_join[i], c->side[i]) == cudaSuccess)
+            cudaStreamWaitEvent(c->stream, c->ev_join[i], 0);
+    }
+  } join{c, false};
   if (fork) {
     FNOCC_CUDA(cudaEventRecord(c->ev_fork, c->stream));
     for (auto sd : c->side) FNOCC_CUDA(cudaStreamWaitEvent(sd, c->ev_fork, 0));
+    join.armed = true;
   }
   off = 0;
   for (int oc = 0; oc < 3; ++oc) {
@@ -516,11 +528,78 @@ void sigma_launches(fnocc_ctx *c, int var, const double *x, double *s, bool left
                  c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
     off += sz[oc];
   }
-  if (fork)
+  if (fork) {
+    join.armed = false;
     for (int i = 0; i < 2; ++i) {
       FNOCC_CUDA(cudaEventRecord(c->ev_join[i], c->side[i]));
       FNOCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join[i], 0));
     }
+  }
+}
+
+// everything the captured launches of a product address, and how they were
+// chosen: a graph replays only while all of it is unchanged
+std::vector<uintptr_t> product_key(fnocc_ctx *c, int var, bool left, const Launch &L, const Operands &ops) {
+  auto &eqs = left ? c->eom_left_eq[var] : c->eom_eq[var];
+  std::vector<uintptr_t> key = {(uintptr_t)c->hbar_version, (uintptr_t)L.precision, (uintptr_t)(L.force_shape + 1),
+                                (uintptr_t)c->gx.p, (uintptr_t)c->gs.p, (uintptr_t)c->scratch.p,
+                                (uintptr_t)c->partials.p, (uintptr_t)c->panels.p, (uintptr_t)ops.f,
+                                (uintptr_t)ops.v, (uintptr_t)ops.t2, (uintptr_t)ops.t3};
+  for (int k = 0; k < 3; ++k) {
+    key.push_back((uintptr_t)c->rd[k].p);
+    key.push_back((uintptr_t)c->sy[k].p);
+  }
+  for (int k = 0; k < 2; ++k) {
+    key.push_back((uintptr_t)c->bscratch[k].p);
+    key.push_back((uintptr_t)c->bpartials[k].p);
+    key.push_back((uintptr_t)c->bpanels[k].p);
+  }
+  for (int oc = 0; oc < 3; ++oc)
+    for (int ic = 0; ic < 3; ++ic) key.push_back((uintptr_t)eqs[oc][ic]->cache_ptr());
+  return key;
+}
+
+// Captures the product's launch sequence (x and s through the fixed buffers
+// gx, gs) into g. Returns false, with nothing captured and nothing launched,
+// when the capture fails (a launch error, or another call of this thread
+// that a capture does not allow) or when a buffer was reallocated during it,
+// whose freed memory the captured launches would address; the caller then
+// launches the sequence directly, which reports any error that persists.
+bool capture_product(fnocc_ctx *c, int var, bool left, const Launch &L, const Operands &ops,
+                     const std::vector<uintptr_t> &key, ProductGraph &g) {
+  g.reset();
+  const uint64_t l0 = c->launches;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  bool ok = true;
+  try {
+    sigma_launches(c, var, c->gx.d(), c->gs.d(), left, L, ops);
+  } catch (const std::exception &) {
+    ok = false;
+  }
+  const uint64_t launches = c->launches - l0;
+  c->launches = l0;
+  cudaGraph_t gr = nullptr;
+  if (cudaStreamEndCapture(c->stream, &gr) != cudaSuccess) ok = false;
+  if (ok && product_key(c, var, left, L, ops) != key) ok = false;
+  cudaGraphExec_t ex = nullptr;
+  if (ok && gr && cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) {
+    ex = nullptr;
+    ok = false;
+  }
+  if (gr) cudaGraphDestroy(gr);
+  if (!ok || !ex) {
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGetLastError();  // a failed capture leaves no error behind
+    g.failed = key;
+    return false;
+  }
+  g.exec = ex;
+  g.key = key;
+  g.launches = launches;
+  return true;
 }
 
 // s = (H-bar x)_c, or with left = true the left product s = x^T H-bar.
@@ -568,57 +647,24 @@ void sigma_dev(fnocc_ctx *c, int var, const double *x, double *s, bool left = fa
       flops += eq.flops();
       if (eq.needs_refresh(c->hbar_version) || eq.tuning_pending(L)) graph = false;
     }
-  if (!graph) {
-    sigma_launches(c, var, x, s, left, L, ops);
-  } else {
+  if (graph) {
     c->gx.reserve(sizeof(double) * dim);
     c->gs.reserve(sizeof(double) * dim);
-    // everything the captured launches address, and how they were chosen
-    std::vector<uintptr_t> key = {(uintptr_t)c->hbar_version, (uintptr_t)L.precision, (uintptr_t)(L.force_shape + 1),
-                                  (uintptr_t)c->gx.p, (uintptr_t)c->gs.p, (uintptr_t)c->scratch.p,
-                                  (uintptr_t)c->partials.p, (uintptr_t)c->panels.p, (uintptr_t)ops.f,
-                                  (uintptr_t)ops.v, (uintptr_t)ops.t2,
-                                  (uintptr_t)ops.t3};
-    for (int k = 0; k < 3; ++k) {
-      key.push_back((uintptr_t)c->rd[k].p);
-      key.push_back((uintptr_t)c->sy[k].p);
-    }
-    for (int k = 0; k < 2; ++k) {
-      key.push_back((uintptr_t)c->bscratch[k].p);
-      key.push_back((uintptr_t)c->bpartials[k].p);
-      key.push_back((uintptr_t)c->bpanels[k].p);
-    }
-    for (int oc = 0; oc < 3; ++oc)
-      for (int ic = 0; ic < 3; ++ic) key.push_back((uintptr_t)eqs[oc][ic]->cache_ptr());
+    const std::vector<uintptr_t> key = product_key(c, var, left, L, ops);
     ProductGraph &g = c->graphs[var][left ? 1 : 0][L.precision];
     if (!g.exec || g.key != key) {
-      g.reset();
-      cudaGraph_t gr = nullptr;
-      const uint64_t l0 = c->launches;
-      FNOCC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-      try {
-        sigma_launches(c, var, c->gx.d(), c->gs.d(), left, L, ops);
-      } catch (...) {
-        cudaStreamEndCapture(c->stream, &gr);
-        if (gr) cudaGraphDestroy(gr);
-        c->launches = l0;
-        throw;
-      }
-      FNOCC_CUDA(cudaStreamEndCapture(c->stream, &gr));
-      cudaGraphExec_t ex = nullptr;
-      const cudaError_t e = cudaGraphInstantiate(&ex, gr, 0);
-      cudaGraphDestroy(gr);
-      FNOCC_CUDA(e);
-      g.exec = ex;
-      g.key = key;
-      g.launches = c->launches - l0;
-      c->launches = l0;
+      // one attempt per key: a capture that failed is not retried until
+      // something it depends on changes
+      if (g.failed == key || !capture_product(c, var, left, L, ops, key, g)) graph = false;
     }
-    FNOCC_CUDA(cudaMemcpyAsync(c->gx.p, x, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
-    FNOCC_CUDA(cudaGraphLaunch(g.exec, c->stream));
-    c->launches += g.launches;
-    FNOCC_CUDA(cudaMemcpyAsync(s, c->gs.p, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
+    if (graph) {
+      FNOCC_CUDA(cudaMemcpyAsync(c->gx.p, x, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
+      FNOCC_CUDA(cudaGraphLaunch(g.exec, c->stream));
+      c->launches += g.launches;
+      FNOCC_CUDA(cudaMemcpyAsync(s, c->gs.p, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->stream));
+    }
   }
+  if (!graph) sigma_launches(c, var, x, s, left, L, ops);
   for (int oc = 0; oc < 3; ++oc)
     for (int ic = 0; ic < 3; ++ic) eq_version(c, var, oc, ic, left) = c->hbar_version;
   c->flops_sigma_last = flops;
@@ -1547,7 +1593,7 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
     }
     auto dgh = to_host(c, dg.d(), dim);
     std::vector<unsigned char> mkh(dim);
-    FNOCC_CUDA(cudaMemcpy(mkh.data(), mk.p, dim, cudaMemcpyDeviceToHost));
+    copy_after(mkh.data(), mk.p, dim, cudaMemcpyDeviceToHost, c->stream);
     std::vector<long long> allowed, pref;
     for (long long i = 0; i < dim; ++i)
       if (mkh[i]) {
@@ -1963,7 +2009,7 @@ fnocc_status fnocc_get_block(fnocc_ctx *c, int which, int root, double *buf, siz
       if (!c->have_amps) throw StatusError(FNOCC_E_STATE, "no amplitudes");
       size_t off = (which >= 2 ? c->nt[1] : 0) + (which >= 3 ? c->nt[2] : 0);
       if (len != c->nt[which]) throw StatusError(FNOCC_E_INVALID, "length mismatch");
-      FNOCC_CUDA(cudaMemcpy(buf, c->tpk.d() + off, sizeof(double) * len, cudaMemcpyDeviceToHost));
+      copy_after(buf, c->tpk.d() + off, sizeof(double) * len, cudaMemcpyDeviceToHost, c->stream);
       return FNOCC_OK;
     }
     if (which >= 11 && which <= 13) {
@@ -1973,8 +2019,8 @@ fnocc_status fnocc_get_block(fnocc_ctx *c, int which, int root, double *buf, siz
       int k = which - 11;
       size_t off = (k >= 1 ? sz[0] : 0) + (k >= 2 ? sz[1] : 0);
       if (len != sz[k]) throw StatusError(FNOCC_E_INVALID, "length mismatch");
-      FNOCC_CUDA(cudaMemcpy(buf, c->eom_vecs.d() + (size_t)root * c->last_dim + off, sizeof(double) * len,
-                            cudaMemcpyDeviceToHost));
+      copy_after(buf, c->eom_vecs.d() + (size_t)root * c->last_dim + off, sizeof(double) * len,
+                 cudaMemcpyDeviceToHost, c->stream);
       return FNOCC_OK;
     }
     throw StatusError(FNOCC_E_INVALID, "unknown block");

@@ -23,6 +23,23 @@ struct CudaError : std::runtime_error {
       throw ::fnocc::CudaError(std::string(#x) + ": " + cudaGetErrorString(e_), (int)e_);     \
   } while (0)
 
+// Copies outside a context's stream order (plan and constant tables,
+// parameter and result reads). A plain cudaMemcpy runs on the legacy default
+// stream, which the library's non-blocking streams are not ordered after,
+// and from pageable host memory it returns once the data is staged, before
+// it has reached the device: a kernel on another stream could then read the
+// table before it lands. copy_now goes through the calling thread's default
+// stream and copy_after through the stream whose queued work the copy must
+// follow; both return with the copy complete.
+inline void copy_after(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+  if (!bytes) return;
+  FNOCC_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, s));
+  FNOCC_CUDA(cudaStreamSynchronize(s));
+}
+inline void copy_now(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+  copy_after(dst, src, bytes, kind, cudaStreamPerThread);
+}
+
 // Grow-only device buffer owned by a context.
 struct DevBuf {
   void *p = nullptr;

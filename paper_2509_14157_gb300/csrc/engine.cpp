@@ -37,12 +37,12 @@ void TupleTable::build(int n_, int k_) {
   }
   if (host.empty()) host.push_back(0);
   dev.reserve(host.size() * sizeof(int));
-  FNOCC_CUDA(cudaMemcpy(dev.p, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice));
+  copy_now(dev.p, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice);
   std::vector<long long> rk((size_t)std::max(k, 1) * (n + 1), 0);
   for (int i = 0; i < k; ++i)
     for (int x = 1; x <= n; ++x) rk[(size_t)i * (n + 1) + x] = rk[(size_t)i * (n + 1) + x - 1] + binom_ll(n - x, k - 1 - i);
   rankdev.reserve(rk.size() * sizeof(long long));
-  FNOCC_CUDA(cudaMemcpy(rankdev.p, rk.data(), rk.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  copy_now(rankdev.p, rk.data(), rk.size() * sizeof(long long), cudaMemcpyHostToDevice);
 }
 
 namespace {
@@ -311,7 +311,7 @@ struct TableBuilder {
       base = keep.data();
     } else {
       buf.reserve(host.size() * sizeof(long long));
-      FNOCC_CUDA(cudaMemcpy(buf.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice));
+      copy_now(buf.p, host.data(), host.size() * sizeof(long long), cudaMemcpyHostToDevice);
       base = buf.as<long long>();
     }
     for (auto &p : pend)
@@ -629,7 +629,7 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
     fb = host_flat_.data();
   } else {
     flat_.reserve(sizeof(long long) * flat_host.size());
-    FNOCC_CUDA(cudaMemcpy(flat_.p, flat_host.data(), sizeof(long long) * flat_host.size(), cudaMemcpyHostToDevice));
+    copy_now(flat_.p, flat_host.data(), sizeof(long long) * flat_host.size(), cudaMemcpyHostToDevice);
     fb = flat_.as<long long>();
   }
   const long long kSms = std::max(1, sms_);
@@ -788,8 +788,8 @@ void ExecEquation::build_launches(const std::vector<long long> &flat_host) {
     ib = host_sid_.data();
   } else {
     gtasks_.reserve(ioff + std::max<size_t>(ibytes, 8));
-    FNOCC_CUDA(cudaMemcpy(gtasks_.p, gt.data(), tbytes, cudaMemcpyHostToDevice));
-    if (ibytes) FNOCC_CUDA(cudaMemcpy((char *)gtasks_.p + ioff, sid.data(), ibytes, cudaMemcpyHostToDevice));
+    copy_now(gtasks_.p, gt.data(), tbytes, cudaMemcpyHostToDevice);
+    if (ibytes) copy_now((char *)gtasks_.p + ioff, sid.data(), ibytes, cudaMemcpyHostToDevice);
     tb = reinterpret_cast<const GTask *>(gtasks_.p);
     ib = reinterpret_cast<const int *>((char *)gtasks_.p + ioff);
   }

@@ -902,9 +902,11 @@ void ensure_perm_tables() {
     } while (std::next_permutation(a, a + k));
     cnt[k] = c;
   }
-  FNOCC_CUDA(cudaMemcpyToSymbol(c_perm, perm, sizeof(perm)));
-  FNOCC_CUDA(cudaMemcpyToSymbol(c_psign, sgn, sizeof(sgn)));
-  FNOCC_CUDA(cudaMemcpyToSymbol(c_pcount, cnt, sizeof(cnt)));
+  // complete before any stream can launch a reader (see copy_now)
+  FNOCC_CUDA(cudaMemcpyToSymbolAsync(c_perm, perm, sizeof(perm), 0, cudaMemcpyHostToDevice, cudaStreamPerThread));
+  FNOCC_CUDA(cudaMemcpyToSymbolAsync(c_psign, sgn, sizeof(sgn), 0, cudaMemcpyHostToDevice, cudaStreamPerThread));
+  FNOCC_CUDA(cudaMemcpyToSymbolAsync(c_pcount, cnt, sizeof(cnt), 0, cudaMemcpyHostToDevice, cudaStreamPerThread));
+  FNOCC_CUDA(cudaStreamSynchronize(cudaStreamPerThread));
   done[dev] = true;
 }
 

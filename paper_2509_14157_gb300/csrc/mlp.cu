@@ -378,12 +378,12 @@ Mlp::~Mlp() {
 
 void Mlp::set_params(const float *host) {
   FNOCC_CUDA(cudaSetDevice(device_));
-  FNOCC_CUDA(cudaMemcpy(params_.p, host, sizeof(float) * nparam_, cudaMemcpyHostToDevice));
+  copy_after(params_.p, host, sizeof(float) * nparam_, cudaMemcpyHostToDevice, stream_);
 }
 
 void Mlp::get_params(float *host) const {
   FNOCC_CUDA(cudaSetDevice(device_));
-  FNOCC_CUDA(cudaMemcpy(host, params_.p, sizeof(float) * nparam_, cudaMemcpyDeviceToHost));
+  copy_after(host, params_.p, sizeof(float) * nparam_, cudaMemcpyDeviceToHost, stream_);
 }
 
 void Mlp::reset_optimizer() {
@@ -683,7 +683,7 @@ fnocc_status fnocc_mlp_loss_grad(fnocc_mlp *m, const float *x, const float *t, c
     FNOCC_CUDA(cudaMemcpyAsync(dw, w, sizeof(float) * ny, cudaMemcpyHostToDevice, net.stream()));
     const double l = net.loss_grad(dx, dt, dw, (int)n);
     if (loss) *loss = l;
-    if (grad) FNOCC_CUDA(cudaMemcpy(grad, net.grad(), sizeof(float) * net.nparam(), cudaMemcpyDeviceToHost));
+    if (grad) fnocc::copy_after(grad, net.grad(), sizeof(float) * net.nparam(), cudaMemcpyDeviceToHost, net.stream());
     return FNOCC_OK;
   });
 }
