@@ -654,22 +654,24 @@ def run_xfno_check(args):
     emit(summary)
 
 
-# learned-guess check: (electrons, orbitals, FNO threshold, variant) of the
-# evaluation systems, 8 roots each
-GC_SYSTEMS = ((16, 80, 1e-6, "dip"), (12, 60, 1e-5, "dip"), (16, 80, 1e-5, "dea"), (12, 60, 1e-6, "dea"))
+# learned-guess check: (electrons, orbitals, kept natural virtuals, variant)
+# of the evaluation systems (12-16 electrons, 30-40 kept virtuals), 8 roots
+# each
+GC_SYSTEMS = ((16, 80, 36, "dip"), (12, 60, 30, "dip"), (16, 80, 32, "dea"), (12, 60, 30, "dea"))
 GC_ROOTS = 8
 
 
 def run_guess_check(args):
     """Davidson starts at a matched 1e-6 Eh target: the guess network is
-    trained on --gc-train seeded systems of 6-10 electrons (the default
-    run's 12; outside every timed region), then DIP and DEA on 12 and 16
-    electrons with 28-41 kept natural virtuals (16 e / 80 orbitals at FNO
-    1e-6 and 1e-5, 12 e / 60 orbitals at 1e-5 and 1e-6), 8 roots each, BF16x3
+    trained on --gc-train seeded systems of 6-10 electrons (outside every
+    timed region; with --gc-diag-samples the preconditioner target is the
+    exact diagonal at that many sampled elements per space, and at most
+    --gc-max-samples samples are kept), then DIP and DEA on 12 and 16
+    electrons with 30-36 kept natural virtuals, 8 roots each, BF16x3
     products throughout (residual 1e-6), from the diagonal, Koopmans and
-    learned starts. Reports products, iterations,
-    wall-clock seconds and the largest root difference to the Koopmans
-    solve; one JSON line per finished solve, then a summary line."""
+    learned starts. Reports products, iterations, wall-clock seconds and the
+    largest root difference to the Koopmans solve; one JSON line per
+    finished solve, then a summary line."""
     import paper_2509_14157_gb300 as pkg
     from paper_2509_14157_gb300 import learned
     import synth
@@ -679,17 +681,22 @@ def run_guess_check(args):
 
     t0 = time.perf_counter()
     X, T, W, info = learned.training_set(learned.seeded_training_systems(args.gc_train, electrons=(6, 8, 10)),
-                                         list(VARIANTS), NROOTS)
-    net, hist = learned.train_guess_model(X, T, W, epochs=30, batch=2048)
-    training = {"seconds": time.perf_counter() - t0, "samples": int(X.shape[0]),
-                "systems": len(set(i[0] for i in info)), "final_loss": float(hist[-1])}
+                                         list(VARIANTS), NROOTS, diag_samples=args.gc_diag_samples,
+                                         max_samples=args.gc_max_samples, workers=args.gc_workers)
+    t_data = time.perf_counter() - t0
+    epochs = args.gc_epochs
+    net, hist = learned.train_guess_model(X, T, W, epochs=epochs, batch=2048 if X.shape[0] < 10 ** 6 else 8192)
+    training = {"seconds": time.perf_counter() - t0, "data_seconds": t_data, "samples": int(X.shape[0]),
+                "systems": len(set(i[0] for i in info)), "requested_systems": args.gc_train,
+                "diag_samples_per_space": args.gc_diag_samples, "epochs": epochs, "workers": args.gc_workers,
+                "first_loss": float(hist[0]), "final_loss": float(hist[-1])}
     emit({"part": "training", **training})
     summary = {"mode": "guess_check", "roots": GC_ROOTS, "precision": "mixed (BF16x3), residual 1e-6",
                "training": training, "data": "synthetic", "systems": []}
-    for ne, norb, thr, var in GC_SYSTEMS:
+    for ne, norb, nkeep, var in GC_SYSTEMS:
         h, eri = synth.hamiltonian(ne, norb, seed=0)
         ctx = pkg.Context(0)
-        fi = ctx.fno_truncate(h, eri, ne // 2, thr)
+        fi = ctx.fno_truncate(h, eri, ne // 2, 0.0, nkeep=nkeep)
         o, v, _ = ctx.dims()
         cc = ctx.ccsdt_solve(precision="mixed", switch_tol=1e-6)
         ctx.set_guess_model(net)
@@ -705,7 +712,7 @@ def run_guess_check(args):
         ref = np.asarray(res["koopmans"]["energies"])
         for guess in res:
             res[guess]["max_root_diff_to_koopmans_eh"] = float(np.max(np.abs(np.asarray(res[guess]["energies"]) - ref)))
-        summary["systems"].append({"electrons": ne, "orbitals": norb, "fno_threshold": thr, "nkept": fi["nkept"],
+        summary["systems"].append({"electrons": ne, "orbitals": norb, "nkeep": nkeep, "nkept": fi["nkept"],
                                    "o": o, "v": v, "variant": var, "ccsdt_converged": cc["converged"],
                                    "solves": res})
         ctx.set_guess_model(None)
@@ -742,6 +749,14 @@ def main():
                          "variant each; FNO and XFNO errors against the untruncated energies")
     ap.add_argument("--gc-train", type=int, default=12,
                     help="with --guess-check: number of seeded training systems")
+    ap.add_argument("--gc-diag-samples", type=int, default=None,
+                    help="with --guess-check: exact-diagonal targets at this many sampled elements per space "
+                         "(default: every element)")
+    ap.add_argument("--gc-max-samples", type=int, default=None,
+                    help="with --guess-check: keep at most this many training samples (seeded draw)")
+    ap.add_argument("--gc-epochs", type=int, default=30, help="with --guess-check: training epochs")
+    ap.add_argument("--gc-workers", type=int, default=1,
+                    help="with --guess-check: host threads (one context each) building the training set")
     ap.add_argument("--precision-check", action="store_true",
                     help="split-product accuracy and speed on 16 electrons / 80 orbitals, IP/EA/DIP x 6 roots")
     ap.add_argument("--pc-variants", default=None,

@@ -418,6 +418,14 @@ fnocc_status fnocc_eom_features(fnocc_ctx *ctx, int variant, float *features);
 /* Exact diagonal H-bar_mumu of the sector's elements (others 0), one sigma
  * product per element: training data on small systems. */
 fnocc_status fnocc_eom_diagonal(fnocc_ctx *ctx, int variant, double *diag);
+/* The same at n chosen elements: out[q] = H-bar_mumu for mu = idx[q] (0 for
+ * an element outside the sector), one sigma product per element inside it,
+ * so that sampled preconditioner targets on larger training systems cost n
+ * products instead of the space's dimension. idx (host, n entries, each in
+ * [0, dim)) and out (host, n entries) belong to the caller; n = 0 does
+ * nothing. FNOCC_E_INVALID for a bad variant or an index out of range,
+ * FNOCC_E_STATE before amplitudes exist. */
+fnocc_status fnocc_eom_diagonal_at(fnocc_ctx *ctx, int variant, long long n, const long long *idx, double *out);
 /* The network FNOCC_GUESS_LEARNED uses (not owned; NULL detaches). */
 fnocc_status fnocc_set_guess_model(fnocc_ctx *ctx, fnocc_mlp *mlp);
 

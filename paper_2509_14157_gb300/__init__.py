@@ -144,6 +144,8 @@ SIGNATURES = {
     "fnocc_mlp_load": (ctypes.c_int, [_cp, ctypes.c_char_p]),
     "fnocc_eom_features": (ctypes.c_int, [_cp, ctypes.c_int, _fp]),
     "fnocc_eom_diagonal": (ctypes.c_int, [_cp, ctypes.c_int, _dp]),
+    "fnocc_eom_diagonal_at": (ctypes.c_int, [_cp, ctypes.c_int, ctypes.c_longlong,
+                                             ctypes.POINTER(ctypes.c_longlong), _dp]),
     "fnocc_set_guess_model": (ctypes.c_int, [_cp, _cp]),
     "fnocc_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(System), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -578,11 +580,19 @@ class Context:
         self._check(self.lib.fnocc_eom_features(self._h, var, f.ctypes.data_as(_fp)))
         return f
 
-    def eom_diagonal(self, variant):
-        """Exact H-bar diagonal of the sector's elements (one product each)."""
+    def eom_diagonal(self, variant, idx=None):
+        """Exact H-bar diagonal of the sector's elements (one product each),
+        or with idx only at those packed indices (fnocc_eom_diagonal_at)."""
         var = VARIANTS.get(variant, variant)
-        d = np.zeros(sum(self.eom_sizes(var)))
-        self._check(self.lib.fnocc_eom_diagonal(self._h, var, d.ctypes.data_as(_dp)))
+        if idx is None:
+            d = np.zeros(sum(self.eom_sizes(var)))
+            self._check(self.lib.fnocc_eom_diagonal(self._h, var, d.ctypes.data_as(_dp)))
+            return d
+        ix = np.ascontiguousarray(idx, dtype=np.int64)
+        d = np.zeros(ix.shape[0])
+        self._check(self.lib.fnocc_eom_diagonal_at(self._h, var, ix.shape[0],
+                                                   ix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                                   d.ctypes.data_as(_dp)))
         return d
 
     def set_guess_model(self, mlp):

@@ -1940,45 +1940,66 @@ fnocc_status fnocc_eom_features(fnocc_ctx *c, int variant, float *features) {
   });
 }
 
+namespace {
+
+// exact diagonal elements H-bar_mumu at the packed indices idx (all of the
+// space when idx is null), one product with a unit vector per element inside
+// the sector; out[q] belongs to idx[q] (to element q without idx)
+void eom_diagonal_elements(fnocc_ctx *c, int variant, long long n, const long long *idx, double *out) {
+  if (variant < 0 || variant >= kEomVariants) throw StatusError(FNOCC_E_INVALID, "bad variant");
+  require_ham(c);
+  FNOCC_CUDA(cudaSetDevice(c->device));
+  size_t sz[3];
+  eom_sizes(c, variant, sz);
+  const long long dim = (long long)(sz[0] + sz[1] + sz[2]);
+  if (!idx) n = dim;
+  for (long long q = 0; idx && q < n; ++q)
+    if (idx[q] < 0 || idx[q] >= dim) throw StatusError(FNOCC_E_INVALID, "element index out of range");
+  prepare_hbar(c);
+  c->precision = FNOCC_FP64;
+  Launch L = c->L();
+  DevBuf mk, x, s, dd;
+  mk.reserve(dim);
+  size_t off = 0;
+  for (int k = 0; k < 3; ++k) {
+    const int nh = kEom[variant][k][0], np = kEom[variant][k][1];
+    ms_mask(L, nh, np, c->otab[nh].dev.as<int>(), c->otab[nh].count, c->vtab[np].dev.as<int>(), c->vtab[np].count,
+            kSectorMs2[variant], mk.as<unsigned char>() + off);
+    off += sz[k];
+  }
+  std::vector<unsigned char> mkh(dim);
+  copy_after(mkh.data(), mk.p, dim, cudaMemcpyDeviceToHost, c->stream);
+  x.reserve(sizeof(double) * dim);
+  s.reserve(sizeof(double) * dim);
+  dd.reserve(sizeof(double) * std::max<long long>(n, 1));
+  FNOCC_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double) * dim, c->stream));
+  FNOCC_CUDA(cudaMemsetAsync(dd.p, 0, sizeof(double) * std::max<long long>(n, 1), c->stream));
+  const double one = 1.0, zero = 0.0;
+  for (long long q = 0; q < n; ++q) {
+    const long long i = idx ? idx[q] : q;
+    if (!mkh[i]) continue;
+    FNOCC_CUDA(cudaMemcpyAsync(x.d() + i, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    sigma_dev(c, variant, x.d(), s.d());
+    FNOCC_CUDA(cudaMemcpyAsync(dd.d() + q, s.d() + i, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    FNOCC_CUDA(cudaMemcpyAsync(x.d() + i, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  if (n > 0) copy_after(out, dd.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+}
+
+}  // namespace
+
 fnocc_status fnocc_eom_diagonal(fnocc_ctx *c, int variant, double *diag) {
   if (!c || !diag) return FNOCC_E_INVALID;
   return guarded(c, [&]() -> fnocc_status {
-    if (variant < 0 || variant >= kEomVariants) throw StatusError(FNOCC_E_INVALID, "bad variant");
-    require_ham(c);
-    FNOCC_CUDA(cudaSetDevice(c->device));
-    prepare_hbar(c);
-    c->precision = FNOCC_FP64;
-    Launch L = c->L();
-    size_t sz[3];
-    eom_sizes(c, variant, sz);
-    const long long dim = (long long)(sz[0] + sz[1] + sz[2]);
-    DevBuf mk, x, s, dd;
-    mk.reserve(dim);
-    size_t off = 0;
-    for (int k = 0; k < 3; ++k) {
-      const int nh = kEom[variant][k][0], np = kEom[variant][k][1];
-      ms_mask(L, nh, np, c->otab[nh].dev.as<int>(), c->otab[nh].count, c->vtab[np].dev.as<int>(), c->vtab[np].count,
-              kSectorMs2[variant], mk.as<unsigned char>() + off);
-      off += sz[k];
-    }
-    std::vector<unsigned char> mkh(dim);
-    FNOCC_CUDA(cudaMemcpyAsync(mkh.data(), mk.p, dim, cudaMemcpyDeviceToHost, c->stream));
-    sync(c);
-    x.reserve(sizeof(double) * dim);
-    s.reserve(sizeof(double) * dim);
-    dd.reserve(sizeof(double) * dim);
-    FNOCC_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double) * dim, c->stream));
-    FNOCC_CUDA(cudaMemsetAsync(dd.p, 0, sizeof(double) * dim, c->stream));
-    const double one = 1.0, zero = 0.0;
-    for (long long i = 0; i < dim; ++i) {
-      if (!mkh[i]) continue;
-      FNOCC_CUDA(cudaMemcpyAsync(x.d() + i, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-      sigma_dev(c, variant, x.d(), s.d());
-      FNOCC_CUDA(cudaMemcpyAsync(dd.d() + i, s.d() + i, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      FNOCC_CUDA(cudaMemcpyAsync(x.d() + i, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    }
-    FNOCC_CUDA(cudaMemcpyAsync(diag, dd.p, sizeof(double) * dim, cudaMemcpyDeviceToHost, c->stream));
-    sync(c);
+    eom_diagonal_elements(c, variant, 0, nullptr, diag);
+    return FNOCC_OK;
+  });
+}
+
+fnocc_status fnocc_eom_diagonal_at(fnocc_ctx *c, int variant, long long n, const long long *idx, double *out) {
+  if (!c || n < 0 || (n > 0 && (!idx || !out))) return FNOCC_E_INVALID;
+  return guarded(c, [&]() -> fnocc_status {
+    if (n > 0) eom_diagonal_elements(c, variant, n, idx, out);
     return FNOCC_OK;
   });
 }

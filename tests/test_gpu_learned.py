@@ -146,6 +146,16 @@ def test_exact_diagonal_matches_oracle(pkg, variant):
     idx = np.where(eom.ms_mask(variant, o, v))[0]
     assert np.max(np.abs(got[idx] - np.diag(m))) < 1e-10
     assert np.all(got[np.setdiff1d(np.arange(got.size), idx)] == 0)
+    # the sampled form: chosen elements, in any order, with repeats and
+    # elements outside the sector (0), equal to the full diagonal there
+    rng = np.random.default_rng(3)
+    pick = np.concatenate([rng.choice(got.size, 12, replace=False), idx[:2], [0]])
+    part = ctx.eom_diagonal(variant, pick)
+    assert np.array_equal(part, got[pick])
+    assert ctx.eom_diagonal(variant, np.zeros(0, dtype=np.int64)).size == 0
+    for bad in ([-1], [got.size]):
+        with pytest.raises(pkg.FnoccError):
+            ctx.eom_diagonal(variant, bad)
     ctx.close()
 
 
@@ -174,3 +184,25 @@ def test_trained_network_saves_products_and_keeps_roots(pkg):
     assert with_net < plain, (with_net, plain)
     ctx.close()
     net.close()
+
+
+def test_training_set_threads_and_sampled_targets(pkg):
+    """The training set built on two host threads (one context each) equals
+    the one built on one, with sampled exact-diagonal targets: each sampled
+    correction equals the full diagonal's, the others carry weight 0."""
+    from paper_2509_14157_gb300 import learned
+    systems = learned.seeded_training_systems(count=4, electrons=(6, 8))
+    one = learned.training_set(systems, ["ip", "dea"], 2, diag_samples=8)
+    two = learned.training_set(systems, ["ip", "dea"], 2, diag_samples=8, workers=2)
+    for a, b in zip(one[:3], two[:3]):
+        assert np.array_equal(a, b)
+    assert one[3] == two[3]
+    X, T, W, info = one
+    assert np.all(W[:, 0] == 1.0)  # sector elements only
+    per_space = [n for _, _, n in info]
+    assert np.sum(W[:, 1]) <= 8 * len(per_space) and np.sum(W[:, 1]) > 0
+    full = learned.training_set(systems[:1], ["ip"], 2)
+    samp = learned.training_set(systems[:1], ["ip"], 2, diag_samples=8)
+    assert np.array_equal(full[0], samp[0])
+    on = samp[2][:, 1] > 0
+    assert np.array_equal(samp[1][on, 1], full[1][on, 1])
