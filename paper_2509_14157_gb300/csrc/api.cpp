@@ -1787,23 +1787,38 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       if (c->precision != FNOCC_FP64 && o.switch_tol > 0) {
         double mx = 0;
         for (double x : norms) mx = std::max(mx, x);
-        // refinement once every residual is below switch_tol, or after a
-        // quarter of the iteration budget in split arithmetic (the roots
-        // selected by principal weight can keep changing when satellites sit
-        // near the weight threshold, and the split products' rounding is of
-        // the size that moves them across it)
-        if (mx < o.switch_tol || it >= std::max(8, o.maxiter / 4)) {
-          // refinement: FP64 from here on; rebuild the subspace from the Ritz
-          // vectors with FP64 products (cached H-bar pieces recomputed too)
+        // refinement once every residual is below switch_tol, or after half
+        // of the iteration budget in split arithmetic (the roots selected by
+        // principal weight can keep changing when satellites sit near the
+        // weight threshold, and the split products' rounding is of the size
+        // that moves them across it: the FP64 half then settles them)
+        if (mx < o.switch_tol || it >= std::max(8, o.maxiter / 2)) {
+          // refinement: FP64 from here on, from a thick restart of the split
+          // phase's subspace: the Ritz vectors of the chosen roots and of the
+          // next candidates (2 nroots in all, as at every restart), their
+          // products recomputed in FP64 (cached H-bar pieces too). With the
+          // chosen roots' vectors alone the FP64 phase took about as many
+          // iterations as a solve from the start.
+          const int nkeep = std::min((int)idx.size(), 2 * nr);
           c->precision = FNOCC_FP64;
           ++c->hbar_version;
           DevBuf keep;
-          keep.reserve(sizeof(double) * na * nr);
-          FNOCC_CUDA(cudaMemcpyAsync(keep.p, xr.p, sizeof(double) * na * nr, cudaMemcpyDeviceToDevice, c->stream));
+          keep.reserve(sizeof(double) * na * nkeep);
+          for (int q = 0; q < nkeep; ++q) {
+            std::vector<double> y(kb);
+            double nn = 0;
+            for (int i = 0; i < kb; ++i) {
+              y[i] = Y[(size_t)i * kb + idx[q]].real();
+              nn += y[i] * y[i];
+            }
+            nn = nn > 0 ? std::sqrt(nn) : 1.0;
+            for (double &t : y) t /= nn;
+            combine_rows(c, na, Vb.d(), kb, y, keep.d() + (size_t)q * na, false);
+          }
           kb = 0;
           G.clear();
           G1.clear();
-          for (int r = 0; r < nr; ++r) add_vector(keep.d() + (size_t)r * na);
+          for (int q = 0; q < nkeep; ++q) add_vector(keep.d() + (size_t)q * na);
           have_old = false;
           continue;
         }
