@@ -135,7 +135,8 @@ typedef struct {
   int maxiter;      /* default 200 */
   int nguess;       /* guess vectors, default 2*nroots */
   int precision;    /* fnocc_precision, default FP64 */
-  double switch_tol;/* MIXED: FP64 once every residual norm is below this, or after maxiter / 2
+  double switch_tol;/* MIXED: FP64 once every residual norm is below this, once the largest
+                       residual has not halved for 25 iterations, or after maxiter / 2
                        iterations in mixed precision (default 1e-5; 0 = never); the FP64
                        subspace starts from the Ritz vectors of the chosen roots and of as many
                        further candidates (a thick restart) */

@@ -1558,6 +1558,8 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
     prepare_hbar(c);  // T1 dressing and amplitude unpacking stay FP64
     c->precision = o.precision;
     int sigma_calls_mixed = 0;
+    double split_best = INFINITY;  // split phase: best largest residual, and when it last halved
+    int split_best_it = 0;
     size_t sz[3];
     eom_sizes(c, variant, sz);
     const long long dim = (long long)(sz[0] + sz[1] + sz[2]);
@@ -1787,12 +1789,18 @@ fnocc_status eom_solve_once(fnocc_ctx *c, int variant, int nroots, int guess, co
       if (c->precision != FNOCC_FP64 && o.switch_tol > 0) {
         double mx = 0;
         for (double x : norms) mx = std::max(mx, x);
-        // refinement once every residual is below switch_tol, or after half
+        // refinement once every residual is below switch_tol, once the
+        // largest residual has not halved for 25 iterations, or after half
         // of the iteration budget in split arithmetic (the roots selected by
         // principal weight can keep changing when satellites sit near the
         // weight threshold, and the split products' rounding is of the size
-        // that moves them across it: the FP64 half then settles them)
-        if (mx < o.switch_tol || it >= std::max(8, o.maxiter / 2)) {
+        // that moves them across it: FP64 then settles them)
+        if (mx < 0.5 * split_best) {
+          split_best = mx;
+          split_best_it = it;
+        }
+        const bool stalled = it - split_best_it >= 25;
+        if (mx < o.switch_tol || stalled || it >= std::max(8, o.maxiter / 2)) {
           // refinement: FP64 from here on, from a thick restart of the split
           // phase's subspace: the Ritz vectors of the chosen roots and of the
           // next candidates (2 nroots in all, as at every restart), their
