@@ -53,16 +53,21 @@ __device__ __forceinline__ int find_task(const GTask *tasks, int ntasks, long lo
 // FP64 tile kernel: threads as TY x TX (TX = 256 / TY), each a TM x TN
 // micro-tile; the block covers (TY*TM) x (TX*TN) outputs; K staged BKG at a
 // time through shared memory (16, or 8 for the short reductions of single
-// spin blocks, e.g. K = 5, where a 16-wide K tile would pad 3.2x).
+// spin blocks, e.g. K = 5, where a 16-wide K tile would pad 3.2x). The
+// operand gathers of the next K tile are issued into registers before the
+// products of the current one (its reduction-index offsets read one tile
+// ahead into a two-slot ring), so that their latency overlaps the FMAs;
+// the order of the additions is that of the K loop either way.
 template <int TY, int TM, int TN, int BKG = 16>
 __global__ void __launch_bounds__(NT) k_ggemm(const GTask *__restrict__ tasks, int ntasks, double alpha,
                                               const double *__restrict__ A, const double *__restrict__ B,
                                               double *__restrict__ C, double *__restrict__ part) {
   static_assert(2 * BKG <= NT, "index staging uses 2 * BKG threads");
   constexpr int TX = NT / TY, TBM = TY * TM, TBN = TX * TN;
+  constexpr int PA = (TBM * BKG + NT - 1) / NT, PB = (TBN * BKG + NT - 1) / NT;  // gathers per thread
   __shared__ double As[BKG][TBM];
   __shared__ double Bs[BKG][TBN];
-  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[BKG], brow_s[BKG];
+  __shared__ long long arow_s[TBM], crow_s[TBM], bcol_s[TBN], ccol_s[TBN], acol_s[2][BKG], brow_s[2][BKG];
   __shared__ GTask t;
   const int tid = threadIdx.x;
   const long long cta = blockIdx.x;
@@ -83,33 +88,65 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GTask *__restrict__ tasks, i
     bcol_s[i] = n < t.N ? t.bcol[n] : 0;
     ccol_s[i] = (!split && n < t.N) ? t.ccol[n] : 0;
   }
+  // reduction-index offsets of the K tile at k0 into ring slot q
+  auto load_tables = [&](long long k0, int q) {
+    if (tid < BKG) {
+      const long long k = k0 + tid;
+      acol_s[q][tid] = k < ke ? t.acol[k] : 0;
+    } else if (tid < 2 * BKG) {
+      const long long k = k0 + tid - BKG;
+      brow_s[q][tid - BKG] = k < ke ? t.brow[k] : 0;
+    }
+  };
+  // operand elements of the K tile at k0 (0 outside the task): thread tid
+  // takes elements tid, tid + NT, ... of the A tile (k fastest) and of the
+  // B tile (columns fastest)
+  double pa[PA], pb[PB];
+  auto gather = [&](long long k0, int q) {
+#pragma unroll
+    for (int j = 0; j < PA; ++j) {
+      const int idx = tid + j * NT;
+      const int kk = idx % BKG, row = idx / BKG;
+      const bool ok = idx < TBM * BKG && (m0 + row < t.M) && (k0 + kk < ke);
+      pa[j] = ok ? __ldg(A + arow_s[row] + acol_s[q][kk]) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+      const int idx = tid + j * NT;
+      const int col = idx % TBN, kk = idx / TBN;
+      const bool ok = idx < TBN * BKG && (n0 + col < t.N) && (k0 + kk < ke);
+      pb[j] = ok ? __ldg(B + brow_s[q][kk] + bcol_s[col]) : 0.0;
+    }
+  };
   const int tx = tid % TX, ty = tid / TX;
   double acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
-  for (long long k0 = kb; k0 < ke; k0 += BKG) {
+  const long long nst = ke > kb ? (ke - kb + BKG - 1) / BKG : 0;
+  if (nst > 0) {
+    load_tables(kb, 0);
     __syncthreads();
-    if (tid < BKG) {
-      const long long k = k0 + tid;
-      acol_s[tid] = k < ke ? t.acol[k] : 0;
-    } else if (tid < 2 * BKG) {
-      const long long k = k0 + tid - BKG;
-      brow_s[tid - BKG] = k < ke ? t.brow[k] : 0;
+    gather(kb, 0);
+  }
+  for (long long st = 0; st < nst; ++st) {
+    const long long k0 = kb + st * BKG;
+    __syncthreads();  // the products of the previous tile have read As and Bs
+#pragma unroll
+    for (int j = 0; j < PA; ++j) {
+      const int idx = tid + j * NT;
+      if (idx < TBM * BKG) As[idx % BKG][idx / BKG] = pa[j];
     }
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+      const int idx = tid + j * NT;
+      if (idx < TBN * BKG) Bs[idx / TBN][idx % TBN] = pb[j];
+    }
+    // slot (st + 1) & 1 was last read by the gathers issued two tiles back
+    if (st + 1 < nst) load_tables(k0 + BKG, (int)((st + 1) & 1));
     __syncthreads();
-    for (int idx = tid; idx < TBM * BKG; idx += NT) {
-      const int kk = idx % BKG, row = idx / BKG;
-      const bool ok = (m0 + row < t.M) && (k0 + kk < ke);
-      As[kk][row] = ok ? __ldg(A + arow_s[row] + acol_s[kk]) : 0.0;
-    }
-    for (int idx = tid; idx < TBN * BKG; idx += NT) {
-      const int col = idx % TBN, kk = idx / TBN;
-      const bool ok = (n0 + col < t.N) && (k0 + kk < ke);
-      Bs[kk][col] = ok ? __ldg(B + brow_s[kk] + bcol_s[col]) : 0.0;
-    }
-    __syncthreads();
+    if (st + 1 < nst) gather(k0 + BKG, (int)((st + 1) & 1));  // in flight during the products below
 #pragma unroll
     for (int kk = 0; kk < BKG; ++kk) {
       double a[TM], b[TN];
