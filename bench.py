@@ -436,7 +436,8 @@ def run_sigma_only(args):
     import torch
     import paper_2509_14157_gb300 as pkg
     import synth
-    ne, norb, thr = (PC_NE, PC_NORB, PC_THRESHOLD) if args.large else (NE, NORB, args.threshold)
+    ne, norb, thr = ((PC_NE, PC_NORB, PC_THRESHOLD) if args.large else
+                     (MID_NE, MID_NORB, MID_THRESHOLD) if args.mid else (NE, NORB, args.threshold))
     h, eri = synth.hamiltonian(ne, norb, seed=0)
     ctx = pkg.Context(0)
     ctx.fno_truncate(h, eri, ne // 2, thr)
@@ -533,6 +534,10 @@ def run_batch(args):
 
 # larger system for the split-product accuracy check: 41 kept natural virtuals
 PC_NE, PC_NORB, PC_THRESHOLD, PC_ROOTS, PC_VARIANTS = 16, 80, 1e-6, 6, ("ip", "ea", "dip")
+# profiling case between the two (--sigma-only V --mid): 12 electrons / 60
+# orbitals, FNO 1e-4 (17 kept natural virtuals, o = 12, v = 34); a DEA
+# product holds a few GB on the device
+MID_NE, MID_NORB, MID_THRESHOLD = 12, 60, 1e-4
 
 
 def run_precision_check(args):
@@ -771,6 +776,8 @@ def main():
                          "per candidate)")
     ap.add_argument("--tile-shape", type=int, default=-1,
                     help="with --sigma-only: force one grouped-GEMM tile shape (fnocc_set_tile_shape)")
+    ap.add_argument("--mid", action="store_true",
+                    help="with --sigma-only: 12 electrons / 60 orbitals, FNO 1e-4 (o = 12, v = 34)")
     ap.add_argument("--large", action="store_true",
                     help="with --sigma-only / --solve-only: the larger system (16 electrons / 80 orbitals, FNO "
                          "1e-6: 41 kept natural virtuals, o = 16, v = 82), 6 roots; mixed solves run CCSDT mixed")
