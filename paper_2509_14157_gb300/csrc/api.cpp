@@ -363,6 +363,15 @@ void dress(fnocc_ctx *c, const double *t1) {
               tp.two[1].bcol, c->hd.d(), tp.two[1].crow, tp.two[1].ccol, false, (long long)n * n, (long long)n * n,
               (long long)n * n);
   normal_order(L, c->hd.d(), c->gd.d(), n, c->o, c->fdr.d(), c->eref2.d());
+  // the contraction engine reads the dressed operators with every index at
+  // its canonical position (the order of its tuple tables: one spin block
+  // contiguous): rewrite both, swapping buffers with the scratch of the same size
+  canonical_layout(L, c->gd.d(), n, c->o, 4, c->tmpA.d());
+  std::swap(c->gd.p, c->tmpA.p);
+  std::swap(c->gd.bytes, c->tmpA.bytes);
+  canonical_layout(L, c->fdr.d(), n, c->o, 2, c->tmph.d());
+  std::swap(c->fdr.p, c->tmph.p);
+  std::swap(c->fdr.bytes, c->tmph.bytes);
   auto er = to_host(c, c->eref2.d(), 2);
   c->e_ref_dressed = er[0] + er[1];
 }
@@ -1334,7 +1343,7 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
       t2dense.reserve(sizeof(double) * (size_t)oo * oo * vv * vv);
       mp2_amplitudes(L, c->gso.d(), c->fdiag.d(), c->n, oo, t2dense.d());
       antisym_pack(L, t2dense.d(), 2, 2, oo, vv, c->otab[2].dev.as<int>(), c->otab[2].count, c->vtab[2].dev.as<int>(),
-                   c->vtab[2].count, c->tpk.d() + n1, 0.25, false);
+                   c->vtab[2].count, c->tpk.d() + n1, 0.25, false, false);  // MP2 amplitudes in spin-orbital order
       sync(c);
     }
     const int md = o.diis;

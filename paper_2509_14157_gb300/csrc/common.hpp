@@ -198,11 +198,19 @@ void gather_axpy(const Launch &L, long long M, double alpha, const double *A, co
 
 // Antisymmetrise a dense [o^nh v^np] accumulator into packed unique elements:
 // out[h,p] = sum_{perm} sign * Y[perm(h), perm(p)] (out overwritten, or
-// accumulated into when accumulate).
+// accumulated into when accumulate). canonical: Y holds every index in the
+// canonical order of the engine's tuple tables (beta spin orbitals first,
+// then alpha, ascending within each: the engine's accumulators); otherwise
+// in spin-orbital order.
 void antisym_pack(const Launch &L, const double *Y, int nh, int np, int o, int v,
                   const int *htab, long long nhtup, const int *ptab, long long nptup, double *out,
-                  double scale, bool accumulate);
-// Dense antisymmetric tensor from packed elements (dense zeroed here).
+                  double scale, bool accumulate, bool canonical = true);
+// A spin-orbital tensor [n^rank] (rank 1-4, indices occupied first, then
+// virtual) rewritten with every index at its canonical position within its
+// space, the layout in which the engine reads its operators.
+void canonical_layout(const Launch &L, const double *in, int n, int o, int rank, double *out);
+// Dense antisymmetric tensor (canonical index order) from packed elements
+// (dense zeroed here).
 // same result as unpack_dense as one coalesced gather (np >= 1); hrank /
 // prank: rank prefix tables of the hole / particle tuple lists
 void unpack_dense_rows(const Launch &L, const double *packed, int nh, int np, int o, int v, const long long *hrank,

@@ -238,10 +238,15 @@ struct TableBuilder {
         for (long long r = 0; r < whole->size; ++r) host.push_back(r * whole->stride);
         cnt = whole->size;
       } else {
-        // label by label: a dense dimension by index value; a single-label
-        // intermediate dimension by the index's canonical position
+        // label by label: every single-label dimension (dense operands and
+        // accumulators as well as intermediates) holds the index at its
+        // canonical position within its space (the order of the one-index
+        // tuple table: one spin block contiguous); the kernels that fill and
+        // drain the dense tensors use the same order
         std::vector<long long> st(dg.k), bs(dg.k);
-        std::vector<std::vector<long long>> pos(dg.k);
+        const GroupEnum &g1 = enumerate_group(n, 1, false);
+        std::vector<long long> pos(n, 0);
+        for (long long r = 0; r < g1.count; ++r) pos[g1.flat[r]] = r;
         for (int j = 0; j < dg.k; ++j) {
           const SDim *hit = nullptr;
           for (auto &d : s.dims)
@@ -249,18 +254,10 @@ struct TableBuilder {
           if (!hit) throw std::runtime_error("engine: label not addressable in operand storage");
           st[j] = hit->stride;
           bs[j] = hit->base;
-          if (hit->positional) {
-            const GroupEnum &g1 = enumerate_group(n, 1, false);
-            pos[j].assign(n, 0);
-            for (long long r = 0; r < g1.count; ++r) pos[j][g1.flat[r]] = r;
-          }
         }
         for (long long r = 0; r < ge.count; ++r) {
           long long off = 0;
-          for (int j = 0; j < dg.k; ++j) {
-            const int x = ge.flat[r * dg.k + j];
-            off += st[j] * (bs[j] + (pos[j].empty() ? x : pos[j][x]));
-          }
+          for (int j = 0; j < dg.k; ++j) off += st[j] * (bs[j] + pos[ge.flat[r * dg.k + j]]);
           host.push_back(off);
         }
         cnt = ge.count;

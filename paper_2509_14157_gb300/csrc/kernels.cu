@@ -377,16 +377,27 @@ __device__ __forceinline__ void dense_strides(int nh, int np, int o, int v, long
   for (int k = nh - 1; k >= 0; --k) { sh[k] = s; s *= o; }
 }
 
+// Dense work tensors (the contraction engine's operands and accumulators)
+// hold each index of a space in the canonical order of the engine's tuple
+// tables: beta spin orbitals (odd p) first, then alpha, ascending within
+// each, so that the elements of one spin block are contiguous. Position of
+// spin orbital x in a space of n (even) spin orbitals, and its inverse.
+__device__ __forceinline__ int canon_pos(int x, int n) { return (x & 1) ? (x >> 1) : (n >> 1) + (x >> 1); }
+__device__ __forceinline__ int canon_index(int d, int n) { return d < (n >> 1) ? 2 * d + 1 : 2 * (d - (n >> 1)); }
+
+// canonical: Y in the canonical order above (the engine's accumulators),
+// else in spin-orbital order
 __global__ void k_antisym_pack(const double *Y, int nh, int np, int o, int v, const int *htab, long long nhtup,
-                               const int *ptab, long long nptup, double *out, double scale, int accumulate) {
+                               const int *ptab, long long nptup, double *out, double scale, int accumulate,
+                               int canonical) {
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= nhtup * nptup) return;
   long long hi = r / nptup, pi = r - hi * nptup;
   long long sh[4], sp[4];
   dense_strides(nh, np, o, v, sh, sp);
   int h[4], pv[4];
-  for (int k = 0; k < nh; ++k) h[k] = htab[hi * nh + k];
-  for (int k = 0; k < np; ++k) pv[k] = ptab[pi * np + k];
+  for (int k = 0; k < nh; ++k) h[k] = canonical ? canon_pos(htab[hi * nh + k], o) : htab[hi * nh + k];
+  for (int k = 0; k < np; ++k) pv[k] = canonical ? canon_pos(ptab[pi * np + k], v) : ptab[pi * np + k];
   double acc = 0.0;
   const int nph = c_pcount[nh], npp = c_pcount[np];
   for (int a = 0; a < nph; ++a) {
@@ -404,6 +415,7 @@ __global__ void k_antisym_pack(const double *Y, int nh, int np, int o, int v, co
   out[r] = accumulate ? out[r] + acc : acc;
 }
 
+// dense in the canonical order (an engine operand)
 __global__ void k_unpack_dense(const double *packed, int nh, int np, int o, int v, const int *htab, long long nhtup,
                                const int *ptab, long long nptup, double *dense) {
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -412,8 +424,8 @@ __global__ void k_unpack_dense(const double *packed, int nh, int np, int o, int 
   long long sh[4], sp[4];
   dense_strides(nh, np, o, v, sh, sp);
   int h[4], pv[4];
-  for (int k = 0; k < nh; ++k) h[k] = htab[hi * nh + k];
-  for (int k = 0; k < np; ++k) pv[k] = ptab[pi * np + k];
+  for (int k = 0; k < nh; ++k) h[k] = canon_pos(htab[hi * nh + k], o);
+  for (int k = 0; k < np; ++k) pv[k] = canon_pos(ptab[pi * np + k], v);
   const double val = packed[r];
   const int nph = c_pcount[nh], npp = c_pcount[np];
   for (int a = 0; a < nph; ++a) {
@@ -440,8 +452,9 @@ __device__ __forceinline__ void sort_small(int *t, int n, int &sgn, bool &dup) {
     }
 }
 
-// Dense antisymmetric tensor [o^NH v^NP] from its packed unique elements, as
-// a coalesced gather (every dense element written once, no prior clear):
+// Dense antisymmetric tensor [o^NH v^NP] (canonical index order, see
+// canon_pos) from its packed unique elements, as a coalesced gather (every
+// dense element written once, no prior clear):
 // block b owns the outer indices (holes and all but the last NI particles),
 // its threads stride over the inner NI particle indices, which are the
 // fastest-varying part of the dense layout. dense = sign(sorting
@@ -461,12 +474,12 @@ __global__ void __launch_bounds__(256) k_unpack_blocks(const double *__restrict_
   int po[NO > 0 ? NO : 1], hh[NH > 0 ? NH : 1];
 #pragma unroll
   for (int k = NO - 1; k >= 0; --k) {
-    po[k] = (int)(rem % v);
+    po[k] = canon_index((int)(rem % v), v);
     rem /= v;
   }
 #pragma unroll
   for (int k = NH - 1; k >= 0; --k) {
-    hh[k] = (int)(rem % o);
+    hh[k] = canon_index((int)(rem % o), o);
     rem /= o;
   }
   int sgn0 = 1;
@@ -490,7 +503,7 @@ __global__ void __launch_bounds__(256) k_unpack_blocks(const double *__restrict_
     unsigned r = (unsigned)j;
 #pragma unroll
     for (int k = NP - 1; k >= NO; --k) {
-      q[k] = (int)(r % uv);
+      q[k] = canon_index((int)(r % uv), v);
       r /= uv;
     }
     int sgn = sgn0;
@@ -1085,18 +1098,45 @@ void gather_axpy(const Launch &L, long long M, double alpha, const double *A, co
 }
 
 void antisym_pack(const Launch &L, const double *Y, int nh, int np, int o, int v, const int *htab, long long nhtup,
-                  const int *ptab, long long nptup, double *out, double scale, bool accumulate) {
+                  const int *ptab, long long nptup, double *out, double scale, bool accumulate, bool canonical) {
   ensure_perm_tables();
+  if ((o | v) & 1) throw std::runtime_error("antisym_pack: odd spin-orbital count");
   long long n = nhtup * nptup;
   if (n <= 0) return;
   k_antisym_pack<<<blocks_for(n, 256), 256, 0, L.stream>>>(Y, nh, np, o, v, htab, nhtup, ptab, nptup, out, scale,
-                                                            accumulate ? 1 : 0);
+                                                            accumulate ? 1 : 0, canonical ? 1 : 0);
+  post(L);
+}
+
+// out = in with every index of a spin-orbital tensor [n^rank] (occupied
+// first, then virtual) moved to its canonical position within its space
+__global__ void k_canonical_layout(const double *in, int n, int o, int rank, double *out) {
+  long long total = 1;
+  for (int k = 0; k < rank; ++k) total *= n;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  long long rem = idx, off = 0, mul = 1;
+  for (int k = 0; k < rank; ++k) {
+    const int p = (int)(rem % n);
+    rem /= n;
+    off += mul * (p < o ? canon_pos(p, o) : o + canon_pos(p - o, n - o));
+    mul *= n;
+  }
+  out[off] = in[idx];
+}
+
+void canonical_layout(const Launch &L, const double *in, int n, int o, int rank, double *out) {
+  if ((o & 1) || ((n - o) & 1) || rank < 1 || rank > 4) throw std::runtime_error("canonical_layout: bad shape");
+  long long total = 1;
+  for (int k = 0; k < rank; ++k) total *= n;
+  k_canonical_layout<<<blocks_for(total, 256), 256, 0, L.stream>>>(in, n, o, rank, out);
   post(L);
 }
 
 void unpack_dense_rows(const Launch &L, const double *packed, int nh, int np, int o, int v, const long long *hrank,
                        const long long *prank, long long nptup, double *dense) {
   if (np < 1 || nh > 4 || np > 4 || v > 160) throw std::runtime_error("unpack_dense_rows: unsupported sizes");
+  if ((o | v) & 1) throw std::runtime_error("unpack_dense_rows: odd spin-orbital count");
   const int ni = std::min(np, 3);  // inner particles: at most v^3 elements per block
   long long outer = 1, inner = 1;
   for (int k = 0; k < nh; ++k) outer *= o;
@@ -1120,6 +1160,7 @@ void unpack_dense_rows(const Launch &L, const double *packed, int nh, int np, in
 void unpack_dense(const Launch &L, const double *packed, int nh, int np, int o, int v, const int *htab,
                   long long nhtup, const int *ptab, long long nptup, double *dense) {
   ensure_perm_tables();
+  if ((o | v) & 1) throw std::runtime_error("unpack_dense: odd spin-orbital count");
   long long dn = 1;
   for (int k = 0; k < nh; ++k) dn *= o;
   for (int k = 0; k < np; ++k) dn *= v;
