@@ -129,15 +129,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _source_block(path, marker, back=0):
+    """Lines of a C++ source from `back` lines above the line containing
+    marker to the next closing brace at the marker's indentation."""
+    lines = open(path).read().split("\n")
+    at = next(i for i, l in enumerate(lines) if marker in l)
+    indent = len(lines[at]) - len(lines[at].lstrip())
+    end = next(i for i in range(at + 1, len(lines))
+               if lines[i].startswith(" " * indent + "}") and len(lines[i]) - len(lines[i].lstrip()) == indent)
+    return "\n".join(lines[at - back:end + 1])
+
+
 def ggemm_source_sha():
-    """sha256 of the FP64 contraction kernel's source text (the k_ggemm
-    template in gemm_grouped.cu, from its template line to its closing
-    brace): the DRAM counters of a capture stay valid while it is unchanged."""
-    src = os.path.join(HERE, "paper_2509_14157_gb300", "csrc", "gemm_grouped.cu")
-    lines = open(src).read().split("\n")
-    start = next(i for i, l in enumerate(lines) if "k_ggemm(const GTask" in l) - 1
-    end = next(i for i in range(start + 1, len(lines)) if lines[i].startswith("}"))
-    return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()
+    """sha256 of what the FP64 contraction kernel's DRAM traffic depends on:
+    the k_ggemm template in gemm_grouped.cu (template line to closing brace)
+    and the engine's offset-table builder in engine.cpp, which fixes the
+    layout the kernel gathers from. The DRAM counters of a capture stay
+    valid while both are unchanged."""
+    csrc = os.path.join(HERE, "paper_2509_14157_gb300", "csrc")
+    text = (_source_block(os.path.join(csrc, "gemm_grouped.cu"), "k_ggemm(const GTask", back=1) + "\n" +
+            _source_block(os.path.join(csrc, "engine.cpp"), "long long add(DMap *map, const std::vector<DimGroup>"))
+    return hashlib.sha256(text.encode()).hexdigest()
 
 
 def read_traffic():
