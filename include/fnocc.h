@@ -38,8 +38,18 @@
  * ABI. fnocc_last_error gives a text for the last failing call on a context.
  * FNOCC_NOT_CONVERGED still fills every output with the last iterate.
  *
+ * Fault hook (tests of the error paths; not in the paper): while the
+ * environment variable FNOCC_FAULT is set, the library takes one error path
+ * on purpose, from the host, without any device fault: "alloc" fails every
+ * device allocation above 1 MiB as on a full device (FNOCC_E_NOMEM); "nan"
+ * makes ccsdt_solve start from a NaN amplitude (FNOCC_E_NUMERIC at its first
+ * energy); "diverge" scales every DIIS extrapolation of the CCSDT amplitudes
+ * by 1e3 (FNOCC_E_NUMERIC or FNOCC_NOT_CONVERGED). The variable is read at
+ * each use; with it unset the context works normally afterwards.
+ *
  * Threading: a context is not thread-safe; use one context per host thread.
- * All GPU work of a context runs on its stream.
+ * All GPU work of a context runs on its stream, with two side streams for
+ * the output components of the EOM products.
  */
 #ifndef FNOCC_H
 #define FNOCC_H

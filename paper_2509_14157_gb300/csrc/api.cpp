@@ -1346,6 +1346,10 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
                    c->vtab[2].count, c->tpk.d() + n1, 0.25, false, false);  // MP2 amplitudes in spin-orbital order
       sync(c);
     }
+    if (fault_mode() == kFaultNan) {  // test hook: a poisoned starting amplitude
+      const double bad = std::nan("");
+      copy_after(c->tpk.p, &bad, sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    }
     const int md = o.diis;
     DevBuf hv, he;
     if (md > 0) {
@@ -1399,6 +1403,8 @@ fnocc_status ccsdt_solve(fnocc_ctx *c, const ccsdt_options *opt, ccsdt_info *out
           rhs[m] = -1.0;
           if (solve_linear(m + 1, B, rhs, x)) {
             std::vector<double> coef(x.begin(), x.begin() + m);
+            if (fault_mode() == kFaultDiverge)  // test hook: a corrupted extrapolation
+              for (double &cf : coef) cf *= 1e3;
             combine_rows(c, tot, hv.d(), m, coef, c->tpk.d(), false);
           }
         }

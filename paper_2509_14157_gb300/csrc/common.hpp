@@ -5,6 +5,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -40,6 +42,24 @@ inline void copy_now(void *dst, const void *src, size_t bytes, cudaMemcpyKind ki
   copy_after(dst, src, bytes, kind, cudaStreamPerThread);
 }
 
+// Host-side fault hook for tests of the error paths (never a device fault):
+// while the environment variable FNOCC_FAULT is set, the library takes one
+// error path on purpose. "alloc": every device allocation above 1 MiB fails
+// as on a full device (FNOCC_E_NOMEM). "nan": ccsdt_solve writes a NaN into
+// its first starting amplitude, which only plain arithmetic kernels carry to
+// the first energy (FNOCC_E_NUMERIC). "diverge": every DIIS extrapolation of
+// the CCSDT amplitudes is scaled by 1e3 (FNOCC_E_NUMERIC or
+// FNOCC_NOT_CONVERGED). Read at each use; unset or empty, nothing changes.
+enum FaultMode { kFaultNone = 0, kFaultAlloc, kFaultNan, kFaultDiverge };
+inline int fault_mode() {
+  const char *e = std::getenv("FNOCC_FAULT");
+  if (!e || !*e) return kFaultNone;
+  if (!std::strcmp(e, "alloc")) return kFaultAlloc;
+  if (!std::strcmp(e, "nan")) return kFaultNan;
+  if (!std::strcmp(e, "diverge")) return kFaultDiverge;
+  return kFaultNone;
+}
+
 // Grow-only device buffer owned by a context.
 struct DevBuf {
   void *p = nullptr;
@@ -57,6 +77,9 @@ struct DevBuf {
     if (nbytes <= bytes && p) return;
     release();
     size_t nb = nbytes ? nbytes : 8;
+    if (nb > (size_t(1) << 20) && fault_mode() == kFaultAlloc)
+      throw CudaError("cudaMalloc of " + std::to_string(nb) + " bytes failed: injected (FNOCC_FAULT=alloc)",
+                      (int)cudaErrorMemoryAllocation);
     cudaError_t e = cudaMalloc(&p, nb);
     if (e != cudaSuccess) {
       p = nullptr;

@@ -1,9 +1,11 @@
 """Status codes of the C ABI on purpose: wrong call order (E_STATE), a NaN in
 the input (E_NUMERIC), too few iterations (NOT_CONVERGED with every output
-filled) and bad arguments (E_INVALID). Every failure is made on the host
-side: the NaN only travels through plain arithmetic kernels (no loop of any
-kernel depends on the values), and the host detects it in the first energy;
-the context stays usable afterwards.
+filled), bad arguments (E_INVALID), and the FNOCC_FAULT hook's failed
+allocations (E_NOMEM), poisoned starting amplitude (E_NUMERIC) and
+corrupted DIIS extrapolation. Every failure is made on the host side: a NaN
+only travels through plain arithmetic kernels (no loop of any kernel
+depends on the values), and the host detects it in the first energy; the
+context stays usable afterwards.
 """
 import ctypes
 import math
@@ -107,4 +109,45 @@ def test_bad_arguments(pkg):
     assert _status(pkg, ctx.eom_solve, 7, 2) == STATUS["E_INVALID"]
     assert _status(pkg, ctx.eom_solve, "ip", 0) == STATUS["E_INVALID"]
     assert ctx.lib.fnocc_set_precision(ctx._h, 9) == STATUS["E_INVALID"]
+    ctx.close()
+
+
+def test_fault_hook_alloc(pkg, monkeypatch):
+    """FNOCC_FAULT=alloc: the device allocations of the FNO setup (the
+    8-electron / 40-orbital integrals are 20 MB) fail as on a full device,
+    E_NOMEM comes back through the ABI, and the same call succeeds once the
+    variable is unset."""
+    h, eri = synth.hamiltonian(8, 40, seed=0)
+    ctx = pkg.Context(0)
+    monkeypatch.setenv("FNOCC_FAULT", "alloc")
+    assert _status(pkg, ctx.fno_truncate, h, eri, 4, 1e-4) == -2
+    assert b"FNOCC_FAULT=alloc" in ctx.lib.fnocc_last_error(ctx._h)
+    monkeypatch.delenv("FNOCC_FAULT")
+    info = ctx.fno_truncate(h, eri, 4, 1e-4)
+    assert info["nkept"] > 0
+    ctx.close()
+
+
+def test_fault_hook_nan_and_diverge(pkg, monkeypatch):
+    """FNOCC_FAULT=nan: CCSDT starts from a NaN amplitude and stops with
+    E_NUMERIC at its first energy. FNOCC_FAULT=diverge: every DIIS
+    extrapolation is scaled by 1e3, and the solve ends in E_NUMERIC or
+    NOT_CONVERGED. Unset, the same context converges to the undisturbed
+    energy."""
+    h, eri = synth.hamiltonian(6, 10, seed=0)
+    ctx = pkg.Context(0)
+    ctx.fno_truncate(h, eri, 3, 1e-4)
+    ref = ctx.ccsdt_solve()
+    assert ref["converged"]
+    monkeypatch.setenv("FNOCC_FAULT", "nan")
+    assert _status(pkg, ctx.ccsdt_solve) == STATUS["E_NUMERIC"]
+    monkeypatch.setenv("FNOCC_FAULT", "diverge")
+    try:
+        res = ctx.ccsdt_solve(maxiter=60)
+        assert not res["converged"]
+    except pkg.FnoccError as e:
+        assert e.status == STATUS["E_NUMERIC"]
+    monkeypatch.delenv("FNOCC_FAULT")
+    again = ctx.ccsdt_solve()
+    assert again["converged"] and abs(again["e_corr"] - ref["e_corr"]) < 1e-10
     ctx.close()
