@@ -23,6 +23,12 @@ of each block, and the roots of every variant.
 
 Run (several hours on 8 cores; the DEA products dominate):
     python tests/golden/make_c2_golden.py [--workers N] [--variants ip,ea,dip,dea]
+
+With --occt F the virtuals are kept by the cumulative-occupation criterion
+instead (the shortest prefix of natural occupations reaching the fraction
+F, the paper's OCCT thresholds), written to c2_occt<F>_oracle.json: at
+F = 0.995, 17 of 43 natural virtuals (o = 10, v = 34), one of the three
+truncations the XFNO extrapolation combines.
 """
 from __future__ import annotations
 
@@ -109,13 +115,25 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--variants", default="ip,ea,dip,dea")
-    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "c2_oracle.json"))
+    ap.add_argument("--occt", type=float, default=None,
+                    help="keep virtuals by cumulative occupation fraction instead of the 1e-4 threshold")
+    ap.add_argument("--out", default=None)
     args = ap.parse_args()
+    here = os.path.dirname(os.path.abspath(__file__))
+    if args.occt is None:
+        tag, crit, thr = "", "abs", THRESHOLD
+        workload = "10 electrons, 48 spatial orbitals, seed 0, FNO occupation threshold 1e-4"
+    else:
+        tag, crit, thr = "_occt%g" % (args.occt * 1000), "occt", args.occt
+        workload = ("10 electrons, 48 spatial orbitals, seed 0, FNO by cumulative occupation fraction %g"
+                    % args.occt)
+    if args.out is None:
+        args.out = os.path.join(here, "c2%s_oracle.json" % tag)
     t0 = time.time()
     h, eri = synth.hamiltonian(NE, NORB, seed=0)
-    act = fno.fno_truncate(h, eri, NE // 2, THRESHOLD)
+    act = fno.fno_truncate(h, eri, NE // 2, thr, criterion=crit)
     f, g, o, v = act["f"], act["g"], act["o"], act["v"]
-    out = dict(workload="10 electrons, 48 spatial orbitals, seed 0, FNO occupation threshold 1e-4",
+    out = dict(workload=workload, criterion=crit, threshold=thr,
                e_rhf=act["e_rhf"], e_mp2=act["e_mp2"], nkept=int(act["nkept"]),
                kept_fraction=act["kept_fraction"], e_ref=act["e_ref"], o=o, v=v, eom={})
     if os.path.exists(args.out):  # resume: keep what an earlier run finished
@@ -140,7 +158,7 @@ def main():
 
         # converged amplitudes kept outside the repository, so that a rerun
         # can resume with the EOM part
-        amp_path = os.path.join(tempfile.gettempdir(), "fnocc_c2_oracle_amplitudes.npz")
+        amp_path = os.path.join(tempfile.gettempdir(), "fnocc_c2%s_oracle_amplitudes.npz" % tag)
         if "e_ccsdt_corr" in out and os.path.exists(amp_path):
             d = np.load(amp_path)
             t1, t2, t3 = (packing.unpack(d["t%d" % r], r, r, o, v) for r in (1, 2, 3))

@@ -282,8 +282,15 @@ def test_c2_sigma_sampled(c2_system, variant):
         off += sizes[oc]
 
 
-def _c2_gold():
-    path = os.path.join(HERE, "golden", "c2_oracle.json")
+# oracle fixtures of the benchmarked system (tests/golden/make_c2_golden.py):
+# the FNO threshold 1e-4 of the benchmark, and the paper's cumulative
+# occupation truncation at 99.5 % (one of the three points XFNO combines)
+C2_FIXTURES = {"abs_1e-4": ("c2_oracle.json", "abs", 1e-4),
+               "occt_0.995": ("c2_occt995_oracle.json", "occt", 0.995)}
+
+
+def _c2_gold(name):
+    path = os.path.join(HERE, "golden", C2_FIXTURES[name][0])
     if not os.path.exists(path):
         pytest.skip("oracle fixture not written")
     gold = json.load(open(path))
@@ -292,27 +299,30 @@ def _c2_gold():
     return gold
 
 
-@pytest.fixture(scope="module")
-def c2_solved(pkg):
-    gold = _c2_gold()
+@pytest.fixture(scope="module", params=sorted(C2_FIXTURES))
+def c2_solved(pkg, request):
+    gold = _c2_gold(request.param)
+    _, crit, thr = C2_FIXTURES[request.param]
     h, eri = synth.hamiltonian(10, 48, seed=0)
     ctx = pkg.Context(0)
-    info = ctx.fno_truncate(h, eri, 5, 1e-4)
+    info = ctx.fno_truncate(h, eri, 5, thr, criterion=crit)
     res = ctx.ccsdt_solve(tol_res=1e-12, tol_e=1e-13)
     yield gold, ctx, info, res
     ctx.close()
 
 
 def test_c2_ground_state_against_oracle_fixture(c2_solved):
-    """The benchmarked workload (10 electrons / 48 orbitals, FNO 1e-4; o = 10,
-    v = 30): FNO quantities, the CCSDT energy and amplitudes (converged to
-    max|R| < 1e-12 on both sides; every T1 element, sampled T2 and T3
-    elements and the block norms to 1e-10) against values the oracle wrote
-    (tests/golden/make_c2_golden.py)."""
+    """The benchmarked system (10 electrons / 48 orbitals) at FNO 1e-4
+    (o = 10, v = 30) and at the cumulative-occupation truncation 99.5 %
+    (o = 10, v = 34): FNO quantities, the CCSDT energy and amplitudes
+    (converged to max|R| < 1e-12 on both sides; every T1 element, sampled T2
+    and T3 elements and the block norms to 1e-10) against values the oracle
+    wrote (tests/golden/make_c2_golden.py)."""
     gold, ctx, info, res = c2_solved
     assert info["nkept"] == gold["nkept"]
     assert abs(info["e_rhf"] - gold["e_rhf"]) < E_TOL
     assert abs(info["e_mp2"] - gold["e_mp2"]) < E_TOL
+    assert abs(info["kept_fraction"] - gold["kept_fraction"]) < 1e-12
     assert res["converged"]
     assert abs(res["e_corr"] - gold["e_ccsdt_corr"]) < E_TOL
     t = {r: ctx.get_block("t%d" % r) for r in (1, 2, 3)}
@@ -326,9 +336,9 @@ def test_c2_ground_state_against_oracle_fixture(c2_solved):
 
 @pytest.mark.parametrize("variant", ["ip", "ea", "dip", "dea"])
 def test_c2_roots_against_oracle_fixture(c2_solved, variant):
-    """The four lowest roots of each variant at the benchmarked workload
-    (Koopmans start, the library's default tolerances) against the oracle's
-    (1e-9 Eh)."""
+    """The four lowest roots of each variant the fixture holds (Koopmans
+    start, the library's default tolerances) against the oracle's (1e-9
+    Eh)."""
     gold, ctx, _, res = c2_solved
     if variant not in gold["eom"]:
         pytest.skip("oracle fixture holds no %s roots yet" % variant)
