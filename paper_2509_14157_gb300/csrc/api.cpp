@@ -148,6 +148,13 @@ struct ProductGraph {
 // buffers: no graph (and no copies through the fixed buffers)
 const size_t kGraphMaxDim = size_t(1) << 26;
 
+// Streams of one EOM product beside the context stream: its nine (output,
+// input) component blocks run on nine streams where the two extra
+// accumulators per output component take at most kSplitAccBytes, else its
+// three output components on three.
+constexpr int kSideStreams = 8;
+constexpr size_t kSplitAccBytes = size_t(1) << 30;
+
 }  // namespace
 
 struct fnocc_ctx {
@@ -214,9 +221,12 @@ struct fnocc_ctx {
   // side streams of a product's output components 1 and 2 (component 0 runs
   // on the context stream), each with its own scratch, split partials and
   // panels; fork and join events
-  cudaStream_t side[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
-  DevBuf bscratch[2], bpartials[2], bpanels[2];
+  // side streams of the EOM products (their blocks run beside the context
+  // stream), with a scratch arena, split-sum partials and tcgen05 panels each
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
+  DevBuf bscratch[kSideStreams], bpartials[kSideStreams], bpanels[kSideStreams];
+  DevBuf syx[3][2];  // block-parallel products: accumulators of input components 1 and 2
   // captured product launch sequences [variant][left][precision] and their
   // fixed input / output buffers
   bool use_graphs = true;
@@ -487,7 +497,15 @@ uint64_t &eq_version(fnocc_ctx *c, int var, int oc, int ic, bool left) {
 }
 
 // the launch sequence of one product: unpack x into the dense work tensors,
-// the nine blocks into the dense accumulators, antisymmetrise-pack into s
+// the nine blocks into the dense accumulators, antisymmetrise-pack into s.
+// The blocks are independent but for their output: in the block-parallel
+// form (small accumulators) block (oc, ic) accumulates into its own tensor
+// on its own stream, and the three tensors of an output component are summed
+// in input order on the context stream before the pack; otherwise the three
+// blocks of an output component share its accumulator and stream. The
+// arithmetic (which tensors, which order of the sums) depends only on the
+// sizes, so that per-launch profiling, which keeps every launch on the
+// context stream (isolated kernel times), gives the same bits.
 void sigma_launches(fnocc_ctx *c, int var, const double *x, double *s, bool left, const Launch &L,
                     const Operands &ops) {
   const int o = c->o, v = c->v;
@@ -499,49 +517,72 @@ void sigma_launches(fnocc_ctx *c, int var, const double *x, double *s, bool left
     unpack(c, L, x + off, kEom[var][k][0], kEom[var][k][1], c->rd[k].d());
     off += sz[k];
   }
-  // the three output components are independent: components 1 and 2 run on
-  // the side streams beside component 0 (each with its own scratch), so that
-  // the small launches of different components share the GPU; per-launch
-  // profiling keeps them on the context stream (isolated kernel times)
+  long long dn[3];
+  size_t extra = 0;
+  for (int oc = 0; oc < 3; ++oc) {
+    dn[oc] = std::max<long long>(1, ipow(o, kEom[var][oc][0]) * ipow(v, kEom[var][oc][1]));
+    extra += 2 * sizeof(double) * (size_t)dn[oc];
+  }
+  const bool split = extra <= kSplitAccBytes;
+  if (split)
+    for (int oc = 0; oc < 3; ++oc)
+      for (int k = 0; k < 2; ++k) c->syx[oc][k].reserve(sizeof(double) * dn[oc]);
   const bool fork = !c->prof.enabled;
+  const int nside = fork ? (split ? 8 : 2) : 0;
   struct Join {  // the side streams rejoin the context stream also when a launch throws
     fnocc_ctx *c;
-    bool armed;
+    int n;
     ~Join() {
-      if (armed)
-        for (int i = 0; i < 2; ++i)
-          if (cudaEventRecord(c->ev_join[i], c->side[i]) == cudaSuccess)
-            cudaStreamWaitEvent(c->stream, c->ev_join[i], 0);
+      for (int i = 0; i < n; ++i)
+        if (cudaEventRecord(c->ev_join[i], c->side[i]) == cudaSuccess)
+          cudaStreamWaitEvent(c->stream, c->ev_join[i], 0);
     }
-  } join{c, false};
-  if (fork) {
+  } join{c, 0};
+  if (nside > 0) {
     FNOCC_CUDA(cudaEventRecord(c->ev_fork, c->stream));
-    for (auto sd : c->side) FNOCC_CUDA(cudaStreamWaitEvent(sd, c->ev_fork, 0));
-    join.armed = true;
+    for (int i = 0; i < nside; ++i) FNOCC_CUDA(cudaStreamWaitEvent(c->side[i], c->ev_fork, 0));
+    join.n = nside;
   }
   off = 0;
   for (int oc = 0; oc < 3; ++oc) {
-    int nh = kEom[var][oc][0], np = kEom[var][oc][1];
-    long long dn = std::max<long long>(1, ipow(o, nh) * ipow(v, np));
+    const int nh = kEom[var][oc][0], np = kEom[var][oc][1];
+    double *Y[3] = {c->sy[oc].d(), split ? c->syx[oc][0].d() : c->sy[oc].d(),
+                    split ? c->syx[oc][1].d() : c->sy[oc].d()};
     Launch Lb = L;
-    DevBuf *scr = &c->scratch;
-    if (fork && oc > 0) {
-      Lb.stream = c->side[oc - 1];
-      Lb.partials = &c->bpartials[oc - 1];
-      Lb.panels = &c->bpanels[oc - 1];
-      scr = &c->bscratch[oc - 1];
+    for (int ic = 0; ic < 3; ++ic) {
+      const int q = split ? 3 * oc + ic : oc;  // slot: 0 the context stream, q > 0 side stream q - 1
+      Lb = L;
+      DevBuf *scr = &c->scratch;
+      if (q > 0 && q <= nside) {
+        Lb.stream = c->side[q - 1];
+        Lb.partials = &c->bpartials[q - 1];
+        Lb.panels = &c->bpanels[q - 1];
+        scr = &c->bscratch[q - 1];
+      }
+      if (split || ic == 0) FNOCC_CUDA(cudaMemsetAsync(Y[ic], 0, sizeof(double) * dn[oc], Lb.stream));
+      eqs[oc][ic]->run(Lb, ops, Y[ic], dn[oc], *scr, c->hbar_version);
     }
-    FNOCC_CUDA(cudaMemsetAsync(c->sy[oc].p, 0, sizeof(double) * dn, Lb.stream));
-    for (int ic = 0; ic < 3; ++ic) eqs[oc][ic]->run(Lb, ops, c->sy[oc].d(), dn, *scr, c->hbar_version);
-    antisym_pack(Lb, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
-                 c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
+    if (!split)  // the component's pack on its own stream, beside the other components
+      antisym_pack(Lb, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
+                   c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
     off += sz[oc];
   }
-  if (fork) {
-    join.armed = false;
-    for (int i = 0; i < 2; ++i) {
+  if (nside > 0) {
+    join.n = 0;
+    for (int i = 0; i < nside; ++i) {
       FNOCC_CUDA(cudaEventRecord(c->ev_join[i], c->side[i]));
       FNOCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join[i], 0));
+    }
+  }
+  if (split) {  // sums in input order and packs on the context stream
+    off = 0;
+    for (int oc = 0; oc < 3; ++oc) {
+      const int nh = kEom[var][oc][0], np = kEom[var][oc][1];
+      axpby(L, dn[oc], 1.0, c->syx[oc][0].d(), 1.0, c->sy[oc].d());
+      axpby(L, dn[oc], 1.0, c->syx[oc][1].d(), 1.0, c->sy[oc].d());
+      antisym_pack(L, c->sy[oc].d(), nh, np, o, v, c->otab[nh].dev.as<int>(), c->otab[nh].count,
+                   c->vtab[np].dev.as<int>(), c->vtab[np].count, s + off, 1.0, false);
+      off += sz[oc];
     }
   }
 }
@@ -558,11 +599,13 @@ std::vector<uintptr_t> product_key(fnocc_ctx *c, int var, bool left, const Launc
     key.push_back((uintptr_t)c->rd[k].p);
     key.push_back((uintptr_t)c->sy[k].p);
   }
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < kSideStreams; ++k) {
     key.push_back((uintptr_t)c->bscratch[k].p);
     key.push_back((uintptr_t)c->bpartials[k].p);
     key.push_back((uintptr_t)c->bpanels[k].p);
   }
+  for (int oc = 0; oc < 3; ++oc)
+    for (int k = 0; k < 2; ++k) key.push_back((uintptr_t)c->syx[oc][k].p);
   for (int oc = 0; oc < 3; ++oc)
     for (int ic = 0; ic < 3; ++ic) key.push_back((uintptr_t)eqs[oc][ic]->cache_ptr());
   return key;
@@ -854,7 +897,7 @@ fnocc_status fnocc_create(fnocc_ctx **out, int device, void *cuda_stream) {
       FNOCC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
       c->own_stream = true;
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kSideStreams; ++i) {
       FNOCC_CUDA(cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
       FNOCC_CUDA(cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming));
     }
@@ -876,7 +919,8 @@ void fnocc_destroy(fnocc_ctx *c) {
   for (auto sd : c->side)
     if (sd) cudaStreamSynchronize(sd);
   bool own = c->own_stream;
-  cudaStream_t s = c->stream, side[2] = {c->side[0], c->side[1]};
+  cudaStream_t s = c->stream, side[kSideStreams];
+  for (int i = 0; i < kSideStreams; ++i) side[i] = c->side[i];
   for (auto ev : c->prof.pool) cudaEventDestroy(ev);
   for (auto ev : c->ev_join)
     if (ev) cudaEventDestroy(ev);
