@@ -48,8 +48,8 @@
  * each use; with it unset the context works normally afterwards.
  *
  * Threading: a context is not thread-safe; use one context per host thread.
- * All GPU work of a context runs on its stream, with two side streams for
- * the output components of the EOM products.
+ * All GPU work of a context runs on its stream, with eight side streams for
+ * the component blocks of the EOM products.
  */
 #ifndef FNOCC_H
 #define FNOCC_H

@@ -112,9 +112,11 @@ def test_solve_with_and_without_replay(pkg):
 
 @pytest.mark.parametrize("variant", ["ip", "dea"])
 def test_side_streams_match_serial(ctx, variant):
-    """The three output components of a product run on three streams
-    (components 1 and 2 beside 0); with per-launch profiling they run one
-    after another on the context stream. Both orders give the same bits."""
+    """The component blocks of a product run on several streams (nine
+    blocks into their own accumulators for IP, three output components for
+    DEA); with per-launch profiling they run one after another on the
+    context stream with the same accumulators and sums. Both orders give the
+    same bits."""
     o, v, _ = ctx.dims()
     ctx.set_precision("fp64")
     ctx.set_graphs(False)
