@@ -424,24 +424,56 @@ double cc_residual_dev(fnocc_ctx *c, const double *tp, double *rp) {
   ops.v_size = nn * nn * nn * nn;
   ops.t2_size = ipow(o, 2) * ipow(v, 2);
   ops.t3_size = std::max<long long>(1, ipow(o, 3) * ipow(v, 3));
+  // the four residual ranks are independent (each its own equation and
+  // accumulator): the triples on the context stream, the energy, singles and
+  // doubles on three side streams beside it (per-launch profiling keeps them
+  // on the context stream); the arithmetic is the same either way
+  const bool fork = !c->prof.enabled;
+  struct Join {
+    fnocc_ctx *c;
+    int n;
+    ~Join() {
+      for (int i = 0; i < n; ++i)
+        if (cudaEventRecord(c->ev_join[i], c->side[i]) == cudaSuccess)
+          cudaStreamWaitEvent(c->stream, c->ev_join[i], 0);
+    }
+  } join{c, 0};
+  if (fork) {
+    FNOCC_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    for (int i = 0; i < 3; ++i) FNOCC_CUDA(cudaStreamWaitEvent(c->side[i], c->ev_fork, 0));
+    join.n = 3;
+  }
   double flops = 0;
-  for (int r = 0; r <= 3; ++r) {
+  size_t offs[4] = {0, 0, c->nt[1], c->nt[1] + c->nt[2]};
+  for (int r = 3; r >= 0; --r) {
+    Launch Lr = L;
+    DevBuf *scr = &c->scratch;
+    if (fork && r < 3) {
+      Lr.stream = c->side[r];
+      Lr.partials = &c->bpartials[r];
+      Lr.panels = &c->bpanels[r];
+      scr = &c->bscratch[r];
+    }
     long long ysz = std::max<long long>(1, ipow(o, r) * ipow(v, r));
     c->Y[r].reserve(sizeof(double) * ysz);
-    FNOCC_CUDA(cudaMemsetAsync(c->Y[r].p, 0, sizeof(double) * ysz, c->stream));
-    c->cc_eq[r]->run(L, ops, c->Y[r].d(), ysz, c->scratch);
+    FNOCC_CUDA(cudaMemsetAsync(c->Y[r].p, 0, sizeof(double) * ysz, Lr.stream));
+    c->cc_eq[r]->run(Lr, ops, c->Y[r].d(), ysz, *scr);
     flops += c->cc_eq[r]->flops();
+    if (r >= 1)
+      antisym_pack(Lr, c->Y[r].d(), r, r, o, v, c->otab[r].dev.as<int>(), c->otab[r].count, c->vtab[r].dev.as<int>(),
+                   c->vtab[r].count, rp + offs[r], 1.0, false);
+  }
+  if (fork) {
+    join.n = 0;
+    for (int i = 0; i < 3; ++i) {
+      FNOCC_CUDA(cudaEventRecord(c->ev_join[i], c->side[i]));
+      FNOCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join[i], 0));
+    }
   }
   c->flops_cc_last = flops;
   c->flops_total += flops;
   if (L.precision == FNOCC_MIXED_BF16X3 && tc_status_take(c->stream))
     throw StatusError(FNOCC_E_TIMEOUT, "a bounded wait of the tcgen05 contraction kernel expired");
-  size_t off = 0;
-  for (int r = 1; r <= 3; ++r) {
-    antisym_pack(L, c->Y[r].d(), r, r, o, v, c->otab[r].dev.as<int>(), c->otab[r].count, c->vtab[r].dev.as<int>(),
-                 c->vtab[r].count, rp + off, 1.0, false);
-    off += c->nt[r];
-  }
   auto y0 = to_host(c, c->Y[0].d(), 1);
   return (c->e_ref_dressed - c->e_ref) + y0[0];
 }
